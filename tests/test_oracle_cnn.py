@@ -1,0 +1,170 @@
+"""Pins of the learned-preconditioner oracle (oracle/cnn.py): a library
+convolution, brute-force loops, the adjoint identity, central finite
+differences, Adam's closed-form first step, and FCG reducing to PCG.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cnn, pic
+
+L = 4.0 * np.pi
+
+
+def test_conv3d_matches_torch_circular():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(3, 5, 6, 7))
+    w = rng.normal(size=(4, 3, 3, 3, 3))
+    xt = torch.nn.functional.pad(torch.from_numpy(x)[None], (1, 1, 1, 1, 1, 1), mode="circular")
+    ref = torch.nn.functional.conv3d(xt, torch.from_numpy(w))[0].numpy()
+    assert np.allclose(cnn.conv3d(x, w), ref, atol=1e-12)
+
+
+def test_conv3d_brute_force_loop():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 4, 4, 4))
+    w = rng.normal(size=(2, 2, 3, 3, 3))
+    ref = np.zeros((2, 4, 4, 4))
+    for o in range(2):
+        for z in range(4):
+            for y in range(4):
+                for xx in range(4):
+                    s = 0.0
+                    for c in range(2):
+                        for tz in range(3):
+                            for ty in range(3):
+                                for tx in range(3):
+                                    s += w[o, c, tz, ty, tx] * x[c, (z + tz - 1) % 4, (y + ty - 1) % 4, (xx + tx - 1) % 4]
+                    ref[o, z, y, xx] = s
+    assert np.allclose(cnn.conv3d(x, w), ref, atol=1e-12)
+
+
+def test_conv3d_single_tap_is_a_shift():
+    x = np.random.default_rng(2).normal(size=(1, 4, 5, 6))
+    w = np.zeros((1, 1, 3, 3, 3))
+    w[0, 0, 2, 1, 0] = 1.0   # offset (+1, 0, -1)
+    y = cnn.conv3d(x, w)
+    assert np.array_equal(y[0], np.roll(x[0], shift=(-1, 0, 1), axis=(0, 1, 2)))
+
+
+def test_bwd_data_is_the_adjoint():
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(3, 4, 5, 6))
+    gy = rng.normal(size=(2, 4, 5, 6))
+    w = rng.normal(size=(2, 3, 3, 3, 3))
+    lhs = np.sum(cnn.conv3d(x, w) * gy)
+    rhs = np.sum(x * cnn.conv3d_bwd_data(gy, w))
+    assert np.isclose(lhs, rhs, rtol=1e-12)
+
+
+def test_bwd_weight_finite_differences():
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(2, 4, 4, 5))
+    gy = rng.normal(size=(3, 4, 4, 5))
+    w = rng.normal(size=(3, 2, 3, 3, 3))
+    gw = cnn.conv3d_bwd_weight(x, gy)
+    eps = 1e-6
+    for idx in [(0, 0, 0, 0, 0), (2, 1, 1, 2, 0), (1, 0, 2, 2, 2), (0, 1, 1, 1, 1)]:
+        wp = w.copy(); wp[idx] += eps
+        wm = w.copy(); wm[idx] -= eps
+        fd = (np.sum(cnn.conv3d(x, wp) * gy) - np.sum(cnn.conv3d(x, wm) * gy)) / (2 * eps)
+        assert np.isclose(gw[idx], fd, rtol=1e-7, atol=1e-8)
+
+
+def test_network_backward_finite_differences():
+    rng = np.random.default_rng(5)
+    ws = cnn.init_weights(11)
+    x = rng.normal(size=(6, 6, 6))
+    gy = rng.normal(size=(6, 6, 6))
+    y, cache = cnn.forward(x, ws)
+    grads = cnn.backward(gy, ws, cache)
+    eps = 1e-6
+    for layer, idx in [(0, (3, 0, 1, 1, 2)), (1, (5, 7, 0, 2, 1)), (2, (15, 15, 2, 2, 2)), (3, (0, 9, 1, 0, 1))]:
+        wp = [w.copy() for w in ws]; wp[layer][idx] += eps
+        wm = [w.copy() for w in ws]; wm[layer][idx] -= eps
+        fd = (np.sum(cnn.forward(x, wp)[0] * gy) - np.sum(cnn.forward(x, wm)[0] * gy)) / (2 * eps)
+        assert np.isclose(grads[layer][idx], fd, rtol=1e-6, atol=1e-9)
+
+
+def test_network_weight_count_and_homogeneity():
+    ws = cnn.init_weights(0)
+    assert sum(w.size for w in ws) == 14688
+    x = np.random.default_rng(6).normal(size=(5, 5, 5))
+    assert np.allclose(cnn.forward(3.0 * x, ws)[0], 3.0 * cnn.forward(x, ws)[0], atol=1e-12)
+
+
+def test_loss_gradient_finite_differences():
+    rng = np.random.default_rng(7)
+    ws = cnn.init_weights(3)
+    r = [rng.normal(size=(10, 10, 10)) for _ in range(2)]
+    e = [rng.normal(size=(10, 10, 10)) for _ in range(2)]
+    h = 0.3
+    loss, grads = cnn.loss_and_grads(ws, r, e, h)
+    eps = 1e-6
+    for layer, idx in [(0, (1, 0, 0, 1, 2)), (2, (4, 9, 1, 1, 0)), (3, (0, 3, 2, 1, 1))]:
+        wp = [w.copy() for w in ws]; wp[layer][idx] += eps
+        wm = [w.copy() for w in ws]; wm[layer][idx] -= eps
+        fd = (cnn.loss_and_grads(wp, r, e, h)[0] - cnn.loss_and_grads(wm, r, e, h)[0]) / (2 * eps)
+        assert np.isclose(grads[layer][idx], fd, rtol=1e-6, atol=1e-10)
+
+
+def test_loss_ignores_crop_border():
+    rng = np.random.default_rng(8)
+    ws = cnn.init_weights(3)
+    r = rng.normal(size=(10, 10, 10))
+    e = rng.normal(size=(10, 10, 10))
+    l0, _ = cnn.loss_and_grads(ws, [r], [e], 1.0)
+    e2 = e.copy(); e2[0, :, :] += 5.0; e2[:, 9, :] -= 2.0     # border only
+    l1, _ = cnn.loss_and_grads(ws, [r], [e2], 1.0)
+    assert l0 == l1
+    # an input change 4 cells from the face moves interior outputs only through the
+    # receptive field; a change on the face itself (distance 0) must not reach them
+    # through wrap-around
+    r2 = r.copy(); r2[:, :, 0] += 1.0
+    y1, _ = cnn.forward(r, ws)
+    y2, _ = cnn.forward(r2, ws)
+    m = cnn.interior_mask(r.shape)
+    assert np.array_equal((y1 != y2) & m & (np.arange(10)[None, None, :] >= 5), np.zeros_like(m))
+
+
+def test_adam_first_step_closed_form():
+    p = [np.array([1.0, -2.0, 0.5])]
+    g = [np.array([0.3, -1e-3, 0.0])]
+    m = [np.zeros(3)]
+    v = [np.zeros(3)]
+    cnn.adam_step(p, g, m, v, 1, lr=0.01)
+    # m_hat = g, v_hat = g^2  =>  step = lr * g / (|g| + eps)
+    ref = np.array([1.0, -2.0, 0.5]) - 0.01 * np.array([0.3, -1e-3, 0.0]) / (np.abs([0.3, -1e-3, 0.0]) + 1e-8)
+    assert np.allclose(p[0], ref, atol=1e-15)
+
+
+def test_fcg_with_jacobi_equals_pcg():
+    N = 8
+    h = L / N
+    b = np.random.default_rng(9).normal(size=N ** 3)
+    x1, it1, rel1, _ = pic.pcg_jacobi(b, np.zeros(N ** 3), N, h, 1e-12, 500)
+    x2, it2, rel2, _ = cnn.fcg(b, np.zeros(N ** 3), N, h, 1e-12, 500, lambda r: r * (h * h / 6.0))
+    assert it1 == it2
+    assert np.allclose(x1, x2, atol=1e-12 * np.abs(x1).max())
+
+
+def test_fcg_nonlinear_preconditioner_converges():
+    N = 8
+    h = L / N
+    b = np.random.default_rng(10).normal(size=N ** 3)
+    prec = lambda r: (h * h / 6.0) * r * (1.0 + 0.3 * np.tanh(r / (np.abs(r).max() + 1e-300)))
+    x, it, rel, ok = cnn.fcg(b, np.zeros(N ** 3), N, h, 1e-11, 500, prec)
+    assert ok
+    ref = pic.spectral_solve(b, N, h)
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_cnn_preconditioner_fcg_reaches_tolerance():
+    N = 8
+    h = L / N
+    b = np.random.default_rng(12).normal(size=N ** 3)
+    ws = cnn.init_weights(5)
+    x, it, rel, ok = cnn.fcg(b, np.zeros(N ** 3), N, h, 1e-10, 2000, lambda r: cnn.precondition(r, ws, N, h))
+    assert ok
+    ref = pic.spectral_solve(b, N, h)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
