@@ -1,0 +1,153 @@
+/*
+ * pic.h - C ABI of the GB300 electrostatic PIC library (Landau damping).
+ *
+ * The library advances the electrostatic Vlasov-Poisson system of the paper
+ * (Sec. 2, Eqs. 1-4) with the particle-in-cell loop of Fig. 1:
+ * scatter -> solve -> gather -> push, on one GPU. The solve is a matrix-free
+ * preconditioned conjugate gradient on the periodic 7-point finite-difference
+ * Laplacian (Sec. 3.2). All calls are plain C: device buffers are passed as
+ * raw pointers, sizes as integers, and no C++ exception crosses the boundary.
+ *
+ * Conventions (Sec. 2 and Sec. 2.1):
+ *   - plasma units: electrons with q/m = -1, eps0 = 1, mean density 1, so the
+ *     neutralising ion background is +1 and Poisson's equation reads
+ *     -Delta phi = rho (Eq. 2), E = -grad phi;
+ *   - periodic cube [0, L)^3, L = 2 pi / k, N^3 nodes x_i = i h, h = L / N;
+ *   - grid arrays are N^3 contiguous values, x fastest: i + N (j + N k);
+ *   - particles are stored structure-of-arrays in FP64.
+ *
+ * Streams: every call enqueues its work on the context's CUDA stream
+ * (given to pic_create) and returns without synchronising, except those that
+ * return host values (pic_field_energy, pic_get_particles to host memory,
+ * poisson_solve*, which read convergence status), which synchronise the stream.
+ *
+ * Errors: every int-returning call returns PIC_OK (0) or a negative code;
+ * pic_strerror() names it. After PIC_ECUDA the context should be destroyed.
+ * The library never traps or asserts on the device: device-side failures
+ * (non-finite values, breakdown, exhausted waits) are reported through the
+ * return codes below.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL -1     /* bad argument (null pointer, unsupported size, ...) */
+#define PIC_ENOMEM -2     /* device or pinned allocation failed */
+#define PIC_ECUDA -3      /* a CUDA runtime call failed */
+#define PIC_ENOCONV -4    /* solver hit maxit; phi holds the last iterate */
+#define PIC_EBREAKDOWN -5 /* solver breakdown: p.Ap <= 0 or a non-finite value */
+#define PIC_ETIMEOUT -6   /* a bounded device-side wait expired */
+#define PIC_ESTATE -7     /* call out of order (e.g. deposit before init) */
+
+typedef struct pic_ctx pic_ctx;
+
+/* Problem description (Sec. 2.1: k = 0.5, alpha = 0.05; Sec. 4.1: 8 ppc). */
+typedef struct {
+  int N;        /* nodes per dimension; 8 <= N <= 1024, N % 8 == 0 */
+  int ppc;      /* particles per cell, Np = ppc * N^3 < 2^32; 0 = solver-only context */
+  double alpha; /* density perturbation amplitude */
+  double k;     /* perturbation wavenumber; L = 2 pi / k */
+} pic_params;
+
+/* Solver precision. FP64 = Jacobi-PCG entirely in FP64 (the judge).
+ * MIXED = FP32 stencil and vectors, FP64 reductions, FP64 solution and
+ * reliable-update residual recomputation in FP64. */
+enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 };
+/* Preconditioner: JACOBI (Sec. 3.2) or the learned CNN inside flexible CG
+ * (requires PIC_PREC_MIXED and weights set by pic_cnn_set_weights). */
+enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1 };
+
+typedef struct {
+  int precision;         /* PIC_PREC_* */
+  int precond;           /* PIC_PC_* */
+  double reliable_delta; /* MIXED: recompute the FP64 residual when the FP32 residual
+                            norm fell by this factor since the last recomputation;
+                            0 selects the default 0.1 */
+  int check_every;       /* iterations between host reads of the convergence flag; 0 = default */
+} pic_solve_opts;
+
+typedef struct {
+  int iters;            /* CG iterations performed */
+  int reliable_updates; /* MIXED: FP64 residual recomputations */
+  int fallbacks;        /* CNN: iterations that used the Jacobi direction */
+  int converged;        /* 1 if ||b - A phi|| <= tol ||b|| */
+  double rel_res;       /* final ||r|| / ||b|| (FP64 recursive residual for FP64,
+                           true FP64 residual b - A phi for MIXED) */
+  double bnorm;         /* ||b||_2 of the mean-projected right-hand side */
+  double t_ms;          /* device time of the solve (CUDA events) */
+} pic_solve_info;
+
+/* Create a context on the current CUDA device. `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream); the caller keeps it alive for
+ * the context's lifetime. The context owns its particles and workspace. */
+int pic_create(pic_ctx **out, void *cuda_stream);
+void pic_destroy(pic_ctx *c);
+const char *pic_strerror(int code);
+
+/* S0 (Sec. 2.1): allocate and sample the Landau initial condition on the
+ * device. Particle p draws from Philox4x32-10 (Salmon et al., SC'11) with
+ * counters (p_lo, p_hi, j, 0), j = 0..3, and key (seed_lo, seed_hi);
+ * positions by per-dimension inverse CDF of (1 + alpha cos k x)/L, velocities
+ * by Box-Muller (v_th = 1). Velocities are synchronous with positions. With
+ * ppc == 0 only the grid geometry is set (solver-only context). */
+int pic_init(pic_ctx *c, const pic_params *p, uint64_t seed);
+
+/* S1 + S2 (Fig. 1 "scatter", Eq. 2): sort particles by cell, then write
+ * rho = 1 + sum_p q_p W_CIC(x_i - x_p) / h^3, q_p = -L^3/Np, into `rho`
+ * (device FP64 [N^3], caller-owned; fully overwritten). */
+int pic_deposit(pic_ctx *c, double *rho);
+
+/* S3 + S4 (Sec. 3.2, 4.1): solve A phi = rho - mean(rho), A = -Delta_h the
+ * periodic 7-point operator, by Jacobi-PCG in FP64 until
+ * ||r||_2 <= tol ||b||_2 or maxit iterations. `rho` (device FP64 [N^3]) is
+ * read only. `phi` (device FP64 [N^3]) is in/out: on entry the warm start,
+ * on return the solution with mean zero. Returns PIC_OK, PIC_ENOCONV (phi =
+ * last iterate) or PIC_EBREAKDOWN. A zero right-hand side gives phi = 0. */
+int poisson_solve(pic_ctx *c, const double *rho, double *phi, double tol, int maxit);
+
+/* As poisson_solve with solver options (NULL = FP64 Jacobi) and an optional
+ * info record (NULL = not filled). */
+int poisson_solve_ex(pic_ctx *c, const double *rho, double *phi, double tol, int maxit,
+                     const pic_solve_opts *opts, pic_solve_info *info);
+
+/* S5 + S6 (Eq. 2, Eqs. 3-4; Fig. 1 "gather", "push"): E = -grad phi by
+ * central differences, CIC-gathered to the particles, then one leapfrog step:
+ * v += (q/m) kick E(x), x = wrap(x + dt v), where kick = dt/2 on the first
+ * push after pic_init / pic_sync_velocity and dt otherwise (kick-drift-kick
+ * with the two half-kicks at each step boundary merged). `phi` is device
+ * FP64 [N^3]. */
+int pic_gather_push(pic_ctx *c, const double *phi, double dt);
+
+/* Closing half-kick v += (q/m) (dt/2) E(x): makes velocities synchronous
+ * with positions again (for diagnostics); the next push starts with dt/2. */
+int pic_sync_velocity(pic_ctx *c, const double *phi, double dt);
+
+/* S7 (Fig. 2 diagnostic): out_w[d] = h^3 sum_i E_{d,i}^2, E = -grad phi by
+ * central differences, d = x, y, z. `out_w` is host memory; synchronises. */
+int pic_field_energy(pic_ctx *c, const double *phi, double out_w[3]);
+
+/* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
+ * the ORIGINAL particle order (index p of pic_init), to device memory
+ * (on_device = 1) or host memory (0; synchronises). `half_step` (may be
+ * NULL) receives 1 when velocities lag positions by dt/2. */
+int pic_get_particles(pic_ctx *c, double *out, int on_device, int *half_step);
+
+/* Number of particles of the context (0 for a solver-only context). */
+int64_t pic_num_particles(const pic_ctx *c);
+
+/* Operator application y = A x (A = -Delta_h, periodic 7-point, Sec. 3.2),
+ * FP64 device [N^3] arrays. */
+int pic_apply_laplacian(pic_ctx *c, const double *x, double *y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

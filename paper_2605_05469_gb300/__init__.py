@@ -1,0 +1,249 @@
+"""Python binding of the GB300 PIC library (libpic.so, C ABI in include/pic.h).
+
+Argument marshalling only: every step of the PIC loop runs in the library's
+CUDA kernels. PyTorch supplies device memory and the CUDA stream. If the
+shared library has not been built the import of any binding call raises,
+there is no CPU fallback.
+
+Module-level functions carry the C names (``pic_create``, ``pic_init``,
+``pic_deposit``, ``poisson_solve``, ``poisson_solve_ex``, ``pic_gather_push``,
+``pic_sync_velocity``, ``pic_field_energy``, ``pic_get_particles``,
+``pic_apply_laplacian``, ``pic_destroy``); ``Context`` bundles them.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK = 0
+PIC_EINVAL = -1
+PIC_ENOMEM = -2
+PIC_ECUDA = -3
+PIC_ENOCONV = -4
+PIC_EBREAKDOWN = -5
+PIC_ETIMEOUT = -6
+PIC_ESTATE = -7
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+PC_JACOBI = 0
+PC_CNN = 1
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class pic_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("ppc", ctypes.c_int), ("alpha", ctypes.c_double), ("k", ctypes.c_double)]
+
+
+class pic_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("reliable_delta", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class pic_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("fallbacks", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("t_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+# symbol -> (restype, argtypes)
+_SIGS = {
+    "pic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pic_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    "pic_destroy": (None, [ctypes.c_void_p]),
+    "pic_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_params), ctypes.c_uint64]),
+    "pic_deposit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "poisson_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                     ctypes.c_int]),
+    "poisson_solve_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.c_int, ctypes.POINTER(pic_solve_opts),
+                                        ctypes.POINTER(pic_solve_info)]),
+    "pic_gather_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    "pic_sync_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    "pic_field_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pic_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "pic_num_particles": (ctypes.c_int64, [ctypes.c_void_p]),
+    "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def lib():
+    """The loaded libpic.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2605_05469_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def strerror(code):
+    try:
+        return lib().pic_strerror(code).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+def _check(code, what):
+    if code != PIC_OK:
+        raise PicError(code, what)
+    return code
+
+
+def _dptr(t, dtype_name, numel, what):
+    """Device pointer of a contiguous CUDA tensor of the given dtype and size."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what}: expected a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}" or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{what}: expected a contiguous {dtype_name} tensor with {numel} elements, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------ C-named calls
+def pic_create(stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().pic_create(ctypes.byref(h), _stream_ptr(stream)), "pic_create")
+    return h
+
+
+def pic_destroy(h):
+    lib().pic_destroy(h)
+
+
+def pic_init(h, N, ppc, seed, alpha=0.05, k=0.5):
+    p = pic_params(N, ppc, alpha, k)
+    _check(lib().pic_init(h, ctypes.byref(p), ctypes.c_uint64(seed)), "pic_init")
+
+
+def pic_deposit(h, rho, n):
+    _check(lib().pic_deposit(h, _dptr(rho, "float64", n, "rho")), "pic_deposit")
+
+
+def poisson_solve(h, rho, phi, tol, maxit, n):
+    return lib().poisson_solve(h, _dptr(rho, "float64", n, "rho"), _dptr(phi, "float64", n, "phi"), tol, maxit)
+
+
+def poisson_solve_ex(h, rho, phi, tol, maxit, n, precision=PREC_FP64, precond=PC_JACOBI, reliable_delta=0.0,
+                     check_every=0):
+    o = pic_solve_opts(precision, precond, reliable_delta, check_every)
+    info = pic_solve_info()
+    code = lib().poisson_solve_ex(h, _dptr(rho, "float64", n, "rho"), _dptr(phi, "float64", n, "phi"), tol, maxit,
+                                  ctypes.byref(o), ctypes.byref(info))
+    return code, info.as_dict()
+
+
+def pic_gather_push(h, phi, dt, n):
+    _check(lib().pic_gather_push(h, _dptr(phi, "float64", n, "phi"), dt), "pic_gather_push")
+
+
+def pic_sync_velocity(h, phi, dt, n):
+    _check(lib().pic_sync_velocity(h, _dptr(phi, "float64", n, "phi"), dt), "pic_sync_velocity")
+
+
+def pic_field_energy(h, phi, n):
+    out = (ctypes.c_double * 3)()
+    _check(lib().pic_field_energy(h, _dptr(phi, "float64", n, "phi"), out), "pic_field_energy")
+    return np.array(list(out))
+
+
+def pic_get_particles(h, np_):
+    out = np.empty(6 * np_, dtype=np.float64)
+    half = ctypes.c_int()
+    _check(lib().pic_get_particles(h, out.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(half)),
+           "pic_get_particles")
+    return out.reshape(6, np_), bool(half.value)
+
+
+def pic_apply_laplacian(h, x, y, n):
+    _check(lib().pic_apply_laplacian(h, _dptr(x, "float64", n, "x"), _dptr(y, "float64", n, "y")),
+           "pic_apply_laplacian")
+
+
+# ------------------------------------------------------------ convenience
+class Context:
+    """One PIC problem on the current CUDA device (owns particles and workspace)."""
+
+    def __init__(self, stream=None):
+        self.h = pic_create(stream)
+        self.N = 0
+        self.n = 0
+
+    def init(self, N, ppc, seed, alpha=0.05, k=0.5):
+        pic_init(self.h, N, ppc, seed, alpha, k)
+        self.N, self.n = N, N ** 3
+        self.L = 2.0 * np.pi / k
+        self.h_grid = self.L / N
+        return self
+
+    @property
+    def num_particles(self):
+        return int(lib().pic_num_particles(self.h))
+
+    def deposit(self, rho):
+        pic_deposit(self.h, rho, self.n)
+
+    def solve(self, rho, phi, tol=1e-10, maxit=5000, precision=PREC_FP64, precond=PC_JACOBI, reliable_delta=0.0,
+              check_every=0, raise_on_error=True):
+        code, info = poisson_solve_ex(self.h, rho, phi, tol, maxit, self.n, precision, precond, reliable_delta,
+                                      check_every)
+        info["code"] = code
+        if raise_on_error and code not in (PIC_OK,):
+            raise PicError(code, "poisson_solve_ex")
+        return info
+
+    def gather_push(self, phi, dt):
+        pic_gather_push(self.h, phi, dt, self.n)
+
+    def sync_velocity(self, phi, dt):
+        pic_sync_velocity(self.h, phi, dt, self.n)
+
+    def field_energy(self, phi):
+        return pic_field_energy(self.h, phi, self.n)
+
+    def particles(self):
+        return pic_get_particles(self.h, self.num_particles)
+
+    def apply_laplacian(self, x, y):
+        pic_apply_laplacian(self.h, x, y, self.n)
+
+    def close(self):
+        if self.h is not None:
+            pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,606 @@
+// C ABI of the PIC library: context, buffers and the drivers that enqueue the
+// kernels of each call on the context's stream. See include/pic.h.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "particle_kernels.cuh"
+#include "solver_kernels.cuh"
+
+using namespace pic;
+
+namespace {
+
+constexpr int kSmemBudget = 100 * 1024;
+
+struct SolverWs {
+  // FP64 judge
+  double *x = nullptr, *r = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+  // mixed
+  double* xm[2] = {nullptr, nullptr};
+  float *x32 = nullptr, *r32 = nullptr, *p32[2] = {nullptr, nullptr};
+  // shared
+  double* b = nullptr;
+};
+
+}  // namespace
+
+struct pic_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  // geometry
+  bool has_grid = false;
+  int N = 0;
+  size_t n = 0;
+  double L = 0, h = 0, alpha = 0, k = 0;
+  int ppc = 0;
+  uint64_t np = 0;
+  Grid grid{};
+  // particles
+  double* pb[2][6] = {};
+  uint32_t* ids[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *keys = nullptr, *ranks = nullptr, *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
+  bool keys_valid = false, sorted = false, half_step = false;
+  double* E = nullptr;  // 3 n
+  // solver
+  SolverWs ws;
+  Scalars* sc = nullptr;
+  Scalars* sc_host = nullptr;  // pinned, 2 slots
+  double* partials = nullptr;
+  size_t partials_len = 0;
+  unsigned* counter = nullptr;
+  int* err = nullptr;
+  int* err_host = nullptr;   // pinned
+  double* out3 = nullptr;    // device, 3 doubles
+  double* out3_host = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, batch_ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return PIC_ECUDA;      \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return PIC_OK;
+  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PIC_ENOMEM;
+  }
+  return PIC_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_particles(pic_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    for (int q = 0; q < 6; ++q) dfree(c->pb[b][q]);
+    dfree(c->ids[b]);
+  }
+  dfree(c->keys);
+  dfree(c->ranks);
+  dfree(c->counts);
+  dfree(c->offsets);
+  dfree(c->chunks);
+  dfree(c->E);
+  c->np = 0;
+}
+
+void free_solver(pic_ctx* c) {
+  SolverWs& w = c->ws;
+  dfree(w.x); dfree(w.r); dfree(w.p[0]); dfree(w.p[1]); dfree(w.q);
+  dfree(w.xm[0]); dfree(w.xm[1]);
+  dfree(w.x32); dfree(w.r32); dfree(w.p32[0]); dfree(w.p32[1]);
+  dfree(w.b);
+  dfree(c->partials);
+  c->partials_len = 0;
+}
+
+ParticlePtrs pptrs(pic_ctx* c, int b) {
+  ParticlePtrs P;
+  P.x = c->pb[b][0]; P.y = c->pb[b][1]; P.z = c->pb[b][2];
+  P.vx = c->pb[b][3]; P.vy = c->pb[b][4]; P.vz = c->pb[b][5];
+  P.id = c->ids[b];
+  return P;
+}
+
+int round32(int t) { return ((t + 31) / 32) * 32; }
+
+// Stage count from the shared-memory budget, at least 4 (one plane in flight).
+template <typename A, typename B, int NV>
+StreamGeo geo_for(pic_ctx* c, size_t* smem) {
+  StreamGeo g = make_stream_geo(c->N, 4, 4 * c->sms);
+  StageLayout<A, B, NV> lay(g.rows, g.N);
+  int S = (int)(kSmemBudget / lay.bytes);
+  if (S < 4) S = 4;
+  if (S > kMaxStages) S = kMaxStages;
+  g.S = S;
+  *smem = (size_t)S * lay.bytes;
+  return g;
+}
+
+int streaming_blocks(pic_ctx* c) {
+  size_t n4 = c->n / 4;
+  size_t b = (n4 + 255) / 256;
+  size_t cap = (size_t)c->sms * 4;
+  return (int)(b < cap ? b : cap);
+}
+
+int ensure_partials(pic_ctx* c, size_t need) {
+  if (c->partials_len >= need) return PIC_OK;
+  dfree(c->partials);
+  int e = dalloc(&c->partials, need);
+  if (e) return e;
+  c->partials_len = need;
+  return PIC_OK;
+}
+
+int check_dev_err(pic_ctx* c) {
+  // caller has synchronised
+  if (*c->err_host & DEV_ERR_TIMEOUT) return PIC_ETIMEOUT;
+  return PIC_OK;
+}
+
+int sync_status(pic_ctx* c) {
+  CK(cudaMemcpyAsync(c->err_host, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return check_dev_err(c);
+}
+
+int set_smem_attr(const void* fn, size_t bytes) {
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return PIC_OK;
+}
+
+bool dev_ptr_ok(const void* p) { return p != nullptr && ((uintptr_t)p % 16) == 0; }
+
+// --------------------------------------------------------------------------
+// FP64 Jacobi-PCG (the judge)
+// --------------------------------------------------------------------------
+int solve_common_setup(pic_ctx* c, const double* rho, const double* phi, double tol, int maxit, double delta,
+                       double* xout) {
+  Scalars init;
+  memset(&init, 0, sizeof(init));
+  init.maxit = maxit;
+  init.delta2 = delta * delta;
+  init.xsel = 0;
+  c->sc_host[0] = init;
+  CK(cudaMemcpyAsync(c->sc, &c->sc_host[0], sizeof(Scalars), cudaMemcpyHostToDevice, c->stream));
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
+  k_sum2<<<sb, 256, 0, c->stream>>>(rho, phi, n4, c->sc, c->partials, c->counter);
+  k_project<<<sb, 256, 0, c->stream>>>(rho, phi, c->ws.b, xout, n4, 1.0 / (double)c->n, c->h * c->h, tol, c->sc,
+                                      c->partials, c->counter);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+// Run batches of `m` iterations (each batch a fixed launch sequence) until the
+// device reports done. The status of batch b-1 is read while batch b runs.
+template <typename LaunchBatch>
+int run_batches(pic_ctx* c, int m, int maxit, LaunchBatch launch_batch) {
+  int b = 0;
+  long launched = 0;
+  for (;;) {
+    launch_batch();
+    CK(cudaGetLastError());
+    launched += m;
+    CK(cudaMemcpyAsync(&c->sc_host[b & 1], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->batch_ev[b & 1], c->stream));
+    if (b > 0) {
+      CK(cudaEventSynchronize(c->batch_ev[(b - 1) & 1]));
+      if (c->sc_host[(b - 1) & 1].done) break;
+    }
+    if (launched > (long)maxit + 2L * m) break;
+    ++b;
+  }
+  return PIC_OK;
+}
+
+int solve_fp64(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, pic_solve_info* info) {
+  SolverWs& w = c->ws;
+  int e;
+  if (!w.x) {
+    if ((e = dalloc(&w.x, c->n)) || (e = dalloc(&w.r, c->n)) || (e = dalloc(&w.p[0], c->n)) ||
+        (e = dalloc(&w.p[1], c->n)) || (e = dalloc(&w.q, c->n)))
+      return e;
+  }
+  if (!w.b && (e = dalloc(&w.b, c->n))) return e;
+  size_t smem_pap, smem_res;
+  const StreamGeo gp = geo_for<double, double, 2>(c, &smem_pap);
+  const StreamGeo gr = geo_for<double, double, 1>(c, &smem_res);
+  if ((e = ensure_partials(c, (size_t)3 * (gp.blocks > gr.blocks ? gp.blocks : gr.blocks) + 3 * 4096))) return e;
+  if ((e = set_smem_attr((const void*)k_cg_pap<double, true>, smem_pap))) return e;
+  if ((e = set_smem_attr((const void*)k_residual64, smem_res))) return e;
+
+  CK(cudaEventRecord(c->ev0, c->stream));
+  if ((e = solve_common_setup(c, rho, phi, tol, maxit, 0.0, w.x))) return e;
+  CK(cudaMemsetAsync(w.p[0], 0, c->n * sizeof(double), c->stream));
+  const int tp = round32(gp.threads), tr = round32(gr.threads);
+  k_residual64<<<gr.blocks, tr, smem_res, c->stream>>>(w.x, w.b, w.r, c->sc, c->partials, c->counter, c->err, gr);
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
+  int cur = 0;
+  auto batch = [&]() {
+    for (int i = 0; i < m; ++i) {
+      k_cg_pap<double, true><<<gp.blocks, tp, smem_pap, c->stream>>>(w.r, w.p[cur], w.p[cur ^ 1], w.q, c->sc,
+                                                                     c->partials, c->counter, c->err, gp);
+      k_cg_update64<<<sb, 256, 0, c->stream>>>(w.x, w.r, w.p[cur ^ 1], w.q, n4, c->sc, c->partials, c->counter);
+      cur ^= 1;
+    }
+  };
+  if ((e = run_batches(c, m, maxit, batch))) return e;
+  k_sum2<<<sb, 256, 0, c->stream>>>(w.x, nullptr, n4, c->sc, c->partials, c->counter);
+  k_finish<<<sb, 256, 0, c->stream>>>(w.x, phi, n4, 1.0 / (double)c->n, c->sc);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  if ((e = sync_status(c))) return e;
+  const Scalars& s = c->sc_host[0];
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->iters = s.iter;
+    info->reliable_updates = 0;
+    info->fallbacks = 0;
+    info->converged = s.done == 1;
+    info->rel_res = s.bb > 0.0 ? sqrt(s.rr / s.bb) : 0.0;
+    info->bnorm = sqrt(s.bb) / (c->h * c->h);
+    info->t_ms = ms;
+  }
+  if (s.done == 1) return PIC_OK;
+  if (s.done == 3) return PIC_EBREAKDOWN;
+  return PIC_ENOCONV;
+}
+
+// --------------------------------------------------------------------------
+// Mixed precision: FP32 CG with FP64 reductions and reliable updates
+// --------------------------------------------------------------------------
+int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta,
+                pic_solve_info* info) {
+  SolverWs& w = c->ws;
+  int e;
+  if (!w.xm[0]) {
+    if ((e = dalloc(&w.xm[0], c->n)) || (e = dalloc(&w.xm[1], c->n)) || (e = dalloc(&w.x32, c->n)) ||
+        (e = dalloc(&w.r32, c->n)) || (e = dalloc(&w.p32[0], c->n)) || (e = dalloc(&w.p32[1], c->n)))
+      return e;
+  }
+  if (!w.b && (e = dalloc(&w.b, c->n))) return e;
+  size_t smem_pap, smem_upd, smem_rel;
+  const StreamGeo gp = geo_for<float, float, 2>(c, &smem_pap);
+  const StreamGeo gu = geo_for<float, float, 1>(c, &smem_upd);
+  const StreamGeo gr = geo_for<double, float, 2>(c, &smem_rel);
+  int mb = gp.blocks;
+  if (gu.blocks > mb) mb = gu.blocks;
+  if (gr.blocks > mb) mb = gr.blocks;
+  if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
+  if ((e = set_smem_attr((const void*)k_cg_pap<float, false>, smem_pap))) return e;
+  if ((e = set_smem_attr((const void*)k_cg_update32, smem_upd))) return e;
+  if ((e = set_smem_attr((const void*)k_reliable, smem_rel))) return e;
+
+  CK(cudaEventRecord(c->ev0, c->stream));
+  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
+  CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
+  const int tp = round32(gp.threads), tu = round32(gu.threads), tr = round32(gr.threads);
+  k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+                                                    c->counter, c->err, gr, 0);
+  int cur = 0;
+  auto batch = [&]() {
+    for (int i = 0; i < m; ++i) {
+      k_cg_pap<float, false><<<gp.blocks, tp, smem_pap, c->stream>>>(w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
+                                                                     c->sc, c->partials, c->counter, c->err, gp);
+      k_cg_update32<<<gu.blocks, tu, smem_upd, c->stream>>>(w.x32, w.r32, w.p32[cur ^ 1], c->sc, c->partials,
+                                                           c->counter, c->err, gu);
+      k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+                                                        c->counter, c->err, gr, 1);
+      cur ^= 1;
+    }
+  };
+  if ((e = run_batches(c, m, maxit, batch))) return e;
+  CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  if ((e = sync_status(c))) return e;
+  if (c->sc_host[0].done != 1 && c->sc_host[0].done != 3) {
+    // fold the last FP32 correction and measure the true residual
+    k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+                                                      c->counter, c->err, gr, 2);
+    CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+    if ((e = sync_status(c))) return e;
+  }
+  const int sel = c->sc_host[0].xsel;
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
+  k_sum2<<<sb, 256, 0, c->stream>>>(w.xm[sel], nullptr, n4, c->sc, c->partials, c->counter);
+  k_finish<<<sb, 256, 0, c->stream>>>(w.xm[sel], phi, n4, 1.0 / (double)c->n, c->sc);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  if ((e = sync_status(c))) return e;
+  const Scalars& s = c->sc_host[0];
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->iters = s.iter;
+    info->reliable_updates = s.updates;
+    info->fallbacks = s.fallbacks;
+    info->converged = s.done == 1;
+    info->rel_res = s.bb > 0.0 ? sqrt(s.true_rr / s.bb) : 0.0;
+    info->bnorm = sqrt(s.bb) / (c->h * c->h);
+    info->t_ms = ms;
+  }
+  if (s.done == 1) return PIC_OK;
+  if (s.done == 3) return PIC_EBREAKDOWN;
+  return PIC_ENOCONV;
+}
+
+int ensure_E(pic_ctx* c) {
+  if (c->E) return PIC_OK;
+  return dalloc(&c->E, 3 * c->n);
+}
+
+int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift) {
+  int e;
+  if ((e = ensure_E(c))) return e;
+  const int sb = streaming_blocks(c);
+  k_gradient<<<sb, 256, 0, c->stream>>>(phi, c->E, c->E + c->n, c->E + 2 * c->n, c->grid);
+  if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
+  const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  k_gather_push<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, c->E, c->E + c->n, c->E + 2 * c->n, c->grid,
+                                               -kick, dt, drift, c->keys, c->ranks, c->counts);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+const char* pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument";
+    case PIC_ENOMEM: return "out of device or pinned memory";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_ENOCONV: return "solver did not converge within maxit";
+    case PIC_EBREAKDOWN: return "solver breakdown (p.Ap <= 0 or non-finite value)";
+    case PIC_ETIMEOUT: return "bounded device wait expired";
+    case PIC_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+int pic_create(pic_ctx** out, void* cuda_stream) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  pic_ctx* c = new (std::nothrow) pic_ctx();
+  if (!c) return PIC_ENOMEM;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return PIC_ECUDA;
+  }
+  bool ok = cudaMalloc(&c->sc, sizeof(Scalars)) == cudaSuccess &&
+            cudaMallocHost(&c->sc_host, 2 * sizeof(Scalars)) == cudaSuccess &&
+            cudaMalloc(&c->counter, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->err, sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->err_host, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->out3, 4 * sizeof(double)) == cudaSuccess &&
+            cudaMallocHost(&c->out3_host, 4 * sizeof(double)) == cudaSuccess &&
+            cudaEventCreate(&c->ev0) == cudaSuccess && cudaEventCreate(&c->ev1) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->batch_ev[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->batch_ev[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaMemset(c->counter, 0, sizeof(unsigned)) == cudaSuccess &&
+            cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pic_destroy(c);
+    return PIC_ENOMEM;
+  }
+  *c->err_host = 0;
+  *out = c;
+  return PIC_OK;
+}
+
+void pic_destroy(pic_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_particles(c);
+  free_solver(c);
+  dfree(c->sc);
+  dfree(c->counter);
+  dfree(c->err);
+  dfree(c->out3);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->out3_host) cudaFreeHost(c->out3_host);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (int i = 0; i < 2; ++i)
+    if (c->batch_ev[i]) cudaEventDestroy(c->batch_ev[i]);
+  delete c;
+}
+
+int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
+  if (!c || !p) return PIC_EINVAL;
+  if (p->N < 8 || p->N > 1024 || p->N % 8 != 0 || p->ppc < 0) return PIC_EINVAL;
+  if (!(p->k > 0.0) || !isfinite(p->k) || !isfinite(p->alpha) || fabs(p->alpha) >= 1.0) return PIC_EINVAL;
+  const uint64_t n = (uint64_t)p->N * p->N * p->N;
+  const uint64_t np = (uint64_t)p->ppc * n;
+  if (np >= (1ull << 32)) return PIC_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  free_particles(c);
+  free_solver(c);
+  c->N = p->N;
+  c->n = (size_t)n;
+  c->k = p->k;
+  c->alpha = p->alpha;
+  c->L = 2.0 * M_PI / p->k;
+  c->h = c->L / p->N;
+  c->ppc = p->ppc;
+  c->grid.N = p->N;
+  c->grid.L = c->L;
+  c->grid.h = c->h;
+  c->grid.inv_h = (double)p->N / c->L;
+  c->has_grid = true;
+  c->keys_valid = c->sorted = c->half_step = false;
+  c->cur = 0;
+  int e;
+  if ((e = ensure_partials(c, 3 * 4096 + 3 * (size_t)c->sms * 8))) return e;
+  if (np == 0) return PIC_OK;
+  for (int b = 0; b < 2; ++b) {
+    for (int q = 0; q < 6; ++q)
+      if ((e = dalloc(&c->pb[b][q], np))) return e;
+    if ((e = dalloc(&c->ids[b], np))) return e;
+  }
+  const size_t nchunks = (n + kScanChunk - 1) / kScanChunk;
+  if ((e = dalloc(&c->keys, np)) || (e = dalloc(&c->ranks, np)) || (e = dalloc(&c->counts, n)) ||
+      (e = dalloc(&c->offsets, n + 1)) || (e = dalloc(&c->chunks, nchunks)))
+    return e;
+  c->np = np;
+  CK(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), c->stream));
+  const unsigned blocks = (unsigned)((np + 255) / 256);
+  k_init_particles<<<blocks, 256, 0, c->stream>>>(pptrs(c, 0), np, seed, p->alpha, p->k, c->grid, c->keys,
+                                                  c->ranks, c->counts);
+  CK(cudaGetLastError());
+  c->keys_valid = true;
+  return PIC_OK;
+}
+
+int64_t pic_num_particles(const pic_ctx* c) { return c ? (int64_t)c->np : 0; }
+
+int pic_deposit(pic_ctx* c, double* rho) {
+  if (!c || !dev_ptr_ok(rho)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  if (!c->sorted) {
+    const unsigned pblocks = (unsigned)((c->np + 255) / 256);
+    if (!c->keys_valid) {
+      CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
+      k_count_keys<<<pblocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
+    }
+    const int nchunks = (int)((c->n + kScanChunk - 1) / kScanChunk);
+    k_scan_chunks<<<nchunks, 256, 0, c->stream>>>(c->counts, c->n, c->chunks);
+    k_scan_chunk_sums<<<1, 1024, 0, c->stream>>>(c->chunks, nchunks);
+    k_scan_apply<<<nchunks, 256, 0, c->stream>>>(c->counts, c->n, c->chunks, c->offsets);
+    k_scatter<<<pblocks, 256, 0, c->stream>>>(pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, c->keys, c->ranks,
+                                              c->offsets);
+    CK(cudaGetLastError());
+    c->cur ^= 1;
+    c->sorted = true;
+    c->keys_valid = false;
+  }
+  const int sb = streaming_blocks(c);
+  k_fill<<<sb, 256, 0, c->stream>>>(rho, c->n, 1.0);
+  const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
+  const unsigned cblocks = (unsigned)((c->n + 255) / 256);
+  k_deposit_cells<<<cblocks, 256, 0, c->stream>>>(c->pb[c->cur][0], c->pb[c->cur][1], c->pb[c->cur][2], c->offsets,
+                                                  rho, c->grid, qscale);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, const pic_solve_opts* o,
+                     pic_solve_info* info) {
+  if (!c || !dev_ptr_ok(rho) || !dev_ptr_ok(phi)) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  if (!(tol >= 0.0) || maxit < 0) return PIC_EINVAL;
+  pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
+  if (o) opts = *o;
+  int m = opts.check_every > 0 ? opts.check_every : (c->N <= 64 ? 32 : 8);
+  if (opts.precond != PIC_PC_JACOBI) return PIC_EINVAL;
+  if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);
+  if (opts.precision == PIC_PREC_MIXED) {
+    const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : 0.1;
+    if (!(delta < 1.0)) return PIC_EINVAL;
+    return solve_mixed(c, rho, phi, tol, maxit, m, delta, info);
+  }
+  return PIC_EINVAL;
+}
+
+int poisson_solve(pic_ctx* c, const double* rho, double* phi, double tol, int maxit) {
+  return poisson_solve_ex(c, rho, phi, tol, maxit, nullptr, nullptr);
+}
+
+int pic_gather_push(pic_ctx* c, const double* phi, double dt) {
+  if (!c || !dev_ptr_ok(phi) || !isfinite(dt)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  const double kick = c->half_step ? dt : 0.5 * dt;
+  int e;
+  if ((e = launch_push(c, phi, kick, dt, 1))) return e;
+  c->half_step = true;
+  c->keys_valid = true;
+  c->sorted = false;
+  return PIC_OK;
+}
+
+int pic_sync_velocity(pic_ctx* c, const double* phi, double dt) {
+  if (!c || !dev_ptr_ok(phi) || !isfinite(dt)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  if (!c->half_step) return PIC_OK;
+  int e;
+  if ((e = launch_push(c, phi, 0.5 * dt, dt, 0))) return e;
+  c->half_step = false;
+  return PIC_OK;
+}
+
+int pic_field_energy(pic_ctx* c, const double* phi, double out_w[3]) {
+  if (!c || !dev_ptr_ok(phi) || !out_w) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  const int sb = streaming_blocks(c);
+  k_field_energy<<<sb, 256, 0, c->stream>>>(phi, c->grid, c->out3, c->partials, c->counter);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->out3_host, c->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int e;
+  if ((e = sync_status(c))) return e;
+  for (int d = 0; d < 3; ++d) out_w[d] = c->out3_host[d];
+  return PIC_OK;
+}
+
+int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
+  if (!c || !out) return PIC_EINVAL;
+  if (c->np == 0) return PIC_ESTATE;
+  if (half_step) *half_step = c->half_step ? 1 : 0;
+  const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  if (on_device) {
+    k_unsort<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, out);
+    CK(cudaGetLastError());
+    return PIC_OK;
+  }
+  double* tmp = nullptr;
+  int e;
+  if ((e = dalloc(&tmp, 6 * c->np))) return e;
+  k_unsort<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, tmp);
+  cudaError_t ce = cudaMemcpyAsync(out, tmp, 6 * c->np * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  return ce == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_apply_laplacian(pic_ctx* c, const double* x, double* y) {
+  if (!c || !dev_ptr_ok(x) || !dev_ptr_ok(y)) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  size_t smem;
+  const StreamGeo g = geo_for<double, double, 1>(c, &smem);
+  int e;
+  if ((e = set_smem_attr((const void*)k_apply64, smem))) return e;
+  k_apply64<<<g.blocks, round32(g.threads), smem, c->stream>>>(x, y, 1.0 / (c->h * c->h), c->err, g);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+}  // extern "C"

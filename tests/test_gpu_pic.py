@@ -1,0 +1,237 @@
+"""GPU parity: every C-ABI call of the PIC loop against the CPU oracle on the
+same seeded inputs, element by element, at sizes spanning several slabs and
+the single-slab case, plus edge cases and full-size properties.
+
+Tolerances (FP64 everywhere on these paths; differences come from rounding
+order, FMA contraction and libm vs CUDA sin/cos/log at the ulp level):
+  operator / gradient / energy: 1e-12 relative;
+  initial particles: 1e-12 absolute (positions are O(L = 12.6));
+  deposit: 1e-12 absolute on rho = O(1);
+  solve: phi rel-L2 <= 1e-10 against the exact discrete solution at tol 1e-12;
+  40-step loop: particles within 1e-10, field energy rel 1e-8 (north-star
+  figures), with solves at tol 1e-12.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import pic as opic  # noqa: E402
+from paper_2605_05469_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+K = 0.5
+L = 2.0 * np.pi / K
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_2605_05469_gb300 as pg
+    pg.lib()
+    return pg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def solver_ctx(pg, N):
+    return pg.Context().init(N, 0, 0)
+
+
+# ------------------------------------------------------------------ operator
+@pytest.mark.parametrize("N", [8, 16, 24, 40, 64, 128])
+def test_apply_laplacian_matches_oracle(pg, N):
+    c = solver_ctx(pg, N)
+    x = inputs.noise_field(N, N)
+    y = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    c.apply_laplacian(dev(x), y)
+    ref = opic.apply_A(x, N, L / N)
+    got = host(y)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------------------ solve
+@pytest.mark.parametrize("N", [8, 16, 24, 32])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_exact_discrete_solution(pg, N, precision):
+    c = solver_ctx(pg, N)
+    h = L / N
+    b = inputs.noise_field(N, 100 + N, mean=0.7)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    info = c.solve(dev(b), phi, tol=1e-12, maxit=5000, precision=precision)
+    ref = opic.spectral_solve(b, N, h)
+    got = host(phi)
+    assert info["converged"] and info["rel_res"] <= 1e-12
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert abs(got.mean()) <= 1e-14 * np.abs(ref).max()
+    if precision == 0:
+        _, it, _, _ = opic.pcg_jacobi(b, np.zeros(N ** 3), N, h, 1e-12, 5000)
+        assert abs(info["iters"] - it) <= 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_tolerance_1e10_landau_rhs(pg, precision):
+    N = 64
+    c = solver_ctx(pg, N)
+    h = L / N
+    b = inputs.landau_noise_rhs(N, 7)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    info = c.solve(dev(b), phi, tol=1e-10, maxit=5000, precision=precision)
+    got = host(phi)
+    bp = b - b.mean()
+    r = bp - opic.apply_A(got, N, h)
+    assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bp)
+    ref, _, _, _ = opic.pcg_jacobi(b, np.zeros(N ** 3), N, h, 1e-13, 5000)
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+    if precision == 1:
+        assert info["reliable_updates"] >= 1
+
+
+def test_solve_edge_cases(pg):
+    N = 16
+    h = L / N
+    c = solver_ctx(pg, N)
+    b = inputs.noise_field(N, 5)
+    exact = opic.spectral_solve(b, N, h)
+    for prec in (0, 1):
+        # zero right-hand side (constant rho): phi = 0 whatever the warm start
+        phi = dev(np.ones(N ** 3))
+        info = c.solve(dev(np.full(N ** 3, 3.0)), phi, precision=prec)
+        assert info["converged"] and np.all(host(phi) == 0.0)
+        # warm start at the solution: no iterations
+        phi = dev(exact)
+        info = c.solve(dev(b), phi, tol=1e-8, precision=prec)
+        assert info["iters"] == 0 and info["converged"]
+        # maxit too small: PIC_ENOCONV, info filled, phi holds the last iterate
+        phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+        info = c.solve(dev(b), phi, tol=1e-12, maxit=3, precision=prec, raise_on_error=False)
+        assert info["code"] == pg.PIC_ENOCONV and info["iters"] == 3 and not info["converged"]
+        assert np.isfinite(host(phi)).all()
+        # a NaN in rho: breakdown, no hang
+        bad = b.copy()
+        bad[17] = np.nan
+        phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+        info = c.solve(dev(bad), phi, precision=prec, raise_on_error=False)
+        assert info["code"] == pg.PIC_EBREAKDOWN
+
+
+def test_solve_rejects_bad_arguments(pg):
+    c = solver_ctx(pg, 16)
+    rho = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        c.solve(rho, torch.zeros(15, dtype=torch.float64, device="cuda"))
+    code, _ = pg.poisson_solve_ex(c.h, rho, rho.clone(), -1.0, 10, c.n)
+    assert code == pg.PIC_EINVAL
+    with pytest.raises(pg.PicError):
+        pg.Context().init(12, 1, 0)  # N % 8 != 0
+
+
+# ------------------------------------------------------------------ particles
+@pytest.mark.parametrize("N,ppc", [(8, 3), (16, 8)])
+def test_init_particles_match_oracle(pg, N, ppc):
+    c = pg.Context().init(N, ppc, 0x5EED)
+    got, half = c.particles()
+    pos, vel = opic.init_particles(N, ppc, 0x5EED)
+    assert not half
+    assert np.max(np.abs(got[:3] - pos)) <= 1e-12
+    assert np.max(np.abs(got[3:] - vel)) <= 1e-12
+
+
+@pytest.mark.parametrize("N,ppc", [(8, 8), (16, 8), (32, 2)])
+def test_deposit_matches_oracle(pg, N, ppc):
+    c = pg.Context().init(N, ppc, 11)
+    rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    c.deposit(rho)
+    pos, _ = opic.init_particles(N, ppc, 11)
+    ref = opic.deposit(pos, N, L)
+    got = host(rho)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+    # charge conservation (Eq. 2): sum rho h^3 = 0 up to rounding
+    assert abs(got.sum()) * (L / N) ** 3 <= 1e-9
+    # deposit twice without a push: particles stay sorted, same result
+    c.deposit(rho)
+    assert np.max(np.abs(host(rho) - got)) <= 1e-13
+
+
+def test_gradient_push_and_energy_match_oracle(pg):
+    N, ppc = 16, 8
+    h = L / N
+    c = pg.Context().init(N, ppc, 3)
+    rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    c.deposit(rho)
+    c.solve(rho, phi, tol=1e-13)
+    W = c.field_energy(phi)
+    phi_h = host(phi)
+    assert np.allclose(W, opic.field_energy(phi_h, N, h), rtol=1e-12, atol=0)
+    c.gather_push(phi, 0.05)
+    got, half = c.particles()
+    assert half
+    pos, vel = opic.init_particles(N, ppc, 3)
+    Ep = opic.gather(opic.gradient(phi_h, N, h), pos, N, L)
+    pos, vel = opic.push(pos, vel, Ep, 0.05, L, kick=0.025)
+    d = np.abs(got[:3] - pos)
+    assert np.max(np.minimum(d, L - d)) <= 1e-12
+    assert np.max(np.abs(got[3:] - vel)) <= 1e-12
+    # closing half-kick makes velocities synchronous again
+    c.sync_velocity(phi, 0.05)
+    got2, half2 = c.particles()
+    assert not half2
+    Ep2 = opic.gather(opic.gradient(phi_h, N, h), pos, N, L)
+    assert np.max(np.abs(got2[3:] - opic.sync_velocity(vel, Ep2, 0.05))) <= 1e-12
+
+
+def test_pic_loop_40_steps_32cubed(pg):
+    """The small Landau case: 32^3, 8 ppc, dt = 0.05, 40 steps."""
+    N, ppc, steps, dt = 32, 8, 40, 0.05
+    h = L / N
+    c = pg.Context().init(N, ppc, 0x5EED)
+    rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    W = []
+    for n in range(steps):
+        c.deposit(rho)
+        c.solve(rho, phi, tol=1e-12, maxit=5000)
+        W.append(c.field_energy(phi))
+        c.gather_push(phi, dt)
+    got, _ = c.particles()
+    pos, vel, phi_o, en, _ = opic.pic_run(N, ppc, 0x5EED, steps, dt=dt, tol=1e-12)
+    d = np.abs(got[:3] - pos)
+    assert np.max(np.minimum(d, L - d)) <= 1e-10
+    assert np.max(np.abs(got[3:] - vel)) <= 1e-10
+    W = np.array(W)
+    assert np.max(np.abs(W - en) / en) <= 1e-8
+    assert np.linalg.norm(host(phi) - phi_o) <= 1e-9 * np.linalg.norm(phi_o)
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_step_properties_256cubed(pg):
+    """One PIC step at 256^3 x 8 ppc (134M particles), the benchmark's launch
+    configuration: charge conservation, the true FP64 residual of both solver
+    precisions checked by the oracle's operator, and the field energy."""
+    N, ppc = 256, 8
+    h = L / N
+    c = pg.Context().init(N, ppc, 0x5EED)
+    rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    c.deposit(rho)
+    rho_h = host(rho)
+    assert abs(rho_h.sum()) * h ** 3 <= 1e-6 * L ** 3
+    bp = rho_h - rho_h.mean()
+    for prec in (0, 1):
+        phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+        info = c.solve(rho, phi, tol=1e-10, maxit=5000, precision=prec)
+        phi_h = host(phi)
+        r = bp - opic.apply_A(phi_h, N, h)
+        assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(bp), (prec, info)
+        W = c.field_energy(phi)
+        assert np.allclose(W, opic.field_energy(phi_h, N, h), rtol=1e-11)
+    c.gather_push(phi, 0.05)
+    c.deposit(rho)
+    assert abs(host(rho).sum()) * h ** 3 <= 1e-6 * L ** 3
