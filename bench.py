@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the Landau-damping PIC loop on GB300.
+
+One step is one pass of the whole hot path of the PIC loop (Fig. 1) through
+the library's C ABI: sort by cell + CIC scatter (pic_deposit), the Poisson
+solve to relative residual 1e-10 (poisson_solve_ex), the field energy
+(pic_field_energy) and E = -grad phi + CIC gather + leapfrog push
+(pic_gather_push). Default workload: 256^3 periodic grid, 8 particles per cell
+(134,217,728 particles, FP64 state, 6.4 GB), Landau initial condition
+(k = 0.5, alpha = 0.05), dt = 0.05, warm-started solves.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver mixed|fp64]
+  python bench.py --impl reference      # the CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own
+independent replica of the workload (the path has no exchange step on one
+GPU); value = steps of all ranks / max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PIC steps/s (Landau 3D, CIC, 7-point FD Poisson solve to rel-res 1e-10)"
+UNIT = "steps/s"
+SEED = 0x5EED
+DT = 0.05
+TOL = 1e-10
+MAXIT = 20000
+
+# algorithmic bytes per cell of one launch of the two CG kernels
+KER_BYTES = {
+    # (precision, kernel): bytes/cell
+    (1, "pap"): 12,      # read r, p_in; write p (FP32)
+    (1, "update"): 20,   # read p, x, r; write x, r (FP32)
+    (0, "pap"): 32,      # read r, p_in; write p, q (FP64)
+    (0, "update"): 48,   # read x, r, p, q; write x, r (FP64)
+}
+# FP64 operations per cell of one launch (the FP64 judge is FP64-pipe bound)
+KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
+                    help="pic: full PIC step; solve: one cold-start Poisson solve of a Landau density + noise rhs")
+    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--ppc", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64-vs-mixed solve comparison")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    except Exception:
+        return 6800.0, "fallback", {}
+
+
+def fp64_peak_tflops():
+    """FP64 FMA peak of GB300: 1.2 TFLOP/s measured with a dependent-chain-free
+    DFMA loop on this machine's GB300 (152 SMs, ~2 GHz); see the FP64 note in the design doc."""
+    return 1.20
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import paper_2605_05469_gb300 as pg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    N, ppc = args.N, args.ppc
+    n = N ** 3
+    prec = pg.PREC_MIXED if args.solver == "mixed" else pg.PREC_FP64
+    stream = torch.cuda.current_stream()
+    solve_only = args.workload == "solve"
+    c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
+    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    if solve_only:
+        from paper_2605_05469_gb300 import inputs
+        rho = inputs.landau_noise_rhs_torch(N, 0xC0FFEE + rank, "cuda")
+    else:
+        rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    infos = []
+
+    def step(record):
+        if solve_only:
+            phi.zero_()
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            W = None
+        else:
+            c.deposit(rho)
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            W = c.field_energy(phi)
+            c.gather_push(phi, DT)
+        if record:
+            infos.append(info)
+        return W
+
+    for _ in range(args.warmup):
+        step(False)
+    c.profile(True)
+    c.profile_read(reset=True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = c.profile_read(reset=True)
+    c.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+    unit = "solves/s" if solve_only else UNIT
+    metric = ("Poisson solves/s to rel-res 1e-10 (7-point FD, cold start)" if solve_only else METRIC)
+
+    # end to end through the public API, host wall clock: per step the host
+    # reads back the step's result (field energy, 3 doubles) and the solver's
+    # status; the particle state is device resident by design.
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(False)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * args.steps / e2e_s, "unit": unit, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": 0 if solve_only else 24,
+           "note": "wall clock through the Python binding; per step the field energy is read to host"}
+
+    # solver-only end to end: rho from pinned host memory, phi back to host
+    rho_host = rho.cpu().pin_memory()
+    phi_host = torch.empty_like(rho_host).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        rho.copy_(rho_host, non_blocking=True)
+        phi.zero_()
+        c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+        phi_host.copy_(phi, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_solve = {"value": reps / (time.perf_counter() - t0), "unit": "solves/s (cold start)",
+                 "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return None
+
+    # roofline of the dominant CG kernel from the sampled CUDA events
+    hbm, peak_kind, _ = peaks()
+    kp = prof["ker_precision"]["pap"]
+    rows = {}
+    for k in ("pap", "update"):
+        if prof["ker_samples"][k]:
+            avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
+            rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k],
+                       "bytes_per_cell": KER_BYTES[(kp, k)],
+                       "gbs": KER_BYTES[(kp, k)] * n / (avg_ms * 1e-3) / 1e9}
+    dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
+    kname = {("pap", 1): "k_cg_pap<float,false>", ("update", 1): "k_cg_update32",
+             ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
+    roof = None
+    if dom is not None:
+        r = rows[dom]
+        if kp == 1:
+            roof = {"kernel": kname[(dom, kp)], "bound": "hbm", "achieved": round(r["gbs"], 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(r["gbs"] / hbm, 4),
+                    "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                    "algorithmic_bytes": r["bytes_per_cell"] * n, "avg_launch_us": round(r["avg_us"], 2)}
+        else:
+            ops = KER_FP64_OPS[(0, dom)] * n
+            tf = ops / (r["avg_us"] * 1e-6) / 1e12
+            roof = {"kernel": kname[(dom, kp)], "bound": "alu", "achieved": round(tf, 4),
+                    "peak": fp64_peak_tflops(), "unit": "FP64 TFLOP/s", "frac": round(tf / fp64_peak_tflops(), 4),
+                    "peak_source": "measured FP64 FMA loop", "traffic": None,
+                    "algorithmic_bytes": r["bytes_per_cell"] * n, "avg_launch_us": round(r["avg_us"], 2)}
+
+    iters = [i["iters"] for i in infos]
+    solve_ms = [i["t_ms"] for i in infos]
+    out = {
+        "metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 particles/grid; solve f32 vectors + f64 reductions" if prec == 1 else "f64",
+        "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
+        "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
+                                f"cold start, rel-res {TOL:g}") if solve_only else
+                               (f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc ({ppc * n} particles), "
+                                f"solve to rel-res {TOL:g}, dt {DT}"),
+                   "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
+                   "warm_start": True, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (particle state 6.4 GB; solver vectors 4 x 67-134 MB per iteration)"},
+        "clocks": clk,
+        "e2e": e2e,
+        "e2e_solve": e2e_solve,
+        "gpu_launches": prof["launches"],
+        "roofline": roof,
+        "kernels": rows,
+        "solve": {"iters_mean": statistics.mean(iters), "ms_mean": statistics.mean(solve_ms),
+                  "rel_res_max": max(i["rel_res"] for i in infos),
+                  "reliable_updates_mean": statistics.mean(i["reliable_updates"] for i in infos)},
+        "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in prof["phase_ms"].items()},
+        "impl": "ours",
+    }
+    if not args.no_compare:
+        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch)
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters))
+    if dist is not None:
+        dist.destroy_process_group()
+    c.close()
+    return out
+
+
+def compare_solvers(c, rho, n, pg, torch):
+    """Cold-start solves of the same right-hand side (the last deposit): the FP64
+    Jacobi-PCG judge against the mixed-precision solver (outside the timed region)."""
+    res = {}
+    for name, prec in (("fp64_jacobi_pcg", pg.PREC_FP64), ("mixed_fp32_fp64", pg.PREC_MIXED)):
+        best = None
+        for _ in range(2):
+            phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            if best is None or info["t_ms"] < best["t_ms"]:
+                best = info
+        res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"]}
+    res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
+    return res
+
+
+# --------------------------------------------------------------------------- oracle
+def cpu_baseline(N, ppc, iters_per_solve, reference_iters=None, budget_s=20.0):
+    """The CPU oracle (numpy, FP64, as it stands) timed on a bounded sample of
+    the same step: a few CG iterations on the full N^3 grid and the particle
+    kernels on a subset of particles, scaled to one step."""
+    from oracle import pic as opic
+    from paper_2605_05469_gb300 import inputs
+
+    L = 4.0 * np.pi
+    h = L / N
+    n = N ** 3
+    b = inputs.landau_noise_rhs(N, 1)
+    t0 = time.perf_counter()
+    k_it = 3
+    opic.pcg_jacobi(b, np.zeros(n), N, h, 0.0, k_it)   # k_it iterations + the initial residual
+    t_cg = (time.perf_counter() - t0) / (k_it + 1)
+    it = reference_iters if reference_iters else iters_per_solve
+    if ppc == 0:
+        step_s = t_cg * it
+        return {"value": 1.0 / step_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "host_cpus": os.cpu_count(),
+                "sample": f"{k_it} CG iterations on the full {N}^3 grid, scaled by {it:.0f} iterations/solve"}
+    ns = min(ppc * n, 1 << 21)
+    rng = np.random.default_rng(3)
+    pos = rng.random((3, ns)) * L
+    vel = rng.normal(size=(3, ns))
+    phi = np.zeros(n)
+    t0 = time.perf_counter()
+    opic.deposit(pos, N, L)
+    Ep = opic.gather(opic.gradient(phi, N, h), pos, N, L)
+    opic.push(pos, vel, Ep, DT, L, kick=DT)
+    t_part = (time.perf_counter() - t0) * (ppc * n / ns)
+    t0 = time.perf_counter()
+    opic.field_energy(phi, N, h)
+    t_en = time.perf_counter() - t0
+    step_s = t_cg * it + t_part + t_en
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host_cpus": os.cpu_count(),
+            "sample": f"{k_it} CG iterations on the full {N}^3 grid (scaled by {it:.0f} iterations/solve), "
+                      f"deposit+gather+push of {ns} of {ppc * n} particles (scaled linearly), one field energy"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    N, ppc = args.N, args.ppc
+    # iterations per warm-started solve: the oracle's Jacobi-PCG on this workload
+    # needs the same count as any exact-arithmetic CG; measured once at 64^3 and
+    # scaled by N (CG iterations grow like sqrt(kappa) ~ N).
+    from oracle import pic as opic
+    N0 = 64
+    pos, _ = opic.init_particles(N0, ppc, SEED)
+    L = 4.0 * np.pi
+    rho = opic.deposit(pos, N0, L)
+    _, it0, _, _ = opic.pcg_jacobi(rho, np.zeros(N0 ** 3), N0, L / N0, TOL, MAXIT)
+    iters = it0 * N / N0
+    t0 = time.perf_counter()
+    base = None
+    for _ in range(max(1, args.steps)):
+        base = cpu_baseline(N, ppc, iters)
+    total = time.perf_counter() - t0
+    out = {
+        "metric": METRIC, "value": round(base["value"], 6), "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 / base["value"], 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded Landau density + particles", "impl": "reference",
+        "config": {"workload": f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc, solve to rel-res {TOL:g}",
+                   "N": N, "ppc": ppc, "iters_per_solve_est": iters},
+        "cpu_baseline": {"value": base["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": base["sample"] + f"; {args.steps} samples in {total:.1f} s"},
+        "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return out
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

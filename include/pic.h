@@ -146,6 +146,26 @@ int64_t pic_num_particles(const pic_ctx *c);
  * FP64 device [N^3] arrays. */
 int pic_apply_laplacian(pic_ctx *c, const double *x, double *y);
 
+/* Profiling (tracing of device time, no effect on results). While enabled,
+ * the library records CUDA events on the context stream around every public
+ * call (per phase) and around a sample of the solver's kernel launches (the
+ * first iteration of every status-check batch), and counts every kernel it
+ * launches. Read and optionally reset the totals with pic_profile_read
+ * (synchronises the stream). */
+enum { PIC_PHASE_DEPOSIT = 0, PIC_PHASE_SOLVE = 1, PIC_PHASE_PUSH = 2, PIC_PHASE_ENERGY = 3, PIC_NPHASE = 4 };
+enum { PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_NKER = 2 };
+typedef struct {
+  int64_t launches;           /* kernels launched by the context (counted always) */
+  int phase_calls[PIC_NPHASE];
+  double phase_ms[PIC_NPHASE];
+  int ker_samples[PIC_NKER];  /* sampled launches of the two CG kernels */
+  double ker_ms[PIC_NKER];    /* their total device time */
+  int ker_precision[PIC_NKER]; /* PIC_PREC_* of the sampled launches (last solve) */
+} pic_profile_stats;
+
+int pic_profile_enable(pic_ctx *c, int on);
+int pic_profile_read(pic_ctx *c, pic_profile_stats *out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,7 +8,8 @@ there is no CPU fallback.
 Module-level functions carry the C names (``pic_create``, ``pic_init``,
 ``pic_deposit``, ``poisson_solve``, ``poisson_solve_ex``, ``pic_gather_push``,
 ``pic_sync_velocity``, ``pic_field_energy``, ``pic_get_particles``,
-``pic_apply_laplacian``, ``pic_destroy``); ``Context`` bundles them.
+``pic_apply_laplacian``, ``pic_profile_enable``, ``pic_profile_read``,
+``pic_destroy``); ``Context`` bundles them.
 """
 import ctypes
 import os
@@ -48,6 +49,24 @@ class pic_solve_opts(ctypes.Structure):
                 ("check_every", ctypes.c_int)]
 
 
+class pic_profile_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("phase_calls", ctypes.c_int * 4), ("phase_ms", ctypes.c_double * 4),
+                ("ker_samples", ctypes.c_int * 2), ("ker_ms", ctypes.c_double * 2),
+                ("ker_precision", ctypes.c_int * 2)]
+
+    def as_dict(self):
+        phases = ("deposit", "solve", "push", "energy")
+        kers = ("pap", "update")
+        return {
+            "launches": int(self.launches),
+            "phase_calls": {p: self.phase_calls[i] for i, p in enumerate(phases)},
+            "phase_ms": {p: self.phase_ms[i] for i, p in enumerate(phases)},
+            "ker_samples": {k: self.ker_samples[i] for i, k in enumerate(kers)},
+            "ker_ms": {k: self.ker_ms[i] for i, k in enumerate(kers)},
+            "ker_precision": {k: self.ker_precision[i] for i, k in enumerate(kers)},
+        }
+
+
 class pic_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("fallbacks", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
@@ -78,6 +97,8 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int)]),
     "pic_num_particles": (ctypes.c_int64, [ctypes.c_void_p]),
     "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pic_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_profile_stats), ctypes.c_int]),
 }
 
 
@@ -190,6 +211,16 @@ def pic_apply_laplacian(h, x, y, n):
            "pic_apply_laplacian")
 
 
+def pic_profile_enable(h, on=True):
+    _check(lib().pic_profile_enable(h, 1 if on else 0), "pic_profile_enable")
+
+
+def pic_profile_read(h, reset=True):
+    st = pic_profile_stats()
+    _check(lib().pic_profile_read(h, ctypes.byref(st), 1 if reset else 0), "pic_profile_read")
+    return st.as_dict()
+
+
 # ------------------------------------------------------------ convenience
 class Context:
     """One PIC problem on the current CUDA device (owns particles and workspace)."""
@@ -236,6 +267,12 @@ class Context:
 
     def apply_laplacian(self, x, y):
         pic_apply_laplacian(self.h, x, y, self.n)
+
+    def profile(self, on=True):
+        pic_profile_enable(self.h, on)
+
+    def profile_read(self, reset=True):
+        return pic_profile_read(self.h, reset)
 
     def close(self):
         if self.h is not None:

@@ -12,7 +12,8 @@ using namespace pic;
 
 namespace {
 
-constexpr int kSmemBudget = 100 * 1024;
+constexpr size_t kSmemBudget32 = 72 * 1024;   // >= 3 blocks per SM
+constexpr size_t kSmemBudget64 = 110 * 1024;  // >= 2 blocks per SM
 
 struct SolverWs {
   // FP64 judge
@@ -25,6 +26,51 @@ struct SolverWs {
 };
 
 }  // namespace
+
+// A pool of CUDA event pairs recorded on the context stream; flushed (elapsed
+// times summed) once the stream has passed them.
+struct EventPool {
+  static constexpr int kCap = 1024;
+  cudaEvent_t ev[kCap][2] = {};
+  int n = 0;         // pending pairs
+  int count = 0;     // flushed pairs
+  double ms = 0.0;   // flushed total
+  bool ready = false;
+  bool init() {
+    for (int i = 0; i < kCap; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (cudaEventCreate(&ev[i][j]) != cudaSuccess) return false;
+    ready = true;
+    return true;
+  }
+  void destroy() {
+    for (int i = 0; i < kCap; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (ev[i][j]) cudaEventDestroy(ev[i][j]);
+    ready = false;
+  }
+  void flush() {
+    for (int i = 0; i < n; ++i) {
+      float t = 0.f;
+      if (cudaEventSynchronize(ev[i][1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i][0], ev[i][1]) == cudaSuccess) {
+        ms += t;
+        ++count;
+      }
+    }
+    n = 0;
+  }
+  // Start a pair; returns its slot or -1 when profiling is off.
+  int begin(cudaStream_t st) {
+    if (!ready) return -1;
+    if (n == kCap) flush();
+    cudaEventRecord(ev[n][0], st);
+    return n++;
+  }
+  void end(int slot, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(ev[slot][1], st);
+  }
+  void reset() { n = 0; count = 0; ms = 0.0; }
+};
 
 struct pic_ctx {
   cudaStream_t stream = nullptr;
@@ -56,6 +102,12 @@ struct pic_ctx {
   double* out3 = nullptr;    // device, 3 doubles
   double* out3_host = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, batch_ev[2] = {nullptr, nullptr};
+  // tracing
+  int64_t launches = 0;
+  bool prof_on = false;
+  EventPool* phase = nullptr;  // [PIC_NPHASE]
+  EventPool* ker = nullptr;    // [PIC_NKER]
+  int ker_prec[PIC_NKER] = {0, 0};
 };
 
 namespace {
@@ -118,17 +170,45 @@ ParticlePtrs pptrs(pic_ctx* c, int b) {
 
 int round32(int t) { return ((t + 31) / 32) * 32; }
 
-// Stage count from the shared-memory budget, at least 4 (one plane in flight).
-template <typename A, typename B, int NV>
-StreamGeo geo_for(pic_ctx* c, size_t* smem) {
-  StreamGeo g = make_stream_geo(c->N, 4, 4 * c->sms);
-  StageLayout<A, B, NV> lay(g.rows, g.N);
-  int S = (int)(kSmemBudget / lay.bytes);
-  if (S < 4) S = 4;
+// Every kernel goes through here: launched on the context stream and counted.
+template <typename... KArgs, typename... Args>
+void launch(pic_ctx* c, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, Args... args) {
+  kernel<<<grid, block, smem, c->stream>>>(args...);
+  ++c->launches;
+}
+
+// Phase timer around one public call (no-op unless profiling is on).
+struct PhaseScope {
+  pic_ctx* c;
+  int phase, slot;
+  PhaseScope(pic_ctx* cc, int ph) : c(cc), phase(ph), slot(-1) {
+    if (c->prof_on) slot = c->phase[phase].begin(c->stream);
+  }
+  ~PhaseScope() {
+    if (slot >= 0) c->phase[phase].end(slot, c->stream);
+  }
+};
+
+// Stage count from a shared-memory budget per block (raw TMA stages + 3 plane
+// buffers, at least 3 stages); persistent grid = resident blocks of `kernel`.
+template <typename TP, typename A, typename B, int NV, typename K>
+int geo_for(pic_ctx* c, K kernel, StreamGeo* out, size_t* smem) {
+  StreamGeo g = make_stream_geo(c->N, 3);
+  const StageLayout<A, B, NV> lay(g.rows, g.N);
+  const size_t budget = sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32;
+  const size_t pb = 3 * (size_t)g.rows * g.N * sizeof(TP);
+  int S = budget > pb ? (int)((budget - pb) / lay.bytes) : 0;
+  if (S < 3) S = 3;
   if (S > kMaxStages) S = kMaxStages;
   g.S = S;
-  *smem = (size_t)S * lay.bytes;
-  return g;
+  *smem = stream_smem_bytes<TP, A, B, NV>(g.rows, g.N, S);
+  CK(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, round32(g.threads), *smem));
+  if (per_sm < 1) return PIC_EINVAL;
+  set_stream_blocks(g, per_sm * c->sms);
+  *out = g;
+  return PIC_OK;
 }
 
 int streaming_blocks(pic_ctx* c) {
@@ -180,8 +260,8 @@ int solve_common_setup(pic_ctx* c, const double* rho, const double* phi, double 
   CK(cudaMemcpyAsync(c->sc, &c->sc_host[0], sizeof(Scalars), cudaMemcpyHostToDevice, c->stream));
   const int sb = streaming_blocks(c);
   const size_t n4 = c->n / 4;
-  k_sum2<<<sb, 256, 0, c->stream>>>(rho, phi, n4, c->sc, c->partials, c->counter);
-  k_project<<<sb, 256, 0, c->stream>>>(rho, phi, c->ws.b, xout, n4, 1.0 / (double)c->n, c->h * c->h, tol, c->sc,
+  launch(c, k_sum2, sb, 256, 0, rho, phi, n4, c->sc, c->partials, c->counter);
+  launch(c, k_project, sb, 256, 0, rho, phi, c->ws.b, xout, n4, 1.0 / (double)c->n, c->h * c->h, tol, c->sc,
                                       c->partials, c->counter);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -219,35 +299,45 @@ int solve_fp64(pic_ctx* c, const double* rho, double* phi, double tol, int maxit
   }
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
   size_t smem_pap, smem_res;
-  const StreamGeo gp = geo_for<double, double, 2>(c, &smem_pap);
-  const StreamGeo gr = geo_for<double, double, 1>(c, &smem_res);
+  StreamGeo gp, gr;
+  if ((e = geo_for<double, double, double, 2>(c, k_cg_pap<double, true>, &gp, &smem_pap))) return e;
+  if ((e = geo_for<double, double, double, 1>(c, k_residual64, &gr, &smem_res))) return e;
   if ((e = ensure_partials(c, (size_t)3 * (gp.blocks > gr.blocks ? gp.blocks : gr.blocks) + 3 * 4096))) return e;
-  if ((e = set_smem_attr((const void*)k_cg_pap<double, true>, smem_pap))) return e;
-  if ((e = set_smem_attr((const void*)k_residual64, smem_res))) return e;
 
   CK(cudaEventRecord(c->ev0, c->stream));
   if ((e = solve_common_setup(c, rho, phi, tol, maxit, 0.0, w.x))) return e;
   CK(cudaMemsetAsync(w.p[0], 0, c->n * sizeof(double), c->stream));
   const int tp = round32(gp.threads), tr = round32(gr.threads);
-  k_residual64<<<gr.blocks, tr, smem_res, c->stream>>>(w.x, w.b, w.r, c->sc, c->partials, c->counter, c->err, gr);
+  launch(c, k_residual64, gr.blocks, tr, smem_res, w.x, w.b, w.r, c->sc, c->partials, c->counter, c->err, gr);
   const int sb = streaming_blocks(c);
   const size_t n4 = c->n / 4;
   int cur = 0;
   auto batch = [&]() {
     for (int i = 0; i < m; ++i) {
-      k_cg_pap<double, true><<<gp.blocks, tp, smem_pap, c->stream>>>(w.r, w.p[cur], w.p[cur ^ 1], w.q, c->sc,
-                                                                     c->partials, c->counter, c->err, gp);
-      k_cg_update64<<<sb, 256, 0, c->stream>>>(w.x, w.r, w.p[cur ^ 1], w.q, n4, c->sc, c->partials, c->counter);
+      const bool sample = c->prof_on && i == 0;
+      int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
+      launch(c, k_cg_pap<double, true>, gp.blocks, tp, smem_pap, w.r, w.p[cur], w.p[cur ^ 1], w.q, c->sc,
+             c->partials, c->counter, c->err, gp);
+      if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
+      slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
+      launch(c, k_cg_update64, sb, 256, 0, w.x, w.r, w.p[cur ^ 1], w.q, n4, c->sc, c->partials, c->counter);
+      if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
       cur ^= 1;
     }
   };
   if ((e = run_batches(c, m, maxit, batch))) return e;
-  k_sum2<<<sb, 256, 0, c->stream>>>(w.x, nullptr, n4, c->sc, c->partials, c->counter);
-  k_finish<<<sb, 256, 0, c->stream>>>(w.x, phi, n4, 1.0 / (double)c->n, c->sc);
+  launch(c, k_sum2, sb, 256, 0, w.x, nullptr, n4, c->sc, c->partials, c->counter);
+  launch(c, k_finish, sb, 256, 0, w.x, phi, n4, 1.0 / (double)c->n, c->sc);
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev1, c->stream));
   CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
   if ((e = sync_status(c))) return e;
+  if (c->prof_on) {
+    for (int kk = 0; kk < PIC_NKER; ++kk) {
+      c->ker[kk].flush();
+      c->ker_prec[kk] = PIC_PREC_FP64;
+    }
+  }
   const Scalars& s = c->sc_host[0];
   if (info) {
     float ms = 0.f;
@@ -279,32 +369,35 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   }
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
   size_t smem_pap, smem_upd, smem_rel;
-  const StreamGeo gp = geo_for<float, float, 2>(c, &smem_pap);
-  const StreamGeo gu = geo_for<float, float, 1>(c, &smem_upd);
-  const StreamGeo gr = geo_for<double, float, 2>(c, &smem_rel);
+  StreamGeo gp, gu, gr;
+  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, false>, &gp, &smem_pap))) return e;
+  if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
+  if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
   int mb = gp.blocks;
   if (gu.blocks > mb) mb = gu.blocks;
   if (gr.blocks > mb) mb = gr.blocks;
   if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
-  if ((e = set_smem_attr((const void*)k_cg_pap<float, false>, smem_pap))) return e;
-  if ((e = set_smem_attr((const void*)k_cg_update32, smem_upd))) return e;
-  if ((e = set_smem_attr((const void*)k_reliable, smem_rel))) return e;
 
   CK(cudaEventRecord(c->ev0, c->stream));
   if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
   CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
   CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
   const int tp = round32(gp.threads), tu = round32(gu.threads), tr = round32(gr.threads);
-  k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+  launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                     c->counter, c->err, gr, 0);
   int cur = 0;
   auto batch = [&]() {
     for (int i = 0; i < m; ++i) {
-      k_cg_pap<float, false><<<gp.blocks, tp, smem_pap, c->stream>>>(w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
-                                                                     c->sc, c->partials, c->counter, c->err, gp);
-      k_cg_update32<<<gu.blocks, tu, smem_upd, c->stream>>>(w.x32, w.r32, w.p32[cur ^ 1], c->sc, c->partials,
-                                                           c->counter, c->err, gu);
-      k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+      const bool sample = c->prof_on && i == 0;
+      int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
+      launch(c, k_cg_pap<float, false>, gp.blocks, tp, smem_pap, w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
+             c->sc, c->partials, c->counter, c->err, gp);
+      if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
+      slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
+      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, w.p32[cur ^ 1], c->sc, c->partials,
+             c->counter, c->err, gu);
+      if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
+      launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                         c->counter, c->err, gr, 1);
       cur ^= 1;
     }
@@ -314,7 +407,7 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   if ((e = sync_status(c))) return e;
   if (c->sc_host[0].done != 1 && c->sc_host[0].done != 3) {
     // fold the last FP32 correction and measure the true residual
-    k_reliable<<<gr.blocks, tr, smem_rel, c->stream>>>(w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
+    launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                       c->counter, c->err, gr, 2);
     CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
     if ((e = sync_status(c))) return e;
@@ -322,12 +415,18 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   const int sel = c->sc_host[0].xsel;
   const int sb = streaming_blocks(c);
   const size_t n4 = c->n / 4;
-  k_sum2<<<sb, 256, 0, c->stream>>>(w.xm[sel], nullptr, n4, c->sc, c->partials, c->counter);
-  k_finish<<<sb, 256, 0, c->stream>>>(w.xm[sel], phi, n4, 1.0 / (double)c->n, c->sc);
+  launch(c, k_sum2, sb, 256, 0, w.xm[sel], nullptr, n4, c->sc, c->partials, c->counter);
+  launch(c, k_finish, sb, 256, 0, w.xm[sel], phi, n4, 1.0 / (double)c->n, c->sc);
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev1, c->stream));
   CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
   if ((e = sync_status(c))) return e;
+  if (c->prof_on) {
+    for (int kk = 0; kk < PIC_NKER; ++kk) {
+      c->ker[kk].flush();
+      c->ker_prec[kk] = PIC_PREC_MIXED;
+    }
+  }
   const Scalars& s = c->sc_host[0];
   if (info) {
     float ms = 0.f;
@@ -354,10 +453,10 @@ int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift
   int e;
   if ((e = ensure_E(c))) return e;
   const int sb = streaming_blocks(c);
-  k_gradient<<<sb, 256, 0, c->stream>>>(phi, c->E, c->E + c->n, c->E + 2 * c->n, c->grid);
+  launch(c, k_gradient, sb, 256, 0, phi, c->E, c->E + c->n, c->E + 2 * c->n, c->grid);
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
-  k_gather_push<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, c->E, c->E + c->n, c->E + 2 * c->n, c->grid,
+  launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, c->E, c->E + c->n, c->E + 2 * c->n, c->grid,
                                                -kick, dt, drift, c->keys, c->ranks, c->counts);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -433,6 +532,14 @@ void pic_destroy(pic_ctx* c) {
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (int i = 0; i < 2; ++i)
     if (c->batch_ev[i]) cudaEventDestroy(c->batch_ev[i]);
+  if (c->phase) {
+    for (int i = 0; i < PIC_NPHASE; ++i) c->phase[i].destroy();
+    delete[] c->phase;
+  }
+  if (c->ker) {
+    for (int i = 0; i < PIC_NKER; ++i) c->ker[i].destroy();
+    delete[] c->ker;
+  }
   delete c;
 }
 
@@ -475,7 +582,7 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
   c->np = np;
   CK(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((np + 255) / 256);
-  k_init_particles<<<blocks, 256, 0, c->stream>>>(pptrs(c, 0), np, seed, p->alpha, p->k, c->grid, c->keys,
+  launch(c, k_init_particles, blocks, 256, 0, pptrs(c, 0), np, seed, p->alpha, p->k, c->grid, c->keys,
                                                   c->ranks, c->counts);
   CK(cudaGetLastError());
   c->keys_valid = true;
@@ -487,17 +594,18 @@ int64_t pic_num_particles(const pic_ctx* c) { return c ? (int64_t)c->np : 0; }
 int pic_deposit(pic_ctx* c, double* rho) {
   if (!c || !dev_ptr_ok(rho)) return PIC_EINVAL;
   if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  PhaseScope ps(c, PIC_PHASE_DEPOSIT);
   if (!c->sorted) {
     const unsigned pblocks = (unsigned)((c->np + 255) / 256);
     if (!c->keys_valid) {
       CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
-      k_count_keys<<<pblocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
+      launch(c, k_count_keys, pblocks, 256, 0, pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
     }
     const int nchunks = (int)((c->n + kScanChunk - 1) / kScanChunk);
-    k_scan_chunks<<<nchunks, 256, 0, c->stream>>>(c->counts, c->n, c->chunks);
-    k_scan_chunk_sums<<<1, 1024, 0, c->stream>>>(c->chunks, nchunks);
-    k_scan_apply<<<nchunks, 256, 0, c->stream>>>(c->counts, c->n, c->chunks, c->offsets);
-    k_scatter<<<pblocks, 256, 0, c->stream>>>(pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, c->keys, c->ranks,
+    launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
+    launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
+    launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
+    launch(c, k_scatter, pblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, c->keys, c->ranks,
                                               c->offsets);
     CK(cudaGetLastError());
     c->cur ^= 1;
@@ -505,10 +613,10 @@ int pic_deposit(pic_ctx* c, double* rho) {
     c->keys_valid = false;
   }
   const int sb = streaming_blocks(c);
-  k_fill<<<sb, 256, 0, c->stream>>>(rho, c->n, 1.0);
+  launch(c, k_fill, sb, 256, 0, rho, c->n, 1.0);
   const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
   const unsigned cblocks = (unsigned)((c->n + 255) / 256);
-  k_deposit_cells<<<cblocks, 256, 0, c->stream>>>(c->pb[c->cur][0], c->pb[c->cur][1], c->pb[c->cur][2], c->offsets,
+  launch(c, k_deposit_cells, cblocks, 256, 0, c->pb[c->cur][0], c->pb[c->cur][1], c->pb[c->cur][2], c->offsets,
                                                   rho, c->grid, qscale);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -523,6 +631,7 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   if (o) opts = *o;
   int m = opts.check_every > 0 ? opts.check_every : (c->N <= 64 ? 32 : 8);
   if (opts.precond != PIC_PC_JACOBI) return PIC_EINVAL;
+  PhaseScope ps(c, PIC_PHASE_SOLVE);
   if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);
   if (opts.precision == PIC_PREC_MIXED) {
     const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : 0.1;
@@ -540,6 +649,7 @@ int pic_gather_push(pic_ctx* c, const double* phi, double dt) {
   if (!c || !dev_ptr_ok(phi) || !isfinite(dt)) return PIC_EINVAL;
   if (!c->has_grid || c->np == 0) return PIC_ESTATE;
   const double kick = c->half_step ? dt : 0.5 * dt;
+  PhaseScope ps(c, PIC_PHASE_PUSH);
   int e;
   if ((e = launch_push(c, phi, kick, dt, 1))) return e;
   c->half_step = true;
@@ -562,7 +672,10 @@ int pic_field_energy(pic_ctx* c, const double* phi, double out_w[3]) {
   if (!c || !dev_ptr_ok(phi) || !out_w) return PIC_EINVAL;
   if (!c->has_grid) return PIC_ESTATE;
   const int sb = streaming_blocks(c);
-  k_field_energy<<<sb, 256, 0, c->stream>>>(phi, c->grid, c->out3, c->partials, c->counter);
+  {
+  PhaseScope ps(c, PIC_PHASE_ENERGY);
+  launch(c, k_field_energy, sb, 256, 0, phi, c->grid, c->out3, c->partials, c->counter);
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->out3_host, c->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   int e;
@@ -577,14 +690,14 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   if (half_step) *half_step = c->half_step ? 1 : 0;
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   if (on_device) {
-    k_unsort<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, out);
+    launch(c, k_unsort, blocks, 256, 0, pptrs(c, c->cur), c->np, out);
     CK(cudaGetLastError());
     return PIC_OK;
   }
   double* tmp = nullptr;
   int e;
   if ((e = dalloc(&tmp, 6 * c->np))) return e;
-  k_unsort<<<blocks, 256, 0, c->stream>>>(pptrs(c, c->cur), c->np, tmp);
+  launch(c, k_unsort, blocks, 256, 0, pptrs(c, c->cur), c->np, tmp);
   cudaError_t ce = cudaMemcpyAsync(out, tmp, 6 * c->np * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   cudaFree(tmp);
@@ -595,11 +708,50 @@ int pic_apply_laplacian(pic_ctx* c, const double* x, double* y) {
   if (!c || !dev_ptr_ok(x) || !dev_ptr_ok(y)) return PIC_EINVAL;
   if (!c->has_grid) return PIC_ESTATE;
   size_t smem;
-  const StreamGeo g = geo_for<double, double, 1>(c, &smem);
+  StreamGeo g;
   int e;
-  if ((e = set_smem_attr((const void*)k_apply64, smem))) return e;
-  k_apply64<<<g.blocks, round32(g.threads), smem, c->stream>>>(x, y, 1.0 / (c->h * c->h), c->err, g);
+  if ((e = geo_for<double, double, double, 1>(c, k_apply64, &g, &smem))) return e;
+  launch(c, k_apply64, g.blocks, round32(g.threads), smem, x, y, 1.0 / (c->h * c->h), c->err, g);
   CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int pic_profile_enable(pic_ctx* c, int on) {
+  if (!c) return PIC_EINVAL;
+  if (on && !c->phase) {
+    c->phase = new (std::nothrow) EventPool[PIC_NPHASE];
+    c->ker = new (std::nothrow) EventPool[PIC_NKER];
+    if (!c->phase || !c->ker) return PIC_ENOMEM;
+    for (int i = 0; i < PIC_NPHASE; ++i)
+      if (!c->phase[i].init()) return PIC_ECUDA;
+    for (int i = 0; i < PIC_NKER; ++i)
+      if (!c->ker[i].init()) return PIC_ECUDA;
+  }
+  c->prof_on = on != 0;
+  return PIC_OK;
+}
+
+int pic_profile_read(pic_ctx* c, pic_profile_stats* out, int reset) {
+  if (!c || !out) return PIC_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof(*out));
+  out->launches = c->launches;
+  if (c->phase) {
+    for (int i = 0; i < PIC_NPHASE; ++i) {
+      c->phase[i].flush();
+      out->phase_calls[i] = c->phase[i].count;
+      out->phase_ms[i] = c->phase[i].ms;
+      if (reset) c->phase[i].reset();
+    }
+    for (int i = 0; i < PIC_NKER; ++i) {
+      c->ker[i].flush();
+      out->ker_samples[i] = c->ker[i].count;
+      out->ker_ms[i] = c->ker[i].ms;
+      out->ker_precision[i] = c->ker_prec[i];
+      if (reset) c->ker[i].reset();
+    }
+  }
+  if (reset) c->launches = 0;
   return PIC_OK;
 }
 

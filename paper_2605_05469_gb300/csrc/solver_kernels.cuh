@@ -36,56 +36,117 @@ struct StageLayout {
   }
 };
 
-// Streams the slab's planes through the stage ring and calls
-//   conv(st)            once per arriving stage (all threads, then a barrier),
-//   body(t, sp, sc, sn) once per output plane t with the stage indices of
-//                       planes z-1, z, z+1.
-// Returns false if a bounded wait expired (the caller skips its epilogue
-// writes but still takes part in its final reduction).
-template <typename A, typename B, int NV, typename Conv, typename Body>
-__device__ __forceinline__ bool stream_slab(const Slab& s, unsigned char* smem, uint64_t* bars, const A* src0,
-                                            const B* src1, int* err, Conv conv, Body body) {
-  const StageLayout<A, B, NV> lay(s.rows, s.N);
-  const int nload = s.ZC + 2;
+// Streams the block's runs of planes through the ring of raw TMA stages.
+// For every arriving plane l of a run, each thread transforms 4 consecutive
+// cells (its own, plus one halo-row chunk for the threads on the slab's first
+// and last row):
+//   ingest(st, e) -> V4<TP>   transformed values at stage element offset e,
+// writes them to plane buffer l % 3 (x-y neighbours of other threads) and
+// keeps its own cells in a register queue (centre and z-neighbours). After a
+// single barrier the raw stage is refilled and output plane t = l - 2 runs:
+//   body(s, t, pb, zm, c, zp) pb = plane buffer of plane t (x-y neighbours),
+//                             zm/c/zp = own cells at planes t-1, t, t+1.
+//   start(s)                  once per run before its first plane (prefetch).
+// Three plane buffers make one barrier per plane sufficient. mbarrier phases
+// continue across runs; every issued copy is waited for before the next run.
+template <typename TP, typename A, typename B, int NV, typename Start, typename Ingest, typename Body>
+__device__ __forceinline__ bool stream_slab(const StreamGeo& g, unsigned char* smem, uint64_t* bars, const A* src0,
+                                            const B* src1, int* err, Start start, Ingest ingest, Body body) {
+  const StageLayout<A, B, NV> lay(g.rows, g.N);
+  const size_t pb_elems = (size_t)g.rows * g.N;
+  TP* pbuf = reinterpret_cast<TP*>(smem + (size_t)g.S * lay.bytes);
   __shared__ int abort_flag;
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int st = 0; st < s.S; ++st) mbar_init(&bars[st], 1);
+    for (int st = 0; st < g.S; ++st) mbar_init(&bars[st], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  const uint32_t tx = plane_bytes<A>(s) + (NV == 2 ? plane_bytes<B>(s) : 0u);
-  auto issue = [&](int l) {
-    const int st = l % s.S;
-    const int z = load_plane(s, l);
-    mbar_arrive_expect_tx(&bars[st], tx);
-    issue_plane(lay.v0(smem, st), src0, s, z, &bars[st]);
-    if (NV == 2) issue_plane(lay.v1(smem, st), src1, s, z, &bars[st]);
-  };
-  if (threadIdx.x == 0) {
-    const int pre = nload < s.S ? nload : s.S;
-    for (int l = 0; l < pre; ++l) issue(l);
-  }
-  auto acquire = [&](int l) {
-    const int st = l % s.S;
-    if (!mbar_wait_bounded(&bars[st], (uint32_t)((l / s.S) & 1), err)) abort_flag = 1;
-    conv(st);
-  };
-  acquire(0);
-  acquire(1);
+  uint32_t base = 0;  // loads issued (and consumed) in earlier runs
   bool ok = true;
-  for (int t = 0; t < s.ZC; ++t) {
-    acquire(t + 2);
-    __syncthreads();
-    if (abort_flag) { ok = false; break; }
-    body(t, t % s.S, (t + 1) % s.S, (t + 2) % s.S);
-    __syncthreads();
-    if (threadIdx.x == 0 && t + s.S < nload) {
+  for_each_run(g, [&](int yt, int z0, int zc) {
+    if (!ok) return;
+    const Slab s = make_slab(g, yt, z0, zc);
+    const int nload = s.ZC + 2;
+    const uint32_t tx = plane_bytes<A>(s) + (NV == 2 ? plane_bytes<B>(s) : 0u);
+    auto issue = [&](int l) {
+      const uint32_t L = base + (uint32_t)l;
+      const int st = (int)(L % (uint32_t)s.S);
+      const int z = load_plane(s, l);
+      mbar_arrive_expect_tx(&bars[st], tx);
+      issue_plane(lay.v0(smem, st), src0, s, z, &bars[st]);
+      if (NV == 2) issue_plane(lay.v1(smem, st), src1, s, z, &bars[st]);
+    };
+    if (threadIdx.x == 0) {
       fence_proxy_async_smem();
-      issue(t + s.S);
+      const int pre = nload < s.S ? nload : s.S;
+      for (int l = 0; l < pre; ++l) issue(l);
     }
-  }
+    if (s.active) start(s);
+    // halo-row chunks owned by this thread (stage rows 0 and TY+1; with
+    // TY == 1 the same thread owns both)
+    const bool halo_lo = s.TY != s.N && s.active && s.ty == 0;
+    const bool halo_hi = s.TY != s.N && s.active && s.ty == s.TY - 1;
+    const size_t own = (size_t)s.srow * s.N + s.x0;
+    const size_t hal_lo = (size_t)s.x0;
+    const size_t hal_hi = (size_t)(s.TY + 1) * s.N + s.x0;
+    V4<TP> q0, q1, q2;
+    for (int l = 0; l < nload; ++l) {
+      const uint32_t L = base + (uint32_t)l;
+      const int st = (int)(L % (uint32_t)s.S);
+      if (!mbar_wait_bounded(&bars[st], (L / (uint32_t)s.S) & 1u, err)) abort_flag = 1;
+      TP* pb = pbuf + (size_t)(L % 3u) * pb_elems;
+      if (s.active) {
+        q0 = q1;
+        q1 = q2;
+        q2 = ingest(st, own);
+        st4(pb + own, q2);
+        if (halo_lo) st4(pb + hal_lo, ingest(st, hal_lo));
+        if (halo_hi) st4(pb + hal_hi, ingest(st, hal_hi));
+      }
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        return;
+      }
+      if (threadIdx.x == 0 && l + s.S < nload) {
+        fence_proxy_async_smem();
+        issue(l + s.S);
+      }
+      if (l >= 2 && s.active) body(s, l - 2, pbuf + (size_t)((L + 2u) % 3u) * pb_elems, q0, q1, q2);
+    }
+    base += (uint32_t)nload;
+  });
   return ok;
+}
+
+// Bytes of dynamic shared memory for stream_slab: S raw stages + 3 plane buffers.
+template <typename TP, typename A, typename B, int NV>
+__host__ __device__ inline size_t stream_smem_bytes(int rows, int N, int S) {
+  const StageLayout<A, B, NV> lay(rows, N);
+  return (size_t)S * lay.bytes + 3 * (size_t)rows * N * sizeof(TP);
+}
+
+// x-y neighbours from the plane buffer, z-neighbours and centre from registers:
+// returns 6 c - (sum of the 6 neighbours) on the thread's 4 cells.
+template <typename T>
+__device__ __forceinline__ V4<T> stencil_q(const T* pb, const Slab& s, const V4<T>& zm, const V4<T>& c,
+                                           const V4<T>& zp) {
+  const int N = s.N;
+  const T* row = pb + (size_t)s.srow * N;
+  const T xm = row[s.x0 == 0 ? N - 1 : s.x0 - 1];
+  const T xp = row[s.x0 + 4 == N ? 0 : s.x0 + 4];
+  const V4<T> ym = ld4(pb + (size_t)s.rm * N + s.x0);
+  const V4<T> yp = ld4(pb + (size_t)s.rp * N + s.x0);
+  V4<T> o;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T l = (i == 0) ? xm : c.v[i - 1];
+    const T r = (i == 3) ? xp : c.v[i + 1];
+    const T sum = ((l + r) + (ym.v[i] + yp.v[i])) + (zm.v[i] + zp.v[i]);
+    o.v[i] = (T)6 * c.v[i] - sum;
+  }
+  return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -98,19 +159,19 @@ __global__ void __launch_bounds__(256) k_cg_pap(const T* __restrict__ r, const T
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (sc->done) return;
-  const Slab s = make_slab(g);
   const T beta = (T)sc->beta;
-  const StageLayout<T, T, 2> lay(s.rows, s.N);
+  const StageLayout<T, T, 2> lay(g.rows, g.N);
   double dot = 0.0;
-  auto conv = [&](int st) {
-    T* R = lay.v0(smem, st);
-    T* P = lay.v1(smem, st);
-    for (size_t i = threadIdx.x; i < lay.e; i += blockDim.x) P[i] = R[i] + beta * P[i];
+  auto ingest = [&](int st, size_t e) {
+    const V4<T> rv = ld4(lay.v0(smem, st) + e);
+    V4<T> pv = ld4(lay.v1(smem, st) + e);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pv.v[i] = rv.v[i] + beta * pv.v[i];
+    return pv;
   };
-  auto body = [&](int t, int sp, int scur, int sn) {
-    if (!s.active) return;
-    V4<T> c;
-    const V4<T> ap = stencil4(lay.v1(smem, sp), lay.v1(smem, scur), lay.v1(smem, sn), s, c);
+  auto start = [&](const Slab&) {};
+  auto body = [&](const Slab& s, int t, const T* pb, const V4<T>& zm, const V4<T>& c, const V4<T>& zp) {
+    const V4<T> ap = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
     st4(pout + off, c);
     if (STORE_Q) st4(q + off, ap);
@@ -119,7 +180,7 @@ __global__ void __launch_bounds__(256) k_cg_pap(const T* __restrict__ r, const T
     for (int i = 1; i < 4; ++i) d += c.v[i] * ap.v[i];
     dot += (double)d;
   };
-  stream_slab<T, T, 2>(s, smem, bars, r, pin, err, conv, body);
+  stream_slab<T, T, T, 2>(g, smem, bars, r, pin, err, start, ingest, body);
   double v[1] = {dot}, tot[1];
   if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double pq = tot[0];
@@ -178,31 +239,42 @@ __global__ void __launch_bounds__(256) k_cg_update32(float* __restrict__ x, floa
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (sc->done) return;
-  const Slab s = make_slab(g);
   const float alpha = (float)sc->alpha;
   const bool x_zero = sc->x32_reset != 0;
-  const StageLayout<float, float, 1> lay(s.rows, s.N);
+  const StageLayout<float, float, 1> lay(g.rows, g.N);
   double acc = 0.0;
-  auto conv = [&](int) {};
-  auto body = [&](int t, int sp, int scur, int sn) {
-    if (!s.active) return;
-    V4<float> c;
-    const V4<float> ap = stencil4(lay.v0(smem, sp), lay.v0(smem, scur), lay.v0(smem, sn), s, c);
+  V4<float> cx, cr;  // x, r of the current output plane, loaded one plane ahead
+  const V4<float> zero4{{0.f, 0.f, 0.f, 0.f}};
+  auto start = [&](const Slab& s) {
+    const size_t off = cell_offset(s, 0);
+    cx = x_zero ? zero4 : ldg4(x + off);
+    cr = ldg4(r + off);
+  };
+  auto ingest = [&](int st, size_t e) { return ld4(lay.v0(smem, st) + e); };
+  auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
+                  const V4<float>& zp) {
+    V4<float> nx = zero4, nr = zero4;
+    if (t + 1 < s.ZC) {
+      const size_t noff = cell_offset(s, t + 1);
+      if (!x_zero) nx = ldg4(x + noff);
+      nr = ldg4(r + noff);
+    }
+    const V4<float> ap = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
-    V4<float> xv = x_zero ? V4<float>{{0.f, 0.f, 0.f, 0.f}} : ldg4(x + off);
-    V4<float> rv = ldg4(r + off);
     float d = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      xv.v[i] = fmaf(alpha, c.v[i], xv.v[i]);
-      rv.v[i] = fmaf(-alpha, ap.v[i], rv.v[i]);
-      d = fmaf(rv.v[i], rv.v[i], d);
+      cx.v[i] = fmaf(alpha, c.v[i], cx.v[i]);
+      cr.v[i] = fmaf(-alpha, ap.v[i], cr.v[i]);
+      d = fmaf(cr.v[i], cr.v[i], d);
     }
-    st4(x + off, xv);
-    st4(r + off, rv);
+    st4(x + off, cx);
+    st4(r + off, cr);
     acc += (double)d;
+    cx = nx;
+    cr = nr;
   };
-  stream_slab<float, float, 1>(s, smem, bars, p, (const float*)nullptr, err, conv, body);
+  stream_slab<float, float, float, 1>(g, smem, bars, p, (const float*)nullptr, err, start, ingest, body);
   double v[1] = {acc}, tot[1];
   if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
@@ -234,16 +306,19 @@ __global__ void __launch_bounds__(256) k_residual64(const double* __restrict__ x
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (sc->done) return;
-  const Slab s = make_slab(g);
-  const StageLayout<double, double, 1> lay(s.rows, s.N);
+  const StageLayout<double, double, 1> lay(g.rows, g.N);
   double acc = 0.0;
-  auto conv = [&](int) {};
-  auto body = [&](int t, int sp, int scur, int sn) {
-    if (!s.active) return;
-    V4<double> c;
-    const V4<double> ax = stencil4(lay.v0(smem, sp), lay.v0(smem, scur), lay.v0(smem, sn), s, c);
+  V4<double> cb;
+  auto start = [&](const Slab& s) { cb = ldg4(b + cell_offset(s, 0)); };
+  auto ingest = [&](int st, size_t e) { return ld4(lay.v0(smem, st) + e); };
+  auto body = [&](const Slab& s, int t, const double* pb, const V4<double>& zm, const V4<double>& c,
+                  const V4<double>& zp) {
+    V4<double> nb = cb;
+    if (t + 1 < s.ZC) nb = ldg4(b + cell_offset(s, t + 1));
+    const V4<double> ax = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
-    const V4<double> bv = ldg4(b + off);
+    const V4<double> bv = cb;
+    cb = nb;
     V4<double> rv;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -252,7 +327,7 @@ __global__ void __launch_bounds__(256) k_residual64(const double* __restrict__ x
     }
     st4(r + off, rv);
   };
-  stream_slab<double, double, 1>(s, smem, bars, x, (const double*)nullptr, err, conv, body);
+  stream_slab<double, double, double, 1>(g, smem, bars, x, (const double*)nullptr, err, start, ingest, body);
   double v[1] = {acc}, tot[1];
   if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
@@ -285,26 +360,32 @@ __global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, dou
   __shared__ uint64_t bars[kMaxStages];
   if (mode == 0 && sc->done) return;
   if (mode == 1 && (sc->done || !sc->need_update)) return;
-  const Slab s = make_slab(g);
   const int sel = sc->xsel;
   const double* xin = sel ? x64b : x64a;
   double* xout = sel ? x64a : x64b;
   // x32 holds a stale correction that has already been folded: read it as zero
   const bool x32_zero = sc->x32_reset != 0;
-  const StageLayout<double, float, 2> lay(s.rows, s.N);
+  const StageLayout<double, float, 2> lay(g.rows, g.N);
   double acc64 = 0.0, acc32 = 0.0;
-  auto conv = [&](int st) {
-    if (x32_zero) return;
-    double* X = lay.v0(smem, st);
-    const float* Y = lay.v1(smem, st);
-    for (size_t i = threadIdx.x; i < lay.e; i += blockDim.x) X[i] += (double)Y[i];
+  V4<double> cb;
+  auto start = [&](const Slab& s) { cb = ldg4(b + cell_offset(s, 0)); };
+  auto ingest = [&](int st, size_t e) {
+    V4<double> xv = ld4(lay.v0(smem, st) + e);
+    if (!x32_zero) {
+      const V4<float> yv = ld4(lay.v1(smem, st) + e);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv.v[i] += (double)yv.v[i];
+    }
+    return xv;
   };
-  auto body = [&](int t, int sp, int scur, int sn) {
-    if (!s.active) return;
-    V4<double> c;
-    const V4<double> ax = stencil4(lay.v0(smem, sp), lay.v0(smem, scur), lay.v0(smem, sn), s, c);
+  auto body = [&](const Slab& s, int t, const double* pb, const V4<double>& zm, const V4<double>& c,
+                  const V4<double>& zp) {
+    V4<double> nb = cb;
+    if (t + 1 < s.ZC) nb = ldg4(b + cell_offset(s, t + 1));
+    const V4<double> ax = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
-    const V4<double> bv = ldg4(b + off);
+    const V4<double> bv = cb;
+    cb = nb;
     V4<float> rf;
     float d = 0.f;
 #pragma unroll
@@ -318,7 +399,7 @@ __global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, dou
     st4(r32 + off, rf);
     acc32 += (double)d;
   };
-  stream_slab<double, float, 2>(s, smem, bars, xin, x32, err, conv, body);
+  stream_slab<double, double, float, 2>(g, smem, bars, xin, x32, err, start, ingest, body);
   double v[2] = {acc64, acc32}, tot[2];
   if (grid_reduce_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double rr64 = tot[0], rr = tot[1];
@@ -419,18 +500,17 @@ __global__ void __launch_bounds__(256) k_apply64(const double* __restrict__ x, d
                                                  int* err, StreamGeo g) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
-  const Slab s = make_slab(g);
-  const StageLayout<double, double, 1> lay(s.rows, s.N);
-  auto conv = [&](int) {};
-  auto body = [&](int t, int sp, int scur, int sn) {
-    if (!s.active) return;
-    V4<double> c;
-    V4<double> ax = stencil4(lay.v0(smem, sp), lay.v0(smem, scur), lay.v0(smem, sn), s, c);
+  const StageLayout<double, double, 1> lay(g.rows, g.N);
+  auto start = [&](const Slab&) {};
+  auto ingest = [&](int st, size_t e) { return ld4(lay.v0(smem, st) + e); };
+  auto body = [&](const Slab& s, int t, const double* pb, const V4<double>& zm, const V4<double>& c,
+                  const V4<double>& zp) {
+    V4<double> ax = stencil_q(pb, s, zm, c, zp);
 #pragma unroll
     for (int i = 0; i < 4; ++i) ax.v[i] *= inv_h2;
     st4(y + cell_offset(s, t), ax);
   };
-  stream_slab<double, double, 1>(s, smem, bars, x, (const double*)nullptr, err, conv, body);
+  stream_slab<double, double, double, 1>(g, smem, bars, x, (const double*)nullptr, err, start, ingest, body);
 }
 
 }  // namespace pic

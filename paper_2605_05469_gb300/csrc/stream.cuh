@@ -1,7 +1,9 @@
 // Plane-streaming machinery for the periodic 7-point stencil (Sec. 3.2).
 //
-// A block owns a slab of TY full x-rows (TY the largest divisor of N with
-// N * TY <= 1024, so a slab plane is at most 1024 cells) and walks ZC consecutive z-planes. For every plane it
+// A slab is TY full x-rows (TY the largest divisor of N with N * TY <= 1024,
+// so a slab plane is at most 1024 cells). Persistent blocks each take an even
+// contiguous share of the (slab, plane) work list and walk its planes in z.
+// For every plane a block
 // needs the slab rows plus one halo row on each side (periodic in y); these
 // are contiguous runs in memory, so each plane arrives as one to three bulk
 // copies issued by one thread on the TMA engine into a ring of S
@@ -14,36 +16,40 @@
 namespace pic {
 
 struct StreamGeo {
-  int N;     // grid size
-  int TY;    // rows per slab
-  int ZC;    // planes per block
-  int rows;  // rows held per stage: TY + 2, or N when TY == N (halo by wrap)
-  int nyt;   // N / TY
-  int S;     // stages
-  int threads;  // N * TY / 4
-  int blocks;   // nyt * (N / ZC)
+  int N;        // grid size
+  int TY;       // rows per slab
+  int rows;     // rows held per stage: TY + 2, or N when TY == N (halo by wrap)
+  int nyt;      // N / TY slabs
+  int S;        // raw stages
+  int threads;  // N * TY / 4 threads that own cells
+  int blocks;   // persistent grid size
+  long total;   // nyt * N plane-tiles of work
 };
 
-inline StreamGeo make_stream_geo(int N, int S, int target_blocks) {
+// Slab height: the largest divisor of N with at most 1024 cells per slab plane.
+inline StreamGeo make_stream_geo(int N, int S) {
   StreamGeo g;
   g.N = N;
-  // largest divisor of N with at most 1024 cells per slab plane
   g.TY = 1;
   for (int d = 1; d <= N; ++d)
     if (N % d == 0 && N * d <= 1024) g.TY = d;
   g.rows = (g.TY == N) ? N : g.TY + 2;
   g.nyt = N / g.TY;
   g.threads = N * g.TY / 4;
-  // largest power-of-two chunk (<= 32 planes) that still gives target_blocks
-  int zc = 32;
-  while (zc > 2 && (N % zc != 0 || g.nyt * (N / zc) < target_blocks)) zc >>= 1;
-  g.ZC = zc;
-  g.blocks = g.nyt * (N / zc);
+  g.total = (long)g.nyt * N;
   g.S = S;
+  g.blocks = 1;
   return g;
 }
 
-// Per-block view of the slab being streamed.
+// Persistent grid: `slots` resident blocks, but at least 4 planes per block.
+inline void set_stream_blocks(StreamGeo& g, int slots) {
+  long b = g.total / 4;
+  if (b < 1) b = 1;
+  g.blocks = (int)(slots < b ? slots : b);
+}
+
+// One contiguous run of planes of one slab, handled by one block.
 struct Slab {
   int N, TY, ZC, rows, S;
   int j0, z0;       // first slab row, first output plane
@@ -53,12 +59,11 @@ struct Slab {
   bool active;      // thread owns cells (threadIdx.x < threads)
 };
 
-__device__ __forceinline__ Slab make_slab(const StreamGeo& g) {
+__device__ __forceinline__ Slab make_slab(const StreamGeo& g, int yt, int z0, int zc) {
   Slab s;
-  s.N = g.N; s.TY = g.TY; s.ZC = g.ZC; s.rows = g.rows; s.S = g.S;
-  const int yt = blockIdx.x % g.nyt, zc = blockIdx.x / g.nyt;
+  s.N = g.N; s.TY = g.TY; s.ZC = zc; s.rows = g.rows; s.S = g.S;
   s.j0 = yt * g.TY;
-  s.z0 = zc * g.ZC;
+  s.z0 = z0;
   const int c = threadIdx.x * 4;
   s.active = threadIdx.x < g.threads;
   s.ty = s.active ? c / g.N : 0;
@@ -73,6 +78,21 @@ __device__ __forceinline__ Slab make_slab(const StreamGeo& g) {
     s.rp = s.ty + 2;
   }
   return s;
+}
+
+// The block's share [b T / P, (b+1) T / P) of the plane-tiles in slab-major
+// order, visited as runs that stay inside one slab: calls f(yt, z0, zc).
+template <typename F>
+__device__ __forceinline__ void for_each_run(const StreamGeo& g, F f) {
+  long a = (long)blockIdx.x * g.total / gridDim.x;
+  const long e = (long)(blockIdx.x + 1) * g.total / gridDim.x;
+  while (a < e) {
+    const int yt = (int)(a / g.N), z0 = (int)(a % g.N);
+    long stop = (long)(yt + 1) * g.N;
+    if (stop > e) stop = e;
+    f(yt, z0, (int)(stop - a));
+    a = stop;
+  }
 }
 
 // Global plane index of load l (l = 0 is the plane before the first output).
