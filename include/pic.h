@@ -146,6 +146,57 @@ int64_t pic_num_particles(const pic_ctx *c);
  * FP64 device [N^3] arrays. */
 int pic_apply_laplacian(pic_ctx *c, const double *x, double *y);
 
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (used with PIC_PC_CNN inside flexible CG). The paper
+ * lists Jacobi, Richardson, Gauss-Seidel and SSOR preconditioners for its PCG
+ * solver (Sec. 3.2); this one is a 4-layer 3x3x3 conv3d network
+ * 1 -> 16 -> 16 -> 16 -> 1 channels, no biases, leaky ReLU (slope 1/8)
+ * between layers, periodic padding, BF16 weights and activations with FP32
+ * accumulation on the tensor cores. As a preconditioner it maps a residual r
+ * to z = s N(r / s), s = RMS(r).
+ *
+ * Weights (14 688 FP32 values) are the four layers concatenated, each in
+ * the order w[out][in][tz][ty][tx] with tap offset (tz-1, ty-1, tx-1):
+ * y[o, p] = sum_{c,t} w[o, c, t] x[c, p + t - 1].
+ * Training arrays are B cubic crops of D^3 cells (D % 16 == 0), FP32, x fastest.
+ * ------------------------------------------------------------------------ */
+#define PIC_CNN_WEIGHTS 14688
+
+/* Set the FP32 master weights from host memory (resets Adam). Synchronises. */
+int pic_cnn_set_weights(pic_ctx *c, const float *w_host);
+/* Copy the FP32 master weights / accumulated gradients to host memory. */
+int pic_cnn_get_weights(pic_ctx *c, float *w_host);
+int pic_cnn_get_grads(pic_ctx *c, float *g_host);
+
+/* Forward pass over B crops: y = N(x) (device FP32 [B][D^3] each); keeps the
+ * activations for pic_cnn_backward. */
+int pic_cnn_forward(pic_ctx *c, const float *x, float *y, int B, int D);
+/* Backward pass of the last forward: adds d(sum gy * y)/dw to the gradients
+ * (data gradients run as flipped-tap convolutions on the tensor cores,
+ * weight gradients on the CUDA cores in FP32). */
+int pic_cnn_backward(pic_ctx *c, const float *gy, int B, int D);
+/* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * accumulated gradients, which are then zeroed. */
+int pic_cnn_adam(pic_ctx *c, double lr);
+
+/* Training batch from CG snapshots on the context grid: B periodic crops of
+ * D^3 cells at host origins (3 ints per crop, x y z) of the residual field r
+ * and of the error e = a - b (a = converged solution, b = iterate), all device
+ * FP64 [N^3]. Writes x = r / s and t = e / (s h2) (s = RMS of the r crop) to
+ * device FP32 [B][D^3] buffers and keeps sum_interior t^2 per crop (interior
+ * = at least 4 cells from every face) for pic_cnn_loss. */
+int pic_cnn_make_batch(pic_ctx *c, const double *r, const double *a, const double *b, const int *origins_host,
+                       int B, int D, float *x, float *t, double h2);
+/* Loss mean_b sum_in (y - t)^2 / sum_in t^2 of the last batch to *loss_host,
+ * and its gradient with respect to y in gy (device FP32 [B][D^3]). */
+int pic_cnn_loss(pic_ctx *c, const float *y, const float *t, int B, int D, float *gy, double *loss_host);
+
+/* One convolution of the packed network without epilogue, for tests: which =
+ * 0..3 forward layers 1..4, 4..6 data-gradient convs of layers 4, 3, 2.
+ * Input: FP32 [B][D^3] for which 0 and 4, else BF16 [B][D^3][16]; output FP32
+ * [B][D^3][16] (accumulator as is). */
+int pic_cnn_conv_raw(pic_ctx *c, int which, const void *in, float *out, int B, int D);
+
 /* Profiling (tracing of device time, no effect on results). While enabled,
  * the library records CUDA events on the context stream around every public
  * call (per phase) and around a sample of the solver's kernel launches (the

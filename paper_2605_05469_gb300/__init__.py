@@ -32,6 +32,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PC_JACOBI = 0
 PC_CNN = 1
+CNN_WEIGHTS = 14688
 
 
 class PicError(RuntimeError):
@@ -99,6 +100,20 @@ _SIGS = {
     "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_profile_stats), ctypes.c_int]),
+    "pic_cnn_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_cnn_get_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_cnn_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_int]),
+    "pic_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "pic_cnn_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "pic_cnn_make_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_double]),
+    "pic_cnn_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pic_cnn_conv_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_int]),
 }
 
 
@@ -267,6 +282,60 @@ class Context:
 
     def apply_laplacian(self, x, y):
         pic_apply_laplacian(self.h, x, y, self.n)
+
+    # ---- learned preconditioner
+    def cnn_set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+        if w.size != CNN_WEIGHTS:
+            raise ValueError(f"expected {CNN_WEIGHTS} weights, got {w.size}")
+        _check(lib().pic_cnn_set_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_set_weights")
+
+    def cnn_get_weights(self):
+        w = np.empty(CNN_WEIGHTS, dtype=np.float32)
+        _check(lib().pic_cnn_get_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_get_weights")
+        return w
+
+    def cnn_get_grads(self):
+        g = np.empty(CNN_WEIGHTS, dtype=np.float32)
+        _check(lib().pic_cnn_get_grads(self.h, g.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_get_grads")
+        return g
+
+    def cnn_forward(self, x, y, B, D):
+        n = B * D ** 3
+        _check(lib().pic_cnn_forward(self.h, _dptr(x, "float32", n, "x"), _dptr(y, "float32", n, "y"), B, D),
+               "pic_cnn_forward")
+
+    def cnn_backward(self, gy, B, D):
+        _check(lib().pic_cnn_backward(self.h, _dptr(gy, "float32", B * D ** 3, "gy"), B, D), "pic_cnn_backward")
+
+    def cnn_adam(self, lr):
+        _check(lib().pic_cnn_adam(self.h, lr), "pic_cnn_adam")
+
+    def cnn_make_batch(self, r, a, b, origins, D, x, t, h2):
+        o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+        B = o.size // 3
+        n, m = self.n, B * D ** 3
+        _check(lib().pic_cnn_make_batch(self.h, _dptr(r, "float64", n, "r"), _dptr(a, "float64", n, "a"),
+                                        _dptr(b, "float64", n, "b"), o.ctypes.data_as(ctypes.c_void_p), B, D,
+                                        _dptr(x, "float32", m, "x"), _dptr(t, "float32", m, "t"), h2),
+               "pic_cnn_make_batch")
+
+    def cnn_loss(self, y, t, B, D, gy):
+        m = B * D ** 3
+        loss = ctypes.c_double()
+        _check(lib().pic_cnn_loss(self.h, _dptr(y, "float32", m, "y"), _dptr(t, "float32", m, "t"), B, D,
+                                  _dptr(gy, "float32", m, "gy"), ctypes.byref(loss)), "pic_cnn_loss")
+        return loss.value
+
+    def cnn_conv_raw(self, which, x, out, B, D):
+        import torch
+        m = B * D ** 3
+        if which in (0, 4):
+            px = _dptr(x, "float32", m, "x")
+        else:
+            px = _dptr(x, "bfloat16", 16 * m, "x")
+        _check(lib().pic_cnn_conv_raw(self.h, which, px, _dptr(out, "float32", 16 * m, "out"), B, D),
+               "pic_cnn_conv_raw")
 
     def profile(self, on=True):
         pic_profile_enable(self.h, on)

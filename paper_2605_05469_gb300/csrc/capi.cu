@@ -5,6 +5,8 @@
 
 #include <new>
 
+#include "cnn.h"
+#include "ctx.h"
 #include "particle_kernels.cuh"
 #include "solver_kernels.cuh"
 
@@ -14,127 +16,6 @@ namespace {
 
 constexpr size_t kSmemBudget32 = 72 * 1024;   // >= 3 blocks per SM
 constexpr size_t kSmemBudget64 = 110 * 1024;  // >= 2 blocks per SM
-
-struct SolverWs {
-  // FP64 judge
-  double *x = nullptr, *r = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
-  // mixed
-  double* xm[2] = {nullptr, nullptr};
-  float *x32 = nullptr, *r32 = nullptr, *p32[2] = {nullptr, nullptr};
-  // shared
-  double* b = nullptr;
-};
-
-}  // namespace
-
-// A pool of CUDA event pairs recorded on the context stream; flushed (elapsed
-// times summed) once the stream has passed them.
-struct EventPool {
-  static constexpr int kCap = 1024;
-  cudaEvent_t ev[kCap][2] = {};
-  int n = 0;         // pending pairs
-  int count = 0;     // flushed pairs
-  double ms = 0.0;   // flushed total
-  bool ready = false;
-  bool init() {
-    for (int i = 0; i < kCap; ++i)
-      for (int j = 0; j < 2; ++j)
-        if (cudaEventCreate(&ev[i][j]) != cudaSuccess) return false;
-    ready = true;
-    return true;
-  }
-  void destroy() {
-    for (int i = 0; i < kCap; ++i)
-      for (int j = 0; j < 2; ++j)
-        if (ev[i][j]) cudaEventDestroy(ev[i][j]);
-    ready = false;
-  }
-  void flush() {
-    for (int i = 0; i < n; ++i) {
-      float t = 0.f;
-      if (cudaEventSynchronize(ev[i][1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i][0], ev[i][1]) == cudaSuccess) {
-        ms += t;
-        ++count;
-      }
-    }
-    n = 0;
-  }
-  // Start a pair; returns its slot or -1 when profiling is off.
-  int begin(cudaStream_t st) {
-    if (!ready) return -1;
-    if (n == kCap) flush();
-    cudaEventRecord(ev[n][0], st);
-    return n++;
-  }
-  void end(int slot, cudaStream_t st) {
-    if (slot >= 0) cudaEventRecord(ev[slot][1], st);
-  }
-  void reset() { n = 0; count = 0; ms = 0.0; }
-};
-
-struct pic_ctx {
-  cudaStream_t stream = nullptr;
-  int device = 0, sms = 0;
-  // geometry
-  bool has_grid = false;
-  int N = 0;
-  size_t n = 0;
-  double L = 0, h = 0, alpha = 0, k = 0;
-  int ppc = 0;
-  uint64_t np = 0;
-  Grid grid{};
-  // particles
-  double* pb[2][6] = {};
-  uint32_t* ids[2] = {nullptr, nullptr};
-  int cur = 0;
-  uint32_t *keys = nullptr, *ranks = nullptr, *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
-  bool keys_valid = false, sorted = false, half_step = false;
-  double* E = nullptr;  // 3 n
-  // solver
-  SolverWs ws;
-  Scalars* sc = nullptr;
-  Scalars* sc_host = nullptr;  // pinned, 2 slots
-  double* partials = nullptr;
-  size_t partials_len = 0;
-  unsigned* counter = nullptr;
-  int* err = nullptr;
-  int* err_host = nullptr;   // pinned
-  double* out3 = nullptr;    // device, 3 doubles
-  double* out3_host = nullptr;  // pinned
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr, batch_ev[2] = {nullptr, nullptr};
-  // tracing
-  int64_t launches = 0;
-  bool prof_on = false;
-  EventPool* phase = nullptr;  // [PIC_NPHASE]
-  EventPool* ker = nullptr;    // [PIC_NKER]
-  int ker_prec[PIC_NKER] = {0, 0};
-};
-
-namespace {
-
-#define CK(call)                                  \
-  do {                                            \
-    cudaError_t e_ = (call);                      \
-    if (e_ != cudaSuccess) return PIC_ECUDA;      \
-  } while (0)
-
-template <typename T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) return PIC_OK;
-  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return PIC_ENOMEM;
-  }
-  return PIC_OK;
-}
-
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
-  p = nullptr;
-}
 
 void free_particles(pic_ctx* c) {
   for (int b = 0; b < 2; ++b) {
@@ -155,6 +36,7 @@ void free_solver(pic_ctx* c) {
   dfree(w.x); dfree(w.r); dfree(w.p[0]); dfree(w.p[1]); dfree(w.q);
   dfree(w.xm[0]); dfree(w.xm[1]);
   dfree(w.x32); dfree(w.r32); dfree(w.p32[0]); dfree(w.p32[1]);
+  dfree(w.z32[0]); dfree(w.z32[1]);
   dfree(w.b);
   dfree(c->partials);
   c->partials_len = 0;
@@ -167,27 +49,6 @@ ParticlePtrs pptrs(pic_ctx* c, int b) {
   P.id = c->ids[b];
   return P;
 }
-
-int round32(int t) { return ((t + 31) / 32) * 32; }
-
-// Every kernel goes through here: launched on the context stream and counted.
-template <typename... KArgs, typename... Args>
-void launch(pic_ctx* c, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, Args... args) {
-  kernel<<<grid, block, smem, c->stream>>>(args...);
-  ++c->launches;
-}
-
-// Phase timer around one public call (no-op unless profiling is on).
-struct PhaseScope {
-  pic_ctx* c;
-  int phase, slot;
-  PhaseScope(pic_ctx* cc, int ph) : c(cc), phase(ph), slot(-1) {
-    if (c->prof_on) slot = c->phase[phase].begin(c->stream);
-  }
-  ~PhaseScope() {
-    if (slot >= 0) c->phase[phase].end(slot, c->stream);
-  }
-};
 
 // Stage count from a shared-memory budget per block (raw TMA stages + 3 plane
 // buffers, at least 3 stages); persistent grid = resident blocks of `kernel`.
@@ -203,6 +64,8 @@ int geo_for(pic_ctx* c, K kernel, StreamGeo* out, size_t* smem) {
   g.S = S;
   *smem = stream_smem_bytes<TP, A, B, NV>(g.rows, g.N, S);
   CK(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+  CK(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                          (int)cudaSharedmemCarveoutMaxShared));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, round32(g.threads), *smem));
   if (per_sm < 1) return PIC_EINVAL;
@@ -394,8 +257,8 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
              c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
-      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, w.p32[cur ^ 1], c->sc, c->partials,
-             c->counter, c->err, gu);
+      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, w.p32[cur ^ 1], (const float*)nullptr,
+             c->sc, c->partials, c->counter, c->err, gu);
       if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
       launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                         c->counter, c->err, gr, 1);
@@ -417,6 +280,118 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   const size_t n4 = c->n / 4;
   launch(c, k_sum2, sb, 256, 0, w.xm[sel], nullptr, n4, c->sc, c->partials, c->counter);
   launch(c, k_finish, sb, 256, 0, w.xm[sel], phi, n4, 1.0 / (double)c->n, c->sc);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(c->ev1, c->stream));
+  CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  if ((e = sync_status(c))) return e;
+  if (c->prof_on) {
+    for (int kk = 0; kk < PIC_NKER; ++kk) {
+      c->ker[kk].flush();
+      c->ker_prec[kk] = PIC_PREC_MIXED;
+    }
+  }
+  const Scalars& s = c->sc_host[0];
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->iters = s.iter;
+    info->reliable_updates = s.updates;
+    info->fallbacks = s.fallbacks;
+    info->converged = s.done == 1;
+    info->rel_res = s.bb > 0.0 ? sqrt(s.true_rr / s.bb) : 0.0;
+    info->bnorm = sqrt(s.bb) / (c->h * c->h);
+    info->t_ms = ms;
+  }
+  if (s.done == 1) return PIC_OK;
+  if (s.done == 3) return PIC_EBREAKDOWN;
+  return PIC_ENOCONV;
+}
+
+// --------------------------------------------------------------------------
+// Flexible CG with the learned preconditioner, FP32 vectors with FP64
+// reductions and reliable updates (as the mixed path). One iteration:
+// pap (z -> p, alpha = (r,z)/(p,Ap)), update (+ (r, z_old)), reliable update
+// if due, network z_new = s N(r/s), (r, z_new) with descent guard and beta,
+// Jacobi fallback if the guard fired.
+// --------------------------------------------------------------------------
+int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta,
+                  pic_solve_info* info) {
+  SolverWs& w = c->ws;
+  int e;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  if (c->N % 16 != 0) return PIC_EINVAL;
+  if (!w.xm[0]) {
+    if ((e = dalloc(&w.xm[0], c->n)) || (e = dalloc(&w.xm[1], c->n)) || (e = dalloc(&w.x32, c->n)) ||
+        (e = dalloc(&w.r32, c->n)) || (e = dalloc(&w.p32[0], c->n)) || (e = dalloc(&w.p32[1], c->n)))
+      return e;
+  }
+  if (!w.z32[0] && ((e = dalloc(&w.z32[0], c->n)) || (e = dalloc(&w.z32[1], c->n)))) return e;
+  if (!w.b && (e = dalloc(&w.b, c->n))) return e;
+  size_t smem_pap, smem_upd, smem_rel;
+  StreamGeo gp, gu, gr;
+  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, false>, &gp, &smem_pap))) return e;
+  if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
+  if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
+  int mb = gp.blocks;
+  if (gu.blocks > mb) mb = gu.blocks;
+  if (gr.blocks > mb) mb = gr.blocks;
+  if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
+
+  CK(cudaEventRecord(c->ev0, c->stream));
+  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
+  c->sc_host[1] = c->sc_host[0];
+  c->sc_host[1].fcg = 1;
+  CK(cudaMemcpyAsync(&c->sc->fcg, &c->sc_host[1].fcg, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
+  CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
+  const int tp = round32(gp.threads), tu = round32(gu.threads), tr = round32(gr.threads);
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
+  launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b, w.r32,
+         c->sc, c->partials, c->counter, c->err, gr, 0);
+  int zc = 0;
+  if ((e = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n))) return e;
+  launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], n4, c->sc, c->partials, c->counter,
+         1);
+  launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
+  int cur = 0;
+  int inner_err = PIC_OK;
+  auto batch = [&]() {
+    for (int i = 0; i < m; ++i) {
+      const bool sample = c->prof_on && i == 0;
+      int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
+      launch(c, k_cg_pap<float, false>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
+             w.p32[cur ^ 1], (float*)nullptr, c->sc, c->partials, c->counter, c->err, gp);
+      if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
+      slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
+      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, (const float*)w.p32[cur ^ 1],
+             (const float*)w.z32[zc], c->sc, c->partials, c->counter, c->err, gu);
+      if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
+      launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
+             w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
+      zc ^= 1;
+      const int ce = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n);
+      if (ce && !inner_err) inner_err = ce;
+      launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], n4, c->sc, c->partials,
+             c->counter, 0);
+      launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
+      cur ^= 1;
+    }
+  };
+  if ((e = run_batches(c, m, maxit, batch))) return e;
+  if (inner_err) return inner_err;
+  CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+  if ((e = sync_status(c))) return e;
+  if (c->sc_host[0].done != 1 && c->sc_host[0].done != 3) {
+    launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
+           w.r32, c->sc, c->partials, c->counter, c->err, gr, 2);
+    CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
+    if ((e = sync_status(c))) return e;
+  }
+  const int sel = c->sc_host[0].xsel;
+  launch(c, k_sum2, sb, 256, 0, (const double*)w.xm[sel], (const double*)nullptr, n4, c->sc, c->partials,
+         c->counter);
+  launch(c, k_finish, sb, 256, 0, (const double*)w.xm[sel], phi, n4, 1.0 / (double)c->n, (const Scalars*)c->sc);
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev1, c->stream));
   CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
@@ -540,6 +515,7 @@ void pic_destroy(pic_ctx* c) {
     for (int i = 0; i < PIC_NKER; ++i) c->ker[i].destroy();
     delete[] c->ker;
   }
+  cnn_state_free(c->cnn);
   delete c;
 }
 
@@ -630,12 +606,14 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
   if (o) opts = *o;
   int m = opts.check_every > 0 ? opts.check_every : (c->N <= 64 ? 32 : 8);
-  if (opts.precond != PIC_PC_JACOBI) return PIC_EINVAL;
+  if (opts.precond != PIC_PC_JACOBI && opts.precond != PIC_PC_CNN) return PIC_EINVAL;
+  if (opts.precond == PIC_PC_CNN && opts.precision != PIC_PREC_MIXED) return PIC_EINVAL;
   PhaseScope ps(c, PIC_PHASE_SOLVE);
   if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);
   if (opts.precision == PIC_PREC_MIXED) {
     const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : 0.1;
     if (!(delta < 1.0)) return PIC_EINVAL;
+    if (opts.precond == PIC_PC_CNN) return solve_fcg_cnn(c, rho, phi, tol, maxit, m, delta, info);
     return solve_mixed(c, rho, phi, tol, maxit, m, delta, info);
   }
   return PIC_EINVAL;

@@ -1,0 +1,306 @@
+// Learned preconditioner: weights, training primitives and inference behind
+// the C ABI (include/pic.h). The network and its kernels are described in
+// cnn_kernels.cuh; this file owns the buffers and sequences the launches.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "cnn.h"
+#include "cnn_kernels.cuh"
+#include "ctx.h"
+
+namespace pic {
+
+struct CnnState {
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grads, Adam moments
+  unsigned char* packed = nullptr;                                // canonical BF16 tiles
+  bool has_weights = false;
+  int adam_t = 0;
+  // training: activations of the last forward (B x D^3 cells)
+  size_t train_cells = 0;
+  __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *ga = nullptr, *gb = nullptr;
+  const float* last_x = nullptr;
+  int last_B = 0, last_D = 0;
+  // inference ping-pong activations at N^3
+  size_t inf_cells = 0;
+  __nv_bfloat16 *i1 = nullptr, *i2 = nullptr;
+  // crops / loss scratch
+  int bmax = 0;
+  double* sums = nullptr;  // [4 * bmax]: ss, ee, den, num
+  int* origins = nullptr;  // [3 * bmax]
+  double* sums_host = nullptr;
+};
+
+}  // namespace pic
+
+using namespace pic;
+using namespace pic::cnn;
+
+namespace {
+
+int ensure_state(pic_ctx* c) {
+  if (c->cnn) return PIC_OK;
+  CnnState* s = new (std::nothrow) CnnState();
+  if (!s) return PIC_ENOMEM;
+  int e;
+  if ((e = dalloc(&s->w, kWeights)) || (e = dalloc(&s->g, kWeights)) || (e = dalloc(&s->m, kWeights)) ||
+      (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes))) {
+    cnn_state_free(s);
+    return e;
+  }
+  if (cudaMemset(s->g, 0, kWeights * 4) != cudaSuccess || cudaMemset(s->m, 0, kWeights * 4) != cudaSuccess ||
+      cudaMemset(s->v, 0, kWeights * 4) != cudaSuccess) {
+    cnn_state_free(s);
+    return PIC_ECUDA;
+  }
+  c->cnn = s;
+  return PIC_OK;
+}
+
+int ensure_train(pic_ctx* c, size_t cells) {
+  CnnState* s = c->cnn;
+  if (s->train_cells >= cells) return PIC_OK;
+  dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
+  s->train_cells = 0;
+  int e;
+  if ((e = dalloc(&s->a1, 16 * cells)) || (e = dalloc(&s->a2, 16 * cells)) || (e = dalloc(&s->a3, 16 * cells)) ||
+      (e = dalloc(&s->ga, 16 * cells)) || (e = dalloc(&s->gb, 16 * cells)))
+    return e;
+  s->train_cells = cells;
+  return PIC_OK;
+}
+
+int ensure_batch(pic_ctx* c, int B) {
+  CnnState* s = c->cnn;
+  if (s->bmax >= B) return PIC_OK;
+  dfree(s->sums); dfree(s->origins);
+  if (s->sums_host) cudaFreeHost(s->sums_host);
+  s->sums_host = nullptr;
+  s->bmax = 0;
+  int e;
+  if ((e = dalloc(&s->sums, 4 * (size_t)B)) || (e = dalloc(&s->origins, 3 * (size_t)B))) return e;
+  if (cudaMallocHost(&s->sums_host, 4 * (size_t)B * sizeof(double)) != cudaSuccess) return PIC_ENOMEM;
+  s->bmax = B;
+  return PIC_OK;
+}
+
+bool dims_ok(int NX, int NY, int NZ) {
+  return NX >= TX && NY >= TY && NZ >= ZT && NX % TX == 0 && NY % TY == 0 && NZ % ZT == 0;
+}
+
+template <int CIN>
+int conv(pic_ctx* c, const void* in, void* out, const unsigned char* w, int mode, int NX, int NY, int NZ, int B,
+         const __nv_bfloat16* gate = nullptr, const double* in_src = nullptr, double in_mul = 0.0,
+         int in_mode = SCALE_ONE, const double* out_src = nullptr, double out_mul = 0.0, int out_mode = SCALE_ONE) {
+  static bool configured = false;
+  const size_t smem = conv_smem_bytes<CIN>();
+  if (!configured) {
+    CK(cudaFuncSetAttribute((const void*)k_conv_tc<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  ConvParams P;
+  P.NX = NX; P.NY = NY; P.NZ = NZ; P.B = B;
+  P.in = in; P.out = out; P.gate = gate; P.w = w;
+  P.in_scale_src = in_src; P.in_scale_mul = in_mul; P.in_scale_mode = in_mode;
+  P.out_scale_src = out_src; P.out_scale_mul = out_mul; P.out_scale_mode = out_mode;
+  P.err = c->err;
+  const long tiles = (long)(NX / TX) * (NY / TY) * (NZ / ZT) * B;
+  launch(c, k_conv_tc<CIN>, (unsigned)tiles, kThreads, smem, P, mode);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+template <int CIN, int COUT>
+int wgrad(pic_ctx* c, const void* gz, const void* a, int D, int B, float* dW) {
+  const long tiles = (long)(D / TX) * (D / TY) * (D / ZT) * B;
+  launch(c, k_wgrad<CIN, COUT>, (unsigned)tiles, 256, 0, gz, a, D, D, D, dW);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int repack(pic_ctx* c) {
+  launch(c, k_pack_weights, 32, 256, 0, (const float*)c->cnn->w, c->cnn->packed);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+}  // namespace
+
+namespace pic {
+
+void cnn_state_free(CnnState* s) {
+  if (!s) return;
+  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed);
+  dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
+  dfree(s->i1); dfree(s->i2);
+  dfree(s->sums); dfree(s->origins);
+  if (s->sums_host) cudaFreeHost(s->sums_host);
+  delete s;
+}
+
+bool cnn_ready(const pic_ctx* c) { return c->cnn && c->cnn->has_weights; }
+
+int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) {
+  CnnState* s = c->cnn;
+  const int N = c->N;
+  if (!dims_ok(N, N, N)) return PIC_EINVAL;
+  if (s->inf_cells < n) {
+    dfree(s->i1); dfree(s->i2);
+    s->inf_cells = 0;
+    int e;
+    if ((e = dalloc(&s->i1, 16 * n)) || (e = dalloc(&s->i2, 16 * n))) return e;
+    s->inf_cells = n;
+  }
+  const double inv_n = 1.0 / (double)n;
+  int e;
+  // z = s N(r / s), s = RMS(r) = sqrt(rr / n)
+  if ((e = conv<1>(c, r, s->i1, s->packed + kPackFwd1, OUT_ACT_BF16, N, N, N, 1, nullptr, rr, inv_n, SCALE_RSQRT)))
+    return e;
+  if ((e = conv<16>(c, s->i1, s->i2, s->packed + kPackFwd2, OUT_ACT_BF16, N, N, N, 1))) return e;
+  if ((e = conv<16>(c, s->i2, s->i1, s->packed + kPackFwd3, OUT_ACT_BF16, N, N, N, 1))) return e;
+  return conv<16>(c, s->i1, z, s->packed + kPackFwd4, OUT_SCALED_F32, N, N, N, 1, nullptr, nullptr, 0.0,
+                  SCALE_ONE, rr, inv_n, SCALE_SQRT);
+}
+
+}  // namespace pic
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+int pic_cnn_set_weights(pic_ctx* c, const float* w_host) {
+  if (!c || !w_host) return PIC_EINVAL;
+  int e;
+  if ((e = ensure_state(c))) return e;
+  CK(cudaMemcpyAsync(c->cnn->w, w_host, kWeights * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->cnn->g, 0, kWeights * 4, c->stream));
+  CK(cudaMemsetAsync(c->cnn->m, 0, kWeights * 4, c->stream));
+  CK(cudaMemsetAsync(c->cnn->v, 0, kWeights * 4, c->stream));
+  c->cnn->adam_t = 0;
+  if ((e = repack(c))) return e;
+  CK(cudaStreamSynchronize(c->stream));
+  c->cnn->has_weights = true;
+  return PIC_OK;
+}
+
+int pic_cnn_get_weights(pic_ctx* c, float* w_host) {
+  if (!c || !w_host) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CK(cudaMemcpyAsync(w_host, c->cnn->w, kWeights * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+int pic_cnn_get_grads(pic_ctx* c, float* g_host) {
+  if (!c || !g_host) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CK(cudaMemcpyAsync(g_host, c->cnn->g, kWeights * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+int pic_cnn_conv_raw(pic_ctx* c, int which, const void* in, float* out, int B, int D) {
+  if (!c || !in || !out || B < 1 || which < 0 || which > 6) return PIC_EINVAL;
+  if (!dims_ok(D, D, D)) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  static const int offs[7] = {kPackFwd1, kPackFwd2, kPackFwd3, kPackFwd4, kPackBwd4, kPackBwd3, kPackBwd2};
+  const unsigned char* w = c->cnn->packed + offs[which];
+  if (which == 0 || which == 4) return conv<1>(c, in, out, w, OUT_RAW_F32, D, D, D, B);
+  return conv<16>(c, in, out, w, OUT_RAW_F32, D, D, D, B);
+}
+
+int pic_cnn_forward(pic_ctx* c, const float* x, float* y, int B, int D) {
+  if (!c || !x || !y || B < 1) return PIC_EINVAL;
+  if (!dims_ok(D, D, D)) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  const size_t cells = (size_t)B * D * D * D;
+  int e;
+  if ((e = ensure_train(c, cells))) return e;
+  if ((e = conv<1>(c, x, s->a1, s->packed + kPackFwd1, OUT_ACT_BF16, D, D, D, B))) return e;
+  if ((e = conv<16>(c, s->a1, s->a2, s->packed + kPackFwd2, OUT_ACT_BF16, D, D, D, B))) return e;
+  if ((e = conv<16>(c, s->a2, s->a3, s->packed + kPackFwd3, OUT_ACT_BF16, D, D, D, B))) return e;
+  if ((e = conv<16>(c, s->a3, y, s->packed + kPackFwd4, OUT_SCALED_F32, D, D, D, B))) return e;
+  s->last_x = x;
+  s->last_B = B;
+  s->last_D = D;
+  return PIC_OK;
+}
+
+int pic_cnn_backward(pic_ctx* c, const float* gy, int B, int D) {
+  if (!c || !gy) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  if (B != s->last_B || D != s->last_D || !s->last_x) return PIC_ESTATE;
+  float* g4 = s->g + kLayerOff[3];
+  float* g3 = s->g + kLayerOff[2];
+  float* g2 = s->g + kLayerOff[1];
+  float* g1 = s->g + kLayerOff[0];
+  int e;
+  // layer 4: dW4 from (gy, a3); gradient to a3 gated by act'(z3)
+  if ((e = wgrad<16, 1>(c, gy, s->a3, D, B, g4))) return e;
+  if ((e = conv<1>(c, gy, s->ga, s->packed + kPackBwd4, OUT_GATED_BF16, D, D, D, B, s->a3))) return e;
+  // layer 3
+  if ((e = wgrad<16, 16>(c, s->ga, s->a2, D, B, g3))) return e;
+  if ((e = conv<16>(c, s->ga, s->gb, s->packed + kPackBwd3, OUT_GATED_BF16, D, D, D, B, s->a2))) return e;
+  // layer 2
+  if ((e = wgrad<16, 16>(c, s->gb, s->a1, D, B, g2))) return e;
+  if ((e = conv<16>(c, s->gb, s->ga, s->packed + kPackBwd2, OUT_GATED_BF16, D, D, D, B, s->a1))) return e;
+  // layer 1
+  return wgrad<1, 16>(c, s->ga, s->last_x, D, B, g1);
+}
+
+int pic_cnn_make_batch(pic_ctx* c, const double* r, const double* a, const double* b, const int* origins_host,
+                       int B, int D, float* x, float* t, double h2) {
+  if (!c || !r || !a || !b || !origins_host || !x || !t || B < 1 || D < 16) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  int e;
+  if ((e = ensure_state(c)) || (e = ensure_batch(c, B))) return e;
+  for (int i = 0; i < 3 * B; ++i)
+    if (origins_host[i] < 0 || origins_host[i] >= c->N) return PIC_EINVAL;
+  CnnState* s = c->cnn;
+  CK(cudaMemcpyAsync(s->origins, origins_host, 3 * (size_t)B * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));  // origins_host may be reused by the caller
+  CK(cudaMemsetAsync(s->sums, 0, 4 * (size_t)B * sizeof(double), c->stream));
+  dim3 grid(64, B);
+  // e = a - b: the crop kernel reads the error as the difference of two fields
+  k_crops_gather_diff<<<grid, 256, 0, c->stream>>>(r, a, b, c->N, s->origins, D, 4, x, t, s->sums, s->sums + B);
+  ++c->launches;
+  k_crops_scale<<<grid, 256, 0, c->stream>>>(x, t, D, h2, s->sums, s->sums + B, s->sums + 2 * B);
+  ++c->launches;
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int pic_cnn_loss(pic_ctx* c, const float* y, const float* t, int B, int D, float* gy, double* loss_host) {
+  if (!c || !y || !t || !gy || !loss_host || B < 1) return PIC_EINVAL;
+  if (!c->cnn || c->cnn->bmax < B) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  CK(cudaMemsetAsync(s->sums + 3 * B, 0, (size_t)B * sizeof(double), c->stream));
+  dim3 grid(64, B);
+  k_loss<<<grid, 256, 0, c->stream>>>(y, t, s->sums + 2 * B, D, B, 4, gy, s->sums + 3 * B);
+  ++c->launches;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(s->sums_host, s->sums, 4 * (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double L = 0.0;
+  for (int b = 0; b < B; ++b) L += s->sums_host[3 * B + b] / s->sums_host[2 * B + b];
+  *loss_host = L / B;
+  return PIC_OK;
+}
+
+int pic_cnn_adam(pic_ctx* c, double lr) {
+  if (!c || !(lr > 0.0)) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  s->adam_t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  launch(c, k_adam, 58, 256, 0, s->w, s->g, s->m, s->v, kWeights, (float)lr, (float)b1, (float)b2, 1e-8f,
+         (float)(1.0 - pow(b1, s->adam_t)), (float)(1.0 - pow(b2, s->adam_t)));
+  CK(cudaGetLastError());
+  return repack(c);
+}
+
+}  // extern "C"

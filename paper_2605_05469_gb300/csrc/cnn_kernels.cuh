@@ -1,0 +1,472 @@
+// Kernels of the learned preconditioner: a 4-layer 3x3x3 conv3d network
+// (1 -> 16 -> 16 -> 16 -> 1 channels, no biases, leaky ReLU with slope 1/8)
+// applied with periodic wrap, its training (dgrad, wgrad, loss, Adam) and
+// crop extraction. The paper solves the Poisson system with preconditioned CG
+// (Sec. 3.2); this learned preconditioner is used inside flexible CG.
+//
+// Convolutions run on the 5th-generation tensor cores as implicit GEMMs:
+// one CTA owns an 8 (x) x 16 (y) x 4 (z) output tile; M = 128 output cells of
+// one z-plane, N = 16 output channels, K = 16 input channels per tap, 27 taps
+// accumulated into one FP32 TMEM accumulator per plane (4 planes = 64 TMEM
+// columns). Activations are BF16 channels-last; the CTA stores its halo tile
+// (10 x 18 x 6 cells) as two 8-channel planes so that each tap's A operand is
+// the tile shifted by a constant: a no-swizzle K-major shared-memory
+// descriptor with start = cell (tz, ty, tx) of the tile, SBO = one tile row
+// (10 cells x 16 B, the next 8 output cells in y) and LBO = the 8-channel
+// plane stride. One thread issues the 27 x 4 tcgen05.mma; tcgen05.commit
+// signals an mbarrier; the 4 warps read their 32 TMEM lanes back with
+// tcgen05.ld and apply the epilogue. One-channel inputs (the first layer and
+// the last layer's data gradient) use an im2col A tile (27 taps padded to
+// K = 32, two MMAs per plane).
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace pic {
+namespace cnn {
+
+constexpr int kLayers = 4;
+constexpr int kWeights = 14688;  // 16*27 + 16*16*27 + 16*16*27 + 16*27
+constexpr int kLayerOff[5] = {0, 432, 7344, 14256, 14688};
+constexpr float kLeak = 0.125f;
+
+// Output tile and halo tile of one CTA.
+constexpr int TX = 8, TY = 16, ZT = 4;
+constexpr int HX = TX + 2, HY = TY + 2, HZ = ZT + 2;
+constexpr int HCELLS = HX * HY * HZ;  // 1080
+constexpr int CHUNK = HCELLS * 16;    // bytes of one 8-channel BF16 plane: 17280
+constexpr int W16_BYTES = 27 * 512;   // 27 taps x (16 x 16 BF16) canonical
+constexpr int W1_BYTES = 1024;        // 16 x 32 BF16 canonical (im2col K)
+constexpr int IM2COL_PLANE = 8192;    // 128 rows x 32 K BF16
+constexpr int kThreads = 128;
+
+// Epilogue modes.
+enum : int {
+  OUT_ACT_BF16 = 0,    // bf16 x16 = leaky_relu(acc)
+  OUT_GATED_BF16 = 1,  // bf16 x16 = acc * (gate > 0 ? 1 : 1/8), gate = forward activation
+  OUT_SCALED_F32 = 2,  // f32 x1  = scale * acc[channel 0]
+  OUT_RAW_F32 = 3,     // f32 x16 = acc (tests)
+};
+
+// Per-launch scale taken from a device scalar: 1, 1/sqrt(*src * mul), or sqrt(*src * mul).
+enum : int { SCALE_ONE = 0, SCALE_RSQRT = 1, SCALE_SQRT = 2 };
+
+__device__ __forceinline__ float scale_from(const double* src, double mul, int mode) {
+  if (mode == SCALE_ONE || src == nullptr) return 1.f;
+  const double v = *src * mul;
+  if (!(v > 0.0)) return 0.f;
+  return mode == SCALE_RSQRT ? (float)(1.0 / sqrt(v)) : (float)sqrt(v);
+}
+
+struct ConvParams {
+  int NX, NY, NZ, B;       // per-sample grid (periodic) and batch
+  const void* in;          // CIN 16: bf16 [cells][16]; CIN 1: f32 [cells]
+  void* out;
+  const __nv_bfloat16* gate;  // OUT_GATED_BF16: forward activation [cells][16]
+  const unsigned char* w;     // canonical BF16 weights of this conv
+  const double* in_scale_src;  // CIN 1 input multiplier (see scale_from)
+  double in_scale_mul;
+  int in_scale_mode;
+  const double* out_scale_src;  // OUT_SCALED_F32 multiplier
+  double out_scale_mul;
+  int out_scale_mode;
+  int* err;
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+  return d;                // base offset 0, no swizzle
+}
+
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, N = 16, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Canonical K-major no-swizzle byte offset of element (row, k) of a matrix
+// whose core matrices are (row/8, k/8) at (row/8) * 128 + (k/8) * lbo.
+__device__ __forceinline__ int canon_off(int row, int k, int lbo) {
+  return (row >> 3) * 128 + (k >> 3) * lbo + (row & 7) * 16 + (k & 7) * 2;
+}
+
+template <int CIN>
+__global__ void __launch_bounds__(kThreads) k_conv_tc(ConvParams P, int mode) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t mma_bar;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = P.NX / TX, tiles_y = P.NY / TY, tiles_z = P.NZ / ZT;
+  int t = blockIdx.x;
+  const int bx = t % tiles_x; t /= tiles_x;
+  const int by = t % tiles_y; t /= tiles_y;
+  const int bz = t % tiles_z; t /= tiles_z;
+  const int b = t;
+  const int x0 = bx * TX, y0 = by * TY, z0 = bz * ZT;
+  const size_t sample = (size_t)P.NX * P.NY * P.NZ;
+  const size_t sbase = (size_t)b * sample;
+
+  constexpr int A_BYTES = CIN == 16 ? 2 * CHUNK : ZT * IM2COL_PLANE;
+  constexpr int W_BYTES = CIN == 16 ? W16_BYTES : W1_BYTES;
+  unsigned char* sA = smem;
+  unsigned char* sW = smem + A_BYTES;
+  float* sF = reinterpret_cast<float*>(smem + A_BYTES + W_BYTES);  // CIN 1: f32 halo tile
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&mma_bar, 1);
+    fence_mbar_init();
+  }
+  // weights
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(P.w);
+    uint4* dst = reinterpret_cast<uint4*>(sW);
+    for (int i = tid; i < W_BYTES / 16; i += kThreads) dst[i] = __ldg(src + i);
+  }
+  if (CIN == 16) {
+    const uint4* in = reinterpret_cast<const uint4*>(P.in);
+    for (int c = tid; c < HCELLS; c += kThreads) {
+      const int hx = c % HX, hy = (c / HX) % HY, hz = c / (HX * HY);
+      const int gx = wrap(x0 - 1 + hx, P.NX), gy = wrap(y0 - 1 + hy, P.NY), gz = wrap(z0 - 1 + hz, P.NZ);
+      const size_t cell = sbase + ((size_t)gz * P.NY + gy) * P.NX + gx;
+      const uint4 lo = __ldg(in + 2 * cell), hi = __ldg(in + 2 * cell + 1);
+      reinterpret_cast<uint4*>(sA)[c] = lo;
+      reinterpret_cast<uint4*>(sA + CHUNK)[c] = hi;
+    }
+  } else {
+    const float* in = reinterpret_cast<const float*>(P.in);
+    const float sc = scale_from(P.in_scale_src, P.in_scale_mul, P.in_scale_mode);
+    for (int c = tid; c < HCELLS; c += kThreads) {
+      const int hx = c % HX, hy = (c / HX) % HY, hz = c / (HX * HY);
+      const int gx = wrap(x0 - 1 + hx, P.NX), gy = wrap(y0 - 1 + hy, P.NY), gz = wrap(z0 - 1 + hz, P.NZ);
+      sF[c] = sc * __ldg(in + sbase + ((size_t)gz * P.NY + gy) * P.NX + gx);
+    }
+    __syncthreads();
+    // im2col: row m = ly * 8 + lx, k = tz * 9 + ty * 3 + tx (k >= 27 zero)
+    const int m = tid, lx = m & 7, ly = m >> 3;
+    for (int zt = 0; zt < ZT; ++zt) {
+      unsigned char* plane = sA + zt * IM2COL_PLANE;
+      for (int k = 0; k < 32; ++k) {
+        float v = 0.f;
+        if (k < 27) {
+          const int tz = k / 9, ty = (k / 3) % 3, tx = k % 3;
+          v = sF[((zt + tz) * HY + (ly + ty)) * HX + (lx + tx)];
+        }
+        *reinterpret_cast<__nv_bfloat16*>(plane + canon_off(m, k, 2048)) = __float2bfloat16_rn(v);
+      }
+    }
+  }
+  // make the generic-proxy shared-memory writes visible to the tensor cores
+  fence_proxy_async_smem();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (tid == 0) {
+    const uint32_t a0 = smem_u32(sA), w0 = smem_u32(sW);
+    for (int zt = 0; zt < ZT; ++zt) {
+      const uint32_t d = tmem + (uint32_t)(zt * 16);
+      if (CIN == 16) {
+        for (int tap = 0; tap < 27; ++tap) {
+          const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
+          const uint32_t a = a0 + (uint32_t)((((zt + tz) * HY + ty) * HX + tx) * 16);
+          mma_bf16(d, smem_desc(a, CHUNK, HX * 16), smem_desc(w0 + tap * 512, 256, 128), tap > 0);
+        }
+      } else {
+        for (int q = 0; q < 2; ++q) {
+          const uint32_t a = a0 + (uint32_t)(zt * IM2COL_PLANE + q * 2 * 2048);
+          mma_bf16(d, smem_desc(a, 2048, 128), smem_desc(w0 + q * 2 * 256, 256, 128), q > 0);
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&mma_bar))
+                 : "memory");
+  }
+  const bool done = mbar_wait_bounded(&mma_bar, 0, P.err);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done) {
+    const int m = warp * 32 + lane, lx = m & 7, ly = m >> 3;
+    const float osc = mode == OUT_SCALED_F32 ? scale_from(P.out_scale_src, P.out_scale_mul, P.out_scale_mode) : 1.f;
+    for (int zt = 0; zt < ZT; ++zt) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zt * 16), v);
+      const size_t cell = sbase + ((size_t)(z0 + zt) * P.NY + (y0 + ly)) * P.NX + (x0 + lx);
+      if (mode == OUT_ACT_BF16 || mode == OUT_GATED_BF16) {
+        float g[16];
+        if (mode == OUT_GATED_BF16) {
+          const uint4* gp = reinterpret_cast<const uint4*>(P.gate) + 2 * cell;
+          uint4 q[2] = {__ldg(gp), __ldg(gp + 1)};
+          const __nv_bfloat16* gb = reinterpret_cast<const __nv_bfloat16*>(q);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) g[i] = __bfloat162float(gb[i]) > 0.f ? 1.f : kLeak;
+        }
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float y = mode == OUT_ACT_BF16 ? (v[i] > 0.f ? v[i] : kLeak * v[i]) : v[i] * g[i];
+          o[i] = __float2bfloat16_rn(y);
+        }
+        uint4* op = reinterpret_cast<uint4*>(P.out) + 2 * cell;
+        op[0] = reinterpret_cast<const uint4*>(o)[0];
+        op[1] = reinterpret_cast<const uint4*>(o)[1];
+      } else if (mode == OUT_SCALED_F32) {
+        reinterpret_cast<float*>(P.out)[cell] = osc * v[0];
+      } else {
+        float4* op = reinterpret_cast<float4*>(P.out) + 4 * cell;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) op[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+}
+
+template <int CIN>
+constexpr size_t conv_smem_bytes() {
+  return CIN == 16 ? (size_t)2 * CHUNK + W16_BYTES : (size_t)ZT * IM2COL_PLANE + W1_BYTES + HCELLS * 4;
+}
+
+// ---------------------------------------------------------------------------
+// Weight packing: FP32 master weights (oracle layout w[o][c][tz][ty][tx] per
+// layer, concatenated) -> canonical BF16 tiles for the forward convs and for
+// the data-gradient convs (flipped taps, in/out channels swapped).
+// Layout of `packed`: fwd1 (1 KB) | fwd2, fwd3, fwd4 (13.5 KB each) |
+//                     bwd4 (1 KB) | bwd3, bwd2 (13.5 KB each)
+// ---------------------------------------------------------------------------
+constexpr int kPackFwd1 = 0;
+constexpr int kPackFwd2 = kPackFwd1 + W1_BYTES;
+constexpr int kPackFwd3 = kPackFwd2 + W16_BYTES;
+constexpr int kPackFwd4 = kPackFwd3 + W16_BYTES;
+constexpr int kPackBwd4 = kPackFwd4 + W16_BYTES;
+constexpr int kPackBwd3 = kPackBwd4 + W1_BYTES;
+constexpr int kPackBwd2 = kPackBwd3 + W16_BYTES;
+constexpr int kPackBytes = kPackBwd2 + W16_BYTES;
+
+__device__ __forceinline__ void put(unsigned char* base, int off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+__global__ void k_pack_weights(const float* __restrict__ w, unsigned char* __restrict__ packed) {
+  const float* w1 = w + kLayerOff[0];
+  const float* w2 = w + kLayerOff[1];
+  const float* w3 = w + kLayerOff[2];
+  const float* w4 = w + kLayerOff[3];
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16 * 32; i += stride) {
+    const int n = i / 32, k = i % 32;
+    // fwd1: B[n = out][k = tap]
+    put(packed + kPackFwd1, canon_off(n, k, 256), k < 27 ? w1[n * 27 + k] : 0.f);
+    // bwd4: B[n = c (input channel of layer 4)][k = flipped tap]
+    put(packed + kPackBwd4, canon_off(n, k, 256), k < 27 ? w4[n * 27 + (26 - k)] : 0.f);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * 256; i += stride) {
+    const int tap = i / 256, n = (i / 16) % 16, k = i % 16;
+    const int off = tap * 512 + canon_off(n, k, 256);
+    // forward: B_tap[n = out][k = in] = w[o = n][c = k][tap]
+    put(packed + kPackFwd2, off, w2[(n * 16 + k) * 27 + tap]);
+    put(packed + kPackFwd3, off, w3[(n * 16 + k) * 27 + tap]);
+    put(packed + kPackFwd4, off, n == 0 ? w4[k * 27 + tap] : 0.f);
+    // data gradient: B_tap'[n = c][k = o] = w[o = k][c = n][26 - tap']
+    put(packed + kPackBwd3, off, w3[(k * 16 + n) * 27 + (26 - tap)]);
+    put(packed + kPackBwd2, off, w2[(k * 16 + n) * 27 + (26 - tap)]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on CUDA cores, FP32:
+//   dW[o][c][tap] += sum_cells gz[cell][o] * a[cell + tap - 1][c]
+// gz: COUT channels (f32 if COUT == 1 else bf16 x16); a: CIN channels (f32 if
+// CIN == 1 else bf16 x16). One CTA per 8 x 16 x 4 tile; 4 x 4 register blocks.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_wgrad(const void* __restrict__ gz_, const void* __restrict__ a_, int NX,
+                                               int NY, int NZ, float* __restrict__ dW) {
+  constexpr int CP = CIN < 4 ? 4 : CIN, OP = COUT < 4 ? 4 : COUT;
+  __shared__ __align__(16) float sa[HCELLS * CP];
+  __shared__ __align__(16) float sg[TX * TY * ZT * OP];
+  const int tiles_x = NX / TX, tiles_y = NY / TY, tiles_z = NZ / ZT;
+  int t = blockIdx.x;
+  const int bx = t % tiles_x; t /= tiles_x;
+  const int by = t % tiles_y; t /= tiles_y;
+  const int bz = t % tiles_z; t /= tiles_z;
+  const int b = t;
+  const int x0 = bx * TX, y0 = by * TY, z0 = bz * ZT;
+  const size_t sbase = (size_t)b * NX * NY * NZ;
+  for (int c = threadIdx.x; c < HCELLS; c += blockDim.x) {
+    const int hx = c % HX, hy = (c / HX) % HY, hz = c / (HX * HY);
+    const size_t cell = sbase + ((size_t)wrap(z0 - 1 + hz, NZ) * NY + wrap(y0 - 1 + hy, NY)) * NX + wrap(x0 - 1 + hx, NX);
+    if (CIN == 1) {
+      sa[c * CP] = reinterpret_cast<const float*>(a_)[cell];
+      sa[c * CP + 1] = sa[c * CP + 2] = sa[c * CP + 3] = 0.f;
+    } else {
+      const __nv_bfloat16* ap = reinterpret_cast<const __nv_bfloat16*>(a_) + 16 * cell;
+      for (int i = 0; i < 16; ++i) sa[c * CP + i] = __bfloat162float(ap[i]);
+    }
+  }
+  for (int c = threadIdx.x; c < TX * TY * ZT; c += blockDim.x) {
+    const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+    const size_t cell = sbase + ((size_t)(z0 + lz) * NY + (y0 + ly)) * NX + (x0 + lx);
+    if (COUT == 1) {
+      sg[c * OP] = reinterpret_cast<const float*>(gz_)[cell];
+      sg[c * OP + 1] = sg[c * OP + 2] = sg[c * OP + 3] = 0.f;
+    } else {
+      const __nv_bfloat16* gp = reinterpret_cast<const __nv_bfloat16*>(gz_) + 16 * cell;
+      for (int i = 0; i < 16; ++i) sg[c * OP + i] = __bfloat162float(gp[i]);
+    }
+  }
+  __syncthreads();
+  constexpr int NOB = OP / 4, NCB = CP / 4, ITEMS = 27 * NOB * NCB;
+  for (int it = threadIdx.x; it < ITEMS; it += blockDim.x) {
+    const int tap = it / (NOB * NCB), ob = (it / NCB) % NOB, cb = it % NCB;
+    const int tz = tap / 9, ty = (tap / 3) % 3, tx = tap % 3;
+    float acc[4][4] = {};
+    for (int c = 0; c < TX * TY * ZT; ++c) {
+      const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+      const float4 g = *reinterpret_cast<const float4*>(&sg[c * OP + ob * 4]);
+      const int hc = ((lz + tz) * HY + (ly + ty)) * HX + (lx + tx);
+      const float4 a = *reinterpret_cast<const float4*>(&sa[hc * CP + cb * 4]);
+      const float gv[4] = {g.x, g.y, g.z, g.w}, av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(gv[i], av[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int o = ob * 4 + i;
+      if (o >= COUT) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = cb * 4 + j;
+        if (cc >= CIN) continue;
+        atomicAdd(&dW[(o * CIN + cc) * 27 + tap], acc[i][j]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Relative interior loss per crop: num[b] += sum_in (y - t)^2; gy = 2 (y - t) /
+// (den[b] B) inside, 0 outside (den[b] = sum_in t^2, computed with the crops).
+// ---------------------------------------------------------------------------
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ tgt, const double* __restrict__ den,
+                       int D, int B, int border, float* __restrict__ gy, double* num) {
+  const size_t per = (size_t)D * D * D;
+  const int b = blockIdx.y;
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), yy = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
+    const bool in = x >= border && x < D - border && yy >= border && yy < D - border && z >= border &&
+                    z < D - border;
+    const size_t j = (size_t)b * per + i;
+    float g = 0.f;
+    if (in) {
+      const float d = y[j] - tgt[j];
+      acc += (double)d * d;
+      g = (float)(2.0 * d / (den[b] * B));
+    }
+    gy[j] = g;
+  }
+  __shared__ double red[32];
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) atomicAdd(&num[b], s);
+}
+
+// ---------------------------------------------------------------------------
+// Crops at periodic origins, in FP32, of a residual field r and an error
+// e = a - b (a = converged solution, b = CG iterate): pass 1 gathers and
+// accumulates ss[b] = sum r^2 (whole crop) and ee[b] = sum_in e^2 (interior,
+// border 4); pass 2 scales x = r / s, t = e / (s h2) with s = RMS(r crop) and
+// sets den[b] = ee[b] / (s^2 h2^2) = sum_in t^2.
+// ---------------------------------------------------------------------------
+__global__ void k_crops_gather_diff(const double* __restrict__ fr, const double* __restrict__ fa,
+                                    const double* __restrict__ fb, int N, const int* __restrict__ origins, int D,
+                                    int border, float* __restrict__ xr, float* __restrict__ xe, double* ss,
+                                    double* ee) {
+  const size_t per = (size_t)D * D * D;
+  const int b = blockIdx.y;
+  const int ox = origins[3 * b], oy = origins[3 * b + 1], oz = origins[3 * b + 2];
+  double s1 = 0.0, s2 = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
+    const size_t src = ((size_t)((oz + z) % N) * N + (size_t)((oy + y) % N)) * N + (size_t)((ox + x) % N);
+    const double rv = fr[src], ev = fa[src] - fb[src];
+    xr[(size_t)b * per + i] = (float)rv;
+    xe[(size_t)b * per + i] = (float)ev;
+    s1 += rv * rv;
+    const bool in = x >= border && x < D - border && y >= border && y < D - border && z >= border && z < D - border;
+    if (in) s2 += ev * ev;
+  }
+  __shared__ double red[32];
+  const double a = block_sum(s1, red);
+  const double c = block_sum(s2, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&ss[b], a);
+    atomicAdd(&ee[b], c);
+  }
+}
+
+__global__ void k_crops_scale(float* xr, float* xe, int D, double h2, const double* ss, const double* ee,
+                              double* den) {
+  const size_t per = (size_t)D * D * D;
+  const int b = blockIdx.y;
+  const double s = sqrt(ss[b] / (double)per);
+  const float ir = s > 0.0 ? (float)(1.0 / s) : 0.f;
+  const float ie = s > 0.0 ? (float)(1.0 / (s * h2)) : 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    xr[(size_t)b * per + i] *= ir;
+    xe[(size_t)b * per + i] *= ie;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) den[b] = s > 0.0 ? ee[b] / (s * s * h2 * h2) : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba 2015) on the FP32 master weights; gradients are zeroed.
+// ---------------------------------------------------------------------------
+__global__ void k_adam(float* w, float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    w[i] -= lr * mh / (sqrtf(vh) + eps);
+    g[i] = 0.f;
+  }
+}
+
+}  // namespace cnn
+}  // namespace pic

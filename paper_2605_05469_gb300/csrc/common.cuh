@@ -15,6 +15,12 @@ enum : int {
   DEV_ERR_BOUNDS = 4,   // a guarded index fell outside its buffer
 };
 
+// Periodic node grid: N^3 nodes x_i = i h on [0, L)^3.
+struct Grid {
+  int N;
+  double L, h, inv_h;
+};
+
 // Solver scalars shared between the kernels of one solve. Written only by the
 // last block of a reduction kernel, read by all blocks of later kernels.
 struct Scalars {
@@ -27,7 +33,7 @@ struct Scalars {
   double rmax2;     // MIXED: (r, r) at the last FP64 residual recomputation
   double delta2;    // MIXED: reliable-update trigger factor squared
   double rz;        // FCG: (r, z)
-  double rz_old;    // FCG: (r, z_old)
+  double rz_old;    // FCG: (r_new, z_old), reduced by the update kernel
   double true_rr;   // MIXED: last recomputed FP64 (r, r)
   double sum0, sum1;  // mean projections
   double scale;     // CNN: RMS of r
@@ -39,6 +45,8 @@ struct Scalars {
   int final_check;  // MIXED: the pending update was triggered by convergence
   int xsel;         // MIXED: which of the two FP64 solution buffers is current
   int x32_reset;    // MIXED: the FP32 correction was folded; read it as zero
+  int fcg;          // flexible CG: alpha = (r, z) / (p, A p)
+  int fallback_now; // FCG: this iteration's z is replaced by the Jacobi direction
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -161,5 +169,20 @@ __device__ __forceinline__ bool grid_reduce_last(const double (&v)[K], double* p
 }
 
 __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// Compensated FP32 running sum (Knuth's TwoSum, branch-free): keeps per-thread
+// partial dot products accurate to a few FP32 ulps of the sum without FP64
+// instructions, which run at 1/58 of the FP32 rate on this GPU. Widened to
+// FP64 once per thread before the FP64 block and grid reduction.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 }  // namespace pic

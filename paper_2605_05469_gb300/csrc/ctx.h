@@ -1,0 +1,156 @@
+// Internal: the context behind the C ABI and the host helpers shared by the
+// library's translation units (not part of the public interface).
+#pragma once
+#include "common.cuh"
+
+namespace pic {
+
+struct CnnState;  // learned-preconditioner state, see cnn.cu
+
+struct SolverWs {
+  // FP64 judge
+  double *x = nullptr, *r = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+  // mixed
+  double* xm[2] = {nullptr, nullptr};
+  float *x32 = nullptr, *r32 = nullptr, *p32[2] = {nullptr, nullptr};
+  // flexible CG with the learned preconditioner
+  float* z32[2] = {nullptr, nullptr};
+  // shared
+  double* b = nullptr;
+};
+
+// A pool of CUDA event pairs recorded on the context stream; flushed (elapsed
+// times summed) once the stream has passed them.
+struct EventPool {
+  static constexpr int kCap = 1024;
+  cudaEvent_t ev[kCap][2] = {};
+  int n = 0;         // pending pairs
+  int count = 0;     // flushed pairs
+  double ms = 0.0;   // flushed total
+  bool ready = false;
+  bool init() {
+    for (int i = 0; i < kCap; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (cudaEventCreate(&ev[i][j]) != cudaSuccess) return false;
+    ready = true;
+    return true;
+  }
+  void destroy() {
+    for (int i = 0; i < kCap; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (ev[i][j]) cudaEventDestroy(ev[i][j]);
+    ready = false;
+  }
+  void flush() {
+    for (int i = 0; i < n; ++i) {
+      float t = 0.f;
+      if (cudaEventSynchronize(ev[i][1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i][0], ev[i][1]) == cudaSuccess) {
+        ms += t;
+        ++count;
+      }
+    }
+    n = 0;
+  }
+  // Start a pair; returns its slot or -1 when profiling is off.
+  int begin(cudaStream_t st) {
+    if (!ready) return -1;
+    if (n == kCap) flush();
+    cudaEventRecord(ev[n][0], st);
+    return n++;
+  }
+  void end(int slot, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(ev[slot][1], st);
+  }
+  void reset() { n = 0; count = 0; ms = 0.0; }
+};
+
+}  // namespace pic
+
+struct pic_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0, sms = 0;
+  // geometry
+  bool has_grid = false;
+  int N = 0;
+  size_t n = 0;
+  double L = 0, h = 0, alpha = 0, k = 0;
+  int ppc = 0;
+  uint64_t np = 0;
+  pic::Grid grid{};
+  // particles
+  double* pb[2][6] = {};
+  uint32_t* ids[2] = {nullptr, nullptr};
+  int cur = 0;
+  uint32_t *keys = nullptr, *ranks = nullptr, *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
+  bool keys_valid = false, sorted = false, half_step = false;
+  double* E = nullptr;  // 3 n
+  // solver
+  pic::SolverWs ws;
+  pic::Scalars* sc = nullptr;
+  pic::Scalars* sc_host = nullptr;  // pinned, 2 slots
+  double* partials = nullptr;
+  size_t partials_len = 0;
+  unsigned* counter = nullptr;
+  int* err = nullptr;
+  int* err_host = nullptr;   // pinned
+  double* out3 = nullptr;    // device, 3 doubles
+  double* out3_host = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, batch_ev[2] = {nullptr, nullptr};
+  // tracing
+  int64_t launches = 0;
+  bool prof_on = false;
+  pic::EventPool* phase = nullptr;  // [PIC_NPHASE]
+  pic::EventPool* ker = nullptr;    // [PIC_NKER]
+  int ker_prec[PIC_NKER] = {0, 0};
+  // learned preconditioner (weights, activations, optimiser state)
+  pic::CnnState* cnn = nullptr;
+};
+
+namespace pic {
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return PIC_ECUDA;      \
+  } while (0)
+
+template <typename T>
+inline int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return PIC_OK;
+  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return PIC_ENOMEM;
+  }
+  return PIC_OK;
+}
+
+template <typename T>
+inline void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+inline int round32(int t) { return ((t + 31) / 32) * 32; }
+
+// Every kernel goes through here: launched on the context stream and counted.
+template <typename... KArgs, typename... Args>
+void launch(pic_ctx* c, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, Args... args) {
+  kernel<<<grid, block, smem, c->stream>>>(args...);
+  ++c->launches;
+}
+
+// Phase timer around one public call (no-op unless profiling is on).
+struct PhaseScope {
+  pic_ctx* c;
+  int phase, slot;
+  PhaseScope(pic_ctx* cc, int ph) : c(cc), phase(ph), slot(-1) {
+    if (c->prof_on) slot = c->phase[phase].begin(c->stream);
+  }
+  ~PhaseScope() {
+    if (slot >= 0) c->phase[phase].end(slot, c->stream);
+  }
+};
+
+}  // namespace pic

@@ -14,11 +14,6 @@
 
 namespace pic {
 
-struct Grid {
-  int N;
-  double L, h, inv_h;
-};
-
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of
 // (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),

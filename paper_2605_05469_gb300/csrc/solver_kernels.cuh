@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(256) k_cg_pap(const T* __restrict__ r, const T
   if (sc->done) return;
   const T beta = (T)sc->beta;
   const StageLayout<T, T, 2> lay(g.rows, g.N);
-  double dot = 0.0;
+  double dot = 0.0;  // FP64 path
+  CompSum dot32;     // FP32 path
   auto ingest = [&](int st, size_t e) {
     const V4<T> rv = ld4(lay.v0(smem, st) + e);
     V4<T> pv = ld4(lay.v1(smem, st) + e);
@@ -178,17 +179,18 @@ __global__ void __launch_bounds__(256) k_cg_pap(const T* __restrict__ r, const T
     T d = c.v[0] * ap.v[0];
 #pragma unroll
     for (int i = 1; i < 4; ++i) d += c.v[i] * ap.v[i];
-    dot += (double)d;
+    if (sizeof(T) == 8) dot += (double)d;
+    else dot32.add((float)d);
   };
   stream_slab<T, T, T, 2>(g, smem, bars, r, pin, err, start, ingest, body);
-  double v[1] = {dot}, tot[1];
+  double v[1] = {sizeof(T) == 8 ? dot : dot32.value()}, tot[1];
   if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double pq = tot[0];
     sc->pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {
       sc->done = 3;
     } else {
-      sc->alpha = sc->rr / pq;
+      sc->alpha = (sc->fcg ? sc->rz : sc->rr) / pq;
     }
   }
 }
@@ -234,50 +236,57 @@ __global__ void __launch_bounds__(256) k_cg_update64(double* __restrict__ x, dou
 // the tolerance.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_cg_update32(float* __restrict__ x, float* __restrict__ r,
-                                                     const float* __restrict__ p, Scalars* sc, double* partials,
-                                                     unsigned* counter, int* err, StreamGeo g) {
+                                                     const float* __restrict__ p, const float* __restrict__ zold,
+                                                     Scalars* sc, double* partials, unsigned* counter, int* err,
+                                                     StreamGeo g) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (sc->done) return;
   const float alpha = (float)sc->alpha;
   const bool x_zero = sc->x32_reset != 0;
   const StageLayout<float, float, 1> lay(g.rows, g.N);
-  double acc = 0.0;
-  V4<float> cx, cr;  // x, r of the current output plane, loaded one plane ahead
+  CompSum acc, acc_z;
+  V4<float> cx, cr, cz;  // x, r (and z_old) of the current output plane, loaded one plane ahead
   const V4<float> zero4{{0.f, 0.f, 0.f, 0.f}};
   auto start = [&](const Slab& s) {
     const size_t off = cell_offset(s, 0);
     cx = x_zero ? zero4 : ldg4(x + off);
     cr = ldg4(r + off);
+    if (zold) cz = ldg4(zold + off);
   };
   auto ingest = [&](int st, size_t e) { return ld4(lay.v0(smem, st) + e); };
   auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
                   const V4<float>& zp) {
-    V4<float> nx = zero4, nr = zero4;
+    V4<float> nx = zero4, nr = zero4, nz = zero4;
     if (t + 1 < s.ZC) {
       const size_t noff = cell_offset(s, t + 1);
       if (!x_zero) nx = ldg4(x + noff);
       nr = ldg4(r + noff);
+      if (zold) nz = ldg4(zold + noff);
     }
     const V4<float> ap = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
-    float d = 0.f;
+    float d = 0.f, dz = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       cx.v[i] = fmaf(alpha, c.v[i], cx.v[i]);
       cr.v[i] = fmaf(-alpha, ap.v[i], cr.v[i]);
       d = fmaf(cr.v[i], cr.v[i], d);
+      if (zold) dz = fmaf(cr.v[i], cz.v[i], dz);
     }
     st4(x + off, cx);
     st4(r + off, cr);
-    acc += (double)d;
+    acc.add(d);
+    if (zold) acc_z.add(dz);
     cx = nx;
     cr = nr;
+    cz = nz;
   };
   stream_slab<float, float, float, 1>(g, smem, bars, p, (const float*)nullptr, err, start, ingest, body);
-  double v[1] = {acc}, tot[1];
-  if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+  double v[2] = {acc.value(), acc_z.value()}, tot[2];
+  if (grid_reduce_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double rr = tot[0];
+    sc->rz_old = tot[1];
     sc->x32_reset = 0;
     sc->rr_prev = sc->rr;
     sc->beta = rr / sc->rr;
@@ -366,7 +375,8 @@ __global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, dou
   // x32 holds a stale correction that has already been folded: read it as zero
   const bool x32_zero = sc->x32_reset != 0;
   const StageLayout<double, float, 2> lay(g.rows, g.N);
-  double acc64 = 0.0, acc32 = 0.0;
+  double acc64 = 0.0;
+  CompSum acc32;
   V4<double> cb;
   auto start = [&](const Slab& s) { cb = ldg4(b + cell_offset(s, 0)); };
   auto ingest = [&](int st, size_t e) {
@@ -397,10 +407,10 @@ __global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, dou
     }
     st4(xout + off, c);
     st4(r32 + off, rf);
-    acc32 += (double)d;
+    acc32.add(d);
   };
   stream_slab<double, double, float, 2>(g, smem, bars, xin, x32, err, start, ingest, body);
-  double v[2] = {acc64, acc32}, tot[2];
+  double v[2] = {acc64, acc32.value()}, tot[2];
   if (grid_reduce_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
     const double rr64 = tot[0], rr = tot[1];
     sc->xsel = sel ^ 1;
@@ -492,6 +502,52 @@ __global__ void __launch_bounds__(256) k_finish(const double* __restrict__ x, do
 #pragma unroll
     for (int k = 0; k < 4; ++k) v.v[k] = zero ? 0.0 : v.v[k] - m;
     st4(phi + 4 * i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Flexible CG (Golub & Ye 1999) with a nonlinear preconditioner z = P(r):
+// (r, z) -> descent guard, beta = (r, z_new - z_old) / (r_old, z_old).
+// init: first direction (beta = 0). When (r, z) <= 0 or is not finite the
+// iteration uses the Jacobi direction z = r / 6 (scaled operator diagonal).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fcg_dot(const float* __restrict__ r, const float* __restrict__ z,
+                                                 size_t n4, Scalars* sc, double* partials, unsigned* counter,
+                                                 int init) {
+  if (sc->done) return;
+  CompSum acc;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const V4<float> rv = ldg4(r + 4 * i), zv = ldg4(z + 4 * i);
+    float d = rv.v[0] * zv.v[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) d = fmaf(rv.v[k], zv.v[k], d);
+    acc.add(d);
+  }
+  double v[1] = {acc.value()}, tot[1];
+  if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double rz = tot[0];
+    sc->fallback_now = 0;
+    if (!(rz > 0.0) || !isfinite(rz)) {
+      sc->fallback_now = 1;
+      sc->fallbacks += 1;
+      rz = sc->rr / 6.0;
+    }
+    sc->beta = init ? 0.0 : (rz - sc->rz_old) / sc->rz;
+    sc->rz = rz;
+    if (!isfinite(sc->beta)) sc->done = 3;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fcg_fallback(const float* __restrict__ r, float* __restrict__ z,
+                                                      size_t n4, const Scalars* sc) {
+  if (sc->done || !sc->fallback_now) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    V4<float> v = ldg4(r + 4 * i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v.v[k] *= (1.0f / 6.0f);
+    st4(z + 4 * i, v);
   }
 }
 

@@ -1,0 +1,185 @@
+"""GPU parity of the learned preconditioner against the CPU oracle
+(oracle/cnn.py).
+
+Single convolutions (tensor cores, BF16 operands, FP32 accumulation) are
+compared with the oracle's FP64 direct-loop convolution of the same
+BF16-rounded inputs and weights: only the accumulation order differs, so the
+tolerance is 1e-5 relative. The full network stores BF16 activations between
+layers, so forward values and the loss are compared at BF16 tolerance (2e-2
+relative), and weight gradients by direction (cosine >= 0.995) and magnitude
+(1e-1 relative L2): they are sums over all cells of products whose signs
+cancel, which magnifies the BF16 rounding of the data gradients. Adam is compared exactly on the
+GPU's own gradients.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cnn as ocnn  # noqa: E402
+from oracle import pic as opic  # noqa: E402
+from paper_2605_05469_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+L = 4.0 * np.pi
+
+
+@pytest.fixture(scope="module")
+def pg():
+    import paper_2605_05469_gb300 as pg
+    pg.lib()
+    return pg
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def rounded_weights(seed, scale=1.0):
+    ws = [bf16_round(w * scale) for w in ocnn.init_weights(seed)]
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    return ws, flat
+
+
+def ctx_with_weights(pg, flat, N=16):
+    c = pg.Context().init(N, 0, 0)
+    c.cnn_set_weights(flat)
+    return c
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("D", [16, 32])
+def test_conv_raw_layers_match_oracle(pg, D):
+    ws, flat = rounded_weights(1)
+    c = ctx_with_weights(pg, flat)
+    B = 2
+    rng = np.random.default_rng(D)
+    x1 = bf16_round(rng.normal(size=(B, D, D, D)))                  # one channel
+    x16 = bf16_round(rng.normal(size=(B, D, D, D, 16)))             # channels last
+    t1 = torch.from_numpy(x1.astype(np.float32)).cuda().reshape(-1)
+    t16 = torch.from_numpy(x16.astype(np.float32)).to(torch.bfloat16).cuda().reshape(-1)
+    out = torch.empty(B * D ** 3 * 16, dtype=torch.float32, device="cuda")
+    cases = {
+        0: (t1, lambda b: ocnn.conv3d(x1[b][None], ws[0])),
+        1: (t16, lambda b: ocnn.conv3d(np.moveaxis(x16[b], -1, 0), ws[1])),
+        2: (t16, lambda b: ocnn.conv3d(np.moveaxis(x16[b], -1, 0), ws[2])),
+        3: (t16, lambda b: ocnn.conv3d(np.moveaxis(x16[b], -1, 0), ws[3])),
+        4: (t1, lambda b: ocnn.conv3d_bwd_data(x1[b][None], ws[3])),
+        5: (t16, lambda b: ocnn.conv3d_bwd_data(np.moveaxis(x16[b], -1, 0), ws[2])),
+        6: (t16, lambda b: ocnn.conv3d_bwd_data(np.moveaxis(x16[b], -1, 0), ws[1])),
+    }
+    for which, (tin, ref_fn) in cases.items():
+        out.fill_(float("nan"))
+        c.cnn_conv_raw(which, tin, out, B, D)
+        got = np.moveaxis(out.cpu().numpy().reshape(B, D, D, D, 16), -1, 1).astype(np.float64)
+        for b in range(B):
+            ref = ref_fn(b)
+            nch = ref.shape[0]
+            assert rel(got[b, :nch], ref) <= 1e-5, (which, b, rel(got[b, :nch], ref))
+            if nch < 16:
+                assert np.all(got[b, nch:] == 0.0), which
+
+
+def test_network_forward_loss_and_gradients_match_oracle(pg):
+    N, D, B = 32, 16, 2
+    h = L / N
+    ws, flat = rounded_weights(2)
+    c = ctx_with_weights(pg, flat, N)
+    r = inputs.noise_field(N, 5)
+    a = inputs.noise_field(N, 6)
+    b = inputs.noise_field(N, 7)
+    origins = np.array([[0, 3, 5], [20, 31, 9]], dtype=np.int32)
+    x = torch.empty(B * D ** 3, dtype=torch.float32, device="cuda")
+    t = torch.empty_like(x)
+    c.cnn_make_batch(torch.from_numpy(r).cuda(), torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
+                     origins, D, x, t, h * h)
+    # oracle crops (periodic) of r and e = a - b
+    def crop(f, o):
+        g = f.reshape(N, N, N)
+        iz = (o[2] + np.arange(D)) % N
+        iy = (o[1] + np.arange(D)) % N
+        ix = (o[0] + np.arange(D)) % N
+        return g[np.ix_(iz, iy, ix)]
+    r_cr = [crop(r, o) for o in origins]
+    e_cr = [crop(a - b, o) for o in origins]
+    xs = x.cpu().numpy().reshape(B, D, D, D)
+    ts = t.cpu().numpy().reshape(B, D, D, D)
+    for i in range(B):
+        s = np.sqrt(np.mean(r_cr[i] ** 2))
+        assert rel(xs[i], r_cr[i] / s) <= 1e-6
+        assert rel(ts[i], e_cr[i] / (s * h * h)) <= 1e-6
+    y = torch.empty_like(x)
+    c.cnn_forward(x, y, B, D)
+    ys = y.cpu().numpy().reshape(B, D, D, D)
+    for i in range(B):
+        ref, _ = ocnn.forward(r_cr[i] / np.sqrt(np.mean(r_cr[i] ** 2)), ws)
+        assert rel(ys[i], ref) <= 2e-2
+    gy = torch.empty_like(x)
+    loss = c.cnn_loss(y, t, B, D, gy)
+    ref_loss, ref_grads = ocnn.loss_and_grads(ws, r_cr, e_cr, h)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    c.cnn_backward(gy, B, D)
+    g = c.cnn_get_grads()
+    off = 0
+    report = []
+    for layer, rg in enumerate(ref_grads):
+        gl = g[off:off + rg.size].reshape(rg.shape).astype(np.float64)
+        off += rg.size
+        cos = np.sum(gl * rg) / (np.linalg.norm(gl) * np.linalg.norm(rg))
+        report.append((layer, rel(gl, rg), cos))
+    # BF16 activations and data gradients, then a sum over all cells with
+    # cancelling signs: the direction is pinned tightly, the magnitude loosely
+    for layer, r_err, cos in report:
+        assert cos >= 0.995 and r_err <= 0.1, report
+
+
+def test_adam_matches_oracle_on_gpu_gradients(pg):
+    ws, flat = rounded_weights(3)
+    c = ctx_with_weights(pg, flat, 16)
+    D, B = 16, 1
+    x = torch.from_numpy(inputs.noise_field(D, 1).astype(np.float32)).cuda()
+    y = torch.empty_like(x)
+    c.cnn_forward(x, y, B, D)
+    c.cnn_backward(torch.ones_like(y), B, D)
+    g = c.cnn_get_grads().astype(np.float64)
+    c.cnn_adam(1e-3)
+    got = c.cnn_get_weights().astype(np.float64)
+    p = [flat.astype(np.float64)]
+    m = [np.zeros_like(p[0])]
+    v = [np.zeros_like(p[0])]
+    ocnn.adam_step(p, [g], m, v, 1, lr=1e-3)
+    assert np.max(np.abs(got - p[0])) <= 1e-6
+    assert np.all(c.cnn_get_grads() == 0.0)
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_fcg_cnn_solve_reaches_true_residual(pg, N):
+    """Flexible CG with the network (random weights: the descent guard keeps
+    it convergent) reaches the same true FP64 relative residual 1e-10 as the
+    Jacobi judge."""
+    h = L / N
+    _, flat = rounded_weights(4)
+    c = ctx_with_weights(pg, flat, N)
+    b = inputs.landau_noise_rhs(N, 11)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    info = c.solve(torch.from_numpy(b).cuda(), phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED,
+                   precond=pg.PC_CNN)
+    got = phi.cpu().numpy()
+    bp = b - b.mean()
+    assert np.linalg.norm(bp - opic.apply_A(got, N, h)) <= 1.05e-10 * np.linalg.norm(bp), info
+    ref, _, _, _ = opic.pcg_jacobi(b, np.zeros(N ** 3), N, h, 1e-13, 5000)
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_cnn_requires_weights_and_mixed_precision(pg):
+    c = pg.Context().init(16, 0, 0)
+    rho = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(rho)
+    code, _ = pg.poisson_solve_ex(c.h, rho, phi, 1e-10, 10, c.n, pg.PREC_MIXED, pg.PC_CNN)
+    assert code == pg.PIC_ESTATE
+    code, _ = pg.poisson_solve_ex(c.h, rho, phi, 1e-10, 10, c.n, pg.PREC_FP64, pg.PC_CNN)
+    assert code == pg.PIC_EINVAL
