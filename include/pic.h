@@ -217,6 +217,22 @@ typedef struct {
 int pic_profile_enable(pic_ctx *c, int on);
 int pic_profile_read(pic_ctx *c, pic_profile_stats *out, int reset);
 
+/* Field energy for callers that cannot allocate device memory (this entry
+ * point has no counterpart in the paper). It needs no pic_ctx: the caller
+ * passes `phi` (device FP64 [N^3], x fastest, 16-byte aligned), the grid size
+ * N (8 <= N <= 1024, N % 8 == 0; larger sizes return PIC_EINVAL) and the
+ * wavenumber k (L = 2 pi / k), and receives out_w[d] = h^3 sum_i E_{d,i}^2,
+ * d = x, y, z, in `out_w` (device memory, 3 doubles), written asynchronously
+ * on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * It calls no cudaMalloc, cudaFree or other allocating routine. Its reduction
+ * scratch is a fixed 48.25 KiB file-scope device array that every GPU loading
+ * the library keeps until exit; all calls on a device share it, so calls that
+ * overlap on the GPU (different streams) race and must be serialised by the
+ * caller. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Returns PIC_OK, PIC_EINVAL or PIC_ECUDA. */
+int pic_field_energy_noalloc(const double *phi, int N, double k, double *out_w, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

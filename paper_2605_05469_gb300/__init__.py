@@ -114,6 +114,8 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pic_cnn_conv_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int]),
+    "pic_field_energy_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
 }
 
 
@@ -234,6 +236,13 @@ def pic_profile_read(h, reset=True):
     st = pic_profile_stats()
     _check(lib().pic_profile_read(h, ctypes.byref(st), 1 if reset else 0), "pic_profile_read")
     return st.as_dict()
+
+
+def pic_field_energy_noalloc(phi, N, k, out_w, stream=None):
+    """Field energy into the device tensor out_w (3 float64) without any
+    allocation inside the library (see include/pic.h); returns the status code."""
+    return lib().pic_field_energy_noalloc(_dptr(phi, "float64", N ** 3, "phi"), N, k,
+                                          _dptr(out_w, "float64", 3, "out_w"), _stream_ptr(stream))
 
 
 # ------------------------------------------------------------ convenience
