@@ -146,6 +146,10 @@ int64_t pic_num_particles(const pic_ctx *c);
  * FP64 device [N^3] arrays. */
 int pic_apply_laplacian(pic_ctx *c, const double *x, double *y);
 
+/* Residual of the solve's system (Sec. 3.2): r = (rho - mean rho) - A (phi -
+ * mean phi), FP64 device [N^3] arrays (used to build training snapshots). */
+int pic_residual(pic_ctx *c, const double *rho, const double *phi, double *r);
+
 /* ------------------------------------------------------------------------
  * Learned preconditioner (used with PIC_PC_CNN inside flexible CG). The paper
  * lists Jacobi, Richardson, Gauss-Seidel and SSOR preconditioners for its PCG
@@ -180,15 +184,20 @@ int pic_cnn_backward(pic_ctx *c, const float *gy, int B, int D);
 int pic_cnn_adam(pic_ctx *c, double lr);
 
 /* Training batch from CG snapshots on the context grid: B periodic crops of
- * D^3 cells at host origins (3 ints per crop, x y z) of the residual field r
- * and of the error e = a - b (a = converged solution, b = iterate), all device
- * FP64 [N^3]. Writes x = r / s and t = e / (s h2) (s = RMS of the r crop) to
- * device FP32 [B][D^3] buffers and keeps sum_interior t^2 per crop (interior
- * = at least 4 cells from every face) for pic_cnn_loss. */
+ * D^3 cells (D % 16 == 0) at host origins (3 ints per crop, x y z) of the
+ * residual field r and of the error e = a - b (a = converged solution, b =
+ * iterate), all device FP64 [N^3]. Writes x = r / s and t = e / (s h2)
+ * (s = RMS of the r crop) to device FP32 [B][D^3] buffers and keeps the
+ * target's two norms for pic_cnn_loss. */
 int pic_cnn_make_batch(pic_ctx *c, const double *r, const double *a, const double *b, const int *origins_host,
                        int B, int D, float *x, float *t, double h2);
-/* Loss mean_b sum_in (y - t)^2 / sum_in t^2 of the last batch to *loss_host,
- * and its gradient with respect to y in gy (device FP32 [B][D^3]). */
+/* Loss of the last batch, mean over crops of E(d)/E(t) + |A_I d|^2/|A_I t|^2
+ * with d = y - t: E(d) is the sum of squared differences of d across the
+ * grid edges inside the crop's valid interior (cells at least 4 from every
+ * face; d^T A d there, the norm CG minimises) and A_I d the 7-point stencil
+ * 6 d_i - sum of neighbours on the cells at least 5 from every face (the
+ * residual norm). Writes the loss to *loss_host and its gradient with respect
+ * to y to gy (device FP32 [B][D^3]). */
 int pic_cnn_loss(pic_ctx *c, const float *y, const float *t, int B, int D, float *gy, double *loss_host);
 
 /* One convolution of the packed network without epilogue, for tests: which =

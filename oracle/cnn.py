@@ -15,12 +15,23 @@ learned variant the GPU library offers, from standard published methods:
   conv(16->1); no biases (14 688 weights); act = leaky ReLU with negative
   slope 1/8. N is positively homogeneous: N(c x) = c N(x) for c > 0.
 * preconditioner P(r) = h^2 * s * N(r / s) - mean, s = RMS(r).
-* training loss on a crop (periodic convs; only outputs at least 4 cells
-  from every crop face are scored, where periodic and valid convolutions
-  agree):  L = sum_in (N(r/s) - e/(s h^2))^2 / sum_in (e/(s h^2))^2.
+* training loss on a crop, the sum of the error in the energy (A-) norm and
+  the residual norm, each relative to the target's:
+    L = E(d) / E(t) + |A_I d|^2 / |A_I t|^2,  d = N(r/s) - t, t = e/(s h^2),
+  with E(d) = sum over grid edges inside the valid interior R4 (cells at
+  least 4 from every crop face, where periodic and valid convolutions agree)
+  of the squared difference across the edge (d^T A d restricted to R4, up to
+  h^2), and A_I d = 6 d_i - sum_nb d_j on the cells of R5 (at least 5 from
+  every face, so the stencil stays in R4). Per Fourier mode k of the residual
+  the two terms weight |r_k|^2 |1 - lambda_k p_k|^2 by 1/lambda_k and by 1:
+  the first fixes the low-frequency gain (CG's condition number), the second
+  keeps lambda_k p_k close to 1 (and positive) at high frequencies.
 * Adam: Kingma & Ba, ICLR 2015, with bias correction.
-* FCG: flexible CG of Golub & Ye (SIAM J. Sci. Comput. 21, 1999) with the
-  Polak-Ribiere-type beta = r_{k+1}.(z_{k+1} - z_k) / (r_k.z_k).
+* FCG: flexible CG with one retained direction, FCG(1) of Notay (SIAM J.
+  Sci. Comput. 22, 2000): the new direction is z_{k+1} made A-conjugate to
+  the previous one, beta = -(z_{k+1}.A p_k) / (p_k.A p_k), which keeps the
+  local optimality for any (nonlinear, nonsymmetric) preconditioner; for a
+  fixed SPD preconditioner it equals the PCG (Polak-Ribiere) beta.
   Descent guard: when the preconditioned residual is not a descent
   direction (r.z <= 0 or not finite), that iteration uses the Jacobi
   direction z = (h^2/6) r instead; Jacobi-PCG is the fallback.
@@ -118,8 +129,58 @@ def interior_mask(shape, border=4):
     return m
 
 
+def interior_energy(d, mask):
+    """E(d) = sum of (d_i - d_j)^2 over neighbour pairs (i, j) along the three
+    axes with both cells inside ``mask`` (no wrap)."""
+    E = 0.0
+    for ax in range(3):
+        a = [slice(None)] * 3
+        b = [slice(None)] * 3
+        a[ax] = slice(0, -1)
+        b[ax] = slice(1, None)
+        both = mask[tuple(a)] & mask[tuple(b)]
+        diff = d[tuple(a)] - d[tuple(b)]
+        E += np.sum(np.where(both, diff * diff, 0.0))
+    return E
+
+
+def interior_energy_grad(d, mask):
+    """dE/dd: 2 sum over the in-mask neighbours j of i of (d_i - d_j)."""
+    g = np.zeros_like(d)
+    for ax in range(3):
+        a = [slice(None)] * 3
+        b = [slice(None)] * 3
+        a[ax] = slice(0, -1)
+        b[ax] = slice(1, None)
+        both = mask[tuple(a)] & mask[tuple(b)]
+        diff = np.where(both, d[tuple(a)] - d[tuple(b)], 0.0)
+        g[tuple(a)] += 2.0 * diff
+        g[tuple(b)] -= 2.0 * diff
+    return g
+
+
+def interior_stencil(d, mask5):
+    """q = 6 d_i - sum of the 6 neighbours d_j (no wrap) on the cells of
+    ``mask5``, zero elsewhere (the caller keeps mask5 one cell inside the
+    crop so the neighbours exist)."""
+    q = 6.0 * d
+    for ax in range(3):
+        q = q - np.roll(d, 1, axis=ax) - np.roll(d, -1, axis=ax)
+    return np.where(mask5, q, 0.0)
+
+
+def interior_stencil_adjoint(q):
+    """Transpose of ``interior_stencil`` applied to q (q zero outside mask5):
+    g_i = 6 q_i - sum of the 6 neighbours q_j."""
+    g = 6.0 * q
+    for ax in range(3):
+        g = g - np.roll(q, 1, axis=ax) - np.roll(q, -1, axis=ax)
+    return g
+
+
 def loss_and_grads(ws, r_crops, e_crops, h):
-    """Mean over crops of the relative interior loss, and its weight gradients."""
+    """Mean over crops of the energy-norm plus residual-norm loss, and its
+    weight gradients."""
     B = len(r_crops)
     total = 0.0
     gsum = [np.zeros_like(w) for w in ws]
@@ -128,11 +189,15 @@ def loss_and_grads(ws, r_crops, e_crops, h):
         x = r / s
         t = e / (s * h * h)
         y, cache = forward(x, ws)
-        m = interior_mask(r.shape)
-        den = np.sum(t[m] ** 2)
-        d = np.where(m, y - t, 0.0)
-        total += np.sum(d * d) / den
-        gy = 2.0 * d / den / B
+        m4 = interior_mask(r.shape, border=4)
+        m5 = interior_mask(r.shape, border=5)
+        den_e = interior_energy(t, m4)
+        qt = interior_stencil(t, m5)
+        den_r = np.sum(qt * qt)
+        d = y - t
+        q = interior_stencil(d, m5)
+        total += interior_energy(d, m4) / den_e + np.sum(q * q) / den_r
+        gy = (interior_energy_grad(d, m4) / den_e + 2.0 * interior_stencil_adjoint(q) / den_r) / B
         for acc, g in zip(gsum, backward(gy, ws, cache)):
             acc += g
     return total / B, gsum
@@ -161,7 +226,7 @@ def precondition(r, ws, N, h):
 
 
 def fcg(b, x0, N, h, tol, maxit, prec):
-    """Flexible CG (Golub & Ye 1999) on A x = b - mean(b) with z = prec(r).
+    """Flexible CG, FCG(1) (Notay 2000), on A x = b - mean(b) with z = prec(r).
 
     Stops when ||r||_2 <= tol ||b||_2 on the recursive residual. Returns
     (x with mean zero, iters, rel_res, converged flag).
@@ -191,14 +256,14 @@ def fcg(b, x0, N, h, tol, maxit, prec):
     rel = np.sqrt(r @ r) / bnorm
     while rel > tol and it < maxit:
         q = pic.apply_A(p, N, h)
-        alpha = rz / (p @ q)
+        pq = p @ q
+        alpha = rz / pq
         x = x + alpha * p
         r = r - alpha * q
-        z_new = guarded(r)
-        beta = (r @ (z_new - z)) / rz
-        rz = r @ z_new
-        p = z_new + beta * p
-        z = z_new
+        z = guarded(r)
+        beta = -(z @ q) / pq
+        rz = r @ z
+        p = z + beta * p
         it += 1
         rel = np.sqrt(r @ r) / bnorm
     fcg.last_fallbacks = fallbacks

@@ -98,6 +98,7 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int)]),
     "pic_num_particles": (ctypes.c_int64, [ctypes.c_void_p]),
     "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_profile_stats), ctypes.c_int]),
     "pic_cnn_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -291,6 +292,10 @@ class Context:
 
     def apply_laplacian(self, x, y):
         pic_apply_laplacian(self.h, x, y, self.n)
+
+    def residual(self, rho, phi, r):
+        _check(lib().pic_residual(self.h, _dptr(rho, "float64", self.n, "rho"), _dptr(phi, "float64", self.n, "phi"),
+                                  _dptr(r, "float64", self.n, "r")), "pic_residual")
 
     # ---- learned preconditioner
     def cnn_set_weights(self, w):

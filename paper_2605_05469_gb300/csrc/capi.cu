@@ -36,7 +36,7 @@ void free_solver(pic_ctx* c) {
   dfree(w.x); dfree(w.r); dfree(w.p[0]); dfree(w.p[1]); dfree(w.q);
   dfree(w.xm[0]); dfree(w.xm[1]);
   dfree(w.x32); dfree(w.r32); dfree(w.p32[0]); dfree(w.p32[1]);
-  dfree(w.z32[0]); dfree(w.z32[1]);
+  dfree(w.z32[0]); dfree(w.z32[1]); dfree(w.q32);
   dfree(w.b);
   dfree(c->partials);
   c->partials_len = 0;
@@ -308,11 +308,11 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
 }
 
 // --------------------------------------------------------------------------
-// Flexible CG with the learned preconditioner, FP32 vectors with FP64
-// reductions and reliable updates (as the mixed path). One iteration:
-// pap (z -> p, alpha = (r,z)/(p,Ap)), update (+ (r, z_old)), reliable update
-// if due, network z_new = s N(r/s), (r, z_new) with descent guard and beta,
-// Jacobi fallback if the guard fired.
+// Flexible CG, FCG(1) (Notay 2000), with the learned preconditioner, FP32
+// vectors with FP64 reductions and reliable updates (as the mixed path). One
+// iteration: pap (p = z + beta p, q = A p, alpha = (r,z)/(p,q)), update,
+// reliable update if due, network z = s N(r/s), dots (r,z), (z,q), (r,q) with
+// the descent guard and beta = -(z,q)/(p,q), Jacobi fallback if it fired.
 // --------------------------------------------------------------------------
 int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta,
                   pic_solve_info* info) {
@@ -325,11 +325,12 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
         (e = dalloc(&w.r32, c->n)) || (e = dalloc(&w.p32[0], c->n)) || (e = dalloc(&w.p32[1], c->n)))
       return e;
   }
-  if (!w.z32[0] && ((e = dalloc(&w.z32[0], c->n)) || (e = dalloc(&w.z32[1], c->n)))) return e;
+  if (!w.z32[0] && ((e = dalloc(&w.z32[0], c->n)) || (e = dalloc(&w.z32[1], c->n)) || (e = dalloc(&w.q32, c->n))))
+    return e;
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
   size_t smem_pap, smem_upd, smem_rel;
   StreamGeo gp, gu, gr;
-  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, false>, &gp, &smem_pap))) return e;
+  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, true>, &gp, &smem_pap))) return e;
   if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
   if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
   int mb = gp.blocks;
@@ -351,8 +352,8 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
          c->sc, c->partials, c->counter, c->err, gr, 0);
   int zc = 0;
   if ((e = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n))) return e;
-  launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], n4, c->sc, c->partials, c->counter,
-         1);
+  launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
+         c->partials, c->counter, 1);
   launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
   int cur = 0;
   int inner_err = PIC_OK;
@@ -360,20 +361,20 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
       int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
-      launch(c, k_cg_pap<float, false>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
-             w.p32[cur ^ 1], (float*)nullptr, c->sc, c->partials, c->counter, c->err, gp);
+      launch(c, k_cg_pap<float, true>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
+             w.p32[cur ^ 1], w.q32, c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
       launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, (const float*)w.p32[cur ^ 1],
-             (const float*)w.z32[zc], c->sc, c->partials, c->counter, c->err, gu);
+             (const float*)nullptr, c->sc, c->partials, c->counter, c->err, gu);
       if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
       launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
       zc ^= 1;
       const int ce = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n);
       if (ce && !inner_err) inner_err = ce;
-      launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], n4, c->sc, c->partials,
-             c->counter, 0);
+      launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
+             c->partials, c->counter, 0);
       launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
       cur ^= 1;
     }
@@ -680,6 +681,37 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   cudaFree(tmp);
   return ce == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_residual(pic_ctx* c, const double* rho, const double* phi, double* r) {
+  if (!c || !dev_ptr_ok(rho) || !dev_ptr_ok(phi) || !dev_ptr_ok(r)) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  SolverWs& w = c->ws;
+  int e;
+  if (!w.x && (e = dalloc(&w.x, c->n))) return e;
+  if (!w.b && (e = dalloc(&w.b, c->n))) return e;
+  size_t smem;
+  StreamGeo g;
+  if ((e = geo_for<double, double, double, 1>(c, k_residual64, &g, &smem))) return e;
+  if ((e = ensure_partials(c, (size_t)3 * g.blocks + 3 * 4096))) return e;
+  Scalars init;
+  memset(&init, 0, sizeof(init));
+  init.maxit = 1;
+  c->sc_host[0] = init;
+  CK(cudaMemcpyAsync(c->sc, &c->sc_host[0], sizeof(Scalars), cudaMemcpyHostToDevice, c->stream));
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
+  // b = h^2 (rho - mean rho), x = phi - mean phi, r = b - (h^2 A) x, then r /= h^2
+  launch(c, k_sum2, sb, 256, 0, rho, phi, n4, c->sc, c->partials, c->counter);
+  launch(c, k_project, sb, 256, 0, rho, phi, w.b, w.x, n4, 1.0 / (double)c->n, c->h * c->h, 1.0, c->sc,
+         c->partials, c->counter);
+  // the residual kernel skips work once a solve is marked done; clear it
+  CK(cudaMemsetAsync(&c->sc->done, 0, sizeof(int), c->stream));
+  launch(c, k_residual64, g.blocks, round32(g.threads), smem, (const double*)w.x, (const double*)w.b, r, c->sc,
+         c->partials, c->counter, c->err, g);
+  launch(c, k_scale64, sb, 256, 0, r, n4, 1.0 / (c->h * c->h));
+  CK(cudaGetLastError());
+  return PIC_OK;
 }
 
 int pic_apply_laplacian(pic_ctx* c, const double* x, double* y) {

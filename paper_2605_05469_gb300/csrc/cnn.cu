@@ -27,9 +27,11 @@ struct CnnState {
   __nv_bfloat16 *i1 = nullptr, *i2 = nullptr;
   // crops / loss scratch
   int bmax = 0;
-  double* sums = nullptr;  // [4 * bmax]: ss, ee, den, num
+  double* sums = nullptr;  // [5 * bmax]: ss, den_e, den_r, num_e, num_r
   int* origins = nullptr;  // [3 * bmax]
   double* sums_host = nullptr;
+  float* q = nullptr;      // loss: A_I (y - t)
+  size_t q_cells = 0;
 };
 
 }  // namespace pic
@@ -38,6 +40,7 @@ using namespace pic;
 using namespace pic::cnn;
 
 namespace {
+
 
 int ensure_state(pic_ctx* c) {
   if (c->cnn) return PIC_OK;
@@ -79,8 +82,8 @@ int ensure_batch(pic_ctx* c, int B) {
   s->sums_host = nullptr;
   s->bmax = 0;
   int e;
-  if ((e = dalloc(&s->sums, 4 * (size_t)B)) || (e = dalloc(&s->origins, 3 * (size_t)B))) return e;
-  if (cudaMallocHost(&s->sums_host, 4 * (size_t)B * sizeof(double)) != cudaSuccess) return PIC_ENOMEM;
+  if ((e = dalloc(&s->sums, 5 * (size_t)B)) || (e = dalloc(&s->origins, 3 * (size_t)B))) return e;
+  if (cudaMallocHost(&s->sums_host, 5 * (size_t)B * sizeof(double)) != cudaSuccess) return PIC_ENOMEM;
   s->bmax = B;
   return PIC_OK;
 }
@@ -134,7 +137,7 @@ void cnn_state_free(CnnState* s) {
   dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed);
   dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
   dfree(s->i1); dfree(s->i2);
-  dfree(s->sums); dfree(s->origins);
+  dfree(s->sums); dfree(s->origins); dfree(s->q);
   if (s->sums_host) cudaFreeHost(s->sums_host);
   delete s;
 }
@@ -254,7 +257,7 @@ int pic_cnn_backward(pic_ctx* c, const float* gy, int B, int D) {
 
 int pic_cnn_make_batch(pic_ctx* c, const double* r, const double* a, const double* b, const int* origins_host,
                        int B, int D, float* x, float* t, double h2) {
-  if (!c || !r || !a || !b || !origins_host || !x || !t || B < 1 || D < 16) return PIC_EINVAL;
+  if (!c || !r || !a || !b || !origins_host || !x || !t || B < 1 || D < 16 || D % 16 != 0) return PIC_EINVAL;
   if (!c->has_grid) return PIC_ESTATE;
   int e;
   if ((e = ensure_state(c)) || (e = ensure_batch(c, B))) return e;
@@ -263,12 +266,14 @@ int pic_cnn_make_batch(pic_ctx* c, const double* r, const double* a, const doubl
   CnnState* s = c->cnn;
   CK(cudaMemcpyAsync(s->origins, origins_host, 3 * (size_t)B * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));  // origins_host may be reused by the caller
-  CK(cudaMemsetAsync(s->sums, 0, 4 * (size_t)B * sizeof(double), c->stream));
+  CK(cudaMemsetAsync(s->sums, 0, 5 * (size_t)B * sizeof(double), c->stream));
   dim3 grid(64, B);
   // e = a - b: the crop kernel reads the error as the difference of two fields
-  k_crops_gather_diff<<<grid, 256, 0, c->stream>>>(r, a, b, c->N, s->origins, D, 4, x, t, s->sums, s->sums + B);
+  k_crops_gather_diff<<<grid, 256, 0, c->stream>>>(r, a, b, c->N, s->origins, D, x, t, s->sums);
   ++c->launches;
-  k_crops_scale<<<grid, 256, 0, c->stream>>>(x, t, D, h2, s->sums, s->sums + B, s->sums + 2 * B);
+  k_crops_scale<<<grid, 256, 0, c->stream>>>(x, t, D, h2, s->sums);
+  ++c->launches;
+  k_crops_den<<<grid, 256, 0, c->stream>>>(t, D, s->sums + B, s->sums + 2 * B);
   ++c->launches;
   CK(cudaGetLastError());
   return PIC_OK;
@@ -278,15 +283,26 @@ int pic_cnn_loss(pic_ctx* c, const float* y, const float* t, int B, int D, float
   if (!c || !y || !t || !gy || !loss_host || B < 1) return PIC_EINVAL;
   if (!c->cnn || c->cnn->bmax < B) return PIC_ESTATE;
   CnnState* s = c->cnn;
-  CK(cudaMemsetAsync(s->sums + 3 * B, 0, (size_t)B * sizeof(double), c->stream));
+  const size_t cells = (size_t)B * D * D * D;
+  if (s->q_cells < cells) {
+    dfree(s->q);
+    s->q_cells = 0;
+    int e;
+    if ((e = dalloc(&s->q, cells))) return e;
+    s->q_cells = cells;
+  }
+  CK(cudaMemsetAsync(s->sums + 3 * B, 0, 2 * (size_t)B * sizeof(double), c->stream));
   dim3 grid(64, B);
-  k_loss<<<grid, 256, 0, c->stream>>>(y, t, s->sums + 2 * B, D, B, 4, gy, s->sums + 3 * B);
+  k_loss_q<<<grid, 256, 0, c->stream>>>(y, t, D, s->q, s->sums + 3 * B, s->sums + 4 * B);
+  ++c->launches;
+  k_loss_grad<<<grid, 256, 0, c->stream>>>(y, t, s->q, D, B, s->sums + B, s->sums + 2 * B, gy);
   ++c->launches;
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(s->sums_host, s->sums, 4 * (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(s->sums_host, s->sums, 5 * (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   double L = 0.0;
-  for (int b = 0; b < B; ++b) L += s->sums_host[3 * B + b] / s->sums_host[2 * B + b];
+  for (int b = 0; b < B; ++b)
+    L += s->sums_host[3 * B + b] / s->sums_host[B + b] + s->sums_host[4 * B + b] / s->sums_host[2 * B + b];
   *loss_host = L / B;
   return PIC_OK;
 }

@@ -377,47 +377,156 @@ __global__ void __launch_bounds__(256) k_wgrad(const void* __restrict__ gz_, con
 }
 
 // ---------------------------------------------------------------------------
-// Relative interior loss per crop: num[b] += sum_in (y - t)^2; gy = 2 (y - t) /
-// (den[b] B) inside, 0 outside (den[b] = sum_in t^2, computed with the crops).
+// Training loss per crop: energy norm plus residual norm of d = y - t,
+//   L_b = E(d) / E(t) + |A_I d|^2 / |A_I t|^2,
+// E(d) = sum over grid edges inside R4 (cells at least 4 from every face) of
+// the squared difference across the edge, A_I d = 6 d_i - sum_nb d_j on R5
+// (at least 5 from every face). Pass 1: q = A_I d, num_e[b] += E(d),
+// num_r[b] += |q|^2. Pass 2: gy = (2 sum_{j in R4 nb of i} (d_i - d_j) / E(t)
+// + 2 A_I^T q / |A_I t|^2) / B.
 // ---------------------------------------------------------------------------
-__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ tgt, const double* __restrict__ den,
-                       int D, int B, int border, float* __restrict__ gy, double* num) {
+__device__ __forceinline__ bool in_interior(int x, int y, int z, int D, int border) {
+  return x >= border && x < D - border && y >= border && y < D - border && z >= border && z < D - border;
+}
+
+// 6 v_i - sum of the 6 neighbours of i inside the crop (absent ones count 0).
+__device__ __forceinline__ float crop_stencil(const float* v, int x, int y, int z, int D) {
+  const size_t i = ((size_t)z * D + y) * D + x;
+  float s = 6.f * v[i];
+  if (x > 0) s -= v[i - 1];
+  if (x < D - 1) s -= v[i + 1];
+  if (y > 0) s -= v[i - D];
+  if (y < D - 1) s -= v[i + D];
+  if (z > 0) s -= v[i - (size_t)D * D];
+  if (z < D - 1) s -= v[i + (size_t)D * D];
+  return s;
+}
+
+__global__ void k_loss_q(const float* __restrict__ y, const float* __restrict__ tgt, int D, float* __restrict__ q,
+                         double* num_e, double* num_r) {
   const size_t per = (size_t)D * D * D;
   const int b = blockIdx.y;
-  double acc = 0.0;
+  const float* yb = y + (size_t)b * per;
+  const float* tb = tgt + (size_t)b * per;
+  double ae = 0.0, ar = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % D), yy = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
-    const bool in = x >= border && x < D - border && yy >= border && yy < D - border && z >= border &&
-                    z < D - border;
-    const size_t j = (size_t)b * per + i;
-    float g = 0.f;
-    if (in) {
-      const float d = y[j] - tgt[j];
-      acc += (double)d * d;
-      g = (float)(2.0 * d / (den[b] * B));
+    float v = 0.f;
+    if (in_interior(x, yy, z, D, 4)) {
+      const float di = yb[i] - tb[i];
+      // forward edges inside R4, each once
+      if (in_interior(x + 1, yy, z, D, 4)) {
+        const float dd = di - (yb[i + 1] - tb[i + 1]);
+        ae += (double)dd * dd;
+      }
+      if (in_interior(x, yy + 1, z, D, 4)) {
+        const float dd = di - (yb[i + D] - tb[i + D]);
+        ae += (double)dd * dd;
+      }
+      if (in_interior(x, yy, z + 1, D, 4)) {
+        const float dd = di - (yb[i + (size_t)D * D] - tb[i + (size_t)D * D]);
+        ae += (double)dd * dd;
+      }
+      if (in_interior(x, yy, z, D, 5)) {
+        float s = 6.f * di;
+        s -= yb[i - 1] - tb[i - 1];
+        s -= yb[i + 1] - tb[i + 1];
+        s -= yb[i - D] - tb[i - D];
+        s -= yb[i + D] - tb[i + D];
+        s -= yb[i - (size_t)D * D] - tb[i - (size_t)D * D];
+        s -= yb[i + (size_t)D * D] - tb[i + (size_t)D * D];
+        v = s;
+        ar += (double)v * v;
+      }
     }
-    gy[j] = g;
+    q[(size_t)b * per + i] = v;
   }
   __shared__ double red[32];
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) atomicAdd(&num[b], s);
+  const double se = block_sum(ae, red);
+  const double sr = block_sum(ar, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&num_e[b], se);
+    atomicAdd(&num_r[b], sr);
+  }
+}
+
+__global__ void k_loss_grad(const float* __restrict__ y, const float* __restrict__ tgt,
+                            const float* __restrict__ q, int D, int B, const double* __restrict__ den_e,
+                            const double* __restrict__ den_r, float* __restrict__ gy) {
+  const size_t per = (size_t)D * D * D;
+  const int b = blockIdx.y;
+  const float* yb = y + (size_t)b * per;
+  const float* tb = tgt + (size_t)b * per;
+  const float fe = (float)(2.0 / (den_e[b] * B)), fr = (float)(2.0 / (den_r[b] * B));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), yy = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
+    float g = fr * crop_stencil(q + (size_t)b * per, x, yy, z, D);
+    if (in_interior(x, yy, z, D, 4)) {
+      const float di = yb[i] - tb[i];
+      float gs = 0.f;
+      const int ox[6] = {1, -1, 0, 0, 0, 0}, oy[6] = {0, 0, 1, -1, 0, 0}, oz[6] = {0, 0, 0, 0, 1, -1};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int xn = x + ox[k], yn = yy + oy[k], zn = z + oz[k];
+        if (!in_interior(xn, yn, zn, D, 4)) continue;
+        const size_t j = ((size_t)zn * D + yn) * D + xn;
+        gs += di - (yb[j] - tb[j]);
+      }
+      g += fe * gs;
+    }
+    gy[(size_t)b * per + i] = g;
+  }
+}
+
+// den_e[b] = E(t) over R4 edges, den_r[b] = |A_I t|^2 over R5.
+__global__ void k_crops_den(const float* __restrict__ t, int D, double* den_e, double* den_r) {
+  const size_t per = (size_t)D * D * D;
+  const int b = blockIdx.y;
+  const float* tb = t + (size_t)b * per;
+  double ae = 0.0, ar = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), yy = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
+    if (!in_interior(x, yy, z, D, 4)) continue;
+    const float ti = tb[i];
+    if (in_interior(x + 1, yy, z, D, 4)) {
+      const float d = ti - tb[i + 1];
+      ae += (double)d * d;
+    }
+    if (in_interior(x, yy + 1, z, D, 4)) {
+      const float d = ti - tb[i + D];
+      ae += (double)d * d;
+    }
+    if (in_interior(x, yy, z + 1, D, 4)) {
+      const float d = ti - tb[i + (size_t)D * D];
+      ae += (double)d * d;
+    }
+    if (in_interior(x, yy, z, D, 5)) {
+      const float v = crop_stencil(tb, x, yy, z, D);
+      ar += (double)v * v;
+    }
+  }
+  __shared__ double red[32];
+  const double se = block_sum(ae, red);
+  const double sr = block_sum(ar, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&den_e[b], se);
+    atomicAdd(&den_r[b], sr);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Crops at periodic origins, in FP32, of a residual field r and an error
 // e = a - b (a = converged solution, b = CG iterate): pass 1 gathers and
-// accumulates ss[b] = sum r^2 (whole crop) and ee[b] = sum_in e^2 (interior,
-// border 4); pass 2 scales x = r / s, t = e / (s h2) with s = RMS(r crop) and
-// sets den[b] = ee[b] / (s^2 h2^2) = sum_in t^2.
+// accumulates ss[b] = sum r^2 (whole crop); pass 2 scales x = r / s and
+// t = e / (s h2) with s = RMS(r crop); k_crops_den then gives E(t) and |A_I t|^2.
 // ---------------------------------------------------------------------------
 __global__ void k_crops_gather_diff(const double* __restrict__ fr, const double* __restrict__ fa,
                                     const double* __restrict__ fb, int N, const int* __restrict__ origins, int D,
-                                    int border, float* __restrict__ xr, float* __restrict__ xe, double* ss,
-                                    double* ee) {
+                                    float* __restrict__ xr, float* __restrict__ xe, double* ss) {
   const size_t per = (size_t)D * D * D;
   const int b = blockIdx.y;
   const int ox = origins[3 * b], oy = origins[3 * b + 1], oz = origins[3 * b + 2];
-  double s1 = 0.0, s2 = 0.0;
+  double s1 = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)(i / ((size_t)D * D));
     const size_t src = ((size_t)((oz + z) % N) * N + (size_t)((oy + y) % N)) * N + (size_t)((ox + x) % N);
@@ -425,20 +534,13 @@ __global__ void k_crops_gather_diff(const double* __restrict__ fr, const double*
     xr[(size_t)b * per + i] = (float)rv;
     xe[(size_t)b * per + i] = (float)ev;
     s1 += rv * rv;
-    const bool in = x >= border && x < D - border && y >= border && y < D - border && z >= border && z < D - border;
-    if (in) s2 += ev * ev;
   }
   __shared__ double red[32];
   const double a = block_sum(s1, red);
-  const double c = block_sum(s2, red);
-  if (threadIdx.x == 0) {
-    atomicAdd(&ss[b], a);
-    atomicAdd(&ee[b], c);
-  }
+  if (threadIdx.x == 0) atomicAdd(&ss[b], a);
 }
 
-__global__ void k_crops_scale(float* xr, float* xe, int D, double h2, const double* ss, const double* ee,
-                              double* den) {
+__global__ void k_crops_scale(float* xr, float* xe, int D, double h2, const double* ss) {
   const size_t per = (size_t)D * D * D;
   const int b = blockIdx.y;
   const double s = sqrt(ss[b] / (double)per);
@@ -448,7 +550,6 @@ __global__ void k_crops_scale(float* xr, float* xe, int D, double h2, const doub
     xr[(size_t)b * per + i] *= ir;
     xe[(size_t)b * per + i] *= ie;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) den[b] = s > 0.0 ? ee[b] / (s * s * h2 * h2) : 1.0;
 }
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,7 @@ struct Scalars {
   double rmax2;     // MIXED: (r, r) at the last FP64 residual recomputation
   double delta2;    // MIXED: reliable-update trigger factor squared
   double rz;        // FCG: (r, z)
-  double rz_old;    // FCG: (r_new, z_old), reduced by the update kernel
+  double rz_old;    // unused
   double true_rr;   // MIXED: last recomputed FP64 (r, r)
   double sum0, sum1;  // mean projections
   double scale;     // CNN: RMS of r

@@ -15,6 +15,7 @@ struct SolverWs {
   float *x32 = nullptr, *r32 = nullptr, *p32[2] = {nullptr, nullptr};
   // flexible CG with the learned preconditioner
   float* z32[2] = {nullptr, nullptr};
+  float* q32 = nullptr;  // A p of the last direction
   // shared
   double* b = nullptr;
 };

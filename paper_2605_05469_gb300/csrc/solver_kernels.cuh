@@ -506,34 +506,50 @@ __global__ void __launch_bounds__(256) k_finish(const double* __restrict__ x, do
 }
 
 // ---------------------------------------------------------------------------
-// Flexible CG (Golub & Ye 1999) with a nonlinear preconditioner z = P(r):
-// (r, z) -> descent guard, beta = (r, z_new - z_old) / (r_old, z_old).
-// init: first direction (beta = 0). When (r, z) <= 0 or is not finite the
-// iteration uses the Jacobi direction z = r / 6 (scaled operator diagonal).
+// Flexible CG, FCG(1) (Notay 2000), with a nonlinear preconditioner z = P(r):
+// the new direction is z made A-conjugate to the previous p,
+// beta = -(z, A p_prev) / (p_prev, A p_prev), with A p_prev = q stored by the
+// pap kernel and (p_prev, A p_prev) = sc->pq. Reduces (r, z), (z, q), (r, q).
+// Descent guard: when (r, z) <= 0 or is not finite the iteration uses the
+// Jacobi direction z = r / 6 (scaled operator diagonal), whose dots follow
+// from (r, r) and (r, q). init: first direction, beta = 0.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fcg_dot(const float* __restrict__ r, const float* __restrict__ z,
-                                                 size_t n4, Scalars* sc, double* partials, unsigned* counter,
-                                                 int init) {
+                                                 const float* __restrict__ q, size_t n4, Scalars* sc,
+                                                 double* partials, unsigned* counter, int init) {
   if (sc->done) return;
-  CompSum acc;
+  CompSum arz, azq, arq;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
     const V4<float> rv = ldg4(r + 4 * i), zv = ldg4(z + 4 * i);
-    float d = rv.v[0] * zv.v[0];
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+    if (init) {
 #pragma unroll
-    for (int k = 1; k < 4; ++k) d = fmaf(rv.v[k], zv.v[k], d);
-    acc.add(d);
+      for (int k = 0; k < 4; ++k) d0 = fmaf(rv.v[k], zv.v[k], d0);
+    } else {
+      const V4<float> qv = ldg4(q + 4 * i);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        d0 = fmaf(rv.v[k], zv.v[k], d0);
+        d1 = fmaf(zv.v[k], qv.v[k], d1);
+        d2 = fmaf(rv.v[k], qv.v[k], d2);
+      }
+    }
+    arz.add(d0);
+    azq.add(d1);
+    arq.add(d2);
   }
-  double v[1] = {acc.value()}, tot[1];
-  if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-    double rz = tot[0];
+  double v[3] = {arz.value(), azq.value(), arq.value()}, tot[3];
+  if (grid_reduce_last<3>(v, partials, counter, tot) && threadIdx.x == 0) {
+    double rz = tot[0], zq = tot[1];
     sc->fallback_now = 0;
-    if (!(rz > 0.0) || !isfinite(rz)) {
+    if (!(rz > 0.0) || !isfinite(rz) || !isfinite(zq)) {
       sc->fallback_now = 1;
       sc->fallbacks += 1;
       rz = sc->rr / 6.0;
+      zq = tot[2] / 6.0;
     }
-    sc->beta = init ? 0.0 : (rz - sc->rz_old) / sc->rz;
+    sc->beta = init ? 0.0 : -zq / sc->pq;
     sc->rz = rz;
     if (!isfinite(sc->beta)) sc->done = 3;
   }
@@ -548,6 +564,17 @@ __global__ void __launch_bounds__(256) k_fcg_fallback(const float* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 4; ++k) v.v[k] *= (1.0f / 6.0f);
     st4(z + 4 * i, v);
+  }
+}
+
+// a *= s (elementwise, FP64).
+__global__ void __launch_bounds__(256) k_scale64(double* __restrict__ a, size_t n4, double sc) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    V4<double> v = ldg4(a + 4 * i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v.v[k] *= sc;
+    st4(a + 4 * i, v);
   }
 }
 

@@ -175,6 +175,35 @@ def test_fcg_cnn_solve_reaches_true_residual(pg, N):
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+def jacobi_network_weights():
+    """Weights for which N(x) = x / 6 exactly: channel 0 carries x, channel 1
+    carries -x through the three leaky ReLUs (act^3(x) - act^3(-x) =
+    (1 + 1/512) x for slope 1/8), and the last layer recombines them. As a
+    preconditioner this is the Jacobi direction r / 6 of the scaled operator."""
+    w1 = np.zeros((16, 1, 27)); w2 = np.zeros((16, 16, 27)); w3 = np.zeros((16, 16, 27)); w4 = np.zeros((1, 16, 27))
+    w1[0, 0, 13], w1[1, 0, 13] = 1.0, -1.0
+    w2[0, 0, 13] = w2[1, 1, 13] = 1.0
+    w3[0, 0, 13] = w3[1, 1, 13] = 1.0
+    a = 512.0 / 513.0 / 6.0
+    w4[0, 0, 13], w4[0, 1, 13] = a, -a
+    return np.concatenate([w.reshape(-1) for w in (w1, w2, w3, w4)]).astype(np.float32)
+
+
+def test_fcg_with_jacobi_network_takes_the_jacobi_iterations(pg):
+    """The whole inference + flexible-CG chain with a network that computes
+    the Jacobi direction must converge like mixed Jacobi-CG."""
+    N = 64
+    c = pg.Context().init(N, 0, 0)
+    c.cnn_set_weights(jacobi_network_weights())
+    b = torch.from_numpy(inputs.landau_noise_rhs(N, 11)).cuda()
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+    ref = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED)
+    phi.zero_()
+    got = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, precond=pg.PC_CNN)
+    assert got["fallbacks"] == 0, got
+    assert got["iters"] <= 1.1 * ref["iters"] + 5, (got, ref)
+
+
 def test_cnn_requires_weights_and_mixed_precision(pg):
     c = pg.Context().init(16, 0, 0)
     rho = torch.zeros(16 ** 3, dtype=torch.float64, device="cuda")

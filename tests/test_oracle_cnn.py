@@ -96,8 +96,8 @@ def test_network_weight_count_and_homogeneity():
 def test_loss_gradient_finite_differences():
     rng = np.random.default_rng(7)
     ws = cnn.init_weights(3)
-    r = [rng.normal(size=(10, 10, 10)) for _ in range(2)]
-    e = [rng.normal(size=(10, 10, 10)) for _ in range(2)]
+    r = [rng.normal(size=(12, 12, 12)) for _ in range(2)]
+    e = [rng.normal(size=(12, 12, 12)) for _ in range(2)]
     h = 0.3
     loss, grads = cnn.loss_and_grads(ws, r, e, h)
     eps = 1e-6
@@ -108,13 +108,61 @@ def test_loss_gradient_finite_differences():
         assert np.isclose(grads[layer][idx], fd, rtol=1e-6, atol=1e-10)
 
 
+def test_interior_stencil_closed_forms():
+    # a linear field has zero 7-point stencil; a quadratic x^2 gives -2
+    m5 = cnn.interior_mask((12, 12, 12), border=5)
+    x = np.broadcast_to(np.arange(12.0)[None, None, :], (12, 12, 12)).copy()
+    assert np.all(cnn.interior_stencil(3.0 * x + 1.0, m5) == 0.0)
+    q = cnn.interior_stencil(x * x, m5)
+    assert np.all(q[m5] == -2.0) and np.all(q[~m5] == 0.0)
+    # the adjoint: <A_I d, q> = <d, A_I^T q> for q supported on the mask
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(12, 12, 12))
+    qq = np.where(m5, rng.normal(size=(12, 12, 12)), 0.0)
+    assert np.isclose(np.sum(cnn.interior_stencil(d, m5) * qq), np.sum(d * cnn.interior_stencil_adjoint(qq)))
+
+
+def test_interior_energy_closed_forms():
+    # d = x index on a 10^3 crop; the valid interior is cells 4..5 along each
+    # axis, so it holds one x-edge per (y, z) row, 2 x 2 rows, each differing
+    # by 1, and no y- or z-edge with a difference
+    m = cnn.interior_mask((10, 10, 10))
+    d = np.broadcast_to(np.arange(10.0)[None, None, :], (10, 10, 10)).copy()
+    assert cnn.interior_energy(d, m) == 4.0
+    assert cnn.interior_energy(np.full((10, 10, 10), 3.0), m) == 0.0
+    full = np.ones((6, 6, 6), dtype=bool)
+    v = np.random.default_rng(0).normal(size=(6, 6, 6))
+    # E is quadratic: E(v) = v . grad / 2
+    assert np.isclose(cnn.interior_energy(v, full), 0.5 * np.sum(v * cnn.interior_energy_grad(v, full)))
+
+
+def test_energy_below_target_gives_descent_direction():
+    # on a periodic grid, E(z - e) < E(e) implies r.z > 0 with r = A e
+    rng = np.random.default_rng(3)
+    N, h = 8, 0.5
+    e = rng.normal(size=N ** 3)
+    r = pic.apply_A(e, N, h)
+    for _ in range(20):
+        z = e + 0.9 * rng.uniform() * np.linalg.norm(e) * rng.normal(size=N ** 3) / np.sqrt(N ** 3)
+        d = z - e
+        if d @ pic.apply_A(d, N, h) < e @ r:
+            assert r @ z > 0
+
+
+def test_residual_loss_ignores_constant_offsets():
+    # a constant offset of the prediction (null space of the stencil) costs nothing
+    m5 = cnn.interior_mask((12, 12, 12), border=5)
+    t = np.random.default_rng(1).normal(size=(12, 12, 12))
+    assert np.allclose(cnn.interior_stencil(t + 2.5, m5), cnn.interior_stencil(t, m5), atol=1e-12)
+
+
 def test_loss_ignores_crop_border():
     rng = np.random.default_rng(8)
     ws = cnn.init_weights(3)
-    r = rng.normal(size=(10, 10, 10))
-    e = rng.normal(size=(10, 10, 10))
+    r = rng.normal(size=(12, 12, 12))
+    e = rng.normal(size=(12, 12, 12))
     l0, _ = cnn.loss_and_grads(ws, [r], [e], 1.0)
-    e2 = e.copy(); e2[0, :, :] += 5.0; e2[:, 9, :] -= 2.0     # border only
+    e2 = e.copy(); e2[0:4, :, :] += 5.0; e2[:, 8:, :] -= 2.0     # within 4 cells of a face only
     l1, _ = cnn.loss_and_grads(ws, [r], [e2], 1.0)
     assert l0 == l1
     # an input change 4 cells from the face moves interior outputs only through the
@@ -124,7 +172,7 @@ def test_loss_ignores_crop_border():
     y1, _ = cnn.forward(r, ws)
     y2, _ = cnn.forward(r2, ws)
     m = cnn.interior_mask(r.shape)
-    assert np.array_equal((y1 != y2) & m & (np.arange(10)[None, None, :] >= 5), np.zeros_like(m))
+    assert np.array_equal((y1 != y2) & m & (np.arange(12)[None, None, :] >= 5), np.zeros_like(m))
 
 
 def test_adam_first_step_closed_form():
