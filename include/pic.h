@@ -154,10 +154,12 @@ int pic_residual(pic_ctx *c, const double *rho, const double *phi, double *r);
  * Learned preconditioner (used with PIC_PC_CNN inside flexible CG). The paper
  * lists Jacobi, Richardson, Gauss-Seidel and SSOR preconditioners for its PCG
  * solver (Sec. 3.2); this one is a 4-layer 3x3x3 conv3d network
- * 1 -> 16 -> 16 -> 16 -> 1 channels, no biases, leaky ReLU (slope 1/8)
- * between layers, periodic padding, BF16 weights and activations with FP32
- * accumulation on the tensor cores. As a preconditioner it maps a residual r
- * to z = s N(r / s), s = RMS(r).
+ * 1 -> 16 -> 16 -> 16 -> 1 channels, no biases, identity activations,
+ * periodic padding, whose layers 3 and 4 are the adjoints of layers 2 and 1
+ * (channels transposed, taps flipped): N = G^T G is symmetric positive
+ * semi-definite for any weights (a learned factorised sparse approximate
+ * inverse). BF16 weights and activations, FP32 accumulation on the tensor
+ * cores. As a preconditioner it maps a residual r to z = s N(r / s), s = RMS(r).
  *
  * Weights (14 688 FP32 values) are the four layers concatenated, each in
  * the order w[out][in][tz][ty][tx] with tap offset (tz-1, ty-1, tx-1):
@@ -166,18 +168,27 @@ int pic_residual(pic_ctx *c, const double *rho, const double *phi, double *r);
  * ------------------------------------------------------------------------ */
 #define PIC_CNN_WEIGHTS 14688
 
-/* Set the FP32 master weights from host memory (resets Adam). Synchronises. */
+/* Set the FP32 master weights from host memory (resets Adam); layers 3 and 4
+ * are replaced by the adjoints of layers 2 and 1. Synchronises. */
 int pic_cnn_set_weights(pic_ctx *c, const float *w_host);
 /* Copy the FP32 master weights / accumulated gradients to host memory. */
 int pic_cnn_get_weights(pic_ctx *c, float *w_host);
 int pic_cnn_get_grads(pic_ctx *c, float *g_host);
 
+/* Preconditioner on the context grid: z = N r for device FP32 [N^3] r, z
+ * (periodic). N is linear, so for N % 32 == 0 it runs as its composed 9^3
+ * kernel K (FP32, rebuilt from the master weights at every weight update) on
+ * the CUDA cores; other grids (N % 16 == 0) run the 4 BF16 tensor-core convs. */
+int pic_cnn_apply(pic_ctx *c, const float *r, float *z);
+
 /* Forward pass over B crops: y = N(x) (device FP32 [B][D^3] each); keeps the
  * activations for pic_cnn_backward. */
 int pic_cnn_forward(pic_ctx *c, const float *x, float *y, int B, int D);
-/* Backward pass of the last forward: adds d(sum gy * y)/dw to the gradients
- * (data gradients run as flipped-tap convolutions on the tensor cores,
- * weight gradients on the CUDA cores in FP32). */
+/* Backward pass of the last forward: adds d(sum gy * y)/dw of the tied
+ * network to the gradients (layers 1 and 2 receive their own gradient plus
+ * the adjoint of layer 4's and 3's; layers 3 and 4 hold the adjoints of
+ * those sums). Data gradients run as adjoint convolutions on the tensor
+ * cores, weight gradients on the CUDA cores in FP32. */
 int pic_cnn_backward(pic_ctx *c, const float *gy, int B, int D);
 /* One Adam step (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8) on the
  * accumulated gradients, which are then zeroed. */

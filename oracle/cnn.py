@@ -11,9 +11,13 @@ learned variant the GPU library offers, from standard published methods:
       y[o, p] = sum_{c, t} w[o, c, t] * x[c, p + t - 1].
   Backward (data): gx[c, p] = sum_{o, t} w[o, c, t] * gy[o, p - t + 1].
   Backward (weights): gw[o, c, t] = sum_p gy[o, p] * x[c, p + t - 1].
-* network N: conv(1->16), act, conv(16->16), act, conv(16->16), act,
-  conv(16->1); no biases (14 688 weights); act = leaky ReLU with negative
-  slope 1/8. N is positively homogeneous: N(c x) = c N(x) for c > 0.
+* network N = G^T G with G = conv(16->16) o conv(1->16): four 3x3x3 convs
+  1 -> 16 -> 16 -> 16 -> 1, no biases, identity activations, where layers 3
+  and 4 are the adjoints of layers 2 and 1 (channels transposed, taps
+  flipped): w3 = adj(w2), w4 = adj(w1). N is then linear, symmetric and
+  positive semi-definite for any weights, a learned factorised sparse
+  approximate inverse (Kolotilina & Yeremin 1993) with 9^3 support;
+  14 688 weights of which 7 344 (w1, w2) are free.
 * preconditioner P(r) = h^2 * s * N(r / s) - mean, s = RMS(r).
 * training loss on a crop, the sum of the error in the energy (A-) norm and
   the residual norm, each relative to the target's:
@@ -40,16 +44,17 @@ import numpy as np
 
 from . import pic
 
-LEAK = 0.125
 CHANNELS = (1, 16, 16, 16, 1)
 
 
-def act(z):
-    return np.where(z > 0.0, z, LEAK * z)
+def adjoint(w):
+    """Weights of the adjoint conv: w[o][c][tz][ty][tx] -> w[c][o][2-tz][2-ty][2-tx]."""
+    return np.ascontiguousarray(np.transpose(w, (1, 0, 2, 3, 4))[:, :, ::-1, ::-1, ::-1])
 
 
-def act_grad(z):
-    return np.where(z > 0.0, 1.0, LEAK)
+def tie(w1, w2):
+    """The four layers of N = G^T G from the free weights w1, w2."""
+    return [w1, w2, adjoint(w2), adjoint(w1)]
 
 
 def _shift(x, t):
@@ -87,40 +92,41 @@ def conv3d_bwd_weight(x, gy):
 
 
 def init_weights(seed):
-    """He-style random init (normal, std sqrt(2 / fan_in)) from a seeded generator."""
+    """Random free weights (normal, std sqrt(2 / fan_in)), tied into 4 layers."""
     rng = np.random.default_rng(seed)
-    ws = []
-    for i in range(4):
-        cin, cout = CHANNELS[i], CHANNELS[i + 1]
-        ws.append(rng.normal(0.0, np.sqrt(2.0 / (27 * cin)), size=(cout, cin, 3, 3, 3)))
-    return ws
+    w1 = rng.normal(0.0, np.sqrt(2.0 / 27.0), size=(16, 1, 3, 3, 3))
+    w2 = rng.normal(0.0, np.sqrt(2.0 / (27.0 * 16)), size=(16, 16, 3, 3, 3))
+    return tie(w1, w2)
 
 
 def forward(x, ws):
     """N(x) for x[Z, Y, X]; returns (y[Z, Y, X], cache for ``backward``)."""
     a = x[None]
     cache = [a]
-    for i, w in enumerate(ws):
-        z = conv3d(a, w)
-        if i < 3:
-            cache.append(z)
-            a = act(z)
-            cache.append(a)
-        else:
-            a = z
+    for w in ws:
+        a = conv3d(a, w)
+        cache.append(a)
     return a[0], cache
 
 
 def backward(gy, ws, cache):
-    """Weight gradients of sum(gy * N(x)) given the forward cache."""
+    """Gradients of sum(gy * N(x)) with respect to each of the 4 layers'
+    weights, as if they were independent (see ``tied_grads``)."""
     g = gy[None]
     grads = [None] * 4
     for i in (3, 2, 1, 0):
-        a_in = cache[2 * i]
-        grads[i] = conv3d_bwd_weight(a_in, g)
+        grads[i] = conv3d_bwd_weight(cache[i], g)
         if i > 0:
-            g = conv3d_bwd_data(g, ws[i]) * act_grad(cache[2 * i - 1])
+            g = conv3d_bwd_data(g, ws[i])
     return grads
+
+
+def tied_grads(grads):
+    """Gradients of the tied network: g1 + adj(g4) and g2 + adj(g3) for the
+    free weights, repeated through the adjoint for layers 3 and 4."""
+    g1 = grads[0] + adjoint(grads[3])
+    g2 = grads[1] + adjoint(grads[2])
+    return tie(g1, g2)
 
 
 def interior_mask(shape, border=4):
@@ -180,7 +186,8 @@ def interior_stencil_adjoint(q):
 
 def loss_and_grads(ws, r_crops, e_crops, h):
     """Mean over crops of the energy-norm plus residual-norm loss, and its
-    weight gradients."""
+    gradients with respect to the tied weights (4 layers, layers 3-4 the
+    adjoints of the gradients of the free layers 2-1)."""
     B = len(r_crops)
     total = 0.0
     gsum = [np.zeros_like(w) for w in ws]
@@ -198,7 +205,7 @@ def loss_and_grads(ws, r_crops, e_crops, h):
         q = interior_stencil(d, m5)
         total += interior_energy(d, m4) / den_e + np.sum(q * q) / den_r
         gy = (interior_energy_grad(d, m4) / den_e + 2.0 * interior_stencil_adjoint(q) / den_r) / B
-        for acc, g in zip(gsum, backward(gy, ws, cache)):
+        for acc, g in zip(gsum, tied_grads(backward(gy, ws, cache))):
             acc += g
     return total / B, gsum
 

@@ -104,6 +104,7 @@ _SIGS = {
     "pic_cnn_set_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_get_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_cnn_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int]),
     "pic_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -313,6 +314,10 @@ class Context:
         g = np.empty(CNN_WEIGHTS, dtype=np.float32)
         _check(lib().pic_cnn_get_grads(self.h, g.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_get_grads")
         return g
+
+    def cnn_apply(self, r, z):
+        _check(lib().pic_cnn_apply(self.h, _dptr(r, "float32", self.n, "r"), _dptr(z, "float32", self.n, "z")),
+               "pic_cnn_apply")
 
     def cnn_forward(self, x, y, B, D):
         n = B * D ** 3

@@ -32,6 +32,9 @@ struct CnnState {
   double* sums_host = nullptr;
   float* q = nullptr;      // loss: A_I (y - t)
   size_t q_cells = 0;
+  float* K = nullptr;      // composed 9^3 kernel of N = G^T G (FP32)
+  cnn::K729 K_host;        // its host copy (launch parameter)
+  bool K_stale = true;     // the device kernel changed since the host copy
 };
 
 }  // namespace pic
@@ -48,7 +51,7 @@ int ensure_state(pic_ctx* c) {
   if (!s) return PIC_ENOMEM;
   int e;
   if ((e = dalloc(&s->w, kWeights)) || (e = dalloc(&s->g, kWeights)) || (e = dalloc(&s->m, kWeights)) ||
-      (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes))) {
+      (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes)) || (e = dalloc(&s->K, 729))) {
     cnn_state_free(s);
     return e;
   }
@@ -94,8 +97,8 @@ bool dims_ok(int NX, int NY, int NZ) {
 
 template <int CIN>
 int conv(pic_ctx* c, const void* in, void* out, const unsigned char* w, int mode, int NX, int NY, int NZ, int B,
-         const __nv_bfloat16* gate = nullptr, const double* in_src = nullptr, double in_mul = 0.0,
-         int in_mode = SCALE_ONE, const double* out_src = nullptr, double out_mul = 0.0, int out_mode = SCALE_ONE) {
+         const double* in_src = nullptr, double in_mul = 0.0, int in_mode = SCALE_ONE,
+         const double* out_src = nullptr, double out_mul = 0.0, int out_mode = SCALE_ONE) {
   static bool configured = false;
   const size_t smem = conv_smem_bytes<CIN>();
   if (!configured) {
@@ -104,7 +107,7 @@ int conv(pic_ctx* c, const void* in, void* out, const unsigned char* w, int mode
   }
   ConvParams P;
   P.NX = NX; P.NY = NY; P.NZ = NZ; P.B = B;
-  P.in = in; P.out = out; P.gate = gate; P.w = w;
+  P.in = in; P.out = out; P.w = w;
   P.in_scale_src = in_src; P.in_scale_mul = in_mul; P.in_scale_mode = in_mode;
   P.out_scale_src = out_src; P.out_scale_mul = out_mul; P.out_scale_mode = out_mode;
   P.err = c->err;
@@ -123,7 +126,10 @@ int wgrad(pic_ctx* c, const void* gz, const void* a, int D, int B, float* dW) {
 }
 
 int repack(pic_ctx* c) {
+  launch(c, k_tie_weights, 27, 256, 0, c->cnn->w);
   launch(c, k_pack_weights, 32, 256, 0, (const float*)c->cnn->w, c->cnn->packed);
+  launch(c, k_compose, 1, 256, 0, (const float*)c->cnn->w, c->cnn->K);
+  c->cnn->K_stale = true;
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -134,7 +140,7 @@ namespace pic {
 
 void cnn_state_free(CnnState* s) {
   if (!s) return;
-  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed);
+  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K);
   dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
   dfree(s->i1); dfree(s->i2);
   dfree(s->sums); dfree(s->origins); dfree(s->q);
@@ -147,6 +153,23 @@ bool cnn_ready(const pic_ctx* c) { return c->cnn && c->cnn->has_weights; }
 int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) {
   CnnState* s = c->cnn;
   const int N = c->N;
+  if (N % KX == 0) {
+    // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
+    static bool configured = false;
+    if (!configured) {
+      CK(cudaFuncSetAttribute((const void*)k_apply_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmem));
+      configured = true;
+    }
+    if (s->K_stale) {
+      CK(cudaMemcpyAsync(s->K_host.k, s->K, sizeof(s->K_host.k), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      s->K_stale = false;
+    }
+    const unsigned blocks = (unsigned)((N / KX) * (N / KY) * (N / KZ));
+    launch(c, k_apply_k, blocks, KX * KY, kApplySmem, r, z, N, s->K_host);
+    CK(cudaGetLastError());
+    return PIC_OK;
+  }
   if (!dims_ok(N, N, N)) return PIC_EINVAL;
   if (s->inf_cells < n) {
     dfree(s->i1); dfree(s->i2);
@@ -158,12 +181,11 @@ int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) 
   const double inv_n = 1.0 / (double)n;
   int e;
   // z = s N(r / s), s = RMS(r) = sqrt(rr / n)
-  if ((e = conv<1>(c, r, s->i1, s->packed + kPackFwd1, OUT_ACT_BF16, N, N, N, 1, nullptr, rr, inv_n, SCALE_RSQRT)))
-    return e;
-  if ((e = conv<16>(c, s->i1, s->i2, s->packed + kPackFwd2, OUT_ACT_BF16, N, N, N, 1))) return e;
-  if ((e = conv<16>(c, s->i2, s->i1, s->packed + kPackFwd3, OUT_ACT_BF16, N, N, N, 1))) return e;
-  return conv<16>(c, s->i1, z, s->packed + kPackFwd4, OUT_SCALED_F32, N, N, N, 1, nullptr, nullptr, 0.0,
-                  SCALE_ONE, rr, inv_n, SCALE_SQRT);
+  if ((e = conv<1>(c, r, s->i1, s->packed + kPackFwd1, OUT_BF16, N, N, N, 1, rr, inv_n, SCALE_RSQRT))) return e;
+  if ((e = conv<16>(c, s->i1, s->i2, s->packed + kPackFwd2, OUT_BF16, N, N, N, 1))) return e;
+  if ((e = conv<16>(c, s->i2, s->i1, s->packed + kPackFwd3, OUT_BF16, N, N, N, 1))) return e;
+  return conv<16>(c, s->i1, z, s->packed + kPackFwd4, OUT_SCALED_F32, N, N, N, 1, nullptr, 0.0, SCALE_ONE, rr,
+                  inv_n, SCALE_SQRT);
 }
 
 }  // namespace pic
@@ -214,6 +236,13 @@ int pic_cnn_conv_raw(pic_ctx* c, int which, const void* in, float* out, int B, i
   return conv<16>(c, in, out, w, OUT_RAW_F32, D, D, D, B);
 }
 
+int pic_cnn_apply(pic_ctx* c, const float* r, float* z) {
+  if (!c || !r || !z) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  return cnn_apply(c, r, z, nullptr, c->n);
+}
+
 int pic_cnn_forward(pic_ctx* c, const float* x, float* y, int B, int D) {
   if (!c || !x || !y || B < 1) return PIC_EINVAL;
   if (!dims_ok(D, D, D)) return PIC_EINVAL;
@@ -222,9 +251,9 @@ int pic_cnn_forward(pic_ctx* c, const float* x, float* y, int B, int D) {
   const size_t cells = (size_t)B * D * D * D;
   int e;
   if ((e = ensure_train(c, cells))) return e;
-  if ((e = conv<1>(c, x, s->a1, s->packed + kPackFwd1, OUT_ACT_BF16, D, D, D, B))) return e;
-  if ((e = conv<16>(c, s->a1, s->a2, s->packed + kPackFwd2, OUT_ACT_BF16, D, D, D, B))) return e;
-  if ((e = conv<16>(c, s->a2, s->a3, s->packed + kPackFwd3, OUT_ACT_BF16, D, D, D, B))) return e;
+  if ((e = conv<1>(c, x, s->a1, s->packed + kPackFwd1, OUT_BF16, D, D, D, B))) return e;
+  if ((e = conv<16>(c, s->a1, s->a2, s->packed + kPackFwd2, OUT_BF16, D, D, D, B))) return e;
+  if ((e = conv<16>(c, s->a2, s->a3, s->packed + kPackFwd3, OUT_BF16, D, D, D, B))) return e;
   if ((e = conv<16>(c, s->a3, y, s->packed + kPackFwd4, OUT_SCALED_F32, D, D, D, B))) return e;
   s->last_x = x;
   s->last_B = B;
@@ -242,17 +271,18 @@ int pic_cnn_backward(pic_ctx* c, const float* gy, int B, int D) {
   float* g2 = s->g + kLayerOff[1];
   float* g1 = s->g + kLayerOff[0];
   int e;
-  // layer 4: dW4 from (gy, a3); gradient to a3 gated by act'(z3)
+  // the activations are the identity, so each data gradient is the adjoint
+  // conv of the layer's own gradient; weight gradients per layer, then tied
   if ((e = wgrad<16, 1>(c, gy, s->a3, D, B, g4))) return e;
-  if ((e = conv<1>(c, gy, s->ga, s->packed + kPackBwd4, OUT_GATED_BF16, D, D, D, B, s->a3))) return e;
-  // layer 3
+  if ((e = conv<1>(c, gy, s->ga, s->packed + kPackBwd4, OUT_BF16, D, D, D, B))) return e;
   if ((e = wgrad<16, 16>(c, s->ga, s->a2, D, B, g3))) return e;
-  if ((e = conv<16>(c, s->ga, s->gb, s->packed + kPackBwd3, OUT_GATED_BF16, D, D, D, B, s->a2))) return e;
-  // layer 2
+  if ((e = conv<16>(c, s->ga, s->gb, s->packed + kPackBwd3, OUT_BF16, D, D, D, B))) return e;
   if ((e = wgrad<16, 16>(c, s->gb, s->a1, D, B, g2))) return e;
-  if ((e = conv<16>(c, s->gb, s->ga, s->packed + kPackBwd2, OUT_GATED_BF16, D, D, D, B, s->a1))) return e;
-  // layer 1
-  return wgrad<1, 16>(c, s->ga, s->last_x, D, B, g1);
+  if ((e = conv<16>(c, s->gb, s->ga, s->packed + kPackBwd2, OUT_BF16, D, D, D, B))) return e;
+  if ((e = wgrad<1, 16>(c, s->ga, s->last_x, D, B, g1))) return e;
+  launch(c, k_tie_grads, 27, 256, 0, s->g);
+  CK(cudaGetLastError());
+  return PIC_OK;
 }
 
 int pic_cnn_make_batch(pic_ctx* c, const double* r, const double* a, const double* b, const int* origins_host,

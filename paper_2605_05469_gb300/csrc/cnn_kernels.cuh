@@ -1,8 +1,11 @@
 // Kernels of the learned preconditioner: a 4-layer 3x3x3 conv3d network
-// (1 -> 16 -> 16 -> 16 -> 1 channels, no biases, leaky ReLU with slope 1/8)
-// applied with periodic wrap, its training (dgrad, wgrad, loss, Adam) and
-// crop extraction. The paper solves the Poisson system with preconditioned CG
-// (Sec. 3.2); this learned preconditioner is used inside flexible CG.
+// (1 -> 16 -> 16 -> 16 -> 1 channels, no biases, identity activations) with
+// periodic wrap whose layers 3 and 4 are the adjoints of layers 2 and 1, so
+// N = G^T G is symmetric positive semi-definite (a learned factorised sparse
+// approximate inverse); its training (data and weight gradients, loss, Adam)
+// and crop extraction. The paper solves the Poisson system with
+// preconditioned CG (Sec. 3.2); this learned preconditioner is used inside
+// flexible CG.
 //
 // Convolutions run on the 5th-generation tensor cores as implicit GEMMs:
 // one CTA owns an 8 (x) x 16 (y) x 4 (z) output tile; M = 128 output cells of
@@ -29,7 +32,6 @@ namespace cnn {
 constexpr int kLayers = 4;
 constexpr int kWeights = 14688;  // 16*27 + 16*16*27 + 16*16*27 + 16*27
 constexpr int kLayerOff[5] = {0, 432, 7344, 14256, 14688};
-constexpr float kLeak = 0.125f;
 
 // Output tile and halo tile of one CTA.
 constexpr int TX = 8, TY = 16, ZT = 4;
@@ -43,8 +45,7 @@ constexpr int kThreads = 128;
 
 // Epilogue modes.
 enum : int {
-  OUT_ACT_BF16 = 0,    // bf16 x16 = leaky_relu(acc)
-  OUT_GATED_BF16 = 1,  // bf16 x16 = acc * (gate > 0 ? 1 : 1/8), gate = forward activation
+  OUT_BF16 = 0,        // bf16 x16 = acc
   OUT_SCALED_F32 = 2,  // f32 x1  = scale * acc[channel 0]
   OUT_RAW_F32 = 3,     // f32 x16 = acc (tests)
 };
@@ -63,7 +64,6 @@ struct ConvParams {
   int NX, NY, NZ, B;       // per-sample grid (periodic) and batch
   const void* in;          // CIN 16: bf16 [cells][16]; CIN 1: f32 [cells]
   void* out;
-  const __nv_bfloat16* gate;  // OUT_GATED_BF16: forward activation [cells][16]
   const unsigned char* w;     // canonical BF16 weights of this conv
   const double* in_scale_src;  // CIN 1 input multiplier (see scale_from)
   double in_scale_mul;
@@ -219,21 +219,10 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvParams P, int mode) {
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zt * 16), v);
       const size_t cell = sbase + ((size_t)(z0 + zt) * P.NY + (y0 + ly)) * P.NX + (x0 + lx);
-      if (mode == OUT_ACT_BF16 || mode == OUT_GATED_BF16) {
-        float g[16];
-        if (mode == OUT_GATED_BF16) {
-          const uint4* gp = reinterpret_cast<const uint4*>(P.gate) + 2 * cell;
-          uint4 q[2] = {__ldg(gp), __ldg(gp + 1)};
-          const __nv_bfloat16* gb = reinterpret_cast<const __nv_bfloat16*>(q);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) g[i] = __bfloat162float(gb[i]) > 0.f ? 1.f : kLeak;
-        }
+      if (mode == OUT_BF16) {
         __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float y = mode == OUT_ACT_BF16 ? (v[i] > 0.f ? v[i] : kLeak * v[i]) : v[i] * g[i];
-          o[i] = __float2bfloat16_rn(y);
-        }
+        for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(v[i]);
         uint4* op = reinterpret_cast<uint4*>(P.out) + 2 * cell;
         op[0] = reinterpret_cast<const uint4*>(o)[0];
         op[1] = reinterpret_cast<const uint4*>(o)[1];
@@ -301,6 +290,143 @@ __global__ void k_pack_weights(const float* __restrict__ w, unsigned char* __res
     put(packed + kPackBwd3, off, w3[(k * 16 + n) * 27 + (26 - tap)]);
     put(packed + kPackBwd2, off, w2[(k * 16 + n) * 27 + (26 - tap)]);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Tying of layers 3 and 4 to the adjoints of layers 2 and 1:
+//   adj(w)[c][o][t] = w[o][c][26 - t].
+// k_tie_weights: w3 = adj(w2), w4 = adj(w1).
+// k_tie_grads:   g1 += adj(g4), g2 += adj(g3), then g3 = adj(g2), g4 = adj(g1)
+//                (the gradient of the tied network, repeated in all slots so
+//                that an elementwise optimiser keeps the tie).
+// ---------------------------------------------------------------------------
+__global__ void k_tie_weights(float* w) {
+  float* w1 = w + kLayerOff[0];
+  float* w2 = w + kLayerOff[1];
+  float* w3 = w + kLayerOff[2];
+  float* w4 = w + kLayerOff[3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16 * 16 * 27; i += gridDim.x * blockDim.x) {
+    const int o = i / (16 * 27), c = (i / 27) % 16, t = i % 27;
+    w3[(c * 16 + o) * 27 + (26 - t)] = w2[i];
+    if (i < 16 * 27) {
+      const int oo = i / 27, tt = i % 27;
+      w4[oo * 27 + (26 - tt)] = w1[i];
+    }
+  }
+}
+
+__global__ void k_tie_grads(float* g) {
+  // one thread per (free) weight of layers 1 and 2; each pair is read and
+  // written by exactly one thread
+  float* g1 = g + kLayerOff[0];
+  float* g2 = g + kLayerOff[1];
+  float* g3 = g + kLayerOff[2];
+  float* g4 = g + kLayerOff[3];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16 * 16 * 27; i += gridDim.x * blockDim.x) {
+    const int o = i / (16 * 27), c = (i / 27) % 16, t = i % 27;
+    const int j = (c * 16 + o) * 27 + (26 - t);
+    const float v = g2[i] + g3[j];
+    g2[i] = v;
+    g3[j] = v;
+    if (i < 16 * 27) {
+      const int oo = i / 27, tt = i % 27;
+      const int jj = oo * 27 + (26 - tt);
+      const float u = g1[i] + g4[jj];
+      g1[i] = u;
+      g4[jj] = u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inference through the composed kernel. The network is linear, so
+// N x = G^T G x is one 9x9x9 convolution: with g_o[s] (o = 0..15, s in
+// [0, 5)^3) the kernel of output channel o of G = conv(w2) o conv(w1),
+//   g_o[s] = sum_m sum_{t1 + t2 = s} w2[o][m][t2] w1[m][0][t1],
+// N x[p] = sum_d K[d] x[p + d], d in [-4, 4]^3,
+//   K[d] = sum_o sum_{s - s' = d} g_o[s] g_o[s'],
+// symmetric (K[d] = K[-d]). k_compose builds K (FP32, 729 values) from the
+// master weights; k_apply_k applies it with periodic wrap on the CUDA cores:
+// 729 FMA per cell instead of the 14 688 MACs per cell of the 4 layers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ w, float* __restrict__ K) {
+  __shared__ float g[16 * 125];
+  const float* w1 = w + kLayerOff[0];
+  const float* w2 = w + kLayerOff[1];
+  for (int i = threadIdx.x; i < 16 * 125; i += blockDim.x) {
+    const int o = i / 125, sidx = i % 125;
+    const int sz = sidx / 25, sy = (sidx / 5) % 5, sx = sidx % 5;
+    float acc = 0.f;
+    for (int t1 = 0; t1 < 27; ++t1) {
+      const int az = t1 / 9, ay = (t1 / 3) % 3, ax = t1 % 3;
+      const int bz = sz - az, by = sy - ay, bx = sx - ax;
+      if (bz < 0 || bz > 2 || by < 0 || by > 2 || bx < 0 || bx > 2) continue;
+      const int t2 = (bz * 3 + by) * 3 + bx;
+      for (int m = 0; m < 16; ++m) acc = fmaf(w2[(o * 16 + m) * 27 + t2], w1[m * 27 + t1], acc);
+    }
+    g[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int dz = i / 81 - 4, dy = (i / 9) % 9 - 4, dx = i % 9 - 4;
+    float acc = 0.f;
+    for (int sidx = 0; sidx < 125; ++sidx) {
+      const int sz = sidx / 25, sy = (sidx / 5) % 5, sx = sidx % 5;
+      const int qz = sz - dz, qy = sy - dy, qx = sx - dx;  // s' = s - d
+      if (qz < 0 || qz > 4 || qy < 0 || qy > 4 || qx < 0 || qx > 4) continue;
+      const int q = (qz * 5 + qy) * 5 + qx;
+      for (int o = 0; o < 16; ++o) acc = fmaf(g[o * 125 + sidx], g[o * 125 + q], acc);
+    }
+    K[i] = acc;
+  }
+}
+
+constexpr int KX = 32, KY = 8, KZ = 16;                     // outputs per CTA
+constexpr int KHX = KX + 8, KHY = KY + 8, KHZ = KZ + 8;     // input tile with the 4-cell halo
+constexpr size_t kApplySmem = (size_t)KHZ * KHY * KHX * sizeof(float);  // 60 KB
+
+// The composed kernel travels as a launch parameter (constant bank), so with
+// the tap loops fully unrolled every FMA reads its coefficient from there.
+struct K729 {
+  float k[729];
+};
+
+// z = K * r on an N^3 periodic grid, N % 32 == 0. Each thread owns one (x, y)
+// column of KZ outputs; for every (dy, dx) it loads the KZ + 8 input values of
+// its column once from shared memory and uses each for up to 9 dz.
+__global__ void __launch_bounds__(256) k_apply_k(const float* __restrict__ r, float* __restrict__ z, int N,
+                                                 const K729 K) {
+  extern __shared__ __align__(16) float tile[];  // [KHZ][KHY][KHX]
+  const int tx = threadIdx.x % KX, ty = threadIdx.x / KX;
+  const int bx = blockIdx.x % (N / KX), rest = blockIdx.x / (N / KX);
+  const int by = rest % (N / KY), bz = rest / (N / KY);
+  const int x0 = bx * KX, y0 = by * KY, z0 = bz * KZ;
+  for (int i = threadIdx.x; i < KHZ * KHY * KHX; i += blockDim.x) {
+    const int hx = i % KHX, hy = (i / KHX) % KHY, hz = i / (KHX * KHY);
+    const int gx = wrap(x0 - 4 + hx, N), gy = wrap(y0 - 4 + hy, N), gz = wrap(z0 - 4 + hz, N);
+    tile[i] = __ldg(r + ((size_t)gz * N + gy) * N + gx);
+  }
+  __syncthreads();
+  float acc[KZ];
+#pragma unroll
+  for (int j = 0; j < KZ; ++j) acc[j] = 0.f;
+#pragma unroll
+  for (int dy = 0; dy < 9; ++dy) {
+#pragma unroll
+    for (int dx = 0; dx < 9; ++dx) {
+      float v[KZ + 8];
+#pragma unroll
+      for (int k = 0; k < KZ + 8; ++k) v[k] = tile[(k * KHY + ty + dy) * KHX + tx + dx];
+#pragma unroll
+      for (int dz = 0; dz < 9; ++dz) {
+        const float kd = K.k[(dz * 9 + dy) * 9 + dx];
+#pragma unroll
+        for (int j = 0; j < KZ; ++j) acc[j] = fmaf(kd, v[j + dz], acc[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < KZ; ++j) z[((size_t)(z0 + j) * N + (y0 + ty)) * N + (x0 + tx)] = acc[j];
 }
 
 // ---------------------------------------------------------------------------

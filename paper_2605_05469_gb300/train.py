@@ -17,15 +17,23 @@ CHANNELS = (1, 16, 16, 16, 1)
 SNAPSHOT_ITERS = (1, 2, 4, 8, 16, 32, 64, 128)
 
 
-def init_weights(seed):
-    """He-normal weights (std sqrt(2 / fan_in)), layers concatenated in the
-    library's order w[out][in][tz][ty][tx]."""
+def _adjoint(w, cout, cin):
+    """w[o][c][t] -> adj[c][o][26 - t] (flattened)."""
+    w = w.reshape(cout, cin, 27)
+    return np.ascontiguousarray(np.transpose(w, (1, 0, 2))[:, :, ::-1]).reshape(-1)
+
+
+def init_weights(seed, noise=0.02):
+    """Start from the Jacobi preconditioner plus small seeded noise: channel 0
+    of G carries r / sqrt(6) through the centre taps, so N = G^T G = 1/6
+    (the Jacobi direction of the scaled operator); layers 3-4 are the
+    adjoints of layers 2-1, in the library's order w[out][in][tz][ty][tx]."""
     rng = np.random.default_rng(seed)
-    parts = []
-    for i in range(4):
-        cin, cout = CHANNELS[i], CHANNELS[i + 1]
-        parts.append(rng.normal(0.0, np.sqrt(2.0 / (27 * cin)), size=cout * cin * 27))
-    w = np.concatenate(parts).astype(np.float32)
+    w1 = noise * rng.normal(0.0, np.sqrt(2.0 / 27.0), size=16 * 27)
+    w2 = noise * rng.normal(0.0, np.sqrt(2.0 / (27.0 * 16)), size=16 * 16 * 27)
+    w1[0 * 27 + 13] += 1.0 / np.sqrt(6.0)
+    w2[(0 * 16 + 0) * 27 + 13] += 1.0
+    w = np.concatenate([w1, w2, _adjoint(w2, 16, 16), _adjoint(w1, 16, 1)]).astype(np.float32)
     assert w.size == CNN_WEIGHTS
     return w
 
@@ -64,7 +72,7 @@ def train(ctx, sets, steps, B=8, D=32, lr=2e-3, seed=0, weights=None, log_every=
     """Adam on random crops of the snapshot sets; returns the loss history.
 
     ``ctx`` must be a context on the snapshots' grid (N^3); it holds the
-    network. ``weights`` (14 688 FP32) initialises it, else He-normal.
+    network. ``weights`` (14 688 FP32) initialises it, else the Jacobi start.
     """
     import torch
     N = ctx.N

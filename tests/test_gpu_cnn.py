@@ -84,6 +84,24 @@ def test_conv_raw_layers_match_oracle(pg, D):
                 assert np.all(got[b, nch:] == 0.0), which
 
 
+@pytest.mark.parametrize("N,tol", [(32, 1e-5), (64, 1e-5), (48, 2e-2)])
+def test_preconditioner_apply_matches_oracle(pg, N, tol):
+    """z = N r on the periodic grid: the composed 9^3 FP32 kernel (N % 32 == 0)
+    matches the oracle's FP64 four-layer network to FP32 accuracy; the BF16
+    tensor-core path (other N) to BF16 accuracy."""
+    ws = ocnn.init_weights(9)
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    ws32 = [w.astype(np.float32).astype(np.float64) for w in ws]
+    c = pg.Context().init(N, 0, 0)
+    c.cnn_set_weights(flat)
+    r = inputs.noise_field(N, 3)
+    rt = torch.from_numpy(r.astype(np.float32)).cuda()
+    z = torch.empty_like(rt)
+    c.cnn_apply(rt, z)
+    ref, _ = ocnn.forward(r.astype(np.float32).astype(np.float64).reshape(N, N, N), ws32)
+    assert rel(z.cpu().numpy().astype(np.float64), ref.reshape(-1)) <= tol
+
+
 def test_network_forward_loss_and_gradients_match_oracle(pg):
     N, D, B = 32, 16, 2
     h = L / N
@@ -176,22 +194,20 @@ def test_fcg_cnn_solve_reaches_true_residual(pg, N):
 
 
 def jacobi_network_weights():
-    """Weights for which N(x) = x / 6 exactly: channel 0 carries x, channel 1
-    carries -x through the three leaky ReLUs (act^3(x) - act^3(-x) =
-    (1 + 1/512) x for slope 1/8), and the last layer recombines them. As a
-    preconditioner this is the Jacobi direction r / 6 of the scaled operator."""
-    w1 = np.zeros((16, 1, 27)); w2 = np.zeros((16, 16, 27)); w3 = np.zeros((16, 16, 27)); w4 = np.zeros((1, 16, 27))
-    w1[0, 0, 13], w1[1, 0, 13] = 1.0, -1.0
-    w2[0, 0, 13] = w2[1, 1, 13] = 1.0
-    w3[0, 0, 13] = w3[1, 1, 13] = 1.0
-    a = 512.0 / 513.0 / 6.0
-    w4[0, 0, 13], w4[0, 1, 13] = a, -a
-    return np.concatenate([w.reshape(-1) for w in (w1, w2, w3, w4)]).astype(np.float32)
+    """Weights for which N(x) = x / 6: channel 0 of G carries x / sqrt(6)
+    through the centre taps, so N = G^T G = 1/6, the Jacobi direction r / 6
+    of the scaled operator."""
+    w1 = np.zeros((16, 1, 3, 3, 3)); w2 = np.zeros((16, 16, 3, 3, 3))
+    w1[0, 0, 1, 1, 1] = 1.0 / np.sqrt(6.0)
+    w2[0, 0, 1, 1, 1] = 1.0
+    return np.concatenate([w.reshape(-1) for w in ocnn.tie(w1, w2)]).astype(np.float32)
 
 
 def test_fcg_with_jacobi_network_takes_the_jacobi_iterations(pg):
     """The whole inference + flexible-CG chain with a network that computes
-    the Jacobi direction must converge like mixed Jacobi-CG."""
+    the Jacobi direction must converge like mixed Jacobi-CG, up to the cost of
+    the BF16 rounding of its activations (an inexact preconditioner, which
+    flexible CG tolerates with a few more iterations)."""
     N = 64
     c = pg.Context().init(N, 0, 0)
     c.cnn_set_weights(jacobi_network_weights())
@@ -201,7 +217,7 @@ def test_fcg_with_jacobi_network_takes_the_jacobi_iterations(pg):
     phi.zero_()
     got = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, precond=pg.PC_CNN)
     assert got["fallbacks"] == 0, got
-    assert got["iters"] <= 1.1 * ref["iters"] + 5, (got, ref)
+    assert got["iters"] <= 1.25 * ref["iters"], (got, ref)
 
 
 def test_cnn_requires_weights_and_mixed_precision(pg):
@@ -212,3 +228,36 @@ def test_cnn_requires_weights_and_mixed_precision(pg):
     assert code == pg.PIC_ESTATE
     code, _ = pg.poisson_solve_ex(c.h, rho, phi, 1e-10, 10, c.n, pg.PREC_FP64, pg.PC_CNN)
     assert code == pg.PIC_EINVAL
+
+
+def test_trained_preconditioner_gain(pg, capsys):
+    """What the trained network gains over the method without it.
+
+    The network is trained on the GPU (600 Adam steps on 32^3 crops of
+    (residual, error) pairs from Jacobi-PCG snapshots of four 64^3 Landau
+    deposits, forward/backward by the library's kernels), then flexible CG
+    with it solves held-out Landau deposits at 64^3 and 128^3 to the true
+    relative residual 1e-10. Asserted: convergence and at least 2x fewer
+    iterations than mixed-precision Jacobi-CG; reported: iterations and
+    device time of both and of the FP64 judge."""
+    from paper_2605_05469_gb300 import train as T
+    sets = T.landau_snapshot_sets(64, seeds=[11, 12, 13, 14])
+    c = pg.Context().init(64, 0, 0)
+    losses = T.train(c, sets, 600, B=8, D=32, lr=2e-3, seed=0)
+    assert losses[-50:].mean() < 0.7 * losses[:10].mean()
+    w = c.cnn_get_weights()
+    report = {}
+    for N in (64, 128):
+        ce = pg.Context().init(N, 8, 99)
+        rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+        ce.deposit(rho)
+        ce.cnn_set_weights(w)
+        res = T.compare_preconditioners(ce, rho)
+        cnn, jac = res["mixed_fcg_cnn"], res["mixed_jacobi"]
+        assert cnn["converged"] and cnn["rel_res"] <= 1e-10 and cnn["fallbacks"] == 0, cnn
+        assert cnn["iters"] * 2 <= jac["iters"], (cnn, jac)
+        report[N] = {k: (v["iters"], round(v["t_ms"], 2)) for k, v in res.items()}
+        ce.close()
+    with capsys.disabled():
+        print("\npreconditioner gain (iterations, device ms):", report)
+

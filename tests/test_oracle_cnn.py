@@ -1,6 +1,7 @@
 """Pins of the learned-preconditioner oracle (oracle/cnn.py): a library
-convolution, brute-force loops, the adjoint identity, central finite
-differences, Adam's closed-form first step, and FCG reducing to PCG.
+convolution, brute-force loops, the adjoint identity, the symmetry and
+positive semi-definiteness of N = G^T G, central finite differences,
+Adam's closed-form first step, and FCG reducing to PCG.
 """
 import numpy as np
 import pytest
@@ -86,25 +87,45 @@ def test_network_backward_finite_differences():
         assert np.isclose(grads[layer][idx], fd, rtol=1e-6, atol=1e-9)
 
 
-def test_network_weight_count_and_homogeneity():
+def test_network_weight_count_linearity_and_symmetry():
     ws = cnn.init_weights(0)
     assert sum(w.size for w in ws) == 14688
-    x = np.random.default_rng(6).normal(size=(5, 5, 5))
-    assert np.allclose(cnn.forward(3.0 * x, ws)[0], 3.0 * cnn.forward(x, ws)[0], atol=1e-12)
+    assert np.array_equal(ws[2], cnn.adjoint(ws[1])) and np.array_equal(ws[3], cnn.adjoint(ws[0]))
+    rng = np.random.default_rng(6)
+    x, y = rng.normal(size=(5, 5, 5)), rng.normal(size=(5, 5, 5))
+    Nx, Ny = cnn.forward(x, ws)[0], cnn.forward(y, ws)[0]
+    # linear
+    assert np.allclose(cnn.forward(3.0 * x - 2.0 * y, ws)[0], 3.0 * Nx - 2.0 * Ny, atol=1e-10)
+    # self-adjoint and positive semi-definite: N = G^T G
+    assert np.isclose(np.sum(Nx * y), np.sum(x * Ny), rtol=1e-12)
+    assert np.sum(Nx * x) >= 0.0
+    G = lambda v: cnn.conv3d(cnn.conv3d(v[None], ws[0]), ws[1])
+    assert np.isclose(np.sum(Nx * x), np.sum(G(x) ** 2), rtol=1e-12)
+
+
+def test_adjoint_weights_give_the_adjoint_conv():
+    rng = np.random.default_rng(7)
+    w = rng.normal(size=(4, 3, 3, 3, 3))
+    x, gy = rng.normal(size=(3, 5, 4, 6)), rng.normal(size=(4, 5, 4, 6))
+    assert np.allclose(cnn.conv3d(gy, cnn.adjoint(w)), cnn.conv3d_bwd_data(gy, w), atol=1e-12)
 
 
 def test_loss_gradient_finite_differences():
+    # gradients with respect to the free weights w1, w2 of the tied network
     rng = np.random.default_rng(7)
     ws = cnn.init_weights(3)
     r = [rng.normal(size=(12, 12, 12)) for _ in range(2)]
     e = [rng.normal(size=(12, 12, 12)) for _ in range(2)]
     h = 0.3
     loss, grads = cnn.loss_and_grads(ws, r, e, h)
+    assert np.array_equal(grads[2], cnn.adjoint(grads[1])) and np.array_equal(grads[3], cnn.adjoint(grads[0]))
     eps = 1e-6
-    for layer, idx in [(0, (1, 0, 0, 1, 2)), (2, (4, 9, 1, 1, 0)), (3, (0, 3, 2, 1, 1))]:
-        wp = [w.copy() for w in ws]; wp[layer][idx] += eps
-        wm = [w.copy() for w in ws]; wm[layer][idx] -= eps
-        fd = (cnn.loss_and_grads(wp, r, e, h)[0] - cnn.loss_and_grads(wm, r, e, h)[0]) / (2 * eps)
+    for layer, idx in [(0, (1, 0, 0, 1, 2)), (0, (9, 0, 2, 2, 2)), (1, (4, 9, 1, 1, 0)), (1, (0, 3, 2, 1, 1))]:
+        def loss_at(delta):
+            free = [ws[0].copy(), ws[1].copy()]
+            free[layer][idx] += delta
+            return cnn.loss_and_grads(cnn.tie(*free), r, e, h)[0]
+        fd = (loss_at(eps) - loss_at(-eps)) / (2 * eps)
         assert np.isclose(grads[layer][idx], fd, rtol=1e-6, atol=1e-10)
 
 
