@@ -47,6 +47,11 @@ KER_BYTES = {
 }
 # FP64 operations per cell of one launch (the FP64 judge is FP64-pipe bound)
 KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
+# learned preconditioner applied as its composed 9^3 kernel: 729 FP32 FMA per cell
+PRECOND_FLOP_PER_CELL = 2 * 729
+# FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP at the 2.07 GHz maximum clock
+# (nominal), and 70.2 TFLOP/s measured with an FMA throughput loop on this GB300
+FP32_PEAK_TFLOPS = 70.2
 
 
 def parse():
@@ -55,7 +60,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="mixed",
+                    help="mixed: FP32 CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
+                         "cnn: mixed flexible CG with the learned preconditioner (trained before timing)")
     ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
                     help="pic: full PIC step; solve: one cold-start Poisson solve of a Landau density + noise rhs")
     ap.add_argument("--N", type=int, default=256)
@@ -143,10 +150,16 @@ def run_ours(args):
 
     N, ppc = args.N, args.ppc
     n = N ** 3
-    prec = pg.PREC_MIXED if args.solver == "mixed" else pg.PREC_FP64
+    prec = pg.PREC_FP64 if args.solver == "fp64" else pg.PREC_MIXED
+    pc = pg.PC_CNN if args.solver == "cnn" else pg.PC_JACOBI
     stream = torch.cuda.current_stream()
     solve_only = args.workload == "solve"
+    weights, train_info = None, None
+    if args.solver == "cnn":
+        weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
+    if weights is not None:
+        c.cnn_set_weights(weights)
     phi = torch.zeros(n, dtype=torch.float64, device="cuda")
     if solve_only:
         from paper_2605_05469_gb300 import inputs
@@ -158,11 +171,11 @@ def run_ours(args):
     def step(record):
         if solve_only:
             phi.zero_()
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
             W = None
         else:
             c.deposit(rho)
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
             W = c.field_energy(phi)
             c.gather_push(phi, DT)
         if record:
@@ -229,7 +242,7 @@ def run_ours(args):
     for _ in range(reps):
         rho.copy_(rho_host, non_blocking=True)
         phi.zero_()
-        c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+        c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
         phi_host.copy_(phi, non_blocking=True)
     torch.cuda.synchronize()
     e2e_solve = {"value": reps / (time.perf_counter() - t0), "unit": "solves/s (cold start)",
@@ -247,14 +260,27 @@ def run_ours(args):
     for k in ("pap", "update"):
         if prof["ker_samples"][k]:
             avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
+            # flexible CG also stores q = A p in the pap kernel (+4 B/cell)
+            bpc = KER_BYTES[(kp, k)] + (4 if (k == "pap" and pc == pg.PC_CNN) else 0)
             rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k],
-                       "bytes_per_cell": KER_BYTES[(kp, k)],
-                       "gbs": KER_BYTES[(kp, k)] * n / (avg_ms * 1e-3) / 1e9}
+                       "bytes_per_cell": bpc, "gbs": bpc * n / (avg_ms * 1e-3) / 1e9}
+    if prof["ker_samples"]["precond"]:
+        avg_ms = prof["ker_ms"]["precond"] / prof["ker_samples"]["precond"]
+        rows["precond"] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"]["precond"],
+                           "flop_per_cell": PRECOND_FLOP_PER_CELL,
+                           "tflops": PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12}
     dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
     kname = {("pap", 1): "k_cg_pap<float,false>", ("update", 1): "k_cg_update32",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
     roof = None
-    if dom is not None:
+    if dom == "precond":
+        r = rows[dom]
+        roof = {"kernel": "k_apply_k (composed 9^3 learned preconditioner)", "bound": "alu",
+                "achieved": round(r["tflops"], 2), "peak": FP32_PEAK_TFLOPS, "unit": "FP32 TFLOP/s",
+                "frac": round(r["tflops"] / FP32_PEAK_TFLOPS, 4),
+                "peak_source": "measured FP32 FMA loop (no FP32 figure in MEASURED_PEAKS.json)",
+                "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n, "avg_launch_us": round(r["avg_us"], 2)}
+    elif dom is not None:
         r = rows[dom]
         if kp == 1:
             roof = {"kernel": kname[(dom, kp)], "bound": "hbm", "achieved": round(r["gbs"], 1),
@@ -275,7 +301,9 @@ def run_ours(args):
         "metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 particles/grid; solve f32 vectors + f64 reductions" if prec == 1 else "f64",
+        "dtype": ("f64" if prec == pg.PREC_FP64 else
+                  "f64 particles/grid; solve f32 vectors + f64 reductions" +
+                  ("; f32 9^3 learned preconditioner" if pc == pg.PC_CNN else "")),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
@@ -296,8 +324,10 @@ def run_ours(args):
         "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in prof["phase_ms"].items()},
         "impl": "ours",
     }
+    if train_info is not None:
+        out["preconditioner_training"] = train_info
     if not args.no_compare:
-        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch)
+        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters))
     if dist is not None:
@@ -306,19 +336,43 @@ def run_ours(args):
     return out
 
 
-def compare_solvers(c, rho, n, pg, torch):
+def train_preconditioner(pg, torch, N=64, steps=600):
+    """Train the learned preconditioner on the GPU before timing (the library's
+    own kernels: Jacobi-PCG snapshots of four 64^3 Landau deposits, 600 Adam
+    steps on 32^3 crops)."""
+    from paper_2605_05469_gb300 import train as T
+    t0 = time.perf_counter()
+    sets = T.landau_snapshot_sets(N, seeds=[11, 12, 13, 14])
+    c = pg.Context().init(N, 0, 0)
+    losses = T.train(c, sets, steps, B=8, D=32, lr=2e-3, seed=0)
+    w = c.cnn_get_weights()
+    c.close()
+    del sets
+    torch.cuda.synchronize()
+    return w, {"grid": N, "steps": steps, "loss_first": float(losses[:10].mean()),
+               "loss_last": float(losses[-50:].mean()), "seconds": round(time.perf_counter() - t0, 2)}
+
+
+def compare_solvers(c, rho, n, pg, torch, with_cnn=False):
     """Cold-start solves of the same right-hand side (the last deposit): the FP64
-    Jacobi-PCG judge against the mixed-precision solver (outside the timed region)."""
+    Jacobi-PCG judge against the mixed-precision solver, and with the learned
+    preconditioner when it is loaded (outside the timed region)."""
     res = {}
-    for name, prec in (("fp64_jacobi_pcg", pg.PREC_FP64), ("mixed_fp32_fp64", pg.PREC_MIXED)):
+    cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI)]
+    if with_cnn:
+        cases.append(("mixed_fcg_learned", pg.PREC_MIXED, pg.PC_CNN))
+    for name, prec, pc in cases:
         best = None
         for _ in range(2):
             phi = torch.zeros(n, dtype=torch.float64, device="cuda")
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec)
+            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc, raise_on_error=False)
             if best is None or info["t_ms"] < best["t_ms"]:
                 best = info
-        res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"]}
+        res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
+                     "converged": bool(best["converged"])}
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
+    if with_cnn:
+        res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
     return res
 
 

@@ -371,7 +371,9 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
       launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
       zc ^= 1;
+      slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
       const int ce = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n);
+      if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
       if (ce && !inner_err) inner_err = ce;
       launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
              c->partials, c->counter, 0);
