@@ -47,8 +47,11 @@ KER_BYTES = {
 }
 # FP64 operations per cell of one launch (the FP64 judge is FP64-pipe bound)
 KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
-# learned preconditioner applied as its composed 9^3 kernel: 729 FP32 FMA per cell
+# learned preconditioner applied as its composed 9^3 kernel: 729 FMA per cell
 PRECOND_FLOP_PER_CELL = 2 * 729
+# ... which the tensor-core form executes as 81 Toeplitz products of K = 32
+# per output, on 40 rows per 32 kept (the 8 rows between y blocks are discarded)
+PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32 * 40 // 32
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP at the 2.07 GHz maximum clock
 # (nominal), and 70.2 TFLOP/s measured with an FMA throughput loop on this GB300
 FP32_PEAK_TFLOPS = 70.2
@@ -63,6 +66,9 @@ def parse():
     ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="mixed",
                     help="mixed: FP32 CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
                          "cnn: mixed flexible CG with the learned preconditioner (trained before timing)")
+    ap.add_argument("--cnn-apply", choices=["tc", "fp32", "layers"], default="tc",
+                    help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
+                         "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
     ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
                     help="pic: full PIC step; solve: one cold-start Poisson solve of a Landau density + noise rhs")
     ap.add_argument("--N", type=int, default=256)
@@ -158,8 +164,10 @@ def run_ours(args):
     if args.solver == "cnn":
         weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
+    apply_mode = {"tc": pg.CNN_APPLY_TC, "fp32": pg.CNN_APPLY_FP32, "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
     if weights is not None:
         c.cnn_set_weights(weights)
+        c.cnn_set_apply(apply_mode)
     phi = torch.zeros(n, dtype=torch.float64, device="cuda")
     if solve_only:
         from paper_2605_05469_gb300 import inputs
@@ -273,7 +281,18 @@ def run_ours(args):
     kname = {("pap", 1): "k_cg_pap<float,false>", ("update", 1): "k_cg_update32",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
     roof = None
-    if dom == "precond":
+    if dom == "precond" and apply_mode == pg.CNN_APPLY_TC:
+        r = rows[dom]
+        _, _, pk = peaks()
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        roof = {"kernel": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16)", "bound": "tensor",
+                "achieved": round(r["tflops"], 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(r["tflops"] / peak, 4),
+                "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long solve)",
+                "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n,
+                "executed_mma_tflops": round(r["tflops"] * PRECOND_MMA_FLOP_PER_CELL / PRECOND_FLOP_PER_CELL, 2),
+                "avg_launch_us": round(r["avg_us"], 2)}
+    elif dom == "precond":
         r = rows[dom]
         roof = {"kernel": "k_apply_k (composed 9^3 learned preconditioner)", "bound": "alu",
                 "achieved": round(r["tflops"], 2), "peak": FP32_PEAK_TFLOPS, "unit": "FP32 TFLOP/s",
@@ -303,7 +322,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": ("f64" if prec == pg.PREC_FP64 else
                   "f64 particles/grid; solve f32 vectors + f64 reductions" +
-                  ("; f32 9^3 learned preconditioner" if pc == pg.PC_CNN else "")),
+                  ((f"; {'bf16 tensor-core' if args.cnn_apply == 'tc' else args.cnn_apply} "
+                    "9^3 learned preconditioner") if pc == pg.PC_CNN else "")),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
@@ -361,7 +381,10 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False):
     cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI)]
     if with_cnn:
         cases.append(("mixed_fcg_learned", pg.PREC_MIXED, pg.PC_CNN))
+        cases.append(("mixed_fcg_learned_fp32", pg.PREC_MIXED, pg.PC_CNN))
     for name, prec, pc in cases:
+        if with_cnn:
+            c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
         best = None
         for _ in range(2):
             phi = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -373,6 +396,7 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False):
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
     if with_cnn:
         res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
+        res["speedup_learned_fp32_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned_fp32"]["s"]
     return res
 
 

@@ -176,10 +176,23 @@ int pic_cnn_get_weights(pic_ctx *c, float *w_host);
 int pic_cnn_get_grads(pic_ctx *c, float *g_host);
 
 /* Preconditioner on the context grid: z = N r for device FP32 [N^3] r, z
- * (periodic). N is linear, so for N % 32 == 0 it runs as its composed 9^3
- * kernel K (FP32, rebuilt from the master weights at every weight update) on
- * the CUDA cores; other grids (N % 16 == 0) run the 4 BF16 tensor-core convs. */
+ * (periodic). N is linear, so it equals one 9^3 convolution with the composed
+ * kernel K (rebuilt from the master weights at every weight update). How it
+ * is evaluated on grids with N % 32 == 0 is set by pic_cnn_set_apply; other
+ * grids (N % 16 == 0) always run the four BF16 tensor-core convs. */
 int pic_cnn_apply(pic_ctx *c, const float *r, float *z);
+
+/* Evaluation of the preconditioner (pic_cnn_apply and the solver's
+ * preconditioner step) on grids with N % 32 == 0:
+ *   PIC_CNN_APPLY_TC     composed kernel on the tensor cores (N % 128 == 0):
+ *                        x-direction Toeplitz products, r and K rounded to
+ *                        BF16, FP32 accumulation (default); on grids that are
+ *                        not a multiple of 128 this mode runs PIC_CNN_APPLY_FP32;
+ *   PIC_CNN_APPLY_FP32   composed kernel on the CUDA cores, FP32 throughout;
+ *   PIC_CNN_APPLY_LAYERS the four BF16 tensor-core convs of the network.
+ * Returns PIC_EINVAL for another mode. */
+enum { PIC_CNN_APPLY_TC = 0, PIC_CNN_APPLY_FP32 = 1, PIC_CNN_APPLY_LAYERS = 2 };
+int pic_cnn_set_apply(pic_ctx *c, int mode);
 
 /* Forward pass over B crops: y = N(x) (device FP32 [B][D^3] each); keeps the
  * activations for pic_cnn_backward. */

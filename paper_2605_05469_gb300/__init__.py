@@ -32,6 +32,9 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PC_JACOBI = 0
 PC_CNN = 1
+CNN_APPLY_TC = 0
+CNN_APPLY_FP32 = 1
+CNN_APPLY_LAYERS = 2
 CNN_WEIGHTS = 14688
 
 
@@ -105,6 +108,7 @@ _SIGS = {
     "pic_cnn_get_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_cnn_set_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int]),
     "pic_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -314,6 +318,10 @@ class Context:
         g = np.empty(CNN_WEIGHTS, dtype=np.float32)
         _check(lib().pic_cnn_get_grads(self.h, g.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_get_grads")
         return g
+
+    def cnn_set_apply(self, mode):
+        _check(lib().pic_cnn_set_apply(self.h, int(mode)), "pic_cnn_set_apply")
+        return self
 
     def cnn_apply(self, r, z):
         _check(lib().pic_cnn_apply(self.h, _dptr(r, "float32", self.n, "r"), _dptr(z, "float32", self.n, "z")),

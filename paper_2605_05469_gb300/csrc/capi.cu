@@ -584,7 +584,9 @@ int pic_deposit(pic_ctx* c, double* rho) {
     launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
     launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
     launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
-    launch(c, k_scatter, pblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, c->keys, c->ranks,
+    const unsigned sblocks = (unsigned)((c->np / 4 + 255) / 256);
+    launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
+           (const uint32_t*)c->ranks,
                                               c->offsets);
     CK(cudaGetLastError());
     c->cur ^= 1;

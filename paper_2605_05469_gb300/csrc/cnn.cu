@@ -33,6 +33,7 @@ struct CnnState {
   float* q = nullptr;      // loss: A_I (y - t)
   size_t q_cells = 0;
   float* K = nullptr;      // composed 9^3 kernel of N = G^T G (FP32)
+  unsigned char* Bt = nullptr;  // its 81 Toeplitz matrices, packed BF16 B operand
   cnn::K729 K_host;        // its host copy (launch parameter)
   bool K_stale = true;     // the device kernel changed since the host copy
 };
@@ -51,7 +52,8 @@ int ensure_state(pic_ctx* c) {
   if (!s) return PIC_ENOMEM;
   int e;
   if ((e = dalloc(&s->w, kWeights)) || (e = dalloc(&s->g, kWeights)) || (e = dalloc(&s->m, kWeights)) ||
-      (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes)) || (e = dalloc(&s->K, 729))) {
+      (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes)) || (e = dalloc(&s->K, 729)) ||
+      (e = dalloc(&s->Bt, (size_t)tck::B_BYTES))) {
     cnn_state_free(s);
     return e;
   }
@@ -129,6 +131,7 @@ int repack(pic_ctx* c) {
   launch(c, k_tie_weights, 27, 256, 0, c->cnn->w);
   launch(c, k_pack_weights, 32, 256, 0, (const float*)c->cnn->w, c->cnn->packed);
   launch(c, k_compose, 1, 256, 0, (const float*)c->cnn->w, c->cnn->K);
+  launch(c, k_pack_toeplitz, 41, 256, 0, (const float*)c->cnn->K, c->cnn->Bt);
   c->cnn->K_stale = true;
   CK(cudaGetLastError());
   return PIC_OK;
@@ -140,7 +143,7 @@ namespace pic {
 
 void cnn_state_free(CnnState* s) {
   if (!s) return;
-  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K);
+  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K); dfree(s->Bt);
   dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
   dfree(s->i1); dfree(s->i2);
   dfree(s->sums); dfree(s->origins); dfree(s->q);
@@ -153,8 +156,23 @@ bool cnn_ready(const pic_ctx* c) { return c->cnn && c->cnn->has_weights; }
 int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) {
   CnnState* s = c->cnn;
   const int N = c->N;
-  if (N % KX == 0) {
-    // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
+  // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
+  if (N % tck::BY == 0 && c->cnn_apply_mode == PIC_CNN_APPLY_TC) {
+    static bool configured_tc = false;
+    if (!configured_tc) {
+      CK(cudaFuncSetAttribute((const void*)k_apply_k_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tck::SMEM));
+      configured_tc = true;
+    }
+    // persistent: one CTA per SM, each a contiguous range of output planes
+    const long units = (long)(N / tck::BX) * (N / tck::BY) * N;
+    const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
+    launch(c, k_apply_k_tc, grid, tck::THREADS, tck::SMEM, r, z, N, (const unsigned char*)s->Bt, c->err);
+    CK(cudaGetLastError());
+    return PIC_OK;
+  }
+  // grids that are not a multiple of 128 run the FP32 composed kernel in TC mode
+  if (N % KX == 0 && c->cnn_apply_mode != PIC_CNN_APPLY_LAYERS) {
     static bool configured = false;
     if (!configured) {
       CK(cudaFuncSetAttribute((const void*)k_apply_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmem));
@@ -241,6 +259,12 @@ int pic_cnn_apply(pic_ctx* c, const float* r, float* z) {
   if (!c->has_grid) return PIC_ESTATE;
   if (!cnn_ready(c)) return PIC_ESTATE;
   return cnn_apply(c, r, z, nullptr, c->n);
+}
+
+int pic_cnn_set_apply(pic_ctx* c, int mode) {
+  if (!c || mode < PIC_CNN_APPLY_TC || mode > PIC_CNN_APPLY_LAYERS) return PIC_EINVAL;
+  c->cnn_apply_mode = mode;
+  return PIC_OK;
 }
 
 int pic_cnn_forward(pic_ctx* c, const float* x, float* y, int B, int D) {

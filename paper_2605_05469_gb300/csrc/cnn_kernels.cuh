@@ -430,6 +430,400 @@ __global__ void __launch_bounds__(256) k_apply_k(const float* __restrict__ r, fl
 }
 
 // ---------------------------------------------------------------------------
+// The composed 9^3 kernel on the tensor cores.
+//
+// For fixed (dz, dy) the x-direction sum over dx of K[dz][dy][dx] r[x + dx - 4]
+// for 16 consecutive outputs x0..x0+15 is a product with the 32 x 16 Toeplitz
+// matrix T_{dz,dy}[k][n] = K[dz][dy][k - n] (0 <= k - n <= 8, else 0) of the
+// 32 inputs x0-4..x0+27. The A operand holds one input plane z' of a column
+// of 128 output rows y0..y0+127 (136 input rows with the y halo, BF16, x
+// along K); the row offset dy is a descriptor offset. The B operand for one dy
+// stacks the nine T_{dz,dy} along N (N = 144), so one MMA gives the
+// contributions of input plane z' to the nine output planes p = z' - dz + 4
+// at once, in nine groups of 16 TMEM columns. The output planes live in a
+// TMEM ring of 32 slots of 16 columns whose slot index decreases with p:
+// group dz of the MMA of plane z' lands in the slot of p = z' - dz + 4, so the
+// dz sum is accumulated by the tensor core itself; an output plane is final
+// once input plane p + 4 has been multiplied, and the epilogue reads it out.
+// Per input plane: 9 dy x 2 K-steps of 16 = 18 MMAs (M 128, N <= 144; 36
+// where the group range wraps around the ring of 32 slots). The epilogue
+// zeroes a slot after reading it, so every MMA accumulates.
+//
+// Work: the unit is one output plane of one column (16 x 128 cells); CTA k of
+// G takes units [k U / G, (k + 1) U / G) of the U = (N/16)(N/128) N units in
+// column-major order, which are one or two runs of consecutive planes of a
+// column; a run of planes [pa, pb) streams input planes pa-4 .. pb+3.
+// Warp-specialised pipeline: producer warps stream input planes through a
+// ring of FP32 stages (cp.async, three planes ahead) and convert them into a
+// ring of BF16 A operands; one thread issues the MMAs as operands become
+// ready; epilogue warps write each output plane back once its last input
+// plane has been multiplied. mbarrier rings hand each plane from one role to
+// the next, so the tensor cores are fed several planes ahead.
+// ---------------------------------------------------------------------------
+namespace tck {
+constexpr int BX = 16;                    // x outputs per Toeplitz group
+constexpr int BY = 128;                   // y outputs per column (the 128 TMEM lanes)
+constexpr int AROWS = BY + 8;             // input rows y0-4 .. y0+131
+// one 8-element K chunk of an input plane; the extra 64 B put chunks 1 and 3
+// on the other half of the shared-memory banks for the fill
+constexpr int CHUNK_B = AROWS * 16 + 64;  // 2240
+constexpr int SLOT_B = 4 * CHUNK_B;       // 8960: one BF16 input plane, 32 x-inputs
+constexpr int BROWS = 9 * 16;             // N rows of the B operand of one dy: (dz, n)
+constexpr int BCHUNK_B = BROWS * 16;      // 2304
+constexpr int BDY_B = 4 * BCHUNK_B;       // 9216
+constexpr int B_BYTES = 9 * BDY_B;        // 82944: all 81 Toeplitz matrices
+constexpr int TSLOTS = 32;                // TMEM ring of output planes
+constexpr int TMEM_COLS = TSLOTS * 16;    // 512: all of the SM's tensor memory
+// warp roles: warp 0 issues the MMAs, warps 1-4 read the finished output
+// planes out of TMEM (warp w reaches TMEM lanes 32 (w % 4) .. + 31), warps
+// 5-8 copy and convert the input planes
+constexpr int EPI_WARP0 = 1, PROD_WARP0 = 5, NWARPS = 9;
+constexpr int THREADS = NWARPS * 32;      // 288
+constexpr int PTHREADS = 128;             // producer threads
+constexpr int LOADS = (AROWS * 8 + PTHREADS - 1) / PTHREADS;  // 16-byte pieces per producer per plane (9)
+constexpr int ASLOTS = 4;                 // BF16 A operands (input planes ready for the tensor cores)
+constexpr int STAGES = 4;                 // FP32 input planes in flight (cp.async)
+constexpr int STAGE_B = AROWS * 128;      // 17408: 136 rows x 32 FP32
+// an output plane's TMEM slot (zeroed by the epilogue after it reads it) is
+// taken again by the output plane TSLOTS later, whose first term comes from
+// the input plane TSLOTS - 8 input planes after the one that completed it
+constexpr int SLOT_REUSE_LAG = TSLOTS - 8;
+constexpr int ERING = 32;                 // plane handshakes between the MMA issuer and the epilogue
+constexpr size_t SMEM = (size_t)B_BYTES + ASLOTS * SLOT_B + STAGES * STAGE_B;  // 188416
+static_assert(SMEM > 114 * 1024 && SMEM <= 227 * 1024, "one CTA per SM");
+static_assert(ERING > SLOT_REUSE_LAG, "the issuer must not lap the epilogue handshakes");
+}  // namespace tck
+
+// Packed B operand (global, built when K changes): for each dy, the canonical
+// K-major N x K matrix with row n' = dz * 16 + n and column k, element
+// T_{dz,dy}[k][n] = K[dz][dy][k - n].
+__global__ void __launch_bounds__(256) k_pack_toeplitz(const float* __restrict__ K, unsigned char* __restrict__ Bg) {
+  using namespace tck;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * BROWS * 32; i += gridDim.x * blockDim.x) {
+    const int dy = i / (BROWS * 32), np = (i / 32) % BROWS, k = i % 32;
+    const int dz = np / 16, n = np % 16, dx = k - n;
+    const float v = (dx >= 0 && dx <= 8) ? K[(dz * 9 + dy) * 9 + dx] : 0.f;
+    const int off = dy * BDY_B + (np >> 3) * 128 + (k >> 3) * BCHUNK_B + (np & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(Bg + off) = __float2bfloat16_rn(v);
+  }
+}
+
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// D += A B^T (the accumulator is always read: the epilogue zeroes each TMEM
+// slot before it is reused, so no MMA needs the overwrite form).
+__device__ __forceinline__ void mma_acc(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 1, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc));
+}
+
+// All MMAs of one input plane, straight-line: for each dy and K-step q the A
+// operand is the plane shifted by dy rows and advanced by 16 x-inputs; one
+// MMA per segment of consecutive dz groups (two where the groups wrap around
+// the TMEM ring). Every offset is a compile-time constant added to the base
+// descriptors, so the issue stream carries no branches.
+template <int SEGS>
+__device__ __forceinline__ void tc_issue_plane(uint64_t ad0, uint64_t b0, uint32_t d0, uint32_t i0, uint64_t b1,
+                                               uint32_t d1, uint32_t i1) {
+  using namespace tck;
+#pragma unroll
+  for (int dy = 0; dy < 9; ++dy) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint64_t a = ad0 + (uint64_t)((dy * 16 + q * 2 * CHUNK_B) >> 4);
+      const uint64_t bo = (uint64_t)((dy * BDY_B + q * 2 * BCHUNK_B) >> 4);
+      mma_acc(d0, a, b0 + bo, i0);
+      if (SEGS == 2) mma_acc(d1, a, b1 + bo, i1);
+    }
+  }
+}
+
+// One input plane of the CTA's stream: column `col`, run of output planes
+// [pa, pb), input plane z (unwrapped, pa-4 <= z <= pb+3).
+struct TcPlane {
+  int col, pa, pb, z;
+};
+
+__device__ __forceinline__ bool tc_run_at(long u, long uend, int N, TcPlane& P) {
+  if (u >= uend) return false;
+  P.col = (int)(u / N);
+  P.pa = (int)(u % N);
+  P.pb = (int)min((long)N, (long)P.pa + (uend - u));
+  P.z = P.pa - 4;
+  return true;
+}
+
+__device__ __forceinline__ bool tc_next(long uend, int N, TcPlane& P) {
+  if (P.z + 1 < P.pb + 4) {
+    ++P.z;
+    return true;
+  }
+  return tc_run_at((long)P.col * N + P.pb, uend, N, P);
+}
+
+__device__ __forceinline__ void tc_origin(const TcPlane& P, int N, int& x0, int& y0) {
+  const int nbx = N / tck::BX;
+  x0 = (P.col % nbx) * tck::BX;
+  y0 = (P.col / nbx) * tck::BY;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Start the copy of input plane P (136 rows x 32 FP32 x-inputs, periodic) into
+// an FP32 stage, row-major. Producer thread t moves pieces t + 128 i (16 B
+// each); it later converts the same pieces, so no barrier separates copy and
+// convert.
+__device__ __forceinline__ void tc_issue(const TcPlane& P, const float* __restrict__ r, int N, unsigned char* stage,
+                                         int ptid) {
+  using namespace tck;
+  int x0, y0;
+  tc_origin(P, N, x0, y0);
+  const int gz = wrap(P.z, N);
+#pragma unroll
+  for (int i = 0; i < LOADS; ++i) {
+    const int idx = ptid + i * PTHREADS;
+    if (idx < AROWS * 8) {
+      const int g = idx & 7, row = idx >> 3;
+      // 4-float pieces never straddle the periodic wrap (x0 - 4 is a multiple of 4)
+      const int gy = wrap(y0 - 4 + row, N), gx = wrap(x0 - 4 + 4 * g, N);
+      cp_async16(stage + idx * 16, r + ((size_t)gz * N + gy) * N + gx);
+    }
+  }
+}
+
+// FP32 stage -> BF16 canonical K-major A operand (the thread's own pieces).
+__device__ __forceinline__ void tc_convert(const unsigned char* stage, unsigned char* slot, int ptid) {
+  using namespace tck;
+#pragma unroll
+  for (int i = 0; i < LOADS; ++i) {
+    const int idx = ptid + i * PTHREADS;
+    if (idx < AROWS * 8) {
+      const int g = idx & 7, row = idx >> 3;
+      const float4 v = *reinterpret_cast<const float4*>(stage + idx * 16);
+      __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+      uint2 packed;
+      packed.x = *reinterpret_cast<uint32_t*>(&lo);
+      packed.y = *reinterpret_cast<uint32_t*>(&hi);
+      // x-input k = 4 g .. 4 g + 3 -> chunk k / 8, byte (k % 8) * 2 of the row
+      *reinterpret_cast<uint2*>(slot + (g >> 1) * CHUNK_B + row * 16 + (g & 1) * 8) = packed;
+    }
+  }
+}
+
+// Zero 16 columns of the calling thread's TMEM lane (32x32b shape: each
+// thread of the warp owns one lane) and wait for the store.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z0 = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z0)
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Output plane p = P.z - 4 is complete once input plane P.z has been
+// multiplied: TMEM slot -> z. Epilogue warp w reads TMEM lanes 32 (w % 4) ..
+// + 31 (rows y), all 16 columns (x) of the slot.
+__device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict__ z, int N, uint32_t tmem,
+                                            long ubegin) {
+  using namespace tck;
+  const int p = P.z - 4;
+  if (p < P.pa) return;  // an input plane of the lower halo: no output completes
+  int x0, y0;
+  tc_origin(P, N, x0, y0);
+  const long vv = (long)P.col * N + p - ubegin;
+  const int s = (int)((-vv) & (TSLOTS - 1));
+  const int quarter = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+  float o[16];
+  const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 16);
+  tmem_ld16(ta, o);
+  tmem_zero16(ta);  // the slot's next output plane starts from zero
+  float4* dst = reinterpret_cast<float4*>(z + ((size_t)p * N + (y0 + quarter * 32 + lane)) * N + x0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another role has given up.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer_ns() - t0 > 2000000000ull) {
+        atomicOr(err, DEV_ERR_TIMEOUT);
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __restrict__ r, float* __restrict__ z,
+                                                                int N, const unsigned char* __restrict__ Bg,
+                                                                int* err) {
+  using namespace tck;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ __align__(8) uint64_t a_full[ASLOTS], a_empty[ASLOTS], acc_full[ERING], acc_empty[ERING], b_bar;
+  unsigned char* Bs = smem;                         // B_BYTES
+  unsigned char* slots = smem + B_BYTES;            // ASLOTS x SLOT_B (BF16 A operands)
+  unsigned char* stages = slots + ASLOTS * SLOT_B;  // STAGES x STAGE_B (FP32 input planes)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long U = (long)(N / BX) * (N / BY) * N;
+  const long ubegin = U * blockIdx.x / gridDim.x, uend = U * (blockIdx.x + 1) / gridDim.x;
+  const bool has_work = ubegin < uend;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < ASLOTS; ++i) {
+      mbar_init(&a_full[i], PTHREADS);
+      mbar_init(&a_empty[i], 1);
+    }
+    for (int i = 0; i < ERING; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
+    mbar_init(&b_bar, 1);
+    fence_mbar_init();
+    if (has_work) {
+      mbar_arrive_expect_tx(&b_bar, B_BYTES);
+      bulk_g2s(Bs, Bg, B_BYTES, &b_bar);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (warp >= EPI_WARP0 && warp < PROD_WARP0) {
+    // every MMA accumulates: start from zeroed slots
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    for (int c = 0; c < TMEM_COLS; c += 16) tmem_zero16(lane_base + (uint32_t)c);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (warp == 0) {
+    // ---- MMA issuer: one thread ----
+    if (lane == 0 && has_work) {
+      TcPlane P;
+      bool have = tc_run_at(ubegin, uend, N, P);
+      const bool b_ok = tc_wait(&b_bar, 0, err, &abort_flag);
+      const uint64_t bd0 = smem_desc(smem_u32(Bs), BCHUNK_B, 128);
+      for (uint32_t j = 0; have && b_ok; ++j) {
+        const uint32_t sa = j % ASLOTS;
+        if (!tc_wait(&a_full[sa], (j / ASLOTS) & 1u, err, &abort_flag)) break;
+        if (j >= (uint32_t)SLOT_REUSE_LAG) {
+          const uint32_t e = j - SLOT_REUSE_LAG;
+          if (!tc_wait(&acc_empty[e % ERING], (e / ERING) & 1u, err, &abort_flag)) break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // groups dz_lo..dz_hi feed output planes z + 4 - dz inside [pa, pb)
+        const int dz_lo = max(0, P.z + 4 - (P.pb - 1)), dz_hi = min(8, P.z + 4 - P.pa);
+        const long v_lo = (long)P.col * N + (P.z - dz_lo + 4) - ubegin;
+        const int s_lo = (int)((-v_lo) & (TSLOTS - 1));
+        const int ng = dz_hi - dz_lo + 1;
+        const int n1 = min(ng, TSLOTS - s_lo);  // groups before the ring wraps
+        const uint64_t ad0 = smem_desc(smem_u32(slots + sa * SLOT_B), CHUNK_B, 128);
+        const uint64_t b0 = bd0 + (uint64_t)(dz_lo * 16);  // 16 B-rows per group = 256 B
+        const uint32_t d0 = tmem + (uint32_t)(s_lo * 16);
+        if (n1 == ng) {
+          tc_issue_plane<1>(ad0, b0, d0, idesc_n(16 * ng), 0, 0, 0);
+        } else {
+          tc_issue_plane<2>(ad0, b0, d0, idesc_n(16 * n1), b0 + (uint64_t)(n1 * 16), tmem,
+                            idesc_n(16 * (ng - n1)));
+        }
+        // both arrive once every MMA issued so far has completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&a_empty[sa]))
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&acc_full[j % ERING]))
+                     : "memory");
+        have = tc_next(uend, N, P);
+      }
+      if (!b_ok) abort_flag = 1;
+    }
+    __syncwarp();
+  } else if (warp < PROD_WARP0) {
+    // ---- epilogue: 128 threads ----
+    TcPlane P;
+    bool have = tc_run_at(ubegin, uend, N, P);
+    for (uint32_t j = 0; have; ++j) {
+      if (!tc_wait(&acc_full[j % ERING], (j / ERING) & 1u, err, &abort_flag)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tc_epilogue(P, z, N, tmem, ubegin);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty[j % ERING]);
+      have = tc_next(uend, N, P);
+    }
+  } else {
+    // ---- producers: 128 threads ----
+    const int ptid = tid - PROD_WARP0 * 32;
+    TcPlane cur, ahead;
+    bool have = tc_run_at(ubegin, uend, N, cur);
+    ahead = cur;
+    bool have_ahead = have;
+    // planes 0 .. STAGES-2 in flight, one cp.async group each
+    for (int st = 0; st < STAGES - 1; ++st) {
+      if (have_ahead) {
+        tc_issue(ahead, r, N, stages + st * STAGE_B, ptid);
+        have_ahead = tc_next(uend, N, ahead);
+      }
+      cp_async_commit();
+    }
+    for (uint32_t j = 0; have; ++j) {
+      const uint32_t sa = j % ASLOTS;
+      cp_async_wait<STAGES - 2>();  // plane j's group (groups complete in order)
+      if (j >= (uint32_t)ASLOTS) {
+        // the MMAs of plane j - ASLOTS, which read this A slot, are done
+        const uint32_t k = j - ASLOTS;
+        if (!tc_wait(&a_empty[sa], (k / ASLOTS) & 1u, err, &abort_flag)) break;
+      }
+      tc_convert(stages + (j % STAGES) * STAGE_B, slots + sa * SLOT_B, ptid);
+      // refill the stage plane j-1 used with plane j + STAGES - 1
+      if (have_ahead) {
+        tc_issue(ahead, r, N, stages + ((j + STAGES - 1) % STAGES) * STAGE_B, ptid);
+        have_ahead = tc_next(uend, N, ahead);
+      }
+      cp_async_commit();
+      fence_proxy_async_smem();  // the BF16 writes, visible to the tensor cores
+      mbar_arrive(&a_full[sa]);
+      have = tc_next(uend, N, cur);
+    }
+    cp_async_wait<0>();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient on CUDA cores, FP32:
 //   dW[o][c][tap] += sum_cells gz[cell][o] * a[cell + tap - 1][c]
 // gz: COUT channels (f32 if COUT == 1 else bf16 x16); a: CIN channels (f32 if

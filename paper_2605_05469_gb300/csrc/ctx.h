@@ -105,6 +105,7 @@ struct pic_ctx {
   int ker_prec[PIC_NKER] = {0, 0, 0};
   // learned preconditioner (weights, activations, optimiser state)
   pic::CnnState* cnn = nullptr;
+  int cnn_apply_mode = 0;  // PIC_CNN_APPLY_*
 };
 
 namespace pic {

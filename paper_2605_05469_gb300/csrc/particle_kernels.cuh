@@ -204,19 +204,38 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
   if (base + 16 >= n && base < n) offsets[n] = run;  // the thread holding the last count
 }
 
-// Move particle p to offsets[key] + rank (the other buffer set).
-__global__ void k_scatter(ParticlePtrs src, ParticlePtrs dst, uint64_t np, const uint32_t* __restrict__ keys,
-                          const uint32_t* __restrict__ ranks, const uint32_t* __restrict__ offsets) {
-  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  const uint64_t d = (uint64_t)offsets[keys[p]] + ranks[p];
-  dst.x[d] = src.x[p];
-  dst.y[d] = src.y[p];
-  dst.z[d] = src.z[p];
-  dst.vx[d] = src.vx[p];
-  dst.vy[d] = src.vy[p];
-  dst.vz[d] = src.vz[p];
-  dst.id[d] = src.id[p];
+// Move particle p to offsets[key] + rank (the other buffer set). Each thread
+// moves 4 consecutive particles with vector loads, so 4 independent
+// key -> offset -> store chains are in flight per thread (np % 4 == 0).
+__global__ void __launch_bounds__(256) k_scatter(ParticlePtrs src, ParticlePtrs dst, uint64_t np,
+                                                 const uint32_t* __restrict__ keys,
+                                                 const uint32_t* __restrict__ ranks,
+                                                 const uint32_t* __restrict__ offsets) {
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * q >= np) return;
+  const uint4 k4 = __ldg(reinterpret_cast<const uint4*>(keys) + q);
+  const uint4 r4 = __ldg(reinterpret_cast<const uint4*>(ranks) + q);
+  uint64_t d[4];
+  d[0] = (uint64_t)__ldg(offsets + k4.x) + r4.x;
+  d[1] = (uint64_t)__ldg(offsets + k4.y) + r4.y;
+  d[2] = (uint64_t)__ldg(offsets + k4.z) + r4.z;
+  d[3] = (uint64_t)__ldg(offsets + k4.w) + r4.w;
+  const double* sf[6] = {src.x, src.y, src.z, src.vx, src.vy, src.vz};
+  double* df[6] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz};
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(sf[f]) + 2 * q);
+    const double2 b = __ldg(reinterpret_cast<const double2*>(sf[f]) + 2 * q + 1);
+    df[f][d[0]] = a.x;
+    df[f][d[1]] = a.y;
+    df[f][d[2]] = b.x;
+    df[f][d[3]] = b.y;
+  }
+  const uint4 i4 = __ldg(reinterpret_cast<const uint4*>(src.id) + q);
+  dst.id[d[0]] = i4.x;
+  dst.id[d[1]] = i4.y;
+  dst.id[d[2]] = i4.z;
+  dst.id[d[3]] = i4.w;
 }
 
 __global__ void k_fill(double* a, size_t n, double v) {

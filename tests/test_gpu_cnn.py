@@ -84,22 +84,76 @@ def test_conv_raw_layers_match_oracle(pg, D):
                 assert np.all(got[b, nch:] == 0.0), which
 
 
-@pytest.mark.parametrize("N,tol", [(32, 1e-5), (64, 1e-5), (48, 2e-2)])
-def test_preconditioner_apply_matches_oracle(pg, N, tol):
-    """z = N r on the periodic grid: the composed 9^3 FP32 kernel (N % 32 == 0)
-    matches the oracle's FP64 four-layer network to FP32 accuracy; the BF16
-    tensor-core path (other N) to BF16 accuracy."""
+@pytest.mark.parametrize("N,mode,tol", [(32, "fp32", 1e-5), (64, "fp32", 1e-5), (64, "tc", 1e-5),
+                                        (64, "layers", 2e-2), (48, "tc", 2e-2)])
+def test_preconditioner_apply_matches_oracle(pg, N, mode, tol):
+    """z = N r on the periodic grid against the oracle's FP64 four-layer
+    network: the composed 9^3 kernel on the CUDA cores to FP32 accuracy (also
+    what the tensor-core mode runs on grids that are not a multiple of 128),
+    the four BF16 convs (what N = 48, not a multiple of 32, runs in every mode)
+    to BF16 accuracy."""
     ws = ocnn.init_weights(9)
     flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
     ws32 = [w.astype(np.float32).astype(np.float64) for w in ws]
     c = pg.Context().init(N, 0, 0)
     c.cnn_set_weights(flat)
+    c.cnn_set_apply({"tc": pg.CNN_APPLY_TC, "fp32": pg.CNN_APPLY_FP32, "layers": pg.CNN_APPLY_LAYERS}[mode])
     r = inputs.noise_field(N, 3)
     rt = torch.from_numpy(r.astype(np.float32)).cuda()
     z = torch.empty_like(rt)
     c.cnn_apply(rt, z)
     ref, _ = ocnn.forward(r.astype(np.float32).astype(np.float64).reshape(N, N, N), ws32)
     assert rel(z.cpu().numpy().astype(np.float64), ref.reshape(-1)) <= tol
+
+
+def oracle_sampled_apply(r, N, ws, points):
+    """The oracle network at sampled cells: N r at p depends on r within
+    distance 4 (four 3x3x3 layers), so the oracle's forward pass on the 9^3
+    periodic crop centred at p gives the exact value at the crop's centre."""
+    g = r.reshape(N, N, N)
+    out = []
+    for (pz, py, px) in points:
+        idx = [(c + np.arange(-4, 5)) % N for c in (pz, py, px)]
+        crop = g[np.ix_(*idx)]
+        y, _ = ocnn.forward(crop, ws)
+        out.append(y[4, 4, 4])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("N", [128, 256])
+def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N):
+    """The composed 9^3 kernel on the tensor cores (BF16 r and K, FP32
+    accumulation in TMEM) against the oracle's FP64 network at 200 sampled
+    cells (BF16 tolerance), and against the FP32 CUDA-core evaluation of the
+    same composed kernel at every cell. The sample includes the grid's corners
+    and faces, where the periodic wrap and the edges of the 16 x 128 column
+    blocks are exercised."""
+    ws = ocnn.init_weights(9)
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    ws32 = [w.astype(np.float32).astype(np.float64) for w in ws]
+    c = pg.Context().init(N, 0, 0)
+    c.cnn_set_weights(flat)
+    r = inputs.noise_field(N, 4)
+    rt = torch.from_numpy(r.astype(np.float32)).cuda()
+    z_tc = torch.full_like(rt, float("nan"))
+    z_32 = torch.full_like(rt, float("nan"))
+    c.cnn_set_apply(pg.CNN_APPLY_TC)
+    c.cnn_apply(rt, z_tc)
+    c.cnn_set_apply(pg.CNN_APPLY_FP32)
+    c.cnn_apply(rt, z_32)
+    zt = z_tc.cpu().numpy().astype(np.float64)
+    z3 = z_32.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(zt))
+    assert rel(zt, z3) <= 1e-2
+    rng = np.random.default_rng(N)
+    pts = [tuple(p) for p in rng.integers(0, N, size=(180, 3))]
+    pts += [(0, 0, 0), (N - 1, N - 1, N - 1), (0, N - 1, 15), (N - 1, 0, 16), (5, 127, 0), (6, 128 % N, N - 1),
+            (N // 2, N - 1, N // 2), (3, 4, N - 16), (N - 4, 124, 31), (1, 1, N - 1), (N - 1, 129 % N, 0),
+            (7, N - 5, 8), (N // 3, 63, 47), (2, N - 2, N - 2), (N - 2, 2, 2), (9, 120, 112), (11, 135 % N, 113),
+            (0, 64, 0), (N - 1, 191 % N, N - 1), (17, 255 % N, 240 % N)]
+    ref = oracle_sampled_apply(r.astype(np.float32).astype(np.float64), N, ws32, pts)
+    got = np.array([zt.reshape(N, N, N)[p] for p in pts])
+    assert rel(got, ref) <= 1e-2
 
 
 def test_network_forward_loss_and_gradients_match_oracle(pg):
