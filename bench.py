@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="mixed",
                     help="mixed: FP32 CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
                          "cnn: mixed flexible CG with the learned preconditioner (trained before timing)")
-    ap.add_argument("--cnn-apply", choices=["tc", "fp32", "layers"], default="tc",
+    ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
     ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
@@ -164,7 +164,8 @@ def run_ours(args):
     if args.solver == "cnn":
         weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
-    apply_mode = {"tc": pg.CNN_APPLY_TC, "fp32": pg.CNN_APPLY_FP32, "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
+    apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
+                  "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
     if weights is not None:
         c.cnn_set_weights(weights)
         c.cnn_set_apply(apply_mode)
@@ -281,7 +282,7 @@ def run_ours(args):
     kname = {("pap", 1): "k_cg_pap<float,false>", ("update", 1): "k_cg_update32",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
     roof = None
-    if dom == "precond" and apply_mode == pg.CNN_APPLY_TC:
+    if dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):
         r = rows[dom]
         _, _, pk = peaks()
         peak = pk.get("bf16_tflops_sustained", 1700.0)

@@ -189,9 +189,13 @@ int pic_cnn_apply(pic_ctx *c, const float *r, float *z);
  *                        BF16, FP32 accumulation (default); on grids that are
  *                        not a multiple of 128 this mode runs PIC_CNN_APPLY_FP32;
  *   PIC_CNN_APPLY_FP32   composed kernel on the CUDA cores, FP32 throughout;
- *   PIC_CNN_APPLY_LAYERS the four BF16 tensor-core convs of the network.
+ *   PIC_CNN_APPLY_LAYERS the four BF16 tensor-core convs of the network;
+ *   PIC_CNN_APPLY_TC_FUSED as PIC_CNN_APPLY_TC, and flexible CG runs its
+ *                        residual/solution update and the direction's dot
+ *                        products inside the preconditioner kernel (one pass
+ *                        instead of three; N % 128 == 0, else as TC).
  * Returns PIC_EINVAL for another mode. */
-enum { PIC_CNN_APPLY_TC = 0, PIC_CNN_APPLY_FP32 = 1, PIC_CNN_APPLY_LAYERS = 2 };
+enum { PIC_CNN_APPLY_TC = 0, PIC_CNN_APPLY_FP32 = 1, PIC_CNN_APPLY_LAYERS = 2, PIC_CNN_APPLY_TC_FUSED = 3 };
 int pic_cnn_set_apply(pic_ctx *c, int mode);
 
 /* Forward pass over B crops: y = N(x) (device FP32 [B][D^3] each); keeps the

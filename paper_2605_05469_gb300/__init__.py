@@ -35,6 +35,7 @@ PC_CNN = 1
 CNN_APPLY_TC = 0
 CNN_APPLY_FP32 = 1
 CNN_APPLY_LAYERS = 2
+CNN_APPLY_TC_FUSED = 3
 CNN_WEIGHTS = 14688
 
 

@@ -35,7 +35,7 @@ void free_solver(pic_ctx* c) {
   SolverWs& w = c->ws;
   dfree(w.x); dfree(w.r); dfree(w.p[0]); dfree(w.p[1]); dfree(w.q);
   dfree(w.xm[0]); dfree(w.xm[1]);
-  dfree(w.x32); dfree(w.r32); dfree(w.p32[0]); dfree(w.p32[1]);
+  dfree(w.x32); dfree(w.r32); dfree(w.r32b); dfree(w.p32[0]); dfree(w.p32[1]);
   dfree(w.z32[0]); dfree(w.z32[1]); dfree(w.q32);
   dfree(w.b);
   dfree(c->partials);
@@ -102,10 +102,6 @@ int sync_status(pic_ctx* c) {
   return check_dev_err(c);
 }
 
-int set_smem_attr(const void* fn, size_t bytes) {
-  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return PIC_OK;
-}
 
 bool dev_ptr_ok(const void* p) { return p != nullptr && ((uintptr_t)p % 16) == 0; }
 
@@ -353,10 +349,41 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   int zc = 0;
   if ((e = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n))) return e;
   launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
-         c->partials, c->counter, 1);
+         c->partials, c->counter, 1, 0);
   launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
   int cur = 0;
   int inner_err = PIC_OK;
+  // Tensor-core preconditioner: the update, the preconditioner and the
+  // direction's dots are one kernel; the residual ping-pongs between r32 and
+  // r32b (rc = current). A reliable update (rare) replaces r, and then z and
+  // the dots are recomputed from it by the redo kernels, which return at once
+  // otherwise.
+  const bool fused = cnn_fused_ok(c);
+  if (fused && !w.r32b && (e = dalloc(&w.r32b, c->n))) return e;
+  float* rbuf[2] = {w.r32, w.r32b};
+  int rc = 0;
+  auto batch_fused = [&]() {
+    for (int i = 0; i < m; ++i) {
+      const bool sample = c->prof_on && i == 0;
+      int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
+      launch(c, k_cg_pap<float, true>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
+             w.p32[cur ^ 1], w.q32, c->sc, c->partials, c->counter, c->err, gp);
+      if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
+      slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
+      int ce = cnn_apply_fused(c, rbuf[rc], rbuf[rc ^ 1], w.z32[zc ^ 1], w.q32, w.p32[cur ^ 1], w.x32);
+      if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
+      rc ^= 1;
+      zc ^= 1;
+      launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
+             rbuf[rc], c->sc, c->partials, c->counter, c->err, gr, 1);
+      if (!ce) ce = cnn_apply_redo(c, rbuf[rc], w.z32[zc]);
+      if (ce && !inner_err) inner_err = ce;
+      launch(c, k_fcg_dot, sb, 256, 0, (const float*)rbuf[rc], (const float*)w.z32[zc], (const float*)w.q32, n4,
+             c->sc, c->partials, c->counter, 0, 1);
+      launch(c, k_fcg_fallback, sb, 256, 0, (const float*)rbuf[rc], w.z32[zc], n4, (const Scalars*)c->sc);
+      cur ^= 1;
+    }
+  };
   auto batch = [&]() {
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
@@ -376,18 +403,22 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
       if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
       if (ce && !inner_err) inner_err = ce;
       launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
-             c->partials, c->counter, 0);
+             c->partials, c->counter, 0, 0);
       launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
       cur ^= 1;
     }
   };
-  if ((e = run_batches(c, m, maxit, batch))) return e;
+  if (fused) {
+    if ((e = run_batches(c, m, maxit, batch_fused))) return e;
+  } else {
+    if ((e = run_batches(c, m, maxit, batch))) return e;
+  }
   if (inner_err) return inner_err;
   CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
   if ((e = sync_status(c))) return e;
   if (c->sc_host[0].done != 1 && c->sc_host[0].done != 3) {
     launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
-           w.r32, c->sc, c->partials, c->counter, c->err, gr, 2);
+           rbuf[rc], c->sc, c->partials, c->counter, c->err, gr, 2);
     CK(cudaMemcpyAsync(&c->sc_host[0], c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream));
     if ((e = sync_status(c))) return e;
   }

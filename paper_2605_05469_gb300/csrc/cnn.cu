@@ -153,23 +153,52 @@ void cnn_state_free(CnnState* s) {
 
 bool cnn_ready(const pic_ctx* c) { return c->cnn && c->cnn->has_weights; }
 
+bool cnn_tc_ok(const pic_ctx* c) {
+  return c->N % tck::BY == 0 && (c->cnn_apply_mode == PIC_CNN_APPLY_TC || c->cnn_apply_mode == PIC_CNN_APPLY_TC_FUSED);
+}
+
+bool cnn_fused_ok(const pic_ctx* c) { return c->N % tck::BY == 0 && c->cnn_apply_mode == PIC_CNN_APPLY_TC_FUSED; }
+
+// The composed kernel on the tensor cores, persistent: one CTA per SM, each a
+// contiguous range of output planes.
+template <bool FUSED>
+int launch_tc(pic_ctx* c, const float* r, float* z, const TcFcg& F) {
+  static bool configured = false;
+  if (!configured) {
+    CK(cudaFuncSetAttribute((const void*)k_apply_k_tc<FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)tck::smem_bytes<FUSED>()));
+    configured = true;
+  }
+  const int N = c->N;
+  const long units = (long)(N / tck::BX) * (N / tck::BY) * N;
+  const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
+  launch(c, k_apply_k_tc<FUSED>, grid, tck::THREADS, tck::smem_bytes<FUSED>(), r, z, N,
+         (const unsigned char*)c->cnn->Bt, c->err, F);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x) {
+  if (!cnn_fused_ok(c)) return PIC_EINVAL;
+  TcFcg F{q, p, x, r_new, c->sc, c->partials, c->counter, 0};
+  return launch_tc<true>(c, r, z, F);
+}
+
+int cnn_apply_redo(pic_ctx* c, const float* r, float* z) {
+  if (!cnn_tc_ok(c)) return PIC_EINVAL;
+  TcFcg F{};
+  F.sc = c->sc;
+  F.only_redo = 1;
+  return launch_tc<false>(c, r, z, F);
+}
+
 int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) {
   CnnState* s = c->cnn;
   const int N = c->N;
   // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
-  if (N % tck::BY == 0 && c->cnn_apply_mode == PIC_CNN_APPLY_TC) {
-    static bool configured_tc = false;
-    if (!configured_tc) {
-      CK(cudaFuncSetAttribute((const void*)k_apply_k_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tck::SMEM));
-      configured_tc = true;
-    }
-    // persistent: one CTA per SM, each a contiguous range of output planes
-    const long units = (long)(N / tck::BX) * (N / tck::BY) * N;
-    const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
-    launch(c, k_apply_k_tc, grid, tck::THREADS, tck::SMEM, r, z, N, (const unsigned char*)s->Bt, c->err);
-    CK(cudaGetLastError());
-    return PIC_OK;
+  if (cnn_tc_ok(c)) {
+    TcFcg F{};
+    return launch_tc<false>(c, r, z, F);
   }
   // grids that are not a multiple of 128 run the FP32 composed kernel in TC mode
   if (N % KX == 0 && c->cnn_apply_mode != PIC_CNN_APPLY_LAYERS) {
@@ -262,7 +291,7 @@ int pic_cnn_apply(pic_ctx* c, const float* r, float* z) {
 }
 
 int pic_cnn_set_apply(pic_ctx* c, int mode) {
-  if (!c || mode < PIC_CNN_APPLY_TC || mode > PIC_CNN_APPLY_LAYERS) return PIC_EINVAL;
+  if (!c || mode < PIC_CNN_APPLY_TC || mode > PIC_CNN_APPLY_TC_FUSED) return PIC_EINVAL;
   c->cnn_apply_mode = mode;
   return PIC_OK;
 }

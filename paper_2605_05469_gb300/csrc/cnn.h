@@ -14,5 +14,15 @@ bool cnn_ready(const pic_ctx* c);
 // z = s N(r / s), s = sqrt(*rr / n): the network applied to the periodic
 // N^3 field r (FP32), enqueued on the context stream.
 int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n);
+// Whether the context's preconditioner runs as the tensor-core composed
+// kernel, and whether flexible CG fuses its update into it (the forms below).
+bool cnn_tc_ok(const pic_ctx* c);
+bool cnn_fused_ok(const pic_ctx* c);
+// One flexible-CG step fused around the preconditioner (tensor-core form):
+// r_new = r - alpha q, x += alpha p, z = N r_new, plus the update's and the
+// direction's reductions and bookkeeping in the context scalars.
+int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x);
+// z = N r, only if a reliable update replaced r in this iteration.
+int cnn_apply_redo(pic_ctx* c, const float* r, float* z);
 
 }  // namespace pic

@@ -441,12 +441,11 @@ __global__ void __launch_bounds__(256) k_apply_k(const float* __restrict__ r, fl
 // stacks the nine T_{dz,dy} along N (N = 144), so one MMA gives the
 // contributions of input plane z' to the nine output planes p = z' - dz + 4
 // at once, in nine groups of 16 TMEM columns. The output planes live in a
-// TMEM ring of 32 slots of 16 columns whose slot index decreases with p:
-// group dz of the MMA of plane z' lands in the slot of p = z' - dz + 4, so the
-// dz sum is accumulated by the tensor core itself; an output plane is final
-// once input plane p + 4 has been multiplied, and the epilogue reads it out.
-// Per input plane: 9 dy x 2 K-steps of 16 = 18 MMAs (M 128, N <= 144; 36
-// where the group range wraps around the ring of 32 slots). The epilogue
+// TMEM ring of 16-column slots whose slot index decreases with p: group dz of
+// the MMA of plane z' lands in the slot of p = z' - dz + 4, so the dz sum is
+// accumulated by the tensor core itself; an output plane is final once input
+// plane p + 4 has been multiplied, and the epilogue reads it out. Per input
+// plane: 9 dy x 2 K-steps of 16 = 18 MMAs (M 128, N <= 144). The epilogue
 // zeroes a slot after reading it, so every MMA accumulates.
 //
 // Work: the unit is one output plane of one column (16 x 128 cells); CTA k of
@@ -472,25 +471,38 @@ constexpr int BROWS = 9 * 16;             // N rows of the B operand of one dy: 
 constexpr int BCHUNK_B = BROWS * 16;      // 2304
 constexpr int BDY_B = 4 * BCHUNK_B;       // 9216
 constexpr int B_BYTES = 9 * BDY_B;        // 82944: all 81 Toeplitz matrices
-constexpr int TSLOTS = 32;                // TMEM ring of output planes
-constexpr int TMEM_COLS = TSLOTS * 16;    // 512: all of the SM's tensor memory
+// TMEM: 32 physical slots of 16 columns (all 512 columns). Output planes
+// take ring slots (-v) mod 24; a plane's nine groups start at a ring slot
+// s < 24 and run on into physical slots up to s + 8 <= 31, so slots 24..31
+// shadow ring slots 0..7 and no MMA ever wraps. An output with ring slot
+// r <= 7 may hold partial sums in r and r + 24; the epilogue adds both.
+constexpr int TSLOTS = 24;
+constexpr int PSLOTS = 32;
+constexpr int TMEM_COLS = PSLOTS * 16;    // 512: all of the SM's tensor memory
 // warp roles: warp 0 issues the MMAs, warps 1-4 read the finished output
 // planes out of TMEM (warp w reaches TMEM lanes 32 (w % 4) .. + 31), warps
-// 5-8 copy and convert the input planes
-constexpr int EPI_WARP0 = 1, PROD_WARP0 = 5, NWARPS = 9;
-constexpr int THREADS = NWARPS * 32;      // 288
-constexpr int PTHREADS = 128;             // producer threads
-constexpr int LOADS = (AROWS * 8 + PTHREADS - 1) / PTHREADS;  // 16-byte pieces per producer per plane (9)
+// 5-12 load and convert the input planes
+constexpr int EPI_WARP0 = 1, PROD_WARP0 = 5, NWARPS = 13;
+constexpr int THREADS = NWARPS * 32;      // 416
+constexpr int PTHREADS = 256;             // producer threads
+constexpr int LOADS = (AROWS * 8 + PTHREADS - 1) / PTHREADS;  // 16-byte pieces per producer per plane (5)
 constexpr int ASLOTS = 4;                 // BF16 A operands (input planes ready for the tensor cores)
-constexpr int STAGES = 4;                 // FP32 input planes in flight (cp.async)
-constexpr int STAGE_B = AROWS * 128;      // 17408: 136 rows x 32 FP32
-// an output plane's TMEM slot (zeroed by the epilogue after it reads it) is
-// taken again by the output plane TSLOTS later, whose first term comes from
-// the input plane TSLOTS - 8 input planes after the one that completed it
+constexpr int TILE_OUT_B = BY * BX * 4;   // 8192: one output plane's 128 x 16 FP32 block
+// the fused form's epilogue operands r, q, p, x of one output plane's block,
+// double-buffered (cp.async two planes ahead)
+constexpr int EPI_PLANE_B = 4 * TILE_OUT_B;
+template <bool FUSED>
+constexpr int epi_bufs() { return FUSED ? 2 : 0; }
+// an output plane's TMEM slots (zeroed by the epilogue after it reads them)
+// are taken again by the output plane TSLOTS later, whose first term comes
+// from the input plane TSLOTS - 8 input planes after the one that completed it
 constexpr int SLOT_REUSE_LAG = TSLOTS - 8;
 constexpr int ERING = 32;                 // plane handshakes between the MMA issuer and the epilogue
-constexpr size_t SMEM = (size_t)B_BYTES + ASLOTS * SLOT_B + STAGES * STAGE_B;  // 188416
-static_assert(SMEM > 114 * 1024 && SMEM <= 227 * 1024, "one CTA per SM");
+template <bool FUSED>
+constexpr size_t smem_bytes() {
+  return (size_t)B_BYTES + ASLOTS * SLOT_B + TILE_OUT_B + epi_bufs<FUSED>() * EPI_PLANE_B;
+}  // 126976 plain, 192512 fused
+static_assert(smem_bytes<false>() > 114 * 1024 && smem_bytes<true>() <= 226 * 1024, "one CTA per SM");
 static_assert(ERING > SLOT_REUSE_LAG, "the issuer must not lap the epilogue handshakes");
 }  // namespace tck
 
@@ -522,14 +534,13 @@ __device__ __forceinline__ void mma_acc(uint32_t tmem_d, uint64_t ad, uint64_t b
       "l"(ad), "l"(bd), "r"(idesc));
 }
 
-// All MMAs of one input plane, straight-line: for each dy and K-step q the A
-// operand is the plane shifted by dy rows and advanced by 16 x-inputs; one
-// MMA per segment of consecutive dz groups (two where the groups wrap around
-// the TMEM ring). Every offset is a compile-time constant added to the base
-// descriptors, so the issue stream carries no branches.
-template <int SEGS>
-__device__ __forceinline__ void tc_issue_plane(uint64_t ad0, uint64_t b0, uint32_t d0, uint32_t i0, uint64_t b1,
-                                               uint32_t d1, uint32_t i1) {
+// All 18 MMAs of one input plane, straight-line: for each dy and K-step q the
+// A operand is the plane shifted by dy rows and advanced by 16 x-inputs, the
+// B operand the dz groups dz_lo.. of T_{., dy}. Every offset is a
+// compile-time constant added to the base descriptors, so the issue stream
+// carries no branches (branches between the MMAs of a plane cost the issuing
+// thread more than the MMAs themselves).
+__device__ __forceinline__ void tc_issue_plane(uint64_t ad0, uint64_t b0, uint32_t d0, uint32_t idesc) {
   using namespace tck;
 #pragma unroll
   for (int dy = 0; dy < 9; ++dy) {
@@ -537,11 +548,13 @@ __device__ __forceinline__ void tc_issue_plane(uint64_t ad0, uint64_t b0, uint32
     for (int q = 0; q < 2; ++q) {
       const uint64_t a = ad0 + (uint64_t)((dy * 16 + q * 2 * CHUNK_B) >> 4);
       const uint64_t bo = (uint64_t)((dy * BDY_B + q * 2 * BCHUNK_B) >> 4);
-      mma_acc(d0, a, b0 + bo, i0);
-      if (SEGS == 2) mma_acc(d1, a, b1 + bo, i1);
+      mma_acc(d0, a, b0 + bo, idesc);
     }
   }
 }
+
+// Ring slot of output index v (v >= 0 counts the CTA's output planes).
+__device__ __forceinline__ int tc_ring_slot(long v) { return (int)((tck::TSLOTS - v % tck::TSLOTS) % tck::TSLOTS); }
 
 // One input plane of the CTA's stream: column `col`, run of output planes
 // [pa, pb), input plane z (unwrapped, pa-4 <= z <= pb+3).
@@ -581,43 +594,76 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Start the copy of input plane P (136 rows x 32 FP32 x-inputs, periodic) into
-// an FP32 stage, row-major. Producer thread t moves pieces t + 128 i (16 B
-// each); it later converts the same pieces, so no barrier separates copy and
-// convert.
-__device__ __forceinline__ void tc_issue(const TcPlane& P, const float* __restrict__ r, int N, unsigned char* stage,
-                                         int ptid) {
+// Producer thread t moves the 16-byte pieces t + 256 i (i < 5) of every
+// input plane: x-inputs 4 g .. 4 g + 3 with g = t % 8 (the same for all its
+// pieces) of rows t / 8 + 32 i. Its source offsets within a plane depend on
+// the column only and are recomputed when the column changes. Planes are
+// loaded into registers two planes ahead of their conversion.
+struct TcRows {
+  int col;
+  int off[tck::LOADS];  // (gy * N + gx) of each piece; -1 past the last row
+};
+
+__device__ __forceinline__ void tc_rows(const TcPlane& P, int N, int ptid, TcRows& R) {
   using namespace tck;
   int x0, y0;
   tc_origin(P, N, x0, y0);
-  const int gz = wrap(P.z, N);
+  R.col = P.col;
+  // 4-float pieces never straddle the periodic wrap (x0 - 4 is a multiple of 4)
+  const int gx = wrap(x0 - 4 + 4 * (ptid & 7), N);
 #pragma unroll
   for (int i = 0; i < LOADS; ++i) {
-    const int idx = ptid + i * PTHREADS;
-    if (idx < AROWS * 8) {
-      const int g = idx & 7, row = idx >> 3;
-      // 4-float pieces never straddle the periodic wrap (x0 - 4 is a multiple of 4)
-      const int gy = wrap(y0 - 4 + row, N), gx = wrap(x0 - 4 + 4 * g, N);
-      cp_async16(stage + idx * 16, r + ((size_t)gz * N + gy) * N + gx);
+    const int row = (ptid >> 3) + 32 * i;
+    R.off[i] = row < AROWS ? wrap(y0 - 4 + row, N) * N + gx : -1;
+  }
+}
+
+// One input plane's pieces of r (and, fused, of q) in registers.
+template <bool FUSED>
+struct TcIn {
+  float4 r[tck::LOADS];
+  float4 q[FUSED ? tck::LOADS : 1];
+};
+
+template <bool FUSED>
+__device__ __forceinline__ void tc_load(const TcPlane& P, const float* __restrict__ r, const float* __restrict__ q,
+                                        int N, int ptid, TcRows& R, TcIn<FUSED>& in) {
+  using namespace tck;
+  if (R.col != P.col) tc_rows(P, N, ptid, R);
+  const size_t plane = (size_t)wrap(P.z, N) * N * N;
+#pragma unroll
+  for (int i = 0; i < LOADS; ++i) {
+    if (R.off[i] >= 0) {
+      in.r[i] = __ldg(reinterpret_cast<const float4*>(r + plane + R.off[i]));
+      if (FUSED) in.q[i] = __ldg(reinterpret_cast<const float4*>(q + plane + R.off[i]));
     }
   }
 }
 
-// FP32 stage -> BF16 canonical K-major A operand (the thread's own pieces).
-__device__ __forceinline__ void tc_convert(const unsigned char* stage, unsigned char* slot, int ptid) {
+// Registers -> BF16 canonical K-major A operand: x-input k = 4 g .. 4 g + 3
+// goes to K-chunk k / 8 at byte (k % 8) * 2 of its row. With FUSED the
+// operand is the updated residual r - alpha q.
+template <bool FUSED>
+__device__ __forceinline__ void tc_store(const TcIn<FUSED>& in, unsigned char* slot, int ptid, float alpha) {
   using namespace tck;
+  const int g = ptid & 7;
+  unsigned char* dst = slot + (g >> 1) * CHUNK_B + (ptid >> 3) * 16 + (g & 1) * 8;
 #pragma unroll
   for (int i = 0; i < LOADS; ++i) {
-    const int idx = ptid + i * PTHREADS;
-    if (idx < AROWS * 8) {
-      const int g = idx & 7, row = idx >> 3;
-      const float4 v = *reinterpret_cast<const float4*>(stage + idx * 16);
+    if ((ptid >> 3) + 32 * i < AROWS) {
+      float4 v = in.r[i];
+      if (FUSED) {
+        const float4 qv = in.q[i];
+        v.x = fmaf(-alpha, qv.x, v.x);
+        v.y = fmaf(-alpha, qv.y, v.y);
+        v.z = fmaf(-alpha, qv.z, v.z);
+        v.w = fmaf(-alpha, qv.w, v.w);
+      }
       __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
       uint2 packed;
       packed.x = *reinterpret_cast<uint32_t*>(&lo);
       packed.y = *reinterpret_cast<uint32_t*>(&hi);
-      // x-input k = 4 g .. 4 g + 3 -> chunk k / 8, byte (k % 8) * 2 of the row
-      *reinterpret_cast<uint2*>(slot + (g >> 1) * CHUNK_B + row * 16 + (g & 1) * 8) = packed;
+      *reinterpret_cast<uint2*>(dst + i * 32 * 16) = packed;  // 32 rows further
     }
   }
 }
@@ -633,26 +679,130 @@ __device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// Output plane p = P.z - 4 is complete once input plane P.z has been
-// multiplied: TMEM slot -> z. Epilogue warp w reads TMEM lanes 32 (w % 4) ..
-// + 31 (rows y), all 16 columns (x) of the slot.
-__device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict__ z, int N, uint32_t tmem,
-                                            long ubegin) {
-  using namespace tck;
-  const int p = P.z - 4;
-  if (p < P.pa) return;  // an input plane of the lower halo: no output completes
+// The CG update fused in front of the preconditioner (flexible CG, one
+// iteration): with q = A p from the direction kernel,
+//   r' = r - alpha q,  x' = x + alpha p  (x read as zero after a reliable
+//   update folded it),  z = N r',
+// and the reductions (r', r'), (r', z), (z, q), (r', q) that the update's
+// convergence test and the next direction need. r' goes to a second buffer:
+// neighbouring CTAs still read r as their halo.
+struct TcFcg {
+  const float* q;
+  const float* p;
+  float* x;
+  float* r_new;
+  Scalars* sc;
+  double* partials;
+  unsigned* counter;
+  int only_redo;  // plain form: run only when a reliable update replaced r
+};
+
+struct TcDots {
+  CompSum rr, rz, zq, rq;
+};
+
+// Epilogue thread et (0..127) moves float4 f = et + 128 k (k < 4) of the
+// plane's 128 x 16 block: row f / 4, x-quarter f % 4.
+__device__ __forceinline__ size_t tc_epi_offset(const TcPlane& P, int N, int et, int k) {
   int x0, y0;
   tc_origin(P, N, x0, y0);
-  const long vv = (long)P.col * N + p - ubegin;
-  const int s = (int)((-vv) & (TSLOTS - 1));
+  const int f = et + 128 * k;
+  return ((size_t)(P.z - 4) * N + (size_t)(y0 + (f >> 2))) * N + x0 + 4 * (f & 3);
+}
+
+// The fused epilogue's operands r, q, p, x for the owned cells of the output
+// plane that P completes, copied two planes ahead (they do not depend on the
+// MMAs) into one of two shared-memory buffers: [array][f] float4 per buffer,
+// each thread its own pieces. One cp.async group per plane, always committed.
+__device__ __forceinline__ void tc_epi_fetch(const TcPlane& P, const float* __restrict__ r, int N, const TcFcg& F,
+                                             bool x_zero, float4* buf) {
+  if (P.z - 4 >= P.pa) {
+    const int et = threadIdx.x - tck::EPI_WARP0 * 32;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int f = et + 128 * k;
+      const size_t off = tc_epi_offset(P, N, et, k);
+      cp_async16(buf + f, r + off);
+      cp_async16(buf + 512 + f, F.q + off);
+      cp_async16(buf + 1024 + f, F.p + off);
+      if (!x_zero) cp_async16(buf + 1536 + f, F.x + off);
+    }
+  }
+  cp_async_commit();
+}
+
+// Float4 slot of (row, c4) in the epilogue's transpose tile: XOR-swizzled so
+// that both the row-per-thread writes and the coalesced reads are free of
+// shared-memory bank conflicts.
+__device__ __forceinline__ int tc_tile_idx(int row, int c4) { return row * 4 + (c4 ^ ((row >> 1) & 3)); }
+
+__device__ __forceinline__ void tc_epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Output plane p = P.z - 4 is complete once input plane P.z has been
+// multiplied. Epilogue warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows y),
+// all 16 columns (x) of the slot, into a shared-memory tile; the 128
+// epilogue threads then move the plane's 128 x 16 block to and from global
+// memory four threads per 64-byte row segment (coalesced).
+template <bool FUSED>
+__device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict__ z, int N, uint32_t tmem,
+                                            long ubegin, const TcFcg& F, float alpha, bool x_zero, TcDots& D,
+                                            float4* tile, const float4* ops) {
+  using namespace tck;
+  const int p = P.z - 4;
+  if (p < P.pa) return;  // an input plane of the lower halo: no output completes (uniform)
+  const int s = tc_ring_slot((long)P.col * N + p - ubegin);
+  const int et = threadIdx.x - EPI_WARP0 * 32;  // 0..127
   const int quarter = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
+  const int row = quarter * 32 + lane;          // TMEM lane = y row of the block
   float o[16];
   const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * 16);
   tmem_ld16(ta, o);
   tmem_zero16(ta);  // the slot's next output plane starts from zero
-  float4* dst = reinterpret_cast<float4*>(z + ((size_t)p * N + (y0 + quarter * 32 + lane)) * N + x0);
+  if (s + TSLOTS < PSLOTS) {
+    // partial sums of the planes whose groups ran into the shadow slot
+    float o2[16];
+    const uint32_t tb = ta + (uint32_t)(TSLOTS * 16);
+    tmem_ld16(tb, o2);
+    tmem_zero16(tb);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) dst[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+    for (int i = 0; i < 16; ++i) o[i] += o2[i];
+  }
+  tc_epi_barrier();  // the previous plane's reads of the tile are done
+#pragma unroll
+  for (int c4 = 0; c4 < 4; ++c4)
+    tile[tc_tile_idx(row, c4)] = make_float4(o[4 * c4], o[4 * c4 + 1], o[4 * c4 + 2], o[4 * c4 + 3]);
+  tc_epi_barrier();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int f = et + 128 * k;
+    const size_t off = tc_epi_offset(P, N, et, k);
+    const float4 zv = tile[tc_tile_idx(f >> 2, f & 3)];
+    *reinterpret_cast<float4*>(z + off) = zv;
+    if (!FUSED) continue;
+    float4 rv = ops[f], xv = x_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : ops[1536 + f];
+    const float4 qv = ops[512 + f], pv = ops[1024 + f];
+    const float* q4 = &qv.x;
+    const float* p4 = &pv.x;
+    const float* z4 = &zv.x;
+    float* r4 = &rv.x;
+    float* x4 = &xv.x;
+    float prr = 0.f, prz = 0.f, pzq = 0.f, prq = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      r4[i] = fmaf(-alpha, q4[i], r4[i]);  // the same value the producers fed the tensor cores
+      x4[i] = fmaf(alpha, p4[i], x4[i]);
+      prr = fmaf(r4[i], r4[i], prr);
+      prz = fmaf(r4[i], z4[i], prz);
+      pzq = fmaf(z4[i], q4[i], pzq);
+      prq = fmaf(r4[i], q4[i], prq);
+    }
+    D.rr.add(prr);
+    D.rz.add(prz);
+    D.zq.add(pzq);
+    D.rq.add(prq);
+    *reinterpret_cast<float4*>(F.r_new + off) = rv;
+    *reinterpret_cast<float4*>(F.x + off) = xv;
+  }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -676,17 +826,26 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err
   }
 }
 
+template <bool FUSED>
 __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __restrict__ r, float* __restrict__ z,
                                                                 int N, const unsigned char* __restrict__ Bg,
-                                                                int* err) {
+                                                                int* err, TcFcg F) {
   using namespace tck;
+  if (F.sc) {
+    if (F.sc->done) return;
+    if (!FUSED && F.only_redo && !F.sc->redo) return;
+  }
+  const float alpha = FUSED ? (float)F.sc->alpha : 0.f;
+  const bool x_zero = FUSED && F.sc->x32_reset != 0;
+  TcDots dots;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ __align__(8) uint64_t a_full[ASLOTS], a_empty[ASLOTS], acc_full[ERING], acc_empty[ERING], b_bar;
-  unsigned char* Bs = smem;                         // B_BYTES
-  unsigned char* slots = smem + B_BYTES;            // ASLOTS x SLOT_B (BF16 A operands)
-  unsigned char* stages = slots + ASLOTS * SLOT_B;  // STAGES x STAGE_B (FP32 input planes)
+  unsigned char* Bs = smem;                                         // B_BYTES
+  unsigned char* slots = smem + B_BYTES;                            // ASLOTS x SLOT_B (BF16 A operands)
+  float4* tile = reinterpret_cast<float4*>(slots + ASLOTS * SLOT_B);  // TILE_OUT_B (epilogue transpose)
+  float4* ebuf = tile + TILE_OUT_B / 16;                            // fused: 2 x EPI_PLANE_B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long U = (long)(N / BX) * (N / BY) * N;
   const long ubegin = U * blockIdx.x / gridDim.x, uend = U * (blockIdx.x + 1) / gridDim.x;
@@ -745,18 +904,11 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
         // groups dz_lo..dz_hi feed output planes z + 4 - dz inside [pa, pb)
         const int dz_lo = max(0, P.z + 4 - (P.pb - 1)), dz_hi = min(8, P.z + 4 - P.pa);
         const long v_lo = (long)P.col * N + (P.z - dz_lo + 4) - ubegin;
-        const int s_lo = (int)((-v_lo) & (TSLOTS - 1));
+        const int s_lo = tc_ring_slot(v_lo);
         const int ng = dz_hi - dz_lo + 1;
-        const int n1 = min(ng, TSLOTS - s_lo);  // groups before the ring wraps
         const uint64_t ad0 = smem_desc(smem_u32(slots + sa * SLOT_B), CHUNK_B, 128);
         const uint64_t b0 = bd0 + (uint64_t)(dz_lo * 16);  // 16 B-rows per group = 256 B
-        const uint32_t d0 = tmem + (uint32_t)(s_lo * 16);
-        if (n1 == ng) {
-          tc_issue_plane<1>(ad0, b0, d0, idesc_n(16 * ng), 0, 0, 0);
-        } else {
-          tc_issue_plane<2>(ad0, b0, d0, idesc_n(16 * n1), b0 + (uint64_t)(n1 * 16), tmem,
-                            idesc_n(16 * (ng - n1)));
-        }
+        tc_issue_plane(ad0, b0, tmem + (uint32_t)(s_lo * 16), idesc_n(16 * ng));
         // both arrive once every MMA issued so far has completed
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&a_empty[sa]))
@@ -773,54 +925,122 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
     // ---- epilogue: 128 threads ----
     TcPlane P;
     bool have = tc_run_at(ubegin, uend, N, P);
+    constexpr int EB = EPI_PLANE_B / 16;  // float4 per operand buffer
+    TcPlane ahead = P;
+    bool have_a = have;
+    if (FUSED) {
+      // operands of planes 0 and 1 in flight
+      for (int b = 0; b < 2; ++b) {
+        if (have_a) {
+          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + b * EB);
+          have_a = tc_next(uend, N, ahead);
+        } else {
+          cp_async_commit();
+        }
+      }
+    }
     for (uint32_t j = 0; have; ++j) {
+      if (FUSED) cp_async_wait<1>();  // plane j's operands (own pieces)
       if (!tc_wait(&acc_full[j % ERING], (j / ERING) & 1u, err, &abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tc_epilogue(P, z, N, tmem, ubegin);
+      tc_epilogue<FUSED>(P, z, N, tmem, ubegin, F, alpha, x_zero, dots, tile, ebuf + (j & 1u) * EB);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[j % ERING]);
+      if (FUSED) {
+        // refill the buffer plane j used with plane j + 2
+        if (have_a) {
+          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + (j & 1u) * EB);
+          have_a = tc_next(uend, N, ahead);
+        } else {
+          cp_async_commit();
+        }
+      }
       have = tc_next(uend, N, P);
     }
+    if (FUSED) cp_async_wait<0>();
   } else {
-    // ---- producers: 128 threads ----
+    // ---- producers: 256 threads, two planes in registers ahead of conversion ----
     const int ptid = tid - PROD_WARP0 * 32;
+    TcRows rows;
+    rows.col = -1;
+    TcIn<FUSED> in0, in1;
     TcPlane cur, ahead;
     bool have = tc_run_at(ubegin, uend, N, cur);
     ahead = cur;
-    bool have_ahead = have;
-    // planes 0 .. STAGES-2 in flight, one cp.async group each
-    for (int st = 0; st < STAGES - 1; ++st) {
-      if (have_ahead) {
-        tc_issue(ahead, r, N, stages + st * STAGE_B, ptid);
-        have_ahead = tc_next(uend, N, ahead);
-      }
-      cp_async_commit();
+    bool have_a = have;
+    if (have_a) {
+      tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in0);
+      have_a = tc_next(uend, N, ahead);
     }
-    for (uint32_t j = 0; have; ++j) {
+    if (have_a) {
+      tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in1);
+      have_a = tc_next(uend, N, ahead);
+    }
+    uint32_t j = 0;
+    // plane j from buffer `in`, which is then refilled with plane j + 2
+    auto step = [&](TcIn<FUSED>& in) -> bool {
       const uint32_t sa = j % ASLOTS;
-      cp_async_wait<STAGES - 2>();  // plane j's group (groups complete in order)
       if (j >= (uint32_t)ASLOTS) {
         // the MMAs of plane j - ASLOTS, which read this A slot, are done
         const uint32_t k = j - ASLOTS;
-        if (!tc_wait(&a_empty[sa], (k / ASLOTS) & 1u, err, &abort_flag)) break;
+        if (!tc_wait(&a_empty[sa], (k / ASLOTS) & 1u, err, &abort_flag)) return false;
       }
-      tc_convert(stages + (j % STAGES) * STAGE_B, slots + sa * SLOT_B, ptid);
-      // refill the stage plane j-1 used with plane j + STAGES - 1
-      if (have_ahead) {
-        tc_issue(ahead, r, N, stages + ((j + STAGES - 1) % STAGES) * STAGE_B, ptid);
-        have_ahead = tc_next(uend, N, ahead);
-      }
-      cp_async_commit();
+      tc_store<FUSED>(in, slots + sa * SLOT_B, ptid, alpha);
       fence_proxy_async_smem();  // the BF16 writes, visible to the tensor cores
       mbar_arrive(&a_full[sa]);
+      if (have_a) {
+        tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in);
+        have_a = tc_next(uend, N, ahead);
+      }
+      ++j;
+      return true;
+    };
+    while (have) {
+      if (!step(in0)) break;
+      if (!(have = tc_next(uend, N, cur))) break;
+      if (!step(in1)) break;
       have = tc_next(uend, N, cur);
     }
-    cp_async_wait<0>();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if (FUSED) {
+    double v[4] = {dots.rr.value(), dots.rz.value(), dots.zq.value(), dots.rq.value()}, tot[4];
+    if (grid_reduce_last<4>(v, F.partials, F.counter, tot) && threadIdx.x == 0) {
+      Scalars* sc = F.sc;
+      // the update's bookkeeping (convergence and the reliable-update trigger)
+      const double rr = tot[0];
+      sc->x32_reset = 0;
+      sc->rr_prev = sc->rr;
+      sc->rr = rr;
+      sc->iter += 1;
+      if (!isfinite(rr)) {
+        sc->done = 3;
+      } else {
+        if (rr <= sc->tol2) {
+          sc->need_update = 1;
+          sc->final_check = 1;
+        } else if (rr <= sc->delta2 * sc->rmax2) {
+          sc->need_update = 1;
+        }
+        if (!sc->need_update && sc->iter >= sc->maxit) sc->done = 2;
+      }
+      // the next direction: beta = -(z, q) / (p, q), with the descent guard
+      double rz = tot[1], zq = tot[2];
+      sc->fallback_now = 0;
+      if (!(rz > 0.0) || !isfinite(rz) || !isfinite(zq)) {
+        sc->fallback_now = 1;
+        sc->fallbacks += 1;
+        rz = rr / 6.0;
+        zq = tot[3] / 6.0;
+      }
+      sc->beta = -zq / sc->pq;
+      sc->rz = rz;
+      if (!isfinite(sc->beta) && !sc->done) sc->done = 3;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

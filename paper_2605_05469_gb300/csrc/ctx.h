@@ -16,6 +16,7 @@ struct SolverWs {
   // flexible CG with the learned preconditioner
   float* z32[2] = {nullptr, nullptr};
   float* q32 = nullptr;  // A p of the last direction
+  float* r32b = nullptr; // second FP32 residual: the fused update writes r' while r is still read as halo
   // shared
   double* b = nullptr;
 };

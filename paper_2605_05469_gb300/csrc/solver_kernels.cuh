@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, dou
       sc->beta = rr / sc->rr_prev;
       sc->rr = rr;
       sc->rmax2 = rr;
+      if (mode == 1) sc->redo = 1;
     }
     sc->need_update = 0;
     sc->final_check = 0;
@@ -488,6 +489,7 @@ __global__ void __launch_bounds__(256) k_project(const double* __restrict__ rho,
     sc->final_check = 0;
     sc->updates = 0;
     sc->fallbacks = 0;
+    sc->redo = 0;
   }
 }
 
@@ -516,8 +518,9 @@ __global__ void __launch_bounds__(256) k_finish(const double* __restrict__ x, do
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fcg_dot(const float* __restrict__ r, const float* __restrict__ z,
                                                  const float* __restrict__ q, size_t n4, Scalars* sc,
-                                                 double* partials, unsigned* counter, int init) {
+                                                 double* partials, unsigned* counter, int init, int only_redo) {
   if (sc->done) return;
+  if (only_redo && !sc->redo) return;
   CompSum arz, azq, arq;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
@@ -551,6 +554,7 @@ __global__ void __launch_bounds__(256) k_fcg_dot(const float* __restrict__ r, co
     }
     sc->beta = init ? 0.0 : -zq / sc->pq;
     sc->rz = rz;
+    sc->redo = 0;
     if (!isfinite(sc->beta)) sc->done = 3;
   }
 }

@@ -247,6 +247,36 @@ def test_fcg_cnn_solve_reaches_true_residual(pg, N):
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+def test_fused_fcg_step_matches_the_unfused_one(pg):
+    """On a 128^3 grid the tensor-core preconditioner runs with the CG update
+    and the direction's dots fused into it (and recomputes z after each
+    reliable update). It must reach the true FP64 relative residual 1e-10
+    (checked with the oracle's operator) in about as many iterations as the
+    unfused sequence with the FP32 evaluation of the same composed kernel, and
+    its solution must agree with that one to the solve tolerance."""
+    N = 128
+    h = L / N
+    ws = ocnn.init_weights(9)
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    c = ctx_with_weights(pg, flat, N)
+    b = inputs.landau_noise_rhs(N, 12)
+    bt = torch.from_numpy(b).cuda()
+    res = {}
+    for mode in ("tc", "fp32"):
+        c.cnn_set_apply(pg.CNN_APPLY_TC_FUSED if mode == "tc" else pg.CNN_APPLY_FP32)
+        phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+        info = c.solve(bt, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, precond=pg.PC_CNN)
+        got = phi.cpu().numpy()
+        bp = b - b.mean()
+        assert np.linalg.norm(bp - opic.apply_A(got, N, h)) <= 1.05e-10 * np.linalg.norm(bp), (mode, info)
+        res[mode] = (info, got)
+    tc, f32 = res["tc"][0], res["fp32"][0]
+    assert tc["reliable_updates"] > 0, tc
+    assert abs(tc["iters"] - f32["iters"]) <= 0.15 * f32["iters"] + 3, (tc, f32)
+    a, r = res["tc"][1], res["fp32"][1]
+    assert np.linalg.norm(a - r) <= 1e-8 * np.linalg.norm(r)
+
+
 def jacobi_network_weights():
     """Weights for which N(x) = x / 6: channel 0 of G carries x / sqrt(6)
     through the centre taps, so N = G^T G = 1/6, the Jacobi direction r / 6
@@ -257,13 +287,16 @@ def jacobi_network_weights():
     return np.concatenate([w.reshape(-1) for w in ocnn.tie(w1, w2)]).astype(np.float32)
 
 
-def test_fcg_with_jacobi_network_takes_the_jacobi_iterations(pg):
+@pytest.mark.parametrize("N", [64, 128])
+def test_fcg_with_jacobi_network_takes_the_jacobi_iterations(pg, N):
     """The whole inference + flexible-CG chain with a network that computes
     the Jacobi direction must converge like mixed Jacobi-CG, up to the cost of
     the BF16 rounding of its activations (an inexact preconditioner, which
-    flexible CG tolerates with a few more iterations)."""
-    N = 64
+    flexible CG tolerates with a few more iterations). N = 128 runs the
+    tensor-core form with the CG update fused into it."""
     c = pg.Context().init(N, 0, 0)
+    if N % 128 == 0:
+        c.cnn_set_apply(pg.CNN_APPLY_TC_FUSED)
     c.cnn_set_weights(jacobi_network_weights())
     b = torch.from_numpy(inputs.landau_noise_rhs(N, 11)).cuda()
     phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
