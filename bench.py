@@ -9,7 +9,7 @@ solve to relative residual 1e-10 (poisson_solve_ex), the field energy
 (134,217,728 particles, FP64 state, 6.4 GB), Landau initial condition
 (k = 0.5, alpha = 0.05), dt = 0.05, warm-started solves.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver cnn|mixed|fp64]
   python bench.py --impl reference      # the CPU oracle on a bounded sample
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own
@@ -63,9 +63,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="mixed",
-                    help="mixed: FP32 CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
-                         "cnn: mixed flexible CG with the learned preconditioner (trained before timing)")
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="cnn",
+                    help="cnn: mixed-precision flexible CG with the learned preconditioner (trained on the GPU "
+                         "before timing); mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge")
     ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--ppc", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-vs-mixed solve comparison")
+    ap.add_argument("--compare-reps", type=int, default=2, help="cold solves per solver in the comparison (best kept)")
+    ap.add_argument("--compare-maxit", type=int, default=MAXIT,
+                    help="iteration cap of the comparison solves (mixed Jacobi-CG stagnates at 1024^3)")
     return ap.parse_args()
 
 
@@ -348,7 +351,8 @@ def run_ours(args):
     if train_info is not None:
         out["preconditioner_training"] = train_info
     if not args.no_compare:
-        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None)
+        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None,
+                                               reps=args.compare_reps, maxit=args.compare_maxit)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters))
     if dist is not None:
@@ -374,7 +378,7 @@ def train_preconditioner(pg, torch, N=64, steps=600):
                "loss_last": float(losses[-50:].mean()), "seconds": round(time.perf_counter() - t0, 2)}
 
 
-def compare_solvers(c, rho, n, pg, torch, with_cnn=False):
+def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
     """Cold-start solves of the same right-hand side (the last deposit): the FP64
     Jacobi-PCG judge against the mixed-precision solver, and with the learned
     preconditioner when it is loaded (outside the timed region)."""
@@ -387,9 +391,9 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False):
         if with_cnn:
             c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
         best = None
-        for _ in range(2):
+        for _ in range(max(1, reps)):
             phi = torch.zeros(n, dtype=torch.float64, device="cuda")
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc, raise_on_error=False)
+            info = c.solve(rho, phi, tol=TOL, maxit=maxit, precision=prec, precond=pc, raise_on_error=False)
             if best is None or info["t_ms"] < best["t_ms"]:
                 best = info
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],

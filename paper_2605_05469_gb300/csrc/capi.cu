@@ -14,8 +14,12 @@ using namespace pic;
 
 namespace {
 
-constexpr size_t kSmemBudget32 = 72 * 1024;   // >= 3 blocks per SM
-constexpr size_t kSmemBudget64 = 110 * 1024;  // >= 2 blocks per SM
+// dynamic shared memory of one plane-streaming block: small blocks leave room
+// for at least three (FP32) or two (FP64) blocks per SM, a tall block has the SM
+constexpr size_t kSmemBudget32 = 72 * 1024;
+constexpr size_t kSmemBudget64 = 110 * 1024;
+constexpr size_t kSmemTall = 220 * 1024;
+constexpr size_t kSmemMax = 226 * 1024;
 
 void free_particles(pic_ctx* c) {
   for (int b = 0; b < 2; ++b) {
@@ -53,10 +57,30 @@ ParticlePtrs pptrs(pic_ctx* c, int b) {
 // Stage count from a shared-memory budget per block (raw TMA stages + 3 plane
 // buffers, at least 3 stages); persistent grid = resident blocks of `kernel`.
 template <typename TP, typename A, typename B, int NV, typename K>
-int geo_for(pic_ctx* c, K kernel, StreamGeo* out, size_t* smem) {
-  StreamGeo g = make_stream_geo(c->N, 3);
+int geo_for(pic_ctx* c, K kernel, StreamGeo* out, size_t* smem, bool tall = false) {
+  // The tallest slab (largest divisor TY of N) whose block fits the thread
+  // cap and, with three raw stages and three plane buffers, the block's
+  // shared-memory budget: the halo rows re-read per plane are (TY + 2) / TY
+  // of the slab. If none fits the budget, the tallest that fits the SM.
+  // Then as many raw stages as the budget allows (at least three).
+  const int N = c->N;
+  const int cap = tall ? kStreamTall : kStreamSmall;
+  const size_t budget = tall ? kSmemTall : (sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32);
+  StreamGeo g{};
+  bool found = false;
+  for (int pass = 0; pass < 2 && !found; ++pass) {
+    const size_t lim = pass == 0 ? budget : kSmemMax;
+    for (int ty = N; ty >= 1 && !found; --ty) {
+      if (N % ty || (long)N * ty / 4 > cap) continue;
+      StreamGeo t = make_stream_geo(N, 3, ty);
+      if (stream_smem_bytes<TP, A, B, NV>(t.rows, t.N, 3) <= lim) {
+        g = t;
+        found = true;
+      }
+    }
+  }
+  if (!found) return PIC_EINVAL;
   const StageLayout<A, B, NV> lay(g.rows, g.N);
-  const size_t budget = sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32;
   const size_t pb = 3 * (size_t)g.rows * g.N * sizeof(TP);
   int S = budget > pb ? (int)((budget - pb) / lay.bytes) : 0;
   if (S < 3) S = 3;
@@ -229,7 +253,9 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
   size_t smem_pap, smem_upd, smem_rel;
   StreamGeo gp, gu, gr;
-  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, false>, &gp, &smem_pap))) return e;
+  const bool tall = c->N >= 512;
+  auto* kpap = tall ? k_cg_pap<float, false, true> : k_cg_pap<float, false, false>;
+  if ((e = geo_for<float, float, float, 2>(c, kpap, &gp, &smem_pap, tall))) return e;
   if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
   if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
   int mb = gp.blocks;
@@ -249,7 +275,7 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
       int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
-      launch(c, k_cg_pap<float, false>, gp.blocks, tp, smem_pap, w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
+      launch(c, kpap, gp.blocks, tp, smem_pap, w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
              c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
@@ -326,7 +352,9 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
   size_t smem_pap, smem_upd, smem_rel;
   StreamGeo gp, gu, gr;
-  if ((e = geo_for<float, float, float, 2>(c, k_cg_pap<float, true>, &gp, &smem_pap))) return e;
+  const bool tall = c->N >= 512;
+  auto* kpap = tall ? k_cg_pap<float, true, true> : k_cg_pap<float, true, false>;
+  if ((e = geo_for<float, float, float, 2>(c, kpap, &gp, &smem_pap, tall))) return e;
   if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
   if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
   int mb = gp.blocks;
@@ -366,7 +394,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
       int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
-      launch(c, k_cg_pap<float, true>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
+      launch(c, kpap, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
              w.p32[cur ^ 1], w.q32, c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
@@ -388,7 +416,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
       int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
-      launch(c, k_cg_pap<float, true>, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
+      launch(c, kpap, gp.blocks, tp, smem_pap, (const float*)w.z32[zc], (const float*)w.p32[cur],
              w.p32[cur ^ 1], w.q32, c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;

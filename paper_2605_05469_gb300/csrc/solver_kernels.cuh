@@ -19,6 +19,12 @@
 namespace pic {
 
 constexpr int kMaxStages = 8;
+// Block sizes of the plane-streaming kernels (4 cells per thread). Small
+// blocks, several per SM, overlap one another's per-plane barrier and copy
+// waits; the tall-slab form of the direction kernel (one 1024-thread block
+// per SM) re-reads fewer halo rows, which pays once N >= 512 (measured).
+constexpr int kStreamSmall = 256;
+constexpr int kStreamTall = 1024;
 
 // Layout of one stage: vector 0 (type A) then optional vector 1 (type B),
 // each rows*N elements; stage size rounded up to 128 bytes.
@@ -152,8 +158,8 @@ __device__ __forceinline__ V4<T> stencil_q(const T* pb, const Slab& s, const V4<
 // ---------------------------------------------------------------------------
 // pap: p = r + beta p_in over the streamed slab; q = (h^2 A) p; (p, q) -> alpha
 // ---------------------------------------------------------------------------
-template <typename T, bool STORE_Q>
-__global__ void __launch_bounds__(256) k_cg_pap(const T* __restrict__ r, const T* __restrict__ pin,
+template <typename T, bool STORE_Q, bool TALL = false>
+__global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_cg_pap(const T* __restrict__ r, const T* __restrict__ pin,
                                                 T* __restrict__ pout, T* __restrict__ q, Scalars* sc,
                                                 double* partials, unsigned* counter, int* err, StreamGeo g) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) k_cg_update64(double* __restrict__ x, dou
 // reliable update when (r, r) fell by delta^2 since the last one, or reached
 // the tolerance.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cg_update32(float* __restrict__ x, float* __restrict__ r,
+__global__ void __launch_bounds__(kStreamSmall) k_cg_update32(float* __restrict__ x, float* __restrict__ r,
                                                      const float* __restrict__ p, const float* __restrict__ zold,
                                                      Scalars* sc, double* partials, unsigned* counter, int* err,
                                                      StreamGeo g) {
@@ -309,7 +315,7 @@ __global__ void __launch_bounds__(256) k_cg_update32(float* __restrict__ x, floa
 // ---------------------------------------------------------------------------
 // Initial FP64 residual of the judge: r = h^2 b - (h^2 A) x, (r, r).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_residual64(const double* __restrict__ x, const double* __restrict__ b,
+__global__ void __launch_bounds__(kStreamSmall) k_residual64(const double* __restrict__ x, const double* __restrict__ b,
                                                     double* __restrict__ r, Scalars* sc, double* partials,
                                                     unsigned* counter, int* err, StreamGeo g) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(256) k_residual64(const double* __restrict__ x
 // zero (x32_reset) instead. mode 0: set-up (always runs); 1: runs only if an
 // update is pending; 2: forced final fold.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_reliable(double* __restrict__ x64a, double* __restrict__ x64b,
+__global__ void __launch_bounds__(kStreamSmall) k_reliable(double* __restrict__ x64a, double* __restrict__ x64b,
                                                   const float* __restrict__ x32, const double* __restrict__ b,
                                                   float* __restrict__ r32, Scalars* sc, double* partials,
                                                   unsigned* counter, int* err, StreamGeo g, int mode) {
@@ -583,7 +589,7 @@ __global__ void __launch_bounds__(256) k_scale64(double* __restrict__ a, size_t 
 }
 
 // y = A x = (h^2 A) x / h^2 in FP64.
-__global__ void __launch_bounds__(256) k_apply64(const double* __restrict__ x, double* __restrict__ y, double inv_h2,
+__global__ void __launch_bounds__(kStreamSmall) k_apply64(const double* __restrict__ x, double* __restrict__ y, double inv_h2,
                                                  int* err, StreamGeo g) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];

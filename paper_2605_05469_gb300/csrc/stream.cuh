@@ -1,6 +1,7 @@
 // Plane-streaming machinery for the periodic 7-point stencil (Sec. 3.2).
 //
-// A slab is TY full x-rows (TY the largest divisor of N with N * TY <= 1024,
+// A slab is TY full x-rows (TY a divisor of N chosen by the host to fit the
+// kernel's thread limit and the shared-memory budget,
 // so a slab plane is at most 1024 cells). Persistent blocks each take an even
 // contiguous share of the (slab, plane) work list and walk its planes in z.
 // For every plane a block
@@ -27,12 +28,10 @@ struct StreamGeo {
 };
 
 // Slab height: the largest divisor of N with at most 1024 cells per slab plane.
-inline StreamGeo make_stream_geo(int N, int S) {
+inline StreamGeo make_stream_geo(int N, int S, int TY) {
   StreamGeo g;
   g.N = N;
-  g.TY = 1;
-  for (int d = 1; d <= N; ++d)
-    if (N % d == 0 && N * d <= 1024) g.TY = d;
+  g.TY = TY;
   g.rows = (g.TY == N) ? N : g.TY + 2;
   g.nyt = N / g.TY;
   g.threads = N * g.TY / 4;
