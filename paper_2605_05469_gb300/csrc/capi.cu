@@ -23,8 +23,7 @@ constexpr size_t kSmemMax = 226 * 1024;
 
 void free_particles(pic_ctx* c) {
   for (int b = 0; b < 2; ++b) {
-    for (int q = 0; q < 6; ++q) dfree(c->pb[b][q]);
-    dfree(c->ids[b]);
+    dfree(c->prec[b]);
   }
   dfree(c->keys);
   dfree(c->ranks);
@@ -46,13 +45,7 @@ void free_solver(pic_ctx* c) {
   c->partials_len = 0;
 }
 
-ParticlePtrs pptrs(pic_ctx* c, int b) {
-  ParticlePtrs P;
-  P.x = c->pb[b][0]; P.y = c->pb[b][1]; P.z = c->pb[b][2];
-  P.vx = c->pb[b][3]; P.vy = c->pb[b][4]; P.vz = c->pb[b][5];
-  P.id = c->ids[b];
-  return P;
-}
+PRec* pptrs(pic_ctx* c, int b) { return c->prec[b]; }
 
 // Stage count from a shared-memory budget per block (raw TMA stages + 3 plane
 // buffers, at least 3 stages); persistent grid = resident blocks of `kernel`.
@@ -608,11 +601,8 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
   int e;
   if ((e = ensure_partials(c, 3 * 4096 + 3 * (size_t)c->sms * 8))) return e;
   if (np == 0) return PIC_OK;
-  for (int b = 0; b < 2; ++b) {
-    for (int q = 0; q < 6; ++q)
-      if ((e = dalloc(&c->pb[b][q], np))) return e;
-    if ((e = dalloc(&c->ids[b], np))) return e;
-  }
+  for (int b = 0; b < 2; ++b)
+    if ((e = dalloc(&c->prec[b], np))) return e;
   const size_t nchunks = (n + kScanChunk - 1) / kScanChunk;
   if ((e = dalloc(&c->keys, np)) || (e = dalloc(&c->ranks, np)) || (e = dalloc(&c->counts, n)) ||
       (e = dalloc(&c->offsets, n + 1)) || (e = dalloc(&c->chunks, nchunks)))
@@ -643,7 +633,7 @@ int pic_deposit(pic_ctx* c, double* rho) {
     launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
     launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
     launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
-    const unsigned sblocks = (unsigned)((c->np / 4 + 255) / 256);
+    const unsigned sblocks = (unsigned)((c->np / 2 + 255) / 256);
     launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
            (const uint32_t*)c->ranks,
                                               c->offsets);
@@ -656,7 +646,7 @@ int pic_deposit(pic_ctx* c, double* rho) {
   launch(c, k_fill, sb, 256, 0, rho, c->n, 1.0);
   const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
   const unsigned cblocks = (unsigned)((c->n + 255) / 256);
-  launch(c, k_deposit_cells, cblocks, 256, 0, c->pb[c->cur][0], c->pb[c->cur][1], c->pb[c->cur][2], c->offsets,
+  launch(c, k_deposit_cells, cblocks, 256, 0, (const PRec*)c->prec[c->cur], c->offsets,
                                                   rho, c->grid, qscale);
   CK(cudaGetLastError());
   return PIC_OK;

@@ -80,8 +80,7 @@ struct pic_ctx {
   uint64_t np = 0;
   pic::Grid grid{};
   // particles
-  double* pb[2][6] = {};
-  uint32_t* ids[2] = {nullptr, nullptr};
+  pic::PRec* prec[2] = {nullptr, nullptr};  // particle records, current sort order and scratch
   int cur = 0;
   uint32_t *keys = nullptr, *ranks = nullptr, *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
   bool keys_valid = false, sorted = false, half_step = false;

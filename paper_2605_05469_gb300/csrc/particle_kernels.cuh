@@ -2,7 +2,7 @@
 // sort by cell, CIC scatter (Eq. 2), E = -grad phi, CIC gather and leapfrog
 // push (Eqs. 3-4), field energy (Fig. 2).
 //
-// Particles are FP64 structure-of-arrays. Each step they are counting-sorted
+// Particles are 64-byte FP64 records (PRec). Each step they are counting-sorted
 // by cell: the push kernel computes every particle's new cell key and takes
 // its rank inside the cell with one integer atomic; a scan turns the cell
 // counts into offsets and a scatter moves the particles. The deposit then
@@ -64,13 +64,16 @@ __device__ __forceinline__ uint32_t key_of(double x, double y, double z, const G
   return (uint32_t)cell_of(x, g) + (uint32_t)g.N * ((uint32_t)cell_of(y, g) + (uint32_t)g.N * (uint32_t)cell_of(z, g));
 }
 
-struct ParticlePtrs {
-  double *x, *y, *z, *vx, *vy, *vz;
-  uint32_t* id;
-};
+__device__ __forceinline__ void rec_pos(const PRec* P, uint64_t p, double& x, double& y, double& z) {
+  const double2* r = reinterpret_cast<const double2*>(P + p);
+  const double2 a = __ldg(r), b = __ldg(r + 1);
+  x = a.x;
+  y = a.y;
+  z = b.x;
+}
 
 // S0: sample particle p of the Landau initial condition, and count its cell.
-__global__ void k_init_particles(ParticlePtrs P, uint64_t np, uint64_t seed, double alpha, double k, Grid g,
+__global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alpha, double k, Grid g,
                                  uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
@@ -91,24 +94,24 @@ __global__ void k_init_particles(ParticlePtrs P, uint64_t np, uint64_t seed, dou
   double s1, c1, s2, c2;
   sincos(two_pi * u[5], &s1, &c1);
   sincos(two_pi * u[7], &s2, &c2);
-  P.x[p] = x;
-  P.y[p] = y;
-  P.z[p] = z;
-  P.vx[p] = r1 * c1;
-  P.vy[p] = r1 * s1;
-  P.vz[p] = r2 * c2;
-  P.id[p] = (uint32_t)p;
+  double2* rec = reinterpret_cast<double2*>(P + p);
+  rec[0] = make_double2(x, y);
+  rec[1] = make_double2(z, r1 * c1);
+  rec[2] = make_double2(r1 * s1, r2 * c2);
+  reinterpret_cast<uint4*>(rec)[3] = make_uint4((uint32_t)p, 0u, 0u, 0u);
   const uint32_t kk = key_of(x, y, z, g);
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
 
 // Cell keys and in-cell ranks of the current particles (after an external load).
-__global__ void k_count_keys(ParticlePtrs P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
+__global__ void k_count_keys(const PRec* P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
                              uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const uint32_t kk = key_of(P.x[p], P.y[p], P.z[p], g);
+  double x, y, z;
+  rec_pos(P, p, x, y, z);
+  const uint32_t kk = key_of(x, y, z, g);
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
@@ -204,38 +207,34 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
   if (base + 16 >= n && base < n) offsets[n] = run;  // the thread holding the last count
 }
 
-// Move particle p to offsets[key] + rank (the other buffer set). Each thread
-// moves 4 consecutive particles with vector loads, so 4 independent
-// key -> offset -> store chains are in flight per thread (np % 4 == 0).
-__global__ void __launch_bounds__(256) k_scatter(ParticlePtrs src, ParticlePtrs dst, uint64_t np,
+// Move particle p to offsets[key] + rank (the other buffer). Each thread
+// moves 2 consecutive particles, 64 bytes each as four 16-byte vectors, so
+// every destination is written in whole sectors (np % 2 == 0).
+__global__ void __launch_bounds__(256) k_scatter(const PRec* __restrict__ src, PRec* __restrict__ dst, uint64_t np,
                                                  const uint32_t* __restrict__ keys,
                                                  const uint32_t* __restrict__ ranks,
                                                  const uint32_t* __restrict__ offsets) {
   const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (4 * q >= np) return;
-  const uint4 k4 = __ldg(reinterpret_cast<const uint4*>(keys) + q);
-  const uint4 r4 = __ldg(reinterpret_cast<const uint4*>(ranks) + q);
-  uint64_t d[4];
-  d[0] = (uint64_t)__ldg(offsets + k4.x) + r4.x;
-  d[1] = (uint64_t)__ldg(offsets + k4.y) + r4.y;
-  d[2] = (uint64_t)__ldg(offsets + k4.z) + r4.z;
-  d[3] = (uint64_t)__ldg(offsets + k4.w) + r4.w;
-  const double* sf[6] = {src.x, src.y, src.z, src.vx, src.vy, src.vz};
-  double* df[6] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz};
+  if (2 * q >= np) return;
+  const uint2 k2 = __ldg(reinterpret_cast<const uint2*>(keys) + q);
+  const uint2 r2 = __ldg(reinterpret_cast<const uint2*>(ranks) + q);
+  const uint64_t d0 = (uint64_t)__ldg(offsets + k2.x) + r2.x;
+  const uint64_t d1 = (uint64_t)__ldg(offsets + k2.y) + r2.y;
+  const uint4* s0 = reinterpret_cast<const uint4*>(src + 2 * q);
+  const uint4* s1 = reinterpret_cast<const uint4*>(src + 2 * q + 1);
+  uint4 a[4], b[4];
 #pragma unroll
-  for (int f = 0; f < 6; ++f) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(sf[f]) + 2 * q);
-    const double2 b = __ldg(reinterpret_cast<const double2*>(sf[f]) + 2 * q + 1);
-    df[f][d[0]] = a.x;
-    df[f][d[1]] = a.y;
-    df[f][d[2]] = b.x;
-    df[f][d[3]] = b.y;
+  for (int i = 0; i < 4; ++i) {
+    a[i] = __ldg(s0 + i);
+    b[i] = __ldg(s1 + i);
   }
-  const uint4 i4 = __ldg(reinterpret_cast<const uint4*>(src.id) + q);
-  dst.id[d[0]] = i4.x;
-  dst.id[d[1]] = i4.y;
-  dst.id[d[2]] = i4.z;
-  dst.id[d[3]] = i4.w;
+  uint4* t0 = reinterpret_cast<uint4*>(dst + d0);
+  uint4* t1 = reinterpret_cast<uint4*>(dst + d1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    t0[i] = a[i];
+    t1[i] = b[i];
+  }
 }
 
 __global__ void k_fill(double* a, size_t n, double v) {
@@ -247,8 +246,7 @@ __global__ void k_fill(double* a, size_t n, double v) {
 // S2: CIC scatter from cell-sorted particles, one thread per cell.
 // rho (pre-filled with the +1 background) += (q_p / h^3) sum_p W.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_deposit_cells(const double* __restrict__ px, const double* __restrict__ py,
-                                                       const double* __restrict__ pz,
+__global__ void __launch_bounds__(256) k_deposit_cells(const PRec* __restrict__ P,
                                                        const uint32_t* __restrict__ offsets, double* rho, Grid g,
                                                        double qscale) {
   const int N = g.N;
@@ -261,9 +259,11 @@ __global__ void __launch_bounds__(256) k_deposit_cells(const double* __restrict_
   const double cx = (double)ix, cy = (double)iy, cz = (double)iz;
   double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (uint32_t p = b; p < e; ++p) {
-    const double fx = fma(__ldg(px + p), g.inv_h, -cx);
-    const double fy = fma(__ldg(py + p), g.inv_h, -cy);
-    const double fz = fma(__ldg(pz + p), g.inv_h, -cz);
+    double px, py, pz;
+    rec_pos(P, p, px, py, pz);
+    const double fx = fma(px, g.inv_h, -cx);
+    const double fy = fma(py, g.inv_h, -cy);
+    const double fz = fma(pz, g.inv_h, -cz);
     const double gx = 1.0 - fx, gy = 1.0 - fy, gz = 1.0 - fz;
     const double w00 = gy * gz, w10 = fy * gz, w01 = gy * fz, w11 = fy * fz;  // (y, z)
     s[0] = fma(gx, w00, s[0]);
@@ -347,13 +347,15 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 // rank (counts must be zero on entry) for the next sort. drift == 0 gives the
 // closing half-kick only (no key update).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather_push(ParticlePtrs P, uint64_t np, const double* __restrict__ Ex,
+__global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const double* __restrict__ Ex,
                                                      const double* __restrict__ Ey, const double* __restrict__ Ez,
                                                      Grid g, double kick_qm, double dt, int drift, uint32_t* keys,
                                                      uint32_t* ranks, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  double x = P.x[p], y = P.y[p], z = P.z[p];
+  double2* rec = reinterpret_cast<double2*>(P + p);
+  const double2 r0 = rec[0], r1 = rec[1], r2 = rec[2];
+  double x = r0.x, y = r0.y, z = r1.x;
   const int N = g.N;
   const int ix = cell_of(x, g), iy = cell_of(y, g), iz = cell_of(z, g);
   const double fx = fma(x, g.inv_h, -(double)ix), fy = fma(y, g.inv_h, -(double)iy),
@@ -373,13 +375,14 @@ __global__ void __launch_bounds__(256) k_gather_push(ParticlePtrs P, uint64_t np
     ey = fma(w[c], __ldg(Ey + idx[c]), ey);
     ez = fma(w[c], __ldg(Ez + idx[c]), ez);
   }
-  double vx = fma(kick_qm, ex, P.vx[p]);
-  double vy = fma(kick_qm, ey, P.vy[p]);
-  double vz = fma(kick_qm, ez, P.vz[p]);
-  P.vx[p] = vx;
-  P.vy[p] = vy;
-  P.vz[p] = vz;
-  if (!drift) return;
+  double vx = fma(kick_qm, ex, r1.y);
+  double vy = fma(kick_qm, ey, r2.x);
+  double vz = fma(kick_qm, ez, r2.y);
+  rec[2] = make_double2(vy, vz);
+  if (!drift) {
+    rec[1] = make_double2(z, vx);
+    return;
+  }
   const double L = g.L;
   x = fma(dt, vx, x);
   y = fma(dt, vy, y);
@@ -388,25 +391,25 @@ __global__ void __launch_bounds__(256) k_gather_push(ParticlePtrs P, uint64_t np
   x = x >= L ? x - L : x; x = x < 0.0 ? x + L : x; x = x >= L ? 0.0 : x;
   y = y >= L ? y - L : y; y = y < 0.0 ? y + L : y; y = y >= L ? 0.0 : y;
   z = z >= L ? z - L : z; z = z < 0.0 ? z + L : z; z = z >= L ? 0.0 : z;
-  P.x[p] = x;
-  P.y[p] = y;
-  P.z[p] = z;
+  rec[0] = make_double2(x, y);
+  rec[1] = make_double2(z, vx);
   const uint32_t kk = key_of(x, y, z, g);
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
 
 // Copy particles back to the original order: out[q * np + id[p]] = field q of p.
-__global__ void k_unsort(ParticlePtrs P, uint64_t np, double* out) {
+__global__ void k_unsort(const PRec* P, uint64_t np, double* out) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const uint64_t d = P.id[p];
-  out[d] = P.x[p];
-  out[np + d] = P.y[p];
-  out[2 * np + d] = P.z[p];
-  out[3 * np + d] = P.vx[p];
-  out[4 * np + d] = P.vy[p];
-  out[5 * np + d] = P.vz[p];
+  const PRec r = P[p];
+  const uint64_t d = r.id;
+  out[d] = r.x;
+  out[np + d] = r.y;
+  out[2 * np + d] = r.z;
+  out[3 * np + d] = r.vx;
+  out[4 * np + d] = r.vy;
+  out[5 * np + d] = r.vz;
 }
 
 }  // namespace pic
