@@ -6,7 +6,7 @@ the library's C ABI: sort by cell + CIC scatter (pic_deposit), the Poisson
 solve to relative residual 1e-10 (poisson_solve_ex), the field energy
 (pic_field_energy) and E = -grad phi + CIC gather + leapfrog push
 (pic_gather_push). Default workload: 256^3 periodic grid, 8 particles per cell
-(134,217,728 particles, FP64 state, 6.4 GB), Landau initial condition
+(134,217,728 particles, 64-byte FP64 records, 8.6 GB), Landau initial condition
 (k = 0.5, alpha = 0.05), dt = 0.05, warm-started solves.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--solver cnn|mixed|fp64]
@@ -50,8 +50,8 @@ KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
 # learned preconditioner applied as its composed 9^3 kernel: 729 FMA per cell
 PRECOND_FLOP_PER_CELL = 2 * 729
 # ... which the tensor-core form executes as 81 Toeplitz products of K = 32
-# per output, on 40 rows per 32 kept (the 8 rows between y blocks are discarded)
-PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32 * 40 // 32
+# x-inputs per output (9 of the 32 weights in each product are nonzero)
+PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP at the 2.07 GHz maximum clock
 # (nominal), and 70.2 TFLOP/s measured with an FMA throughput loop on this GB300
 FP32_PEAK_TFLOPS = 70.2
@@ -335,7 +335,7 @@ def run_ours(args):
                                 f"solve to rel-res {TOL:g}, dt {DT}"),
                    "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
                    "warm_start": True, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (particle state 6.4 GB; solver vectors 4 x 67-134 MB per iteration)"},
+                   "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
         "clocks": clk,
         "e2e": e2e,
         "e2e_solve": e2e_solve,
@@ -361,21 +361,25 @@ def run_ours(args):
     return out
 
 
-def train_preconditioner(pg, torch, N=64, steps=600):
+def train_preconditioner(pg, torch, N=64, steps=600, val_grid=128, val_every=100):
     """Train the learned preconditioner on the GPU before timing (the library's
     own kernels: Jacobi-PCG snapshots of four 64^3 Landau deposits, 600 Adam
-    steps on 32^3 crops)."""
+    steps on 32^3 crops); the weights kept are those with the fewest
+    flexible-CG iterations, scored every 100 steps on a held-out 128^3
+    deposit (another seed)."""
     from paper_2605_05469_gb300 import train as T
     t0 = time.perf_counter()
     sets = T.landau_snapshot_sets(N, seeds=[11, 12, 13, 14])
     c = pg.Context().init(N, 0, 0)
-    losses = T.train(c, sets, steps, B=8, D=32, lr=2e-3, seed=0)
+    val = T.fcg_iterations(val_grid)
+    losses = T.train(c, sets, steps, B=8, D=32, lr=2e-3, seed=0, validate=val, validate_every=val_every)
     w = c.cnn_get_weights()
     c.close()
-    del sets
+    del sets, val
     torch.cuda.synchronize()
     return w, {"grid": N, "steps": steps, "loss_first": float(losses[:10].mean()),
-               "loss_last": float(losses[-50:].mean()), "seconds": round(time.perf_counter() - t0, 2)}
+               "loss_last": float(losses[-50:].mean()), "selected_by": f"FCG iterations on a {val_grid}^3 deposit",
+               "seconds": round(time.perf_counter() - t0, 2)}
 
 
 def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):

@@ -68,11 +68,18 @@ def landau_snapshot_sets(N, seeds, ppc=8, iters=SNAPSHOT_ITERS):
     return sets
 
 
-def train(ctx, sets, steps, B=8, D=32, lr=2e-3, seed=0, weights=None, log_every=0):
+def train(ctx, sets, steps, B=8, D=32, lr=2e-3, seed=0, weights=None, log_every=0, lr_final=None,
+          validate=None, validate_every=0):
     """Adam on random crops of the snapshot sets; returns the loss history.
 
     ``ctx`` must be a context on the snapshots' grid (N^3); it holds the
     network. ``weights`` (14 688 FP32) initialises it, else the Jacobi start.
+    With ``lr_final`` the step size follows a cosine from ``lr`` down to it.
+    With ``validate`` (weights -> cost, e.g. flexible-CG iterations on a
+    held-out right-hand side) the weights are scored every
+    ``validate_every`` steps and at the end, and the best scored weights are
+    loaded into ``ctx`` when training ends (the loss is only a proxy for
+    the iteration count).
     """
     import torch
     N = ctx.N
@@ -85,6 +92,15 @@ def train(ctx, sets, steps, B=8, D=32, lr=2e-3, seed=0, weights=None, log_every=
     y = torch.empty_like(x)
     gy = torch.empty_like(x)
     losses = []
+    best = None
+
+    def score():
+        nonlocal best
+        w = ctx.cnn_get_weights()
+        cost = validate(w)
+        if best is None or cost < best[0]:
+            best = (cost, w)
+
     for step in range(steps):
         rho, phi_star, snaps = sets[rng.integers(len(sets))]
         rk, xk = snaps[rng.integers(len(snaps))]
@@ -93,10 +109,37 @@ def train(ctx, sets, steps, B=8, D=32, lr=2e-3, seed=0, weights=None, log_every=
         ctx.cnn_forward(x, y, B, D)
         losses.append(ctx.cnn_loss(y, t, B, D, gy))
         ctx.cnn_backward(gy, B, D)
-        ctx.cnn_adam(lr)
+        step_lr = lr
+        if lr_final is not None and steps > 1:
+            step_lr = lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * step / (steps - 1)))
+        ctx.cnn_adam(step_lr)
         if log_every and (step + 1) % log_every == 0:
             print(f"step {step + 1}: loss {np.mean(losses[-log_every:]):.4f}", flush=True)
+        if validate is not None and validate_every and (step + 1) % validate_every == 0 and step + 1 < steps:
+            score()
+    if validate is not None:
+        score()
+        ctx.cnn_set_weights(best[1])
     return np.array(losses)
+
+
+def fcg_iterations(N=128, seed=21, tol=1e-10, maxit=2000):
+    """Validation cost for ``train``: flexible-CG iterations of a solve of
+    the CIC deposit of a seeded N^3 x 8 ppc Landau initial condition with
+    the given weights (a held-out right-hand side: other seed and grid than
+    the training snapshots)."""
+    import torch
+    c = Context().init(N, 8, seed)
+    rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    c.deposit(rho)
+    phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+
+    def cost(w):
+        c.cnn_set_weights(w)
+        phi.zero_()
+        info = c.solve(rho, phi, tol=tol, maxit=maxit, precision=PREC_MIXED, precond=PC_CNN, raise_on_error=False)
+        return info["iters"] if info["converged"] else maxit + 1
+    return cost
 
 
 def compare_preconditioners(ctx, rho, tol=1e-10, maxit=20000):
