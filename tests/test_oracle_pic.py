@@ -182,6 +182,30 @@ def test_spectral_solve_matches_numpy_fft():
     assert np.allclose(pic.spectral_solve(b, N, h), ref, atol=1e-14 * np.abs(ref).max())
 
 
+def test_fft_spectral_solve_matches_the_brute_force_dft_and_the_operator():
+    """spectral_solve_fft (numpy FFT) against the brute-force DFT form at 16^3
+    (independent transform), against the operator itself at 64^3 (A phi =
+    b - mean(b), mean(phi) = 0), and on a single Fourier mode, where the exact
+    solution is the mode divided by its closed-form eigenvalue."""
+    N = 16
+    h = L / N
+    b = np.random.default_rng(7).normal(size=N ** 3) + 1.5
+    ref = pic.spectral_solve(b, N, h)
+    assert np.allclose(pic.spectral_solve_fft(b, N, h), ref, atol=1e-13 * np.abs(ref).max())
+    N = 64
+    h = L / N
+    b = np.random.default_rng(8).normal(size=N ** 3)
+    phi = pic.spectral_solve_fft(b, N, h)
+    bp = b - b.mean()
+    assert np.linalg.norm(pic.apply_A(phi, N, h) - bp) <= 1e-12 * np.linalg.norm(bp)
+    assert abs(phi.mean()) <= 1e-15 * np.abs(phi).max()
+    i = np.arange(N ** 3)
+    x, y, z = i % N, (i // N) % N, i // (N * N)
+    mode = np.cos(2 * np.pi * (3 * x + 5 * z) / N)
+    lam = pic.laplacian_eigenvalue((3, 0, 5), N, h)
+    assert np.allclose(pic.spectral_solve_fft(mode, N, h), mode / lam, atol=1e-13 / lam)
+
+
 @pytest.mark.parametrize("N", [8, 16, 12])
 def test_pcg_matches_exact_discrete_solution(N):
     h = L / N
