@@ -57,6 +57,24 @@ PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32
 FP32_PEAK_TFLOPS = 70.2
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process
+    group): every rank's timed region is bracketed by a barrier, and the job
+    takes as long as its slowest rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps_per_rank, seconds):
+    """Units of all ranks (each runs its own replica) per second of the
+    slowest rank."""
+    return world * steps_per_rank / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,11 +237,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = c.profile_read(reset=True)
     c.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(world, args.steps, ms / 1e3)
     unit = "solves/s" if solve_only else UNIT
     metric = ("Poisson solves/s to rel-res 1e-10 (7-point FD, cold start)" if solve_only else METRIC)
 
@@ -237,11 +252,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * args.steps / e2e_s, "unit": unit, "h2d_bytes_per_step": 0,
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e = {"value": whole_job_rate(world, args.steps, e2e_s), "unit": unit, "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": 0 if solve_only else 24,
            "note": "wall clock through the Python binding; per step the field energy is read to host"}
 
