@@ -51,14 +51,14 @@ struct Scalars {
                     // z and the direction's dots are recomputed from it
 };
 
-// One particle: FP64 position and velocity and its 32-bit id (the index it
-// was sampled with), padded to 64 bytes so that a particle moved by the sort
-// fills exactly two 32-byte sectors and the kernels read it with four 16-byte
-// loads.
+// One particle: FP64 position and velocity, its 32-bit id (the index it was
+// sampled with) and the key of the cell that contains its position, padded to
+// 64 bytes so that a particle moved by the sort fills exactly two 32-byte
+// sectors and the kernels read it with four 16-byte loads.
 struct __align__(64) PRec {
   double x, y, z, vx, vy, vz;
-  uint32_t id, pad0;
-  double pad1;
+  uint32_t id, key;
+  double pad;
 };
 static_assert(sizeof(PRec) == 64, "particle record");
 

@@ -98,20 +98,21 @@ __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alp
   rec[0] = make_double2(x, y);
   rec[1] = make_double2(z, r1 * c1);
   rec[2] = make_double2(r1 * s1, r2 * c2);
-  reinterpret_cast<uint4*>(rec)[3] = make_uint4((uint32_t)p, 0u, 0u, 0u);
   const uint32_t kk = key_of(x, y, z, g);
+  reinterpret_cast<uint4*>(rec)[3] = make_uint4((uint32_t)p, kk, 0u, 0u);
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
 
 // Cell keys and in-cell ranks of the current particles (after an external load).
-__global__ void k_count_keys(const PRec* P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
+__global__ void k_count_keys(PRec* P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
                              uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   double x, y, z;
   rec_pos(P, p, x, y, z);
   const uint32_t kk = key_of(x, y, z, g);
+  P[p].key = kk;
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
@@ -257,24 +258,36 @@ __global__ void __launch_bounds__(256) k_deposit_cells(const PRec* __restrict__ 
   if (b == e) return;
   const int ix = (int)(c % N), iy = (int)((c / N) % N), iz = (int)(c / ((size_t)N * N));
   const double cx = (double)ix, cy = (double)iy, cz = (double)iz;
-  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // the 8 corner weights summed over the cell's particles follow from the
+  // moments of the offsets f in [0, 1)^3: sum_p prod_d (f_d or 1 - f_d)
+  // expands into the count and sums of f_x, f_y, f_z, f_x f_y, f_x f_z,
+  // f_y f_z, f_x f_y f_z (14 FP64 operations per particle instead of 18)
+  double mx = 0, my = 0, mz = 0, mxy = 0, mxz = 0, myz = 0, mxyz = 0;
   for (uint32_t p = b; p < e; ++p) {
     double px, py, pz;
     rec_pos(P, p, px, py, pz);
     const double fx = fma(px, g.inv_h, -cx);
     const double fy = fma(py, g.inv_h, -cy);
     const double fz = fma(pz, g.inv_h, -cz);
-    const double gx = 1.0 - fx, gy = 1.0 - fy, gz = 1.0 - fz;
-    const double w00 = gy * gz, w10 = fy * gz, w01 = gy * fz, w11 = fy * fz;  // (y, z)
-    s[0] = fma(gx, w00, s[0]);
-    s[1] = fma(fx, w00, s[1]);
-    s[2] = fma(gx, w10, s[2]);
-    s[3] = fma(fx, w10, s[3]);
-    s[4] = fma(gx, w01, s[4]);
-    s[5] = fma(fx, w01, s[5]);
-    s[6] = fma(gx, w11, s[6]);
-    s[7] = fma(fx, w11, s[7]);
+    const double fxy = fx * fy;
+    mx += fx;
+    my += fy;
+    mz += fz;
+    mxy += fxy;
+    mxz = fma(fx, fz, mxz);
+    myz = fma(fy, fz, myz);
+    mxyz = fma(fxy, fz, mxyz);
   }
+  const double cnt = (double)(e - b);
+  double s[8];
+  s[7] = mxyz;                                  // f_x f_y f_z
+  s[3] = mxy - mxyz;                            // f_x f_y (1 - f_z)
+  s[5] = mxz - mxyz;                            // f_x (1 - f_y) f_z
+  s[6] = myz - mxyz;                            // (1 - f_x) f_y f_z
+  s[1] = mx - mxy - mxz + mxyz;                 // f_x (1 - f_y)(1 - f_z)
+  s[2] = my - mxy - myz + mxyz;                 // (1 - f_x) f_y (1 - f_z)
+  s[4] = mz - mxz - myz + mxyz;                 // (1 - f_x)(1 - f_y) f_z
+  s[0] = cnt - mx - my - mz + mxy + mxz + myz - mxyz;  // (1 - f_x)(1 - f_y)(1 - f_z)
   const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
   const size_t Ns = N;
   const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
@@ -355,9 +368,14 @@ __global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const
   if (p >= np) return;
   double2* rec = reinterpret_cast<double2*>(P + p);
   const double2 r0 = rec[0], r1 = rec[1], r2 = rec[2];
+  const uint4 r3 = reinterpret_cast<const uint4*>(rec)[3];
   double x = r0.x, y = r0.y, z = r1.x;
   const int N = g.N;
-  const int ix = cell_of(x, g), iy = cell_of(y, g), iz = cell_of(z, g);
+  // the cell of the current position, kept in the record since its key was
+  // computed (integer decode instead of three FP64 floors)
+  const uint32_t key = r3.y;
+  const int ix = (int)(key % (uint32_t)N), iy = (int)((key / (uint32_t)N) % (uint32_t)N),
+            iz = (int)(key / ((uint32_t)N * (uint32_t)N));
   const double fx = fma(x, g.inv_h, -(double)ix), fy = fma(y, g.inv_h, -(double)iy),
                fz = fma(z, g.inv_h, -(double)iz);
   const double gx = 1.0 - fx, gy = 1.0 - fy, gz = 1.0 - fz;
@@ -394,6 +412,7 @@ __global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const
   rec[0] = make_double2(x, y);
   rec[1] = make_double2(z, vx);
   const uint32_t kk = key_of(x, y, z, g);
+  reinterpret_cast<uint4*>(rec)[3] = make_uint4(r3.x, kk, 0u, 0u);
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
 }
