@@ -405,10 +405,18 @@ __global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const
   x = fma(dt, vx, x);
   y = fma(dt, vy, y);
   z = fma(dt, vz, z);
-  // periodic wrap into [0, L); a value that rounds to L becomes 0
-  x = x >= L ? x - L : x; x = x < 0.0 ? x + L : x; x = x >= L ? 0.0 : x;
-  y = y >= L ? y - L : y; y = y < 0.0 ? y + L : y; y = y >= L ? 0.0 : y;
-  z = z >= L ? z - L : z; z = z < 0.0 ? z + L : z; z = z >= L ? 0.0 : z;
+  // periodic wrap into [0, L); a value that rounds to L becomes 0. Only the
+  // few particles that left the box take the full sequence; for the others
+  // it is the identity (same result, fewer FP64 operations).
+  if (x < 0.0 || x >= L) {
+    x = x >= L ? x - L : x; x = x < 0.0 ? x + L : x; x = x >= L ? 0.0 : x;
+  }
+  if (y < 0.0 || y >= L) {
+    y = y >= L ? y - L : y; y = y < 0.0 ? y + L : y; y = y >= L ? 0.0 : y;
+  }
+  if (z < 0.0 || z >= L) {
+    z = z >= L ? z - L : z; z = z < 0.0 ? z + L : z; z = z >= L ? 0.0 : z;
+  }
   rec[0] = make_double2(x, y);
   rec[1] = make_double2(z, vx);
   const uint32_t kk = key_of(x, y, z, g);
