@@ -120,7 +120,7 @@ def oracle_sampled_apply(r, N, ws, points):
     return np.array(out)
 
 
-@pytest.mark.parametrize("N", [128, 256])
+@pytest.mark.parametrize("N", [128, 256, 384])
 def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N):
     """The composed 9^3 kernel on the tensor cores (BF16 r and K, FP32
     accumulation in TMEM) against the oracle's FP64 network at 200 sampled
