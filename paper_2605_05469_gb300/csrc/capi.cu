@@ -413,8 +413,8 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
              w.p32[cur ^ 1], w.q32, c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
-      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, (const float*)w.p32[cur ^ 1],
-             (const float*)nullptr, c->sc, c->partials, c->counter, c->err, gu);
+      launch(c, k_fcg_update32, sb, 256, 0, w.x32, w.r32, (const float*)w.p32[cur ^ 1], (const float*)w.q32, n4,
+             c->sc, c->partials, c->counter);
       if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
       launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b,
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);

@@ -313,6 +313,56 @@ __global__ void __launch_bounds__(kStreamSmall) k_cg_update32(float* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// FP32 update of flexible CG, where q = (h^2 A) p was stored by the direction
+// kernel: x += alpha p, r -= alpha q as a plain stream (no stencil, no halo),
+// (r, r) and the same convergence / reliable-update bookkeeping as above.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fcg_update32(float* __restrict__ x, float* __restrict__ r,
+                                                      const float* __restrict__ p, const float* __restrict__ q,
+                                                      size_t n4, Scalars* sc, double* partials, unsigned* counter) {
+  if (sc->done) return;
+  const float alpha = (float)sc->alpha;
+  const bool x_zero = sc->x32_reset != 0;
+  CompSum acc;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const V4<float> pv = ldg4(p + 4 * i), qv = ldg4(q + 4 * i);
+    V4<float> xv = x_zero ? V4<float>{{0.f, 0.f, 0.f, 0.f}} : ld4(x + 4 * i);
+    V4<float> rv = ld4(r + 4 * i);
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      xv.v[k] = fmaf(alpha, pv.v[k], xv.v[k]);
+      rv.v[k] = fmaf(-alpha, qv.v[k], rv.v[k]);
+      d = fmaf(rv.v[k], rv.v[k], d);
+    }
+    st4(x + 4 * i, xv);
+    st4(r + 4 * i, rv);
+    acc.add(d);
+  }
+  double v[1] = {acc.value()}, tot[1];
+  if (grid_reduce_last<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+    const double rr = tot[0];
+    sc->x32_reset = 0;
+    sc->rr_prev = sc->rr;
+    sc->beta = rr / sc->rr;
+    sc->rr = rr;
+    sc->iter += 1;
+    if (!isfinite(rr)) {
+      sc->done = 3;
+    } else {
+      if (rr <= sc->tol2) {
+        sc->need_update = 1;
+        sc->final_check = 1;
+      } else if (rr <= sc->delta2 * sc->rmax2) {
+        sc->need_update = 1;
+      }
+      if (!sc->need_update && sc->iter >= sc->maxit) sc->done = 2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Initial FP64 residual of the judge: r = h^2 b - (h^2 A) x, (r, r).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStreamSmall) k_residual64(const double* __restrict__ x, const double* __restrict__ b,
