@@ -284,9 +284,10 @@ def run_ours(args):
     for k in ("pap", "update"):
         if prof["ker_samples"][k]:
             avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
-            # flexible CG also stores q = A p in the pap kernel (+4 B/cell), and
-            # its update streams q instead of recomputing A p from p's halo (+4)
-            bpc = KER_BYTES[(kp, k)] + (4 if pc == pg.PC_CNN else 0)
+            # the mixed-precision solvers store q = A p in the direction kernel
+            # (+4 B/cell) and stream q in the update instead of recomputing
+            # A p from p's halo (+4 B/cell)
+            bpc = KER_BYTES[(kp, k)] + (4 if kp == 1 else 0)
             rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k],
                        "bytes_per_cell": bpc, "gbs": bpc * n / (avg_ms * 1e-3) / 1e9}
     if prof["ker_samples"]["precond"]:
@@ -295,7 +296,7 @@ def run_ours(args):
                            "flop_per_cell": PRECOND_FLOP_PER_CELL,
                            "tflops": PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12}
     dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
-    kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32" if pc == pg.PC_CNN else "k_cg_update32",
+    kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
     roof = None
     if dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):

@@ -244,15 +244,19 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
       return e;
   }
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
-  size_t smem_pap, smem_upd, smem_rel;
-  StreamGeo gp, gu, gr;
+  // the direction kernel stores q = A p, so the update streams x, r, p, q
+  // (no stencil): more bytes than recomputing A p, but at streaming speed
+  if (!w.q32 && (e = dalloc(&w.q32, c->n))) return e;
+  size_t smem_pap, smem_rel;
+  StreamGeo gp, gr;
   const bool tall = c->N >= 512;
-  auto* kpap = tall ? k_cg_pap<float, false, true> : k_cg_pap<float, false, false>;
+  auto* kpap = tall ? k_cg_pap<float, true, true> : k_cg_pap<float, true, false>;
   if ((e = geo_for<float, float, float, 2>(c, kpap, &gp, &smem_pap, tall))) return e;
-  if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
   if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
+  const int sb = streaming_blocks(c);
+  const size_t n4 = c->n / 4;
   int mb = gp.blocks;
-  if (gu.blocks > mb) mb = gu.blocks;
+  if (sb > mb) mb = sb;
   if (gr.blocks > mb) mb = gr.blocks;
   if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
 
@@ -260,7 +264,7 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
   CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
   CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
-  const int tp = round32(gp.threads), tu = round32(gu.threads), tr = round32(gr.threads);
+  const int tp = round32(gp.threads), tr = round32(gr.threads);
   launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                     c->counter, c->err, gr, 0);
   int cur = 0;
@@ -268,12 +272,12 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
     for (int i = 0; i < m; ++i) {
       const bool sample = c->prof_on && i == 0;
       int slot = sample ? c->ker[PIC_KER_PAP].begin(c->stream) : -1;
-      launch(c, kpap, gp.blocks, tp, smem_pap, w.r32, w.p32[cur], w.p32[cur ^ 1], nullptr,
+      launch(c, kpap, gp.blocks, tp, smem_pap, w.r32, w.p32[cur], w.p32[cur ^ 1], w.q32,
              c->sc, c->partials, c->counter, c->err, gp);
       if (sample) c->ker[PIC_KER_PAP].end(slot, c->stream);
       slot = sample ? c->ker[PIC_KER_UPDATE].begin(c->stream) : -1;
-      launch(c, k_cg_update32, gu.blocks, tu, smem_upd, w.x32, w.r32, w.p32[cur ^ 1], (const float*)nullptr,
-             c->sc, c->partials, c->counter, c->err, gu);
+      launch(c, k_fcg_update32, sb, 256, 0, w.x32, w.r32, (const float*)w.p32[cur ^ 1], (const float*)w.q32, n4,
+             c->sc, c->partials, c->counter);
       if (sample) c->ker[PIC_KER_UPDATE].end(slot, c->stream);
       launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], w.x32, w.b, w.r32, c->sc, c->partials,
                                                         c->counter, c->err, gr, 1);
@@ -291,8 +295,6 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
     if ((e = sync_status(c))) return e;
   }
   const int sel = c->sc_host[0].xsel;
-  const int sb = streaming_blocks(c);
-  const size_t n4 = c->n / 4;
   launch(c, k_sum2, sb, 256, 0, w.xm[sel], nullptr, n4, c->sc, c->partials, c->counter);
   launch(c, k_finish, sb, 256, 0, w.xm[sel], phi, n4, 1.0 / (double)c->n, c->sc);
   CK(cudaGetLastError());
@@ -343,17 +345,16 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   if (!w.z32[0] && ((e = dalloc(&w.z32[0], c->n)) || (e = dalloc(&w.z32[1], c->n)) || (e = dalloc(&w.q32, c->n))))
     return e;
   if (!w.b && (e = dalloc(&w.b, c->n))) return e;
-  size_t smem_pap, smem_upd, smem_rel;
-  StreamGeo gp, gu, gr;
+  size_t smem_pap, smem_rel;
+  StreamGeo gp, gr;
   const bool tall = c->N >= 512;
   auto* kpap = tall ? k_cg_pap<float, true, true> : k_cg_pap<float, true, false>;
   if ((e = geo_for<float, float, float, 2>(c, kpap, &gp, &smem_pap, tall))) return e;
-  if ((e = geo_for<float, float, float, 1>(c, k_cg_update32, &gu, &smem_upd))) return e;
   if ((e = geo_for<double, double, float, 2>(c, k_reliable, &gr, &smem_rel))) return e;
   int mb = gp.blocks;
-  if (gu.blocks > mb) mb = gu.blocks;
+  if (streaming_blocks(c) > mb) mb = streaming_blocks(c);
   if (gr.blocks > mb) mb = gr.blocks;
-  if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
+  if ((e = ensure_partials(c, (size_t)4 * mb + 3 * 4096))) return e;
 
   CK(cudaEventRecord(c->ev0, c->stream));
   if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
@@ -362,7 +363,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   CK(cudaMemcpyAsync(&c->sc->fcg, &c->sc_host[1].fcg, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
   CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
-  const int tp = round32(gp.threads), tu = round32(gu.threads), tr = round32(gr.threads);
+  const int tp = round32(gp.threads), tr = round32(gr.threads);
   const int sb = streaming_blocks(c);
   const size_t n4 = c->n / 4;
   launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b, w.r32,

@@ -237,85 +237,11 @@ __global__ void __launch_bounds__(256) k_cg_update64(double* __restrict__ x, dou
 }
 
 // ---------------------------------------------------------------------------
-// FP32 update: x += alpha p; r -= alpha (h^2 A) p; (r, r) -> beta; triggers a
-// reliable update when (r, r) fell by delta^2 since the last one, or reached
-// the tolerance.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kStreamSmall) k_cg_update32(float* __restrict__ x, float* __restrict__ r,
-                                                     const float* __restrict__ p, const float* __restrict__ zold,
-                                                     Scalars* sc, double* partials, unsigned* counter, int* err,
-                                                     StreamGeo g) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[kMaxStages];
-  if (sc->done) return;
-  const float alpha = (float)sc->alpha;
-  const bool x_zero = sc->x32_reset != 0;
-  const StageLayout<float, float, 1> lay(g.rows, g.N);
-  CompSum acc, acc_z;
-  V4<float> cx, cr, cz;  // x, r (and z_old) of the current output plane, loaded one plane ahead
-  const V4<float> zero4{{0.f, 0.f, 0.f, 0.f}};
-  auto start = [&](const Slab& s) {
-    const size_t off = cell_offset(s, 0);
-    cx = x_zero ? zero4 : ldg4(x + off);
-    cr = ldg4(r + off);
-    if (zold) cz = ldg4(zold + off);
-  };
-  auto ingest = [&](int st, size_t e) { return ld4(lay.v0(smem, st) + e); };
-  auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
-                  const V4<float>& zp) {
-    V4<float> nx = zero4, nr = zero4, nz = zero4;
-    if (t + 1 < s.ZC) {
-      const size_t noff = cell_offset(s, t + 1);
-      if (!x_zero) nx = ldg4(x + noff);
-      nr = ldg4(r + noff);
-      if (zold) nz = ldg4(zold + noff);
-    }
-    const V4<float> ap = stencil_q(pb, s, zm, c, zp);
-    const size_t off = cell_offset(s, t);
-    float d = 0.f, dz = 0.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      cx.v[i] = fmaf(alpha, c.v[i], cx.v[i]);
-      cr.v[i] = fmaf(-alpha, ap.v[i], cr.v[i]);
-      d = fmaf(cr.v[i], cr.v[i], d);
-      if (zold) dz = fmaf(cr.v[i], cz.v[i], dz);
-    }
-    st4(x + off, cx);
-    st4(r + off, cr);
-    acc.add(d);
-    if (zold) acc_z.add(dz);
-    cx = nx;
-    cr = nr;
-    cz = nz;
-  };
-  stream_slab<float, float, float, 1>(g, smem, bars, p, (const float*)nullptr, err, start, ingest, body);
-  double v[2] = {acc.value(), acc_z.value()}, tot[2];
-  if (grid_reduce_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-    const double rr = tot[0];
-    sc->rz_old = tot[1];
-    sc->x32_reset = 0;
-    sc->rr_prev = sc->rr;
-    sc->beta = rr / sc->rr;
-    sc->rr = rr;
-    sc->iter += 1;
-    if (!isfinite(rr)) {
-      sc->done = 3;
-    } else {
-      if (rr <= sc->tol2) {
-        sc->need_update = 1;
-        sc->final_check = 1;
-      } else if (rr <= sc->delta2 * sc->rmax2) {
-        sc->need_update = 1;
-      }
-      if (!sc->need_update && sc->iter >= sc->maxit) sc->done = 2;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 update of flexible CG, where q = (h^2 A) p was stored by the direction
-// kernel: x += alpha p, r -= alpha q as a plain stream (no stencil, no halo),
-// (r, r) and the same convergence / reliable-update bookkeeping as above.
+// FP32 update of the mixed-precision solvers (Jacobi-CG and flexible CG),
+// where q = (h^2 A) p was stored by the direction kernel: x += alpha p,
+// r -= alpha q as a plain stream (no stencil, no halo), (r, r) -> beta, and a
+// reliable update is triggered when (r, r) fell by delta^2 since the last one
+// or reached the tolerance.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_fcg_update32(float* __restrict__ x, float* __restrict__ r,
                                                       const float* __restrict__ p, const float* __restrict__ q,
