@@ -290,13 +290,17 @@ def run_ours(args):
             bpc = KER_BYTES[(kp, k)] + (4 if kp == 1 else 0)
             rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k],
                        "bytes_per_cell": bpc, "gbs": bpc * n / (avg_ms * 1e-3) / 1e9}
+    if prof["ker_samples"].get("dot"):
+        avg_ms = prof["ker_ms"]["dot"] / prof["ker_samples"]["dot"]
+        rows["dot"] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"]["dot"], "bytes_per_cell": 12,
+                       "gbs": 12 * n / (avg_ms * 1e-3) / 1e9}
     if prof["ker_samples"]["precond"]:
         avg_ms = prof["ker_ms"]["precond"] / prof["ker_samples"]["precond"]
         rows["precond"] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"]["precond"],
                            "flop_per_cell": PRECOND_FLOP_PER_CELL,
                            "tflops": PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12}
     dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
-    kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32",
+    kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32", ("dot", 1): "k_fcg_dot",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
     roof = None
     if dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):

@@ -69,7 +69,8 @@ typedef struct {
   int precond;           /* PIC_PC_* */
   double reliable_delta; /* MIXED: recompute the FP64 residual when the FP32 residual
                             norm fell by this factor since the last recomputation;
-                            0 selects the default 0.1 */
+                            0 selects the default: 0.1 with Jacobi, 0.03 with
+                            the learned preconditioner */
   int check_every;       /* iterations between host reads of the convergence flag; 0 = default */
 } pic_solve_opts;
 
@@ -241,13 +242,14 @@ int pic_cnn_conv_raw(pic_ctx *c, int which, const void *in, float *out, int B, i
  * launches. Read and optionally reset the totals with pic_profile_read
  * (synchronises the stream). */
 enum { PIC_PHASE_DEPOSIT = 0, PIC_PHASE_SOLVE = 1, PIC_PHASE_PUSH = 2, PIC_PHASE_ENERGY = 3, PIC_NPHASE = 4 };
-enum { PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_KER_PRECOND = 2, PIC_NKER = 3 };
+enum { PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_KER_PRECOND = 2, PIC_KER_DOT = 3, PIC_NKER = 4 };
 typedef struct {
   int64_t launches;           /* kernels launched by the context (counted always) */
   int phase_calls[PIC_NPHASE];
   double phase_ms[PIC_NPHASE];
-  int ker_samples[PIC_NKER];  /* sampled launches of the two CG kernels and of the
-                                 learned preconditioner's application */
+  int ker_samples[PIC_NKER];  /* sampled launches of the CG direction and update
+                                 kernels, of the learned preconditioner's
+                                 application and of flexible CG's dot products */
   double ker_ms[PIC_NKER];    /* their total device time */
   int ker_precision[PIC_NKER]; /* PIC_PREC_* of the sampled launches (last solve) */
 } pic_profile_stats;

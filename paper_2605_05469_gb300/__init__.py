@@ -56,12 +56,12 @@ class pic_solve_opts(ctypes.Structure):
 
 class pic_profile_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("phase_calls", ctypes.c_int * 4), ("phase_ms", ctypes.c_double * 4),
-                ("ker_samples", ctypes.c_int * 3), ("ker_ms", ctypes.c_double * 3),
-                ("ker_precision", ctypes.c_int * 3)]
+                ("ker_samples", ctypes.c_int * 4), ("ker_ms", ctypes.c_double * 4),
+                ("ker_precision", ctypes.c_int * 4)]
 
     def as_dict(self):
         phases = ("deposit", "solve", "push", "energy")
-        kers = ("pap", "update", "precond")
+        kers = ("pap", "update", "precond", "dot")
         return {
             "launches": int(self.launches),
             "phase_calls": {p: self.phase_calls[i] for i, p in enumerate(phases)},
