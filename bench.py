@@ -81,9 +81,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn"], default="cnn",
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn"], default="cnn",
                     help="cnn: mixed-precision flexible CG with the learned preconditioner (trained on the GPU "
-                         "before timing); mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge")
+                         "before timing); mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
+                         "mg: flexible CG with a multigrid V-cycle (damped Jacobi smoothing); mg_cnn: the V-cycle "
+                         "with the learned network smoothing the finest level")
     ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
@@ -178,11 +180,11 @@ def run_ours(args):
     N, ppc = args.N, args.ppc
     n = N ** 3
     prec = pg.PREC_FP64 if args.solver == "fp64" else pg.PREC_MIXED
-    pc = pg.PC_CNN if args.solver == "cnn" else pg.PC_JACOBI
+    pc = {"cnn": pg.PC_CNN, "mg": pg.PC_MG, "mg_cnn": pg.PC_MG_CNN}.get(args.solver, pg.PC_JACOBI)
     stream = torch.cuda.current_stream()
     solve_only = args.workload == "solve"
     weights, train_info = None, None
-    if args.solver == "cnn":
+    if args.solver in ("cnn", "mg_cnn"):
         weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
     apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
@@ -402,13 +404,17 @@ def train_preconditioner(pg, torch, N=64, steps=600, val_grid=128, val_every=100
 
 def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
     """Cold-start solves of the same right-hand side (the last deposit): the FP64
-    Jacobi-PCG judge against the mixed-precision solver, and with the learned
-    preconditioner when it is loaded (outside the timed region)."""
+    Jacobi-PCG judge against the mixed-precision solvers (Jacobi-CG, flexible
+    CG with the multigrid V-cycle, and with the learned preconditioner and the
+    V-cycle with the learned smoother when the network is loaded), outside the
+    timed region."""
     res = {}
-    cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI)]
+    cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI),
+             ("mixed_fcg_multigrid", pg.PREC_MIXED, pg.PC_MG)]
     if with_cnn:
         cases.append(("mixed_fcg_learned", pg.PREC_MIXED, pg.PC_CNN))
         cases.append(("mixed_fcg_learned_fp32", pg.PREC_MIXED, pg.PC_CNN))
+        cases.append(("mixed_fcg_multigrid_learned_smoother", pg.PREC_MIXED, pg.PC_MG_CNN))
     for name, prec, pc in cases:
         if with_cnn:
             c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
@@ -421,9 +427,12 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
                      "converged": bool(best["converged"])}
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
+    res["speedup_multigrid_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_multigrid"]["s"]
     if with_cnn:
         res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
         res["speedup_learned_fp32_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned_fp32"]["s"]
+        res["speedup_multigrid_learned_vs_fp64"] = (res["fp64_jacobi_pcg"]["s"] /
+                                                     res["mixed_fcg_multigrid_learned_smoother"]["s"])
     return res
 
 

@@ -60,9 +60,13 @@ typedef struct {
  * MIXED = FP32 stencil and vectors, FP64 reductions, FP64 solution and
  * reliable-update residual recomputation in FP64. */
 enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 };
-/* Preconditioner: JACOBI (Sec. 3.2) or the learned CNN inside flexible CG
- * (requires PIC_PREC_MIXED and weights set by pic_cnn_set_weights). */
-enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1 };
+/* Preconditioner: JACOBI (Sec. 3.2); the learned CNN inside flexible CG
+ * (requires PIC_PREC_MIXED and weights set by pic_cnn_set_weights); a
+ * geometric multigrid V-cycle inside flexible CG (the paper's named
+ * follow-on, Sec. 6; requires PIC_PREC_MIXED): MG smooths every level with
+ * damped Jacobi, MG_CNN smooths the finest level with the learned network
+ * (requires weights). See pic_mg_apply for the cycle. */
+enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1, PIC_PC_MG = 2, PIC_PC_MG_CNN = 3 };
 
 typedef struct {
   int precision;         /* PIC_PREC_* */
@@ -182,6 +186,17 @@ int pic_cnn_get_grads(pic_ctx *c, float *g_host);
  * is evaluated on grids with N % 32 == 0 is set by pic_cnn_set_apply; other
  * grids (N % 16 == 0) always run the four BF16 tensor-core convs. */
 int pic_cnn_apply(pic_ctx *c, const float *r, float *z);
+
+/* One multigrid V-cycle z = V(r) on the context grid (device FP32 [N^3],
+ * periodic), for the scaled system (6 I - adj) z = r, i.e. r = h^2 times the
+ * physical residual. Levels N, N/2, ... while even and above 4 (the coarsest:
+ * 40 damped Jacobi sweeps); full-weighting restriction (coarse right-hand
+ * side 4 R r), trilinear prolongation (R = P^T / 8); two damped-Jacobi
+ * sweeps (omega = 6/7) before and after the coarse-grid correction on every
+ * level, or, with learned != 0, one application of the network before and
+ * after on the finest level (requires weights). Levels of at most 16^3 run
+ * in one thread block. */
+int pic_mg_apply(pic_ctx *c, const float *r, float *z, int learned);
 
 /* Evaluation of the preconditioner (pic_cnn_apply and the solver's
  * preconditioner step) on grids with N % 32 == 0:

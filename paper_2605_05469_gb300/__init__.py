@@ -32,6 +32,8 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 PC_JACOBI = 0
 PC_CNN = 1
+PC_MG = 2
+PC_MG_CNN = 3
 CNN_APPLY_TC = 0
 CNN_APPLY_FP32 = 1
 CNN_APPLY_LAYERS = 2
@@ -110,6 +112,7 @@ _SIGS = {
     "pic_cnn_get_grads": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_set_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pic_mg_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "pic_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int]),
     "pic_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -319,6 +322,10 @@ class Context:
         g = np.empty(CNN_WEIGHTS, dtype=np.float32)
         _check(lib().pic_cnn_get_grads(self.h, g.ctypes.data_as(ctypes.c_void_p)), "pic_cnn_get_grads")
         return g
+
+    def mg_apply(self, r, z, learned=False):
+        _check(lib().pic_mg_apply(self.h, _dptr(r, "float32", self.n, "r"), _dptr(z, "float32", self.n, "z"),
+                                  1 if learned else 0), "pic_mg_apply")
 
     def cnn_set_apply(self, mode):
         _check(lib().pic_cnn_set_apply(self.h, int(mode)), "pic_cnn_set_apply")

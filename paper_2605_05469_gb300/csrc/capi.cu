@@ -6,6 +6,7 @@
 #include <new>
 
 #include "cnn.h"
+#include "mg.h"
 #include "ctx.h"
 #include "particle_kernels.cuh"
 #include "solver_kernels.cuh"
@@ -331,12 +332,18 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
 // reliable update if due, network z = s N(r/s), dots (r,z), (z,q), (r,q) with
 // the descent guard and beta = -(z,q)/(p,q), Jacobi fallback if it fired.
 // --------------------------------------------------------------------------
-int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta,
-                  pic_solve_info* info) {
+int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta, int pc,
+              pic_solve_info* info) {
   SolverWs& w = c->ws;
   int e;
-  if (!cnn_ready(c)) return PIC_ESTATE;
-  if (c->N % 16 != 0) return PIC_EINVAL;
+  const bool uses_net = pc == PIC_PC_CNN || pc == PIC_PC_MG_CNN;
+  if (uses_net && !cnn_ready(c)) return PIC_ESTATE;
+  if (pc == PIC_PC_CNN && c->N % 16 != 0) return PIC_EINVAL;
+  // z = M r for the chosen preconditioner (enqueued on the context stream)
+  auto precond = [&](const float* r, float* z) -> int {
+    if (pc == PIC_PC_CNN) return cnn_apply(c, r, z, &c->sc->rr, c->n);
+    return mg_apply(c, r, z, pc == PIC_PC_MG_CNN, &c->sc->done);
+  };
   if (!w.xm[0]) {
     if ((e = dalloc(&w.xm[0], c->n)) || (e = dalloc(&w.xm[1], c->n)) || (e = dalloc(&w.x32, c->n)) ||
         (e = dalloc(&w.r32, c->n)) || (e = dalloc(&w.p32[0], c->n)) || (e = dalloc(&w.p32[1], c->n)))
@@ -369,7 +376,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b, w.r32,
          c->sc, c->partials, c->counter, c->err, gr, 0);
   int zc = 0;
-  if ((e = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n))) return e;
+  if ((e = precond(w.r32, w.z32[zc]))) return e;
   launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
          c->partials, c->counter, 1, 0);
   launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
@@ -380,7 +387,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
   // r32b (rc = current). A reliable update (rare) replaces r, and then z and
   // the dots are recomputed from it by the redo kernels, which return at once
   // otherwise.
-  const bool fused = cnn_fused_ok(c);
+  const bool fused = pc == PIC_PC_CNN && cnn_fused_ok(c);
   if (fused && !w.r32b && (e = dalloc(&w.r32b, c->n))) return e;
   float* rbuf[2] = {w.r32, w.r32b};
   int rc = 0;
@@ -421,7 +428,7 @@ int solve_fcg_cnn(pic_ctx* c, const double* rho, double* phi, double tol, int ma
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
       zc ^= 1;
       slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
-      const int ce = cnn_apply(c, w.r32, w.z32[zc], &c->sc->rr, c->n);
+      const int ce = precond(w.r32, w.z32[zc]);
       if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
       if (ce && !inner_err) inner_err = ce;
       slot = sample ? c->ker[PIC_KER_DOT].begin(c->stream) : -1;
@@ -574,6 +581,7 @@ void pic_destroy(pic_ctx* c) {
     delete[] c->ker;
   }
   cnn_state_free(c->cnn);
+  mg_state_free(c->mg);
   delete c;
 }
 
@@ -663,8 +671,8 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
   if (o) opts = *o;
   int m = opts.check_every > 0 ? opts.check_every : (c->N <= 64 ? 32 : 8);
-  if (opts.precond != PIC_PC_JACOBI && opts.precond != PIC_PC_CNN) return PIC_EINVAL;
-  if (opts.precond == PIC_PC_CNN && opts.precision != PIC_PREC_MIXED) return PIC_EINVAL;
+  if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_MG_CNN) return PIC_EINVAL;
+  if (opts.precond != PIC_PC_JACOBI && opts.precision != PIC_PREC_MIXED) return PIC_EINVAL;
   PhaseScope ps(c, PIC_PHASE_SOLVE);
   if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);
   if (opts.precision == PIC_PREC_MIXED) {
@@ -673,9 +681,9 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
     // deposits), 0.1 is best for Jacobi-CG (smaller values cost iterations)
     // and 0.03 for flexible CG with the learned preconditioner (fewer FP64
     // recomputations at the same iteration count)
-    const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : (opts.precond == PIC_PC_CNN ? 0.03 : 0.1);
+    const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : (opts.precond == PIC_PC_JACOBI ? 0.1 : 0.03);
     if (!(delta < 1.0)) return PIC_EINVAL;
-    if (opts.precond == PIC_PC_CNN) return solve_fcg_cnn(c, rho, phi, tol, maxit, m, delta, info);
+    if (opts.precond != PIC_PC_JACOBI) return solve_fcg(c, rho, phi, tol, maxit, m, delta, opts.precond, info);
     return solve_mixed(c, rho, phi, tol, maxit, m, delta, info);
   }
   return PIC_EINVAL;

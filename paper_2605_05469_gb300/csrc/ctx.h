@@ -6,6 +6,7 @@
 namespace pic {
 
 struct CnnState;  // learned-preconditioner state, see cnn.cu
+struct MgState;   // multigrid hierarchy, see mg.cu
 
 struct SolverWs {
   // FP64 judge
@@ -106,6 +107,8 @@ struct pic_ctx {
   // learned preconditioner (weights, activations, optimiser state)
   pic::CnnState* cnn = nullptr;
   int cnn_apply_mode = 0;  // PIC_CNN_APPLY_*
+  // multigrid preconditioner (level buffers)
+  pic::MgState* mg = nullptr;
 };
 
 namespace pic {

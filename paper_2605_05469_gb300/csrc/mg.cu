@@ -1,0 +1,153 @@
+// Multigrid V-cycle preconditioner: level hierarchy, buffers and the launch
+// sequence (kernels in mg_kernels.cuh).
+#include <new>
+
+#include "cnn.h"
+#include "ctx.h"
+#include "mg.h"
+#include "mg_kernels.cuh"
+
+namespace pic {
+
+struct MgLevel {
+  int N = 0;
+  float *x = nullptr, *r = nullptr, *t = nullptr, *res = nullptr;
+};
+
+struct MgState {
+  int N0 = 0;
+  int nbig = 0;              // levels above kSmallN (level 0 = the context grid)
+  MgLevel lev[12];           // lev[nbig] is the first small level (its r and x only)
+  mg::SmallLevels small{};
+  size_t small_smem = 0;
+};
+
+void mg_state_free(MgState* s) {
+  if (!s) return;
+  for (auto& L : s->lev) {
+    dfree(L.x); dfree(L.r); dfree(L.t); dfree(L.res);
+  }
+  delete s;
+}
+
+namespace {
+
+int grid_for(const pic_ctx* c, size_t n) {
+  size_t b = (n + 255) / 256;
+  const size_t cap = (size_t)c->sms * 8;
+  return (int)(b < cap ? b : cap);
+}
+
+// The hierarchy of the oracle's V-cycle: halve while the level is even and
+// above the coarsest size; levels at or below kSmallN run in one CTA.
+int ensure_state(pic_ctx* c) {
+  if (c->mg && c->mg->N0 == c->N) return PIC_OK;
+  if (c->mg) {
+    mg_state_free(c->mg);
+    c->mg = nullptr;
+  }
+  MgState* s = new (std::nothrow) MgState();
+  if (!s) return PIC_ENOMEM;
+  s->N0 = c->N;
+  int sizes[24], nl = 0;
+  for (int N = c->N;; N /= 2) {
+    sizes[nl++] = N;
+    if (N <= mg::kCoarsestN || N % 2) break;
+  }
+  int b = 0;
+  while (b < nl && sizes[b] > mg::kSmallN) ++b;
+  s->nbig = b;
+  int e = PIC_OK;
+  for (int l = 0; l <= b && l < nl && !e; ++l) {
+    MgLevel& L = s->lev[l];
+    L.N = sizes[l];
+    const size_t n = (size_t)L.N * L.N * L.N;
+    if (l > 0) {
+      if ((e = dalloc(&L.x, n)) || (e = dalloc(&L.r, n))) break;
+    }
+    if (l < b) {
+      if ((e = dalloc(&L.t, n)) || (e = dalloc(&L.res, n))) break;
+    }
+  }
+  // the small levels (first one = lev[b])
+  mg::SmallLevels& S = s->small;
+  S.n = nl - b;
+  int off = 0;
+  for (int q = 0; q < S.n; ++q) {
+    S.N[q] = sizes[b + q];
+    S.off[q] = off;
+    off += S.N[q] * S.N[q] * S.N[q];
+  }
+  S.total = off;
+  s->small_smem = (size_t)3 * off * sizeof(float);
+  if (!e && b == 0) {
+    // the context grid itself is small: the CTA kernel does the whole cycle
+    s->lev[0].N = sizes[0];
+  }
+  if (e) {
+    mg_state_free(s);
+    return e;
+  }
+  c->mg = s;
+  return PIC_OK;
+}
+
+}  // namespace
+
+int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done) {
+  int e;
+  if ((e = ensure_state(c))) return e;
+  MgState* s = c->mg;
+  static bool configured = false;
+  if (!configured) {
+    CK(cudaFuncSetAttribute((const void*)mg::k_mg_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)(3 * (16 * 16 * 16 + 8 * 8 * 8 + 4 * 4 * 4) * sizeof(float))));
+    configured = true;
+  }
+  const int B = s->nbig;
+  auto xl = [&](int l) { return l == 0 ? z : s->lev[l].x; };
+  auto rl = [&](int l) { return l == 0 ? r : (const float*)s->lev[l].r; };
+  // down
+  for (int l = 0; l < B; ++l) {
+    MgLevel& L = s->lev[l];
+    const size_t n = (size_t)L.N * L.N * L.N;
+    const int g = grid_for(c, n);
+    if (l == 0 && learned) {
+      if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
+    } else {
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)nullptr, rl(l), L.t, L.N, done);
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
+    }
+    launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(l), rl(l), L.res, L.N, done);
+    const size_t nc = n / 8;
+    launch(c, mg::k_mg_restrict, grid_for(c, nc), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
+  }
+  // the small levels in one CTA
+  launch(c, mg::k_mg_small, 1, mg::kSmallThreads, s->small_smem, rl(B), xl(B), s->small, 2, done);
+  // up
+  for (int l = B - 1; l >= 0; --l) {
+    MgLevel& L = s->lev[l];
+    const size_t n = (size_t)L.N * L.N * L.N;
+    const int g = grid_for(c, n);
+    launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), (const float*)xl(l + 1), L.N / 2, done);
+    if (l == 0 && learned) {
+      launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(0), rl(0), L.res, L.N, done);
+      if ((e = cnn_apply(c, L.res, L.t, nullptr, n))) return e;
+      launch(c, mg::k_mg_add, grid_for(c, n / 4), 256, 0, xl(0), (const float*)L.t, n / 4, done);
+    } else {
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
+    }
+  }
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+}  // namespace pic
+
+extern "C" int pic_mg_apply(pic_ctx* c, const float* r, float* z, int learned) {
+  if (!c || !r || !z) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  if (learned && !pic::cnn_ready(c)) return PIC_ESTATE;
+  return pic::mg_apply(c, r, z, learned != 0, nullptr);
+}
