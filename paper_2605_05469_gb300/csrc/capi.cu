@@ -9,18 +9,12 @@
 #include "mg.h"
 #include "ctx.h"
 #include "particle_kernels.cuh"
+#include "slab_geo.h"
 #include "solver_kernels.cuh"
 
 using namespace pic;
 
 namespace {
-
-// dynamic shared memory of one plane-streaming block: small blocks leave room
-// for at least three (FP32) or two (FP64) blocks per SM, a tall block has the SM
-constexpr size_t kSmemBudget32 = 72 * 1024;
-constexpr size_t kSmemBudget64 = 110 * 1024;
-constexpr size_t kSmemTall = 220 * 1024;
-constexpr size_t kSmemMax = 226 * 1024;
 
 void free_particles(pic_ctx* c) {
   for (int b = 0; b < 2; ++b) {
@@ -48,48 +42,10 @@ void free_solver(pic_ctx* c) {
 
 PRec* pptrs(pic_ctx* c, int b) { return c->prec[b]; }
 
-// Stage count from a shared-memory budget per block (raw TMA stages + 3 plane
-// buffers, at least 3 stages); persistent grid = resident blocks of `kernel`.
+// Slab geometry of a plane-streaming kernel on the context grid.
 template <typename TP, typename A, typename B, int NV, typename K>
 int geo_for(pic_ctx* c, K kernel, StreamGeo* out, size_t* smem, bool tall = false) {
-  // The tallest slab (largest divisor TY of N) whose block fits the thread
-  // cap and, with three raw stages and three plane buffers, the block's
-  // shared-memory budget: the halo rows re-read per plane are (TY + 2) / TY
-  // of the slab. If none fits the budget, the tallest that fits the SM.
-  // Then as many raw stages as the budget allows (at least three).
-  const int N = c->N;
-  const int cap = tall ? kStreamTall : kStreamSmall;
-  const size_t budget = tall ? kSmemTall : (sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32);
-  StreamGeo g{};
-  bool found = false;
-  for (int pass = 0; pass < 2 && !found; ++pass) {
-    const size_t lim = pass == 0 ? budget : kSmemMax;
-    for (int ty = N; ty >= 1 && !found; --ty) {
-      if (N % ty || (long)N * ty / 4 > cap) continue;
-      StreamGeo t = make_stream_geo(N, 3, ty);
-      if (stream_smem_bytes<TP, A, B, NV>(t.rows, t.N, 3) <= lim) {
-        g = t;
-        found = true;
-      }
-    }
-  }
-  if (!found) return PIC_EINVAL;
-  const StageLayout<A, B, NV> lay(g.rows, g.N);
-  const size_t pb = 3 * (size_t)g.rows * g.N * sizeof(TP);
-  int S = budget > pb ? (int)((budget - pb) / lay.bytes) : 0;
-  if (S < 3) S = 3;
-  if (S > kMaxStages) S = kMaxStages;
-  g.S = S;
-  *smem = stream_smem_bytes<TP, A, B, NV>(g.rows, g.N, S);
-  CK(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
-  CK(cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                          (int)cudaSharedmemCarveoutMaxShared));
-  int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, round32(g.threads), *smem));
-  if (per_sm < 1) return PIC_EINVAL;
-  set_stream_blocks(g, per_sm * c->sms);
-  *out = g;
-  return PIC_OK;
+  return slab_geometry<TP, A, B, NV>(c, c->N, kernel, out, smem, tall);
 }
 
 int streaming_blocks(pic_ctx* c) {
@@ -670,8 +626,12 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   if (!(tol >= 0.0) || maxit < 0) return PIC_EINVAL;
   pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
   if (o) opts = *o;
-  int m = opts.check_every > 0 ? opts.check_every : (c->N <= 64 ? 32 : 8);
   if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_MG_CNN) return PIC_EINVAL;
+  // status-check cadence: the multigrid solve converges in about ten
+  // iterations, so its batches are short (each batch launched past
+  // convergence still costs the launches of its kernels)
+  const bool mgpc = opts.precond == PIC_PC_MG || opts.precond == PIC_PC_MG_CNN;
+  int m = opts.check_every > 0 ? opts.check_every : (mgpc ? 2 : (c->N <= 64 ? 32 : 8));
   if (opts.precond != PIC_PC_JACOBI && opts.precision != PIC_PREC_MIXED) return PIC_EINVAL;
   PhaseScope ps(c, PIC_PHASE_SOLVE);
   if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);

@@ -6,12 +6,19 @@
 #include "ctx.h"
 #include "mg.h"
 #include "mg_kernels.cuh"
+#include "slab_geo.h"
 
 namespace pic {
+
+// The plane-streamed kernels of a level (its size a multiple of 4).
+enum MgKer { kPre, kResid, kResidProlong, kSmoothProlong, kSmooth, kNumMgKer };
 
 struct MgLevel {
   int N = 0;
   float *x = nullptr, *r = nullptr, *t = nullptr, *res = nullptr;
+  bool streamed = false;          // N % 4 == 0: plane-streamed kernels
+  StreamGeo geo[kNumMgKer]{};
+  size_t smem[kNumMgKer]{};
 };
 
 struct MgState {
@@ -69,6 +76,26 @@ int ensure_state(pic_ctx* c) {
       if ((e = dalloc(&L.t, n)) || (e = dalloc(&L.res, n))) break;
     }
   }
+  // slab geometry of every streamed level; each kernel's shared-memory limit
+  // ends at the largest size any level launches it with
+  void* kers[kNumMgKer] = {(void*)mg::k_mg_pre, (void*)mg::k_mg_stencil<mg::kResid, false>,
+                           (void*)mg::k_mg_stencil<mg::kResid, true>, (void*)mg::k_mg_stencil<mg::kSmooth, true>,
+                           (void*)mg::k_mg_stencil<mg::kSmooth, false>};
+  size_t smax[kNumMgKer] = {};
+  for (int l = 0; l < b && !e; ++l) {
+    MgLevel& L = s->lev[l];
+    L.streamed = L.N % 4 == 0;
+    if (!L.streamed) continue;
+    for (int k = 0; k < kNumMgKer && !e; ++k) {
+      e = slab_geometry<float, float, float, 1>(c, L.N, (const void*)kers[k], &L.geo[k], &L.smem[k]);
+      if (L.smem[k] > smax[k]) smax[k] = L.smem[k];
+    }
+  }
+  for (int k = 0; k < kNumMgKer && !e; ++k) {
+    if (smax[k] && cudaFuncSetAttribute(kers[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax[k]) !=
+                       cudaSuccess)
+      e = PIC_ECUDA;
+  }
   // the small levels (first one = lev[b])
   mg::SmallLevels& S = s->small;
   S.n = nl - b;
@@ -105,36 +132,65 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     configured = true;
   }
   const int B = s->nbig;
+  // the learned smoother works on the finest of the full-grid levels
+  if (learned && B == 0) return PIC_EINVAL;
   auto xl = [&](int l) { return l == 0 ? z : s->lev[l].x; };
   auto rl = [&](int l) { return l == 0 ? r : (const float*)s->lev[l].r; };
-  // down
+  // plane-streamed kernel k of level L
+  auto slab = [&](const MgLevel& L, MgKer k, auto kernel, auto... args) {
+    const StreamGeo& g = L.geo[k];
+    launch(c, kernel, g.blocks, round32(g.threads), L.smem[k], args..., c->err, g, done);
+  };
+  const float* nul = nullptr;
+  float* nulw = nullptr;
+  // down: pre-smooth, residual, restrict
   for (int l = 0; l < B; ++l) {
     MgLevel& L = s->lev[l];
     const size_t n = (size_t)L.N * L.N * L.N;
     const int g = grid_for(c, n);
     if (l == 0 && learned) {
       if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
+    } else if (L.streamed) {
+      slab(L, kPre, mg::k_mg_pre, rl(l), xl(l));
     } else {
-      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)nullptr, rl(l), L.t, L.N, done);
+      launch(c, mg::k_mg_jacobi, g, 256, 0, nul, rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
     }
-    launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(l), rl(l), L.res, L.N, done);
-    const size_t nc = n / 8;
-    launch(c, mg::k_mg_restrict, grid_for(c, nc), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
+    if (L.streamed) {
+      slab(L, kResid, mg::k_mg_stencil<mg::kResid, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
+      const int Nc = L.N / 2;
+      const unsigned per_plane = (unsigned)(Nc / 2) * (unsigned)Nc;
+      const unsigned bx = (per_plane + 255) / 256;
+      launch(c, mg::k_mg_restrict2, dim3(bx, Nc), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
+    } else {
+      launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(l), rl(l), L.res, L.N, done);
+      launch(c, mg::k_mg_restrict, grid_for(c, n / 8), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
+    }
   }
   // the small levels in one CTA
   launch(c, mg::k_mg_small, 1, mg::kSmallThreads, s->small_smem, rl(B), xl(B), s->small, 2, done);
-  // up
+  // up: prolong-add, post-smooth
   for (int l = B - 1; l >= 0; --l) {
     MgLevel& L = s->lev[l];
     const size_t n = (size_t)L.N * L.N * L.N;
     const int g = grid_for(c, n);
-    launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), (const float*)xl(l + 1), L.N / 2, done);
+    const float* ec = xl(l + 1);
     if (l == 0 && learned) {
-      launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(0), rl(0), L.res, L.N, done);
-      if ((e = cnn_apply(c, L.res, L.t, nullptr, n))) return e;
+      // x' = x + P e_c (into t), res = r - A^ x', x = x' + K res
+      if (L.streamed) {
+        slab(L, kResidProlong, mg::k_mg_stencil<mg::kResid, true>, (const float*)xl(0), rl(0), L.res, L.t, ec);
+      } else {
+        launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(0), ec, L.N / 2, done);
+        launch(c, mg::k_mg_copy, grid_for(c, n), 256, 0, (const float*)xl(0), L.t, n, done);
+        launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(0), rl(0), L.res, L.N, done);
+      }
+      if ((e = cnn_apply(c, L.res, xl(0), nullptr, n))) return e;
       launch(c, mg::k_mg_add, grid_for(c, n / 4), 256, 0, xl(0), (const float*)L.t, n / 4, done);
+    } else if (L.streamed) {
+      slab(L, kSmoothProlong, mg::k_mg_stencil<mg::kSmooth, true>, (const float*)xl(l), rl(l), L.t, nulw, ec);
+      slab(L, kSmooth, mg::k_mg_stencil<mg::kSmooth, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
     } else {
+      launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), ec, L.N / 2, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
     }

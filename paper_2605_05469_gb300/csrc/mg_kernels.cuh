@@ -11,8 +11,19 @@
 // R full weighting (coarse node I <- fine 2I and its 26 neighbours, weights
 // prod_d w(o_d), w(0) = 1/2, w(+-1) = 1/4), P trilinear interpolation
 // (R = P^T / 8). FP32 throughout.
+//
+// Levels whose size is a multiple of 4 stream their planes through the
+// shared-memory slabs of the CG kernels (one HBM pass per kernel, 4 cells a
+// thread) with the passes fused where the arithmetic allows:
+//   pre-smoothing   both sweeps from x = 0 in one pass, x = w (2 r - w A^ r);
+//   post-smoothing  the prolongation folded into the first sweep, the fine
+//                   x' = x + P e_c formed as each plane arrives;
+//   residual        (with the prolongation, for the learned smoother);
+//   restriction     two coarse nodes a thread from float4 rows.
+// Other sizes take the per-cell kernels below them.
 #pragma once
 #include "common.cuh"
+#include "stream.cuh"
 
 namespace pic {
 namespace mg {
@@ -36,6 +47,144 @@ __device__ __forceinline__ float apply_hat(const float* __restrict__ x, int N, i
   return 6.0f * c - (((xm + xp) + (ym + yp)) + (zm + zp));
 }
 
+// ---------------------------------------------------------------------------
+// Plane-streamed kernels (N % 4 == 0)
+// ---------------------------------------------------------------------------
+
+// v += (P e_c) on the 4 cells at stage offset e of plane z (fine grid s.N,
+// coarse Nc = s.N / 2 even): fine x = 2I is coarse I, fine x = 2I+1 the mean
+// of I and I+1; likewise in y and z, so the 4 cells need coarse x-nodes
+// I0, I0+1, I0+2 (I0 = x0 / 2 even) summed over the 1, 2 or 4 (J, K) pairs.
+__device__ __forceinline__ void add_prolonged(V4<float>& v, const float* __restrict__ ec, const Slab& s, size_t e,
+                                              int z) {
+  const int N = s.N, Nc = N >> 1;
+  const unsigned sr = (unsigned)e / (unsigned)N;
+  const int i0 = (int)((unsigned)e - sr * (unsigned)N);
+  const int j = (s.TY == N) ? (int)sr : wrapi(s.j0 - 1 + (int)sr, N);
+  const int I0 = i0 >> 1;
+  const int I2 = (I0 + 2 == Nc) ? 0 : I0 + 2;
+  const int J0 = j >> 1, K0 = z >> 1;
+  const int J1 = (J0 + 1 == Nc) ? 0 : J0 + 1;
+  const int K1 = (K0 + 1 == Nc) ? 0 : K0 + 1;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  auto acc = [&](int J, int K) {
+    const float* row = ec + ((size_t)K * Nc + J) * Nc;
+    const float2 a = __ldg(reinterpret_cast<const float2*>(row + I0));
+    s0 += a.x;
+    s1 += a.y;
+    s2 += __ldg(row + I2);
+  };
+  acc(J0, K0);
+  if (j & 1) acc(J1, K0);
+  if (z & 1) {
+    acc(J0, K1);
+    if (j & 1) acc(J1, K1);
+  }
+  const float wyz = ((j & 1) ? 0.5f : 1.f) * ((z & 1) ? 0.5f : 1.f);
+  v.v[0] += wyz * s0;
+  v.v[1] += wyz * (0.5f * (s0 + s1));
+  v.v[2] += wyz * s1;
+  v.v[3] += wyz * (0.5f * (s1 + s2));
+}
+
+// Pre-smoothing, nu1 = 2 damped sweeps from x = 0 in one pass:
+// x1 = w r, x2 = x1 + w (r - A^ x1) = w (2 r - w A^ r), w = omega / 6.
+__global__ void __launch_bounds__(kStreamSmall) k_mg_pre(const float* __restrict__ r, float* __restrict__ x, int* err,
+                                                         StreamGeo g, const int* done) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  if (done && *done) return;
+  const StageLayout<float, float, 1> lay(g.rows, g.N);
+  const float w = kOmega / 6.0f;
+  auto start = [&](const Slab&) {};
+  auto ingest = [&](int st, size_t e, const Slab&, int) { return ld4(lay.v0(smem, st) + e); };
+  auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
+                  const V4<float>& zp) {
+    const V4<float> ar = stencil_q(pb, s, zm, c, zp);
+    V4<float> o;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o.v[i] = w * (2.0f * c.v[i] - w * ar.v[i]);
+    st4(x + cell_offset(s, t), o);
+  };
+  stream_slab<float, float, float, 1>(g, smem, bars, r, (const float*)nullptr, err, start, ingest, body);
+}
+
+enum : int { kResid = 0, kSmooth = 1 };
+
+// With x' = x (PROLONG false) or x' = x + P e_c (PROLONG true):
+//   kResid : out = r - A^ x'        (and xout = x' when PROLONG)
+//   kSmooth: out = x' + w (r - A^ x')
+// out and xout must not alias x (other blocks read x's halo rows).
+template <int MODE, bool PROLONG>
+__global__ void __launch_bounds__(kStreamSmall) k_mg_stencil(const float* __restrict__ x, const float* __restrict__ r,
+                                                             float* __restrict__ out, float* __restrict__ xout,
+                                                             const float* __restrict__ ec, int* err, StreamGeo g,
+                                                             const int* done) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bars[kMaxStages];
+  if (done && *done) return;
+  const StageLayout<float, float, 1> lay(g.rows, g.N);
+  const float w = kOmega / 6.0f;
+  V4<float> cb;
+  auto start = [&](const Slab& s) { cb = ldg4(r + cell_offset(s, 0)); };
+  auto ingest = [&](int st, size_t e, const Slab& s, int z) {
+    V4<float> v = ld4(lay.v0(smem, st) + e);
+    if (PROLONG) add_prolonged(v, ec, s, e, z);
+    return v;
+  };
+  auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
+                  const V4<float>& zp) {
+    V4<float> nb = cb;
+    if (t + 1 < s.ZC) nb = ldg4(r + cell_offset(s, t + 1));
+    const V4<float> ax = stencil_q(pb, s, zm, c, zp);
+    const size_t off = cell_offset(s, t);
+    V4<float> o;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o.v[i] = MODE == kResid ? cb.v[i] - ax.v[i] : c.v[i] + w * (cb.v[i] - ax.v[i]);
+    cb = nb;
+    st4(out + off, o);
+    if (PROLONG && MODE == kResid) st4(xout + off, c);
+  };
+  stream_slab<float, float, float, 1>(g, smem, bars, x, (const float*)nullptr, err, start, ingest, body);
+}
+
+// rc = 4 R res onto the coarse grid Nf/2 (Nf % 4 == 0): each thread the
+// coarse pair (2P, 2P+1) of row J of plane K = blockIdx.y, from the fine
+// float4 at x = 4P and the scalar at 4P - 1 of each of the 9 fine rows.
+__global__ void __launch_bounds__(256) k_mg_restrict2(const float* __restrict__ res, float* __restrict__ rc, int Nf,
+                                                      const int* done) {
+  if (done && *done) return;
+  const int Nc = Nf >> 1, Np = Nc >> 1;
+  const unsigned per_plane = (unsigned)Np * (unsigned)Nc;
+  const int K = blockIdx.y;
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < per_plane; q += gridDim.x * blockDim.x) {
+    const int J = (int)(q / (unsigned)Np), P = (int)(q - (unsigned)J * (unsigned)Np);
+    const int i0 = 4 * P, im = i0 == 0 ? Nf - 1 : i0 - 1;
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int oz = -1; oz <= 1; ++oz) {
+      const size_t zb = (size_t)wrapi(2 * K + oz, Nf) * Nf;
+      const float wz = oz ? 0.25f : 0.5f;
+      float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+      for (int oy = -1; oy <= 1; ++oy) {
+        const float* row = res + (zb + (size_t)wrapi(2 * J + oy, Nf)) * Nf;
+        const float wy = oy ? 0.25f : 0.5f;
+        const float4 v = __ldg(reinterpret_cast<const float4*>(row + i0));
+        const float m = __ldg(row + im);
+        b0 = fmaf(wy, 0.25f * m + 0.5f * v.x + 0.25f * v.y, b0);
+        b1 = fmaf(wy, 0.25f * v.y + 0.5f * v.z + 0.25f * v.w, b1);
+      }
+      a0 = fmaf(wz, b0, a0);
+      a1 = fmaf(wz, b1, a1);
+    }
+    *reinterpret_cast<float2*>(rc + ((size_t)K * Nc + J) * Nc + 2 * P) = make_float2(4.0f * a0, 4.0f * a1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-cell kernels (any even N)
+// ---------------------------------------------------------------------------
 // out = x + (omega/6)(r - A^ x); x == nullptr reads x as zero.
 // Every kernel returns at once when the solve it serves has finished (done
 // != nullptr and *done set), so batches launched past convergence cost no work.
@@ -126,6 +275,14 @@ __global__ void __launch_bounds__(256) k_mg_prolong_add(float* __restrict__ x, c
   }
 }
 
+// y = x.
+__global__ void __launch_bounds__(256) k_mg_copy(const float* __restrict__ x, float* __restrict__ y, size_t n,
+                                                 const int* done) {
+  if (done && *done) return;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    y[c] = x[c];
+}
+
 // x += y.
 __global__ void __launch_bounds__(256) k_mg_add(float* __restrict__ x, const float* __restrict__ y, size_t n4,
                                                 const int* done) {
@@ -152,23 +309,42 @@ struct SmallLevels {
   int total;      // elements per region
 };
 
-__device__ __forceinline__ void sm_jacobi(const float* x, const float* r, float* out, int N, bool x_zero) {
+// One damped Jacobi sweep out = x + w (r - A^ x) (x_zero: x = 0) over the
+// threads [0, nt), then a barrier of those threads (the block, or warp 0).
+template <bool WARP>
+__device__ __forceinline__ void sm_sweep(const float* x, const float* r, float* out, int N, bool x_zero) {
   const int n = N * N * N;
   const float w = kOmega / 6.0f;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    if (x_zero) {
-      out[c] = w * r[c];
-    } else {
-      const int i = c % N, j = (c / N) % N, k = c / (N * N);
-      out[c] = x[c] + w * (r[c] - apply_hat(x, N, i, j, k));
+  const int nt = WARP ? 32 : (int)blockDim.x;
+  if (!WARP || threadIdx.x < 32) {
+    for (int c = threadIdx.x; c < n; c += nt) {
+      if (x_zero) {
+        out[c] = w * r[c];
+      } else {
+        const int i = c % N, j = (c / N) % N, k = c / (N * N);
+        out[c] = x[c] + w * (r[c] - apply_hat(x, N, i, j, k));
+      }
     }
   }
-  __syncthreads();
+  if (WARP) __syncwarp();
+  else __syncthreads();
 }
 
-__device__ __forceinline__ void sm_copy(const float* a, float* b, int n) {
-  for (int c = threadIdx.x; c < n; c += blockDim.x) b[c] = a[c];
-  __syncthreads();
+// nu sweeps on level (x, r) with scratch t, ping-ponging x -> t -> x; the
+// result ends in x (one copy when nu is odd).
+template <bool WARP>
+__device__ __forceinline__ void sm_smooth(float* x, const float* r, float* t, int N, int nu, bool from_zero) {
+  for (int s = 0; s < nu; ++s) {
+    const bool into_t = (s % 2) == 0;
+    sm_sweep<WARP>(into_t ? x : t, r, into_t ? t : x, N, from_zero && s == 0);
+  }
+  if (nu % 2) {
+    const int n = N * N * N, nt = WARP ? 32 : (int)blockDim.x;
+    if (!WARP || threadIdx.x < 32)
+      for (int c = threadIdx.x; c < n; c += nt) x[c] = t[c];
+    if (WARP) __syncwarp();
+    else __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restrict__ r_in, float* __restrict__ x_out,
@@ -185,10 +361,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restr
   for (int l = 0; l + 1 < S.n; ++l) {
     const int N = S.N[l], n = N * N * N;
     float *x = X + S.off[l], *r = R + S.off[l], *t = T + S.off[l];
-    for (int s = 0; s < nu; ++s) {
-      sm_jacobi(s ? x : nullptr, r, t, N, s == 0);
-      sm_copy(t, x, n);
-    }
+    sm_smooth<false>(x, r, t, N, nu, true);
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int i = c % N, j = (c / N) % N, k = c / (N * N);
       t[c] = r[c] - apply_hat(x, N, i, j, k);
@@ -209,13 +382,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restr
     }
     __syncthreads();
   }
-  // coarsest: damped Jacobi sweeps from zero
+  // coarsest: damped Jacobi sweeps from zero (one warp when the level is tiny)
   {
-    const int l = S.n - 1, N = S.N[l], n = N * N * N;
+    const int l = S.n - 1, N = S.N[l];
     float *x = X + S.off[l], *r = R + S.off[l], *t = T + S.off[l];
-    for (int s = 0; s < kCoarseSweeps; ++s) {
-      sm_jacobi(s ? x : nullptr, r, t, N, s == 0);
-      sm_copy(t, x, n);
+    if (N * N * N <= 256) {
+      sm_smooth<true>(x, r, t, N, kCoarseSweeps, true);
+      __syncthreads();
+    } else {
+      sm_smooth<false>(x, r, t, N, kCoarseSweeps, true);
     }
   }
   // up: prolong-add, post-smooth
@@ -247,10 +422,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restr
       x[c] += w * v;
     }
     __syncthreads();
-    for (int s = 0; s < nu; ++s) {
-      sm_jacobi(x, r, t, N, false);
-      sm_copy(t, x, n);
-    }
+    sm_smooth<false>(x, r, t, N, nu, false);
   }
   for (int c = threadIdx.x; c < n0; c += blockDim.x) x_out[c] = X[c];
 }

@@ -188,4 +188,143 @@ __device__ __forceinline__ size_t cell_offset(const Slab& s, int t) {
   return ((size_t)(s.z0 + t) * N + (size_t)(s.j0 + s.ty)) * N + s.x0;
 }
 
+constexpr int kMaxStages = 8;
+// Block sizes of the plane-streaming kernels (4 cells per thread). Small
+// blocks, several per SM, overlap one another's per-plane barrier and copy
+// waits; the tall-slab form of the direction kernel (one 1024-thread block
+// per SM) re-reads fewer halo rows, which pays once N >= 512 (measured).
+constexpr int kStreamSmall = 256;
+constexpr int kStreamTall = 1024;
+
+// Layout of one stage: vector 0 (type A) then optional vector 1 (type B),
+// each rows*N elements; stage size rounded up to 128 bytes.
+template <typename A, typename B, int NV>
+struct StageLayout {
+  size_t e, bytes;
+  __host__ __device__ StageLayout(int rows, int N) {
+    e = (size_t)rows * N;
+    size_t b = e * sizeof(A) + (NV == 2 ? e * sizeof(B) : 0);
+    bytes = (b + 127) & ~(size_t)127;
+  }
+  __device__ A* v0(unsigned char* base, int st) const { return reinterpret_cast<A*>(base + st * bytes); }
+  __device__ B* v1(unsigned char* base, int st) const {
+    return reinterpret_cast<B*>(base + st * bytes + e * sizeof(A));
+  }
+};
+
+// Streams the block's runs of planes through the ring of raw TMA stages.
+// For every arriving plane l of a run, each thread transforms 4 consecutive
+// cells (its own, plus one halo-row chunk for the threads on the slab's first
+// and last row):
+//   ingest(st, e, s, z) -> V4<TP>   transformed values at stage element
+//                             offset e of global plane z,
+// writes them to plane buffer l % 3 (x-y neighbours of other threads) and
+// keeps its own cells in a register queue (centre and z-neighbours). After a
+// single barrier the raw stage is refilled and output plane t = l - 2 runs:
+//   body(s, t, pb, zm, c, zp) pb = plane buffer of plane t (x-y neighbours),
+//                             zm/c/zp = own cells at planes t-1, t, t+1.
+//   start(s)                  once per run before its first plane (prefetch).
+// Three plane buffers make one barrier per plane sufficient. mbarrier phases
+// continue across runs; every issued copy is waited for before the next run.
+template <typename TP, typename A, typename B, int NV, typename Start, typename Ingest, typename Body>
+__device__ __forceinline__ bool stream_slab(const StreamGeo& g, unsigned char* smem, uint64_t* bars, const A* src0,
+                                            const B* src1, int* err, Start start, Ingest ingest, Body body) {
+  const StageLayout<A, B, NV> lay(g.rows, g.N);
+  const size_t pb_elems = (size_t)g.rows * g.N;
+  TP* pbuf = reinterpret_cast<TP*>(smem + (size_t)g.S * lay.bytes);
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < g.S; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t base = 0;  // loads issued (and consumed) in earlier runs
+  bool ok = true;
+  for_each_run(g, [&](int yt, int z0, int zc) {
+    if (!ok) return;
+    const Slab s = make_slab(g, yt, z0, zc);
+    const int nload = s.ZC + 2;
+    const uint32_t tx = plane_bytes<A>(s) + (NV == 2 ? plane_bytes<B>(s) : 0u);
+    auto issue = [&](int l) {
+      const uint32_t L = base + (uint32_t)l;
+      const int st = (int)(L % (uint32_t)s.S);
+      const int z = load_plane(s, l);
+      mbar_arrive_expect_tx(&bars[st], tx);
+      issue_plane(lay.v0(smem, st), src0, s, z, &bars[st]);
+      if (NV == 2) issue_plane(lay.v1(smem, st), src1, s, z, &bars[st]);
+    };
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      const int pre = nload < s.S ? nload : s.S;
+      for (int l = 0; l < pre; ++l) issue(l);
+    }
+    if (s.active) start(s);
+    // halo-row chunks owned by this thread (stage rows 0 and TY+1; with
+    // TY == 1 the same thread owns both)
+    const bool halo_lo = s.TY != s.N && s.active && s.ty == 0;
+    const bool halo_hi = s.TY != s.N && s.active && s.ty == s.TY - 1;
+    const size_t own = (size_t)s.srow * s.N + s.x0;
+    const size_t hal_lo = (size_t)s.x0;
+    const size_t hal_hi = (size_t)(s.TY + 1) * s.N + s.x0;
+    V4<TP> q0, q1, q2;
+    for (int l = 0; l < nload; ++l) {
+      const uint32_t L = base + (uint32_t)l;
+      const int st = (int)(L % (uint32_t)s.S);
+      if (!mbar_wait_bounded(&bars[st], (L / (uint32_t)s.S) & 1u, err)) abort_flag = 1;
+      TP* pb = pbuf + (size_t)(L % 3u) * pb_elems;
+      if (s.active) {
+        const int zl = load_plane(s, l);
+        q0 = q1;
+        q1 = q2;
+        q2 = ingest(st, own, s, zl);
+        st4(pb + own, q2);
+        if (halo_lo) st4(pb + hal_lo, ingest(st, hal_lo, s, zl));
+        if (halo_hi) st4(pb + hal_hi, ingest(st, hal_hi, s, zl));
+      }
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        return;
+      }
+      if (threadIdx.x == 0 && l + s.S < nload) {
+        fence_proxy_async_smem();
+        issue(l + s.S);
+      }
+      if (l >= 2 && s.active) body(s, l - 2, pbuf + (size_t)((L + 2u) % 3u) * pb_elems, q0, q1, q2);
+    }
+    base += (uint32_t)nload;
+  });
+  return ok;
+}
+
+// Bytes of dynamic shared memory for stream_slab: S raw stages + 3 plane buffers.
+template <typename TP, typename A, typename B, int NV>
+__host__ __device__ inline size_t stream_smem_bytes(int rows, int N, int S) {
+  const StageLayout<A, B, NV> lay(rows, N);
+  return (size_t)S * lay.bytes + 3 * (size_t)rows * N * sizeof(TP);
+}
+
+// x-y neighbours from the plane buffer, z-neighbours and centre from registers:
+// returns 6 c - (sum of the 6 neighbours) on the thread's 4 cells.
+template <typename T>
+__device__ __forceinline__ V4<T> stencil_q(const T* pb, const Slab& s, const V4<T>& zm, const V4<T>& c,
+                                           const V4<T>& zp) {
+  const int N = s.N;
+  const T* row = pb + (size_t)s.srow * N;
+  const T xm = row[s.x0 == 0 ? N - 1 : s.x0 - 1];
+  const T xp = row[s.x0 + 4 == N ? 0 : s.x0 + 4];
+  const V4<T> ym = ld4(pb + (size_t)s.rm * N + s.x0);
+  const V4<T> yp = ld4(pb + (size_t)s.rp * N + s.x0);
+  V4<T> o;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T l = (i == 0) ? xm : c.v[i - 1];
+    const T r = (i == 3) ? xp : c.v[i + 1];
+    const T sum = ((l + r) + (ym.v[i] + yp.v[i])) + (zm.v[i] + zp.v[i]);
+    o.v[i] = (T)6 * c.v[i] - sum;
+  }
+  return o;
+}
+
 }  // namespace pic
