@@ -52,6 +52,30 @@ PRECOND_FLOP_PER_CELL = 2 * 729
 # ... which the tensor-core form executes as 81 Toeplitz products of K = 32
 # x-inputs per output (9 of the 32 weights in each product are nonzero)
 PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32
+# algorithmic bytes per fine cell of the V-cycle's finest-level kernels (FP32)
+MG_BYTES = {
+    "mg_pre": 8,               # read r; write x (both damped sweeps from x = 0)
+    "mg_resid": 12,            # read x, r; write res
+    "mg_restrict": 4.5,        # read res; write the coarse r.h.s. (1/8 of a cell)
+    "mg_prolong_smooth": 12.5,  # read x, e_c (1/8), r; write the first post-sweep
+    "mg_smooth": 12,           # read it and r; write x (second post-sweep)
+}
+# with the learned smoother the prolongation slot is the residual of x + P e_c:
+# read x, e_c, r; write res and x + P e_c
+MG_BYTES_PROLONG_RESID = 16.5
+# coarse-grid levels streamed like the finest (sizes above 16, halving while even)
+MG_SMALL_N = 16
+
+
+def mg_level_fraction(N):
+    """Cells of all plane-streamed V-cycle levels per fine cell."""
+    f, l = 0.0, N
+    while l > MG_SMALL_N and l % 2 == 0:
+        f += (l / N) ** 3
+        l //= 2
+    return f
+
+
 # FP32 FMA peak: 152 SMs x 128 lanes x 2 FLOP at the 2.07 GHz maximum clock
 # (nominal), and 70.2 TFLOP/s measured with an FMA throughput loop on this GB300
 FP32_PEAK_TFLOPS = 70.2
@@ -81,11 +105,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn"], default="cnn",
-                    help="cnn: mixed-precision flexible CG with the learned preconditioner (trained on the GPU "
-                         "before timing); mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; "
-                         "mg: flexible CG with a multigrid V-cycle (damped Jacobi smoothing); mg_cnn: the V-cycle "
-                         "with the learned network smoothing the finest level")
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn"], default="mg",
+                    help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
+                         "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
+                         "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
+                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge. The learned "
+                         "solvers are always trained and timed in the solve comparison as well")
     ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
@@ -184,12 +209,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     solve_only = args.workload == "solve"
     weights, train_info = None, None
-    if args.solver in ("cnn", "mg_cnn"):
+    if args.solver in ("cnn", "mg_cnn") or not args.no_compare:
         weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
     apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
                   "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
-    if weights is not None:
+    if weights is not None and pc in (pg.PC_CNN, pg.PC_MG_CNN):
         c.cnn_set_weights(weights)
         c.cnn_set_apply(apply_mode)
     phi = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -296,14 +321,44 @@ def run_ours(args):
         avg_ms = prof["ker_ms"]["dot"] / prof["ker_samples"]["dot"]
         rows["dot"] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"]["dot"], "bytes_per_cell": 12,
                        "gbs": 12 * n / (avg_ms * 1e-3) / 1e9}
-    if prof["ker_samples"]["precond"]:
+    is_mg = pc in (pg.PC_MG, pg.PC_MG_CNN)
+    if prof["ker_samples"]["precond"] and not is_mg:
         avg_ms = prof["ker_ms"]["precond"] / prof["ker_samples"]["precond"]
         rows["precond"] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"]["precond"],
                            "flop_per_cell": PRECOND_FLOP_PER_CELL,
                            "tflops": PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12}
+    vcycle = None
+    if is_mg:
+        for k, b in MG_BYTES.items():
+            if not prof["ker_samples"].get(k):
+                continue
+            if k == "mg_prolong_smooth" and pc == pg.PC_MG_CNN:
+                b = MG_BYTES_PROLONG_RESID
+            avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
+            rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "bytes_per_cell": b,
+                       "gbs": b * n / (avg_ms * 1e-3) / 1e9}
+        if prof["ker_samples"]["precond"]:
+            # the whole cycle (all levels, the one-block coarse cycle, and with
+            # the learned smoother its two network applications) for context
+            avg_ms = prof["ker_ms"]["precond"] / prof["ker_samples"]["precond"]
+            frac = mg_level_fraction(N)
+            jac = sum(MG_BYTES.values())
+            # learned smoother on the finest level: network r -> x (8), residual,
+            # restriction, residual of x + P e_c, network res -> x (8), x += t (12)
+            fine = jac if pc == pg.PC_MG else (8 + MG_BYTES["mg_resid"] + MG_BYTES["mg_restrict"] +
+                                               MG_BYTES_PROLONG_RESID + 8 + 12)
+            bpc = fine + jac * (frac - 1.0)
+            vcycle = {"avg_us": round(avg_ms * 1e3, 2), "samples": prof["ker_samples"]["precond"],
+                      "bytes_per_fine_cell": round(bpc, 3), "gbs": round(bpc * n / (avg_ms * 1e-3) / 1e9, 1),
+                      "note": "one V-cycle, every level; bytes of the plane-streamed levels"}
     dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
     kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32", ("dot", 1): "k_fcg_dot",
-             ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64"}
+             ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64",
+             ("mg_pre", 1): "k_mg_pre (finest level)", ("mg_resid", 1): "k_mg_stencil<kResid> (finest level)",
+             ("mg_restrict", 1): "k_mg_restrict2 (finest level)",
+             ("mg_prolong_smooth", 1): ("k_mg_stencil<kSmooth, prolong> (finest level)" if pc == pg.PC_MG else
+                                        "k_mg_stencil<kResid, prolong> (finest level)"),
+             ("mg_smooth", 1): "k_mg_stencil<kSmooth> (finest level)"}
     roof = None
     if dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):
         r = rows[dom]
@@ -347,7 +402,9 @@ def run_ours(args):
         "dtype": ("f64" if prec == pg.PREC_FP64 else
                   "f64 particles/grid; solve f32 vectors + f64 reductions" +
                   ((f"; {'bf16 tensor-core' if args.cnn_apply == 'tc' else args.cnn_apply} "
-                    "9^3 learned preconditioner") if pc == pg.PC_CNN else "")),
+                    "9^3 learned preconditioner") if pc == pg.PC_CNN else "") +
+                  ("; f32 multigrid V-cycle" if pc == pg.PC_MG else "") +
+                  ("; f32 multigrid V-cycle, learned finest-level smoother" if pc == pg.PC_MG_CNN else "")),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
@@ -362,6 +419,7 @@ def run_ours(args):
         "gpu_launches": prof["launches"],
         "roofline": roof,
         "kernels": rows,
+        "vcycle": vcycle,
         "solve": {"iters_mean": statistics.mean(iters), "ms_mean": statistics.mean(solve_ms),
                   "rel_res_max": max(i["rel_res"] for i in infos),
                   "reliable_updates_mean": statistics.mean(i["reliable_updates"] for i in infos)},
@@ -371,10 +429,14 @@ def run_ours(args):
     if train_info is not None:
         out["preconditioner_training"] = train_info
     if not args.no_compare:
-        out["solve_compare"] = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None,
-                                               reps=args.compare_reps, maxit=args.compare_maxit)
+        if weights is not None:
+            c.cnn_set_weights(weights)
+        out["solve_compare"], learned_roof = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None,
+                                                             reps=args.compare_reps, maxit=args.compare_maxit)
+        if learned_roof is not None:
+            out["roofline_learned_preconditioner"] = learned_roof
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters))
+        out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters), args.solver)
     if dist is not None:
         dist.destroy_process_group()
     c.close()
@@ -415,15 +477,26 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
         cases.append(("mixed_fcg_learned", pg.PREC_MIXED, pg.PC_CNN))
         cases.append(("mixed_fcg_learned_fp32", pg.PREC_MIXED, pg.PC_CNN))
         cases.append(("mixed_fcg_multigrid_learned_smoother", pg.PREC_MIXED, pg.PC_MG_CNN))
+    learned_roof = None
     for name, prec, pc in cases:
         if with_cnn:
             c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
         best = None
+        # the tensor-core preconditioner's launches are sampled in the first
+        # learned solve for its roofline
+        sample = name == "mixed_fcg_learned"
+        if sample:
+            c.profile(True)
+            c.profile_read(reset=True)
         for _ in range(max(1, reps)):
             phi = torch.zeros(n, dtype=torch.float64, device="cuda")
             info = c.solve(rho, phi, tol=TOL, maxit=maxit, precision=prec, precond=pc, raise_on_error=False)
             if best is None or info["t_ms"] < best["t_ms"]:
                 best = info
+        if sample:
+            prof = c.profile_read(reset=True)
+            c.profile(False)
+            learned_roof = tc_roofline(prof, n)
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
                      "converged": bool(best["converged"])}
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
@@ -433,31 +506,88 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
         res["speedup_learned_fp32_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned_fp32"]["s"]
         res["speedup_multigrid_learned_vs_fp64"] = (res["fp64_jacobi_pcg"]["s"] /
                                                      res["mixed_fcg_multigrid_learned_smoother"]["s"])
-    return res
+    return res, learned_roof
+
+
+def tc_roofline(prof, n):
+    """Roofline of the tensor-core learned preconditioner (k_apply_k_tc) from
+    its sampled launches: algorithmic FLOP of the composed 9^3 kernel per
+    launch over the average CUDA-event duration, against the measured
+    sustained BF16 peak."""
+    k = prof["ker_samples"]["precond"]
+    if not k:
+        return None
+    avg_ms = prof["ker_ms"]["precond"] / k
+    tf = PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12
+    _, _, pk = peaks()
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    return {"kernel": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16)", "bound": "tensor",
+            "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tf / peak, 4),
+            "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long solve)",
+            "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n,
+            "executed_mma_tflops": round(tf * PRECOND_MMA_FLOP_PER_CELL / PRECOND_FLOP_PER_CELL, 2),
+            "avg_launch_us": round(avg_ms * 1e3, 2), "samples": k}
 
 
 # --------------------------------------------------------------------------- oracle
-def cpu_baseline(N, ppc, iters_per_solve, reference_iters=None, budget_s=20.0):
-    """The CPU oracle (numpy, FP64, as it stands) timed on a bounded sample of
-    the same step: a few CG iterations on the full N^3 grid and the particle
-    kernels on a subset of particles, scaled to one step."""
+def oracle_iteration_seconds(N, solver):
+    """Seconds of one solver iteration of the CPU oracle (as it stands) on an
+    N^3 grid, with the same algorithm as the GPU solver: Jacobi-PCG for the
+    mixed and FP64 solvers (timed on the full grid), flexible CG with the
+    V-cycle or with the network (timed on a smaller grid and scaled by the
+    cell count, the oracle's cost being linear in it)."""
+    from oracle import cnn as ocnn
+    from oracle import mg as omg
     from oracle import pic as opic
     from paper_2605_05469_gb300 import inputs
 
     L = 4.0 * np.pi
+    Ns = min(N, {"mg": 128, "cnn": 32, "mg_cnn": 32}.get(solver, N))
+    h = L / Ns
+    b = inputs.landau_noise_rhs(Ns, 1)
+    x0 = np.zeros(Ns ** 3)
+    if solver in ("mg", "cnn", "mg_cnn"):
+        ws = ocnn.init_weights(0)
+
+        def net(q):
+            return h * h * ocnn.forward(q.reshape(Ns, Ns, Ns), ws)[0].reshape(-1)
+        prec = {"mg": lambda r: omg.vcycle(r, Ns, h),
+                "cnn": lambda r: ocnn.precondition(r, ws, Ns, h),
+                "mg_cnn": lambda r: omg.vcycle(r, Ns, h, smoother=net)}[solver]
+        k_it = 1
+        t0 = time.perf_counter()
+        ocnn.fcg(b, x0, Ns, h, 0.0, k_it, prec)   # k_it iterations + the initial preconditioning
+        dt = (time.perf_counter() - t0) / (k_it + 1)
+        what = {"mg": "flexible-CG iterations with the multigrid V-cycle",
+                "cnn": "flexible-CG iterations with the network preconditioner",
+                "mg_cnn": "flexible-CG iterations with the V-cycle and network smoother"}[solver]
+    else:
+        k_it = 3
+        t0 = time.perf_counter()
+        opic.pcg_jacobi(b, x0, Ns, h, 0.0, k_it)   # k_it iterations + the initial residual
+        dt = (time.perf_counter() - t0) / (k_it + 1)
+        what = "Jacobi-PCG iterations"
+    scale = (N / Ns) ** 3
+    desc = f"{k_it + 1} {what} on a {Ns}^3 grid" + (f" (scaled by cells x{scale:g})" if Ns != N else "")
+    return dt * scale, desc
+
+
+def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", reference_iters=None, budget_s=20.0):
+    """The CPU oracle (numpy, FP64, as it stands) timed on a bounded sample of
+    the same step: solver iterations of the same algorithm as the GPU solve
+    and the particle kernels on a subset of particles, scaled to one step."""
+    from oracle import pic as opic
+
+    L = 4.0 * np.pi
     h = L / N
     n = N ** 3
-    b = inputs.landau_noise_rhs(N, 1)
-    t0 = time.perf_counter()
-    k_it = 3
-    opic.pcg_jacobi(b, np.zeros(n), N, h, 0.0, k_it)   # k_it iterations + the initial residual
-    t_cg = (time.perf_counter() - t0) / (k_it + 1)
+    t_cg, cg_desc = oracle_iteration_seconds(N, solver)
     it = reference_iters if reference_iters else iters_per_solve
     if ppc == 0:
         step_s = t_cg * it
         return {"value": 1.0 / step_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
                 "host_cpus": os.cpu_count(),
-                "sample": f"{k_it} CG iterations on the full {N}^3 grid, scaled by {it:.0f} iterations/solve"}
+                "sample": f"{cg_desc}, scaled by {it:.0f} iterations/solve"}
     ns = min(ppc * n, 1 << 21)
     rng = np.random.default_rng(3)
     pos = rng.random((3, ns)) * L
@@ -474,7 +604,7 @@ def cpu_baseline(N, ppc, iters_per_solve, reference_iters=None, budget_s=20.0):
     step_s = t_cg * it + t_part + t_en
     return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
             "host_cpus": os.cpu_count(),
-            "sample": f"{k_it} CG iterations on the full {N}^3 grid (scaled by {it:.0f} iterations/solve), "
+            "sample": f"{cg_desc} (scaled by {it:.0f} iterations/solve), "
                       f"deposit+gather+push of {ns} of {ppc * n} particles (scaled linearly), one field energy"}
 
 

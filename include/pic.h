@@ -74,8 +74,9 @@ typedef struct {
   double reliable_delta; /* MIXED: recompute the FP64 residual when the FP32 residual
                             norm fell by this factor since the last recomputation;
                             0 selects the default: 0.1 with Jacobi, 0.03 with
-                            the learned preconditioner */
-  int check_every;       /* iterations between host reads of the convergence flag; 0 = default */
+                            the learned preconditioner, 0.003 with the V-cycle */
+  int check_every;       /* iterations between host reads of the convergence flag;
+                            0 = default (1 with the V-cycle, 32 up to 64^3, else 8) */
 } pic_solve_opts;
 
 typedef struct {
@@ -257,14 +258,22 @@ int pic_cnn_conv_raw(pic_ctx *c, int which, const void *in, float *out, int B, i
  * launches. Read and optionally reset the totals with pic_profile_read
  * (synchronises the stream). */
 enum { PIC_PHASE_DEPOSIT = 0, PIC_PHASE_SOLVE = 1, PIC_PHASE_PUSH = 2, PIC_PHASE_ENERGY = 3, PIC_NPHASE = 4 };
-enum { PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_KER_PRECOND = 2, PIC_KER_DOT = 3, PIC_NKER = 4 };
+/* Sampled kernels: the CG direction and update kernels, the whole
+ * preconditioner application (learned kernel or V-cycle), flexible CG's dot
+ * products, and the finest-level kernels of the multigrid V-cycle (two-sweep
+ * pre-smoothing, residual, restriction, prolongation + first post-sweep,
+ * second post-sweep; with the learned smoother the residual after the
+ * prolongation counts as the prolongation slot). */
+enum {
+  PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_KER_PRECOND = 2, PIC_KER_DOT = 3,
+  PIC_KER_MG_PRE = 4, PIC_KER_MG_RESID = 5, PIC_KER_MG_RESTRICT = 6, PIC_KER_MG_PROLONG_SMOOTH = 7,
+  PIC_KER_MG_SMOOTH = 8, PIC_NKER = 9
+};
 typedef struct {
   int64_t launches;           /* kernels launched by the context (counted always) */
   int phase_calls[PIC_NPHASE];
   double phase_ms[PIC_NPHASE];
-  int ker_samples[PIC_NKER];  /* sampled launches of the CG direction and update
-                                 kernels, of the learned preconditioner's
-                                 application and of flexible CG's dot products */
+  int ker_samples[PIC_NKER];  /* sampled launches of each PIC_KER_* kernel */
   double ker_ms[PIC_NKER];    /* their total device time */
   int ker_precision[PIC_NKER]; /* PIC_PREC_* of the sampled launches (last solve) */
 } pic_profile_stats;

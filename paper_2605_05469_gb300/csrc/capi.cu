@@ -296,9 +296,9 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   if (uses_net && !cnn_ready(c)) return PIC_ESTATE;
   if (pc == PIC_PC_CNN && c->N % 16 != 0) return PIC_EINVAL;
   // z = M r for the chosen preconditioner (enqueued on the context stream)
-  auto precond = [&](const float* r, float* z) -> int {
+  auto precond = [&](const float* r, float* z, bool sample) -> int {
     if (pc == PIC_PC_CNN) return cnn_apply(c, r, z, &c->sc->rr, c->n);
-    return mg_apply(c, r, z, pc == PIC_PC_MG_CNN, &c->sc->done);
+    return mg_apply(c, r, z, pc == PIC_PC_MG_CNN, &c->sc->done, sample);
   };
   if (!w.xm[0]) {
     if ((e = dalloc(&w.xm[0], c->n)) || (e = dalloc(&w.xm[1], c->n)) || (e = dalloc(&w.x32, c->n)) ||
@@ -332,7 +332,7 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   launch(c, k_reliable, gr.blocks, tr, smem_rel, w.xm[0], w.xm[1], (const float*)w.x32, (const double*)w.b, w.r32,
          c->sc, c->partials, c->counter, c->err, gr, 0);
   int zc = 0;
-  if ((e = precond(w.r32, w.z32[zc]))) return e;
+  if ((e = precond(w.r32, w.z32[zc], false))) return e;
   launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
          c->partials, c->counter, 1, 0);
   launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
@@ -384,7 +384,7 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
       zc ^= 1;
       slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
-      const int ce = precond(w.r32, w.z32[zc]);
+      const int ce = precond(w.r32, w.z32[zc], sample);
       if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
       if (ce && !inner_err) inner_err = ce;
       slot = sample ? c->ker[PIC_KER_DOT].begin(c->stream) : -1;
@@ -628,20 +628,23 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   if (o) opts = *o;
   if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_MG_CNN) return PIC_EINVAL;
   // status-check cadence: the multigrid solve converges in about ten
-  // iterations, so its batches are short (each batch launched past
-  // convergence still costs the launches of its kernels)
+  // iterations, so its batches are single iterations (each iteration
+  // launched past convergence still costs the launches of its kernels)
   const bool mgpc = opts.precond == PIC_PC_MG || opts.precond == PIC_PC_MG_CNN;
-  int m = opts.check_every > 0 ? opts.check_every : (mgpc ? 2 : (c->N <= 64 ? 32 : 8));
+  int m = opts.check_every > 0 ? opts.check_every : (mgpc ? 1 : (c->N <= 64 ? 32 : 8));
   if (opts.precond != PIC_PC_JACOBI && opts.precision != PIC_PREC_MIXED) return PIC_EINVAL;
   PhaseScope ps(c, PIC_PHASE_SOLVE);
   if (opts.precision == PIC_PREC_FP64) return solve_fp64(c, rho, phi, tol, maxit, m, info);
   if (opts.precision == PIC_PREC_MIXED) {
     // reliable-update trigger: a recomputation of the FP64 residual each time
     // (r, r) falls by delta^2; measured on GB300 (256^3, 512^3 Landau
-    // deposits), 0.1 is best for Jacobi-CG (smaller values cost iterations)
-    // and 0.03 for flexible CG with the learned preconditioner (fewer FP64
-    // recomputations at the same iteration count)
-    const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta : (opts.precond == PIC_PC_JACOBI ? 0.1 : 0.03);
+    // deposits), 0.1 is best for Jacobi-CG (smaller values cost iterations),
+    // 0.03 for flexible CG with the learned preconditioner (fewer FP64
+    // recomputations at the same iteration count) and 0.003 with the V-cycle
+    // (its residual falls ~10x an iteration; each FP64 recomputation costs
+    // about half a V-cycle)
+    const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta
+                                                   : (opts.precond == PIC_PC_JACOBI ? 0.1 : (mgpc ? 0.003 : 0.03));
     if (!(delta < 1.0)) return PIC_EINVAL;
     if (opts.precond != PIC_PC_JACOBI) return solve_fcg(c, rho, phi, tol, maxit, m, delta, opts.precond, info);
     return solve_mixed(c, rho, phi, tol, maxit, m, delta, info);

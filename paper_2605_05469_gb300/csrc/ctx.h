@@ -103,7 +103,7 @@ struct pic_ctx {
   bool prof_on = false;
   pic::EventPool* phase = nullptr;  // [PIC_NPHASE]
   pic::EventPool* ker = nullptr;    // [PIC_NKER]
-  int ker_prec[PIC_NKER] = {0, 0, 0, 0};
+  int ker_prec[PIC_NKER] = {};
   // learned preconditioner (weights, activations, optimiser state)
   pic::CnnState* cnn = nullptr;
   int cnn_apply_mode = 0;  // PIC_CNN_APPLY_*

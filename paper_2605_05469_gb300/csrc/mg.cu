@@ -86,8 +86,11 @@ int ensure_state(pic_ctx* c) {
     MgLevel& L = s->lev[l];
     L.streamed = L.N % 4 == 0;
     if (!L.streamed) continue;
+    // coarse levels are latency-bound: more blocks with fewer planes each
+    const int min_planes = L.N >= 256 ? 4 : (L.N >= 128 ? 2 : 1);
     for (int k = 0; k < kNumMgKer && !e; ++k) {
-      e = slab_geometry<float, float, float, 1>(c, L.N, (const void*)kers[k], &L.geo[k], &L.smem[k]);
+      e = slab_geometry<float, float, float, 1>(c, L.N, (const void*)kers[k], &L.geo[k], &L.smem[k], false,
+                                                min_planes);
       if (L.smem[k] > smax[k]) smax[k] = L.smem[k];
     }
   }
@@ -121,7 +124,7 @@ int ensure_state(pic_ctx* c) {
 
 }  // namespace
 
-int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done) {
+int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done, bool sample) {
   int e;
   if ((e = ensure_state(c))) return e;
   MgState* s = c->mg;
@@ -136,10 +139,15 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
   if (learned && B == 0) return PIC_EINVAL;
   auto xl = [&](int l) { return l == 0 ? z : s->lev[l].x; };
   auto rl = [&](int l) { return l == 0 ? r : (const float*)s->lev[l].r; };
-  // plane-streamed kernel k of level L
-  auto slab = [&](const MgLevel& L, MgKer k, auto kernel, auto... args) {
+  // plane-streamed kernel k of level L; the finest level's launches are
+  // timed into event pool `pool` when sampling
+  sample = sample && c->prof_on;
+  auto slab = [&](const MgLevel& L, MgKer k, int pool, auto kernel, auto... args) {
     const StreamGeo& g = L.geo[k];
+    const bool t = sample && &L == &s->lev[0];
+    const int slot = t ? c->ker[pool].begin(c->stream) : -1;
     launch(c, kernel, g.blocks, round32(g.threads), L.smem[k], args..., c->err, g, done);
+    if (t) c->ker[pool].end(slot, c->stream);
   };
   const float* nul = nullptr;
   float* nulw = nullptr;
@@ -151,17 +159,20 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     if (l == 0 && learned) {
       if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
     } else if (L.streamed) {
-      slab(L, kPre, mg::k_mg_pre, rl(l), xl(l));
+      slab(L, kPre, PIC_KER_MG_PRE, mg::k_mg_pre, rl(l), xl(l));
     } else {
       launch(c, mg::k_mg_jacobi, g, 256, 0, nul, rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
     }
     if (L.streamed) {
-      slab(L, kResid, mg::k_mg_stencil<mg::kResid, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
+      slab(L, kResid, PIC_KER_MG_RESID, mg::k_mg_stencil<mg::kResid, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
       const int Nc = L.N / 2;
       const unsigned per_plane = (unsigned)(Nc / 2) * (unsigned)Nc;
       const unsigned bx = (per_plane + 255) / 256;
+      const bool t = sample && l == 0;
+      const int slot = t ? c->ker[PIC_KER_MG_RESTRICT].begin(c->stream) : -1;
       launch(c, mg::k_mg_restrict2, dim3(bx, Nc), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
+      if (t) c->ker[PIC_KER_MG_RESTRICT].end(slot, c->stream);
     } else {
       launch(c, mg::k_mg_residual, g, 256, 0, (const float*)xl(l), rl(l), L.res, L.N, done);
       launch(c, mg::k_mg_restrict, grid_for(c, n / 8), 256, 0, (const float*)L.res, s->lev[l + 1].r, L.N, done);
@@ -178,7 +189,7 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     if (l == 0 && learned) {
       // x' = x + P e_c (into t), res = r - A^ x', x = x' + K res
       if (L.streamed) {
-        slab(L, kResidProlong, mg::k_mg_stencil<mg::kResid, true>, (const float*)xl(0), rl(0), L.res, L.t, ec);
+        slab(L, kResidProlong, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_stencil<mg::kResid, true>, (const float*)xl(0), rl(0), L.res, L.t, ec);
       } else {
         launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(0), ec, L.N / 2, done);
         launch(c, mg::k_mg_copy, grid_for(c, n), 256, 0, (const float*)xl(0), L.t, n, done);
@@ -187,8 +198,8 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
       if ((e = cnn_apply(c, L.res, xl(0), nullptr, n))) return e;
       launch(c, mg::k_mg_add, grid_for(c, n / 4), 256, 0, xl(0), (const float*)L.t, n / 4, done);
     } else if (L.streamed) {
-      slab(L, kSmoothProlong, mg::k_mg_stencil<mg::kSmooth, true>, (const float*)xl(l), rl(l), L.t, nulw, ec);
-      slab(L, kSmooth, mg::k_mg_stencil<mg::kSmooth, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
+      slab(L, kSmoothProlong, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_stencil<mg::kSmooth, true>, (const float*)xl(l), rl(l), L.t, nulw, ec);
+      slab(L, kSmooth, PIC_KER_MG_SMOOTH, mg::k_mg_stencil<mg::kSmooth, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
     } else {
       launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), ec, L.N / 2, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);

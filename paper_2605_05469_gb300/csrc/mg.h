@@ -14,6 +14,8 @@ void mg_state_free(MgState* s);
 // stream; learned = the network's composed kernel smooths the finest level.
 // done (device flag, may be null): when set, the launched kernels return at
 // once (iterations launched past convergence).
-int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done);
+// sample: time the finest level's kernels with the PIC_KER_MG_* event pools
+// (profiling on).
+int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done, bool sample = false);
 
 }  // namespace pic

@@ -309,6 +309,40 @@ struct SmallLevels {
   int total;      // elements per region
 };
 
+// The cells c = t, t + nt, t + 2 nt, ... of an N^3 grid (t = threadIdx.x)
+// with their coordinates (i, j, k), advanced by additions with carries
+// instead of three divisions per cell.
+struct CellWalk {
+  int c, i, j, k, di, dj, dk, n, N, nt;
+  __device__ __forceinline__ CellWalk(int N_, int nt_) : N(N_), nt(nt_) {
+    n = N * N * N;
+    c = threadIdx.x;
+    i = c % N;
+    j = (c / N) % N;
+    k = c / (N * N);
+    di = nt % N;
+    dj = (nt / N) % N;
+    dk = nt / (N * N);
+  }
+  __device__ __forceinline__ bool ok() const { return c < n; }
+  __device__ __forceinline__ void next() {
+    c += nt;
+    i += di;
+    int carry = 0;
+    if (i >= N) {
+      i -= N;
+      carry = 1;
+    }
+    j += dj + carry;
+    carry = 0;
+    if (j >= N) {
+      j -= N;
+      carry = 1;
+    }
+    k += dk + carry;
+  }
+};
+
 // One damped Jacobi sweep out = x + w (r - A^ x) (x_zero: x = 0) over the
 // threads [0, nt), then a barrier of those threads (the block, or warp 0).
 template <bool WARP>
@@ -317,13 +351,11 @@ __device__ __forceinline__ void sm_sweep(const float* x, const float* r, float* 
   const float w = kOmega / 6.0f;
   const int nt = WARP ? 32 : (int)blockDim.x;
   if (!WARP || threadIdx.x < 32) {
-    for (int c = threadIdx.x; c < n; c += nt) {
-      if (x_zero) {
-        out[c] = w * r[c];
-      } else {
-        const int i = c % N, j = (c / N) % N, k = c / (N * N);
-        out[c] = x[c] + w * (r[c] - apply_hat(x, N, i, j, k));
-      }
+    if (x_zero) {
+      for (int c = threadIdx.x; c < n; c += nt) out[c] = w * r[c];
+    } else {
+      for (CellWalk q(N, nt); q.ok(); q.next())
+        out[q.c] = x[q.c] + w * (r[q.c] - apply_hat(x, N, q.i, q.j, q.k));
     }
   }
   if (WARP) __syncwarp();
@@ -362,15 +394,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restr
     const int N = S.N[l], n = N * N * N;
     float *x = X + S.off[l], *r = R + S.off[l], *t = T + S.off[l];
     sm_smooth<false>(x, r, t, N, nu, true);
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      const int i = c % N, j = (c / N) % N, k = c / (N * N);
-      t[c] = r[c] - apply_hat(x, N, i, j, k);
-    }
+    for (CellWalk q(N, blockDim.x); q.ok(); q.next()) t[q.c] = r[q.c] - apply_hat(x, N, q.i, q.j, q.k);
     __syncthreads();
-    const int Nc = S.N[l + 1], nc = Nc * Nc * Nc;
+    const int Nc = S.N[l + 1];
     float* rc = R + S.off[l + 1];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const int I = c % Nc, J = (c / Nc) % Nc, K = c / (Nc * Nc);
+    for (CellWalk q(Nc, blockDim.x); q.ok(); q.next()) {
+      const int c = q.c, I = q.i, J = q.j, K = q.k;
       float acc = 0.f;
       for (int oz = -1; oz <= 1; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
@@ -398,8 +427,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_mg_small(const float* __restr
     const int N = S.N[l], n = N * N * N, Nc = S.N[l + 1];
     float *x = X + S.off[l], *r = R + S.off[l], *t = T + S.off[l];
     const float* ec = X + S.off[l + 1];
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      const int i = c % N, j = (c / N) % N, k = c / (N * N);
+    for (CellWalk q(N, blockDim.x); q.ok(); q.next()) {
+      const int c = q.c, i = q.i, j = q.j, k = q.k;
       const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
       const int I1 = (i & 1) ? wrapi(I0 + 1, Nc) : I0, J1 = (j & 1) ? wrapi(J0 + 1, Nc) : J0,
                 K1 = (k & 1) ? wrapi(K0 + 1, Nc) : K0;

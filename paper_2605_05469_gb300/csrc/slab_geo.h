@@ -18,10 +18,12 @@ constexpr size_t kSmemMax = 226 * 1024;
 // budget: the halo rows re-read per plane are (TY + 2) / TY of the slab. If
 // none fits the budget, the tallest that fits the SM. Then as many raw stages
 // as the budget allows (at least three, at most kMaxStages). The persistent
-// grid is the resident blocks of `kernel`. Sets the kernel's dynamic
-// shared-memory limit to the size returned in *smem.
+// grid is the resident blocks of `kernel`, but at least `min_planes` planes
+// per block. Sets the kernel's dynamic shared-memory limit to the size
+// returned in *smem.
 template <typename TP, typename A, typename B, int NV, typename K>
-int slab_geometry(pic_ctx* c, int N, K kernel, StreamGeo* out, size_t* smem, bool tall = false) {
+int slab_geometry(pic_ctx* c, int N, K kernel, StreamGeo* out, size_t* smem, bool tall = false,
+                  int min_planes = 4) {
   if (N < 4 || N % 4) return PIC_EINVAL;
   const int cap = tall ? kStreamTall : kStreamSmall;
   const size_t budget = tall ? kSmemTall : (sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32);
@@ -52,7 +54,7 @@ int slab_geometry(pic_ctx* c, int N, K kernel, StreamGeo* out, size_t* smem, boo
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, round32(g.threads), *smem));
   if (per_sm < 1) return PIC_EINVAL;
-  set_stream_blocks(g, per_sm * c->sms);
+  set_stream_blocks(g, per_sm * c->sms, min_planes);
   *out = g;
   return PIC_OK;
 }

@@ -41,9 +41,10 @@ inline StreamGeo make_stream_geo(int N, int S, int TY) {
   return g;
 }
 
-// Persistent grid: `slots` resident blocks, but at least 4 planes per block.
-inline void set_stream_blocks(StreamGeo& g, int slots) {
-  long b = g.total / 4;
+// Persistent grid: `slots` resident blocks, but at least `min_planes` planes
+// per block (each block re-reads two halo planes per run).
+inline void set_stream_blocks(StreamGeo& g, int slots, int min_planes = 4) {
+  long b = g.total / min_planes;
   if (b < 1) b = 1;
   g.blocks = (int)(slots < b ? slots : b);
 }
