@@ -62,8 +62,9 @@ typedef struct {
 enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 };
 /* Preconditioner: JACOBI (Sec. 3.2); the learned CNN inside flexible CG
  * (requires PIC_PREC_MIXED and weights set by pic_cnn_set_weights); a
- * geometric multigrid V-cycle inside flexible CG (the paper's named
- * follow-on, Sec. 6; requires PIC_PREC_MIXED): MG smooths every level with
+ * geometric multigrid V-cycle inside flexible CG (beyond the paper, whose
+ * conclusion, Sec. 5, sets PCG beside the multigrid solvers of a cited
+ * comparison; requires PIC_PREC_MIXED): MG smooths every level with
  * damped Jacobi, MG_CNN smooths the finest level with the learned network
  * (requires weights). See pic_mg_apply for the cycle. */
 enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1, PIC_PC_MG = 2, PIC_PC_MG_CNN = 3 };

@@ -2,8 +2,9 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-The paper names multigrid as the follow-on of its PCG solver (Sec. 6); it
-prints no algorithm for it. This module defines the V-cycle the GPU library
+The paper's conclusion (Sec. 5) sets its PCG solver beside the multigrid
+solvers of a cited comparison and names better preconditioning as future
+work (Secs. 4.3, 5); it prints no multigrid algorithm. This module defines the V-cycle the GPU library
 offers, from the textbook geometric multigrid for the periodic 7-point
 Laplacian (Trottenberg, Oosterlee & Schueller, "Multigrid", 2001, ch. 2-4):
 

@@ -1,5 +1,7 @@
 // Geometric multigrid V-cycle, the preconditioner of flexible CG beyond the
-// paper's Jacobi-PCG (the paper names multigrid as the follow-on, Sec. 6).
+// paper's Jacobi-PCG (its conclusion, Sec. 5, sets PCG beside the multigrid
+// solvers of a cited comparison; better preconditioning is its named future
+// work, Secs. 4.3 and 5).
 //
 // All levels work in the solver's scaled units: on level l (N_l^3 nodes,
 // spacing h_l = 2^l h) the system is A^ x = r^ with A^ = 6 I - (sum of the
