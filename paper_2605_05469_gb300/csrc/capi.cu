@@ -26,6 +26,7 @@ void free_particles(pic_ctx* c) {
   dfree(c->offsets);
   dfree(c->chunks);
   dfree(c->E);
+  dfree(c->dep);
   c->np = 0;
 }
 
@@ -445,6 +446,12 @@ int ensure_E(pic_ctx* c) {
   return dalloc(&c->E, 3 * c->n);
 }
 
+// A double-float constant (hi, lo) for the particle kernels.
+float2 df_const(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, (float)(x - (double)hi));
+}
+
 int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift) {
   int e;
   if ((e = ensure_E(c))) return e;
@@ -452,8 +459,9 @@ int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift
   launch(c, k_gradient, sb, 256, 0, phi, c->E, c->E + c->n, c->E + 2 * c->n, c->grid);
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
-  launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, c->E, c->E + c->n, c->E + 2 * c->n, c->grid,
-                                               -kick, dt, drift, c->keys, c->ranks, c->counts);
+  launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
+         (const float2*)(c->E + c->n), (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
+         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts);
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -609,12 +617,15 @@ int pic_deposit(pic_ctx* c, double* rho) {
     c->sorted = true;
     c->keys_valid = false;
   }
-  const int sb = streaming_blocks(c);
-  launch(c, k_fill, sb, 256, 0, rho, c->n, 1.0);
+  int e;
+  if (!c->dep && (e = dalloc(&c->dep, 8 * c->n))) return e;
   const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
   const unsigned cblocks = (unsigned)((c->n + 255) / 256);
-  launch(c, k_deposit_cells, cblocks, 256, 0, (const PRec*)c->prec[c->cur], c->offsets,
-                                                  rho, c->grid, qscale);
+  launch(c, k_deposit_cells, cblocks, 256, 0, (const PRec*)c->prec[c->cur], (const uint32_t*)c->offsets, c->dep,
+         c->n);
+  const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
+  launch(c, k_deposit_nodes, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)c->dep, rho, c->N,
+         qscale);
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -701,14 +712,14 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   if (half_step) *half_step = c->half_step ? 1 : 0;
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   if (on_device) {
-    launch(c, k_unsort, blocks, 256, 0, pptrs(c, c->cur), c->np, out);
+    launch(c, k_unsort, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, c->grid, out);
     CK(cudaGetLastError());
     return PIC_OK;
   }
   double* tmp = nullptr;
   int e;
   if ((e = dalloc(&tmp, 6 * c->np))) return e;
-  launch(c, k_unsort, blocks, 256, 0, pptrs(c, c->cur), c->np, tmp);
+  launch(c, k_unsort, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, c->grid, tmp);
   cudaError_t ce = cudaMemcpyAsync(out, tmp, 6 * c->np * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   cudaFree(tmp);

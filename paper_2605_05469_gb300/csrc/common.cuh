@@ -51,14 +51,19 @@ struct Scalars {
                     // z and the direction's dots are recomputed from it
 };
 
-// One particle: FP64 position and velocity, its 32-bit id (the index it was
-// sampled with) and the key of the cell that contains its position, padded to
-// 64 bytes so that a particle moved by the sort fills exactly two 32-byte
-// sectors and the kernels read it with four 16-byte loads.
+// One particle, 64 bytes, so that a particle moved by the sort fills exactly
+// two 32-byte sectors and the kernels read it with four 16-byte loads:
+//   fx, fy, fz  position inside its cell in units of 2^-64 h (exact fixed
+//               point: cell changes and the periodic wrap are integer adds);
+//   vx, vy, vz  velocity as double-float pairs (hi + lo, ~48-bit significand;
+//               the push runs on the FP32 pipes);
+//   id          the index the particle was sampled with;
+//   key         its cell ix + N (iy + N iz), and ix, iy, iz themselves.
 struct __align__(64) PRec {
-  double x, y, z, vx, vy, vz;
+  uint64_t fx, fy, fz;
+  float2 vx, vy, vz;
   uint32_t id, key;
-  double pad;
+  uint16_t ix, iy, iz, pad;
 };
 static_assert(sizeof(PRec) == 64, "particle record");
 

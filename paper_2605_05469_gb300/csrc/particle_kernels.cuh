@@ -2,15 +2,20 @@
 // sort by cell, CIC scatter (Eq. 2), E = -grad phi, CIC gather and leapfrog
 // push (Eqs. 3-4), field energy (Fig. 2).
 //
-// Particles are 64-byte FP64 records (PRec). Each step they are counting-sorted
-// by cell: the push kernel computes every particle's new cell key and takes
-// its rank inside the cell with one integer atomic; a scan turns the cell
-// counts into offsets and a scatter moves the particles. The deposit then
-// runs one thread per cell over that cell's contiguous particles, sums the 8
-// corner weights in registers and issues 8 FP64 reductions per cell instead of
-// 8 per particle.
+// Particles are 64-byte records (PRec): the position as the cell and a 64-bit
+// fixed-point offset inside it, the velocity as double-float pairs. All
+// per-particle arithmetic runs in double-float on the FP32 pipes (GB300's
+// FP64 rate is 1/58 of its FP32 rate); the grid-side quantities keep FP64
+// (phi, rho) and the conversions happen once per node. Each step the particles
+// are counting-sorted by cell: the push computes every particle's new cell and
+// its rank inside the cell (one integer atomic per group of equal cells in a
+// warp); a scan turns the cell counts into offsets and a scatter moves the
+// records. The deposit then runs one thread per cell over the cell's
+// contiguous particles and writes the cell's 8 corner charges, and one thread
+// per node adds the 8 charges that reach it (no atomics).
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace pic {
 
@@ -60,19 +65,81 @@ __device__ __forceinline__ int cell_of(double x, const Grid& g) {
   return i > g.N - 1 ? g.N - 1 : i;
 }
 
-__device__ __forceinline__ uint32_t key_of(double x, double y, double z, const Grid& g) {
-  return (uint32_t)cell_of(x, g) + (uint32_t)g.N * ((uint32_t)cell_of(y, g) + (uint32_t)g.N * (uint32_t)cell_of(z, g));
+__device__ __forceinline__ uint32_t cell_key(int ix, int iy, int iz, int N) {
+  return (uint32_t)ix + (uint32_t)N * ((uint32_t)iy + (uint32_t)N * (uint32_t)iz);
 }
 
-__device__ __forceinline__ void rec_pos(const PRec* P, uint64_t p, double& x, double& y, double& z) {
-  const double2* r = reinterpret_cast<const double2*>(P + p);
-  const double2 a = __ldg(r), b = __ldg(r + 1);
-  x = a.x;
-  y = a.y;
-  z = b.x;
+// A position coordinate x in [0, L] as its cell and 64-bit offset (FP64 in,
+// for the initial condition and loads only). A value that rounds to the top of
+// the box wraps to 0.
+__device__ __forceinline__ void to_cell_offset(double x, const Grid& g, int& i, uint64_t& f) {
+  const double u = x * g.inv_h;
+  i = cell_of(x, g);
+  double r = u - (double)i;
+  if (!(r < 1.0)) {  // x == L after rounding (or the clamp at N - 1)
+    i = 0;
+    r = 0.0;
+  }
+  if (r < 0.0) r = 0.0;
+  f = __double2ull_rn(r * 18446744073709551616.0);  // r 2^64 < 2^64
 }
 
-// S0: sample particle p of the Landau initial condition, and count its cell.
+// The coordinate (i + f 2^-64) h in FP64 (outputs only).
+__device__ __forceinline__ double from_cell_offset(int i, uint64_t f, const Grid& g) {
+  return ((double)i + (double)(f >> 11) * (1.0 / 9007199254740992.0)) * g.h;
+}
+
+// The offset f 2^-64 in [0, 1) as a double-float: its top 24 bits and the next
+// 24 (each exactly an FP32 value), normalised; the 16 lowest bits are dropped
+// (2^-48 of a cell).
+__device__ __forceinline__ df frac_df(uint64_t f) {
+  const float hi = __uint2float_rn((uint32_t)(f >> 40)) * 0x1p-24f;
+  const float lo = __uint2float_rn((uint32_t)(f >> 16) & 0xFFFFFFu) * 0x1p-48f;
+  return fast_two_sum(hi, lo);  // hi == 0 or hi >= 2^-24 > lo
+}
+
+// 1 - f 2^-64 as a double-float (2^64 - f in the same fixed point; f == 0 is 1).
+__device__ __forceinline__ df one_minus_frac_df(uint64_t f) {
+  if (f == 0) return {1.0f, 0.0f};
+  return frac_df(0ull - f);
+}
+
+// Moves one coordinate by d cells (double-float): the offset takes the
+// fraction of d in exact 64-bit arithmetic, the carries and the integer part
+// of d move the cell index, which wraps periodically. Needs |d| < 2^20.
+// The leading word splits as n + r with n = trunc(d.hi): r = d.hi - n is then
+// exact (its bits are a subset of d.hi's), which d.hi - floor(d.hi) is not
+// for negative d.hi (-0.3 + 1 needs one more bit than 0.7 has).
+__device__ __forceinline__ void move_coord(uint64_t& f, int& i, df d, int N) {
+  const float n = truncf(d.hi);
+  const float r = __fsub_rn(d.hi, n);  // exact, |r| < 1, sign of d.hi
+  uint64_t f1;
+  int carry;
+  if (r >= 0.0f) {
+    f1 = f + __float2ull_rn(__fmul_rn(r, 0x1p64f));
+    carry = f1 < f ? 1 : 0;
+  } else {
+    f1 = f - __float2ull_rn(__fmul_rn(-r, 0x1p64f));
+    carry = f1 > f ? -1 : 0;
+  }
+  const int64_t B = __float2ll_rn(__fmul_rn(d.lo, 0x1p64f));
+  const uint64_t f2 = f1 + (uint64_t)B;
+  if (B >= 0) carry += f2 < f1 ? 1 : 0;
+  else carry -= f2 > f1 ? 1 : 0;
+  f = f2;
+  int t = i + (int)n + carry;
+  if (t < 0 || t >= N) {
+    t %= N;
+    if (t < 0) t += N;
+  }
+  i = t;
+}
+
+// A double-float constant passed from the host as (hi, lo).
+__device__ __forceinline__ df dfc(float2 v) { return {v.x, v.y}; }
+
+// S0: sample particle p of the Landau initial condition (FP64), store it as a
+// record, and count its cell.
 __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alpha, double k, Grid g,
                                  uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,24 +161,31 @@ __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alp
   double s1, c1, s2, c2;
   sincos(two_pi * u[5], &s1, &c1);
   sincos(two_pi * u[7], &s2, &c2);
-  double2* rec = reinterpret_cast<double2*>(P + p);
-  rec[0] = make_double2(x, y);
-  rec[1] = make_double2(z, r1 * c1);
-  rec[2] = make_double2(r1 * s1, r2 * c2);
-  const uint32_t kk = key_of(x, y, z, g);
-  reinterpret_cast<uint4*>(rec)[3] = make_uint4((uint32_t)p, kk, 0u, 0u);
-  keys[p] = kk;
-  ranks[p] = atomicAdd(&counts[kk], 1u);
+  PRec rec;
+  int ix, iy, iz;
+  to_cell_offset(x, g, ix, rec.fx);
+  to_cell_offset(y, g, iy, rec.fy);
+  to_cell_offset(z, g, iz, rec.fz);
+  rec.vx = df_pack(df_of_double(r1 * c1));
+  rec.vy = df_pack(df_of_double(r1 * s1));
+  rec.vz = df_pack(df_of_double(r2 * c2));
+  rec.id = (uint32_t)p;
+  rec.key = cell_key(ix, iy, iz, g.N);
+  rec.ix = (uint16_t)ix;
+  rec.iy = (uint16_t)iy;
+  rec.iz = (uint16_t)iz;
+  rec.pad = 0;
+  P[p] = rec;
+  keys[p] = rec.key;
+  ranks[p] = atomicAdd(&counts[rec.key], 1u);
 }
 
-// Cell keys and in-cell ranks of the current particles (after an external load).
+// Cell keys and in-cell ranks of the current particles.
 __global__ void k_count_keys(PRec* P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
                              uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  double x, y, z;
-  rec_pos(P, p, x, y, z);
-  const uint32_t kk = key_of(x, y, z, g);
+  const uint32_t kk = cell_key(P[p].ix, P[p].iy, P[p].iz, g.N);
   P[p].key = kk;
   keys[p] = kk;
   ranks[p] = atomicAdd(&counts[kk], 1u);
@@ -244,68 +318,78 @@ __global__ void k_fill(double* a, size_t n, double v) {
 }
 
 // ---------------------------------------------------------------------------
-// S2: CIC scatter from cell-sorted particles, one thread per cell.
-// rho (pre-filled with the +1 background) += (q_p / h^3) sum_p W.
+// S2: CIC scatter from cell-sorted particles (Eq. 2), in two passes.
+// Cells: one thread per cell sums, over the cell's particles, the corner
+// weights prod_d (f_d or 1 - f_d) of its 8 corners from the moments of the
+// offsets f in [0, 1)^3 (count, f_x, f_y, f_z, f_x f_y, f_x f_z, f_y f_z,
+// f_x f_y f_z), in double-float, and writes them to dep[corner][cell].
+// Nodes: one thread per node adds the 8 corner sums that reach it and writes
+// rho = 1 + (q_p / h^3) sum (the +1 background) in FP64.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_deposit_cells(const PRec* __restrict__ P,
-                                                       const uint32_t* __restrict__ offsets, double* rho, Grid g,
-                                                       double qscale) {
-  const int N = g.N;
-  const size_t n = (size_t)N * N * N;
+                                                       const uint32_t* __restrict__ offsets, float2* __restrict__ dep,
+                                                       size_t n) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const uint32_t b = offsets[c], e = offsets[c + 1];
-  if (b == e) return;
-  const int ix = (int)(c % N), iy = (int)((c / N) % N), iz = (int)(c / ((size_t)N * N));
-  const double cx = (double)ix, cy = (double)iy, cz = (double)iz;
-  // the 8 corner weights summed over the cell's particles follow from the
-  // moments of the offsets f in [0, 1)^3: sum_p prod_d (f_d or 1 - f_d)
-  // expands into the count and sums of f_x, f_y, f_z, f_x f_y, f_x f_z,
-  // f_y f_z, f_x f_y f_z (14 FP64 operations per particle instead of 18)
-  double mx = 0, my = 0, mz = 0, mxy = 0, mxz = 0, myz = 0, mxyz = 0;
+  DfAcc mx, my, mz, mxy, mxz, myz, mxyz;
   for (uint32_t p = b; p < e; ++p) {
-    double px, py, pz;
-    rec_pos(P, p, px, py, pz);
-    const double fx = fma(px, g.inv_h, -cx);
-    const double fy = fma(py, g.inv_h, -cy);
-    const double fz = fma(pz, g.inv_h, -cz);
-    const double fxy = fx * fy;
-    mx += fx;
-    my += fy;
-    mz += fz;
-    mxy += fxy;
-    mxz = fma(fx, fz, mxz);
-    myz = fma(fy, fz, myz);
-    mxyz = fma(fxy, fz, mxyz);
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(P + p));
+    const unsigned long long fz = __ldg(reinterpret_cast<const unsigned long long*>(P + p) + 2);
+    const df fx = frac_df(a.x), fy = frac_df(a.y), fzd = frac_df(fz);
+    const df fxy = df_mul(fx, fy);
+    mx.add(fx);
+    my.add(fy);
+    mz.add(fzd);
+    mxy.add(fxy);
+    mxz.add_mul(fx, fzd);
+    myz.add_mul(fy, fzd);
+    mxyz.add_mul(fxy, fzd);
   }
-  const double cnt = (double)(e - b);
-  double s[8];
-  s[7] = mxyz;                                  // f_x f_y f_z
-  s[3] = mxy - mxyz;                            // f_x f_y (1 - f_z)
-  s[5] = mxz - mxyz;                            // f_x (1 - f_y) f_z
-  s[6] = myz - mxyz;                            // (1 - f_x) f_y f_z
-  s[1] = mx - mxy - mxz + mxyz;                 // f_x (1 - f_y)(1 - f_z)
-  s[2] = my - mxy - myz + mxyz;                 // (1 - f_x) f_y (1 - f_z)
-  s[4] = mz - mxz - myz + mxyz;                 // (1 - f_x)(1 - f_y) f_z
-  s[0] = cnt - mx - my - mz + mxy + mxz + myz - mxyz;  // (1 - f_x)(1 - f_y)(1 - f_z)
-  const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
-  const size_t Ns = N;
-  const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
-  atomicAdd(rho + z0 + y0 + ix, qscale * s[0]);
-  atomicAdd(rho + z0 + y0 + jx, qscale * s[1]);
-  atomicAdd(rho + z0 + y1 + ix, qscale * s[2]);
-  atomicAdd(rho + z0 + y1 + jx, qscale * s[3]);
-  atomicAdd(rho + z1 + y0 + ix, qscale * s[4]);
-  atomicAdd(rho + z1 + y0 + jx, qscale * s[5]);
-  atomicAdd(rho + z1 + y1 + ix, qscale * s[6]);
-  atomicAdd(rho + z1 + y1 + jx, qscale * s[7]);
+  const df Mx = mx.value(), My = my.value(), Mz = mz.value(), Mxy = mxy.value(), Mxz = mxz.value(),
+           Myz = myz.value(), Mxyz = mxyz.value();
+  const df cnt = {(float)(e - b), 0.0f};  // exact below 2^24 particles per cell
+  df s[8];
+  s[7] = Mxyz;                                            // f_x f_y f_z
+  s[3] = df_sub(Mxy, Mxyz);                               // f_x f_y (1 - f_z)
+  s[5] = df_sub(Mxz, Mxyz);                               // f_x (1 - f_y) f_z
+  s[6] = df_sub(Myz, Mxyz);                               // (1 - f_x) f_y f_z
+  s[1] = df_sub(Mx, df_add(df_add(Mxy, Mxz), df_neg(Mxyz)));  // f_x (1 - f_y)(1 - f_z)
+  s[2] = df_sub(My, df_add(df_add(Mxy, Myz), df_neg(Mxyz)));  // (1 - f_x) f_y (1 - f_z)
+  s[4] = df_sub(Mz, df_add(df_add(Mxz, Myz), df_neg(Mxyz)));  // (1 - f_x)(1 - f_y) f_z
+  // (1 - f_x)(1 - f_y)(1 - f_z) = cnt - mx - my - mz + mxy + mxz + myz - mxyz
+  s[0] = df_add(df_sub(cnt, df_add(df_add(Mx, My), Mz)), df_sub(df_add(df_add(Mxy, Mxz), Myz), Mxyz));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dep[(size_t)k * n + c] = df_pack(s[k]);
+}
+
+// Node (i, j, k) is corner (a, b, c) of cell (i - a, j - b, k - c).
+__global__ void __launch_bounds__(256) k_deposit_nodes(const float2* __restrict__ dep, double* __restrict__ rho,
+                                                       int N, double qscale) {
+  const size_t Ns = N, n = Ns * Ns * Ns;
+  const int k = blockIdx.y;
+  const unsigned per_plane = (unsigned)N * (unsigned)N;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < per_plane; t += gridDim.x * blockDim.x) {
+    const int j = (int)(t / (unsigned)N), i = (int)(t - (unsigned)j * (unsigned)N);
+    const int im = i == 0 ? N - 1 : i - 1, jm = j == 0 ? N - 1 : j - 1, km = k == 0 ? N - 1 : k - 1;
+    const int xs[2] = {i, im}, ys[2] = {j, jm}, zs[2] = {k, km};
+    DfAcc acc;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+      const size_t cell = ((size_t)zs[c] * Ns + ys[b]) * Ns + xs[a];
+      acc.add(df_from(__ldg(dep + (size_t)q * n + cell)));
+    }
+    rho[(size_t)k * per_plane + t] = fma(qscale, double_of_df(acc.value()), 1.0);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// S5: E = -grad phi, central differences, periodic. Ex = (phi[i-1] - phi[i+1]) / 2h.
+// S5: E = -grad phi, central differences, periodic (Eq. 2). Ex = (phi[i-1] -
+// phi[i+1]) / 2h in FP64, stored as double-float for the gather.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gradient(const double* __restrict__ phi, double* __restrict__ Ex,
-                                                  double* __restrict__ Ey, double* __restrict__ Ez, Grid g) {
+__global__ void __launch_bounds__(256) k_gradient(const double* __restrict__ phi, float2* __restrict__ Ex,
+                                                  float2* __restrict__ Ey, float2* __restrict__ Ez, Grid g) {
   const int N = g.N;
   const size_t Ns = N, n = Ns * Ns * Ns;
   const double s = 0.5 * g.inv_h;
@@ -320,9 +404,9 @@ __global__ void __launch_bounds__(256) k_gradient(const double* __restrict__ phi
     const size_t col = c - (size_t)iz * Ns * Ns;
     const double zm = __ldg(phi + col + (size_t)(iz == 0 ? N - 1 : iz - 1) * Ns * Ns);
     const double zp = __ldg(phi + col + (size_t)(iz == N - 1 ? 0 : iz + 1) * Ns * Ns);
-    Ex[c] = (xm - xp) * s;
-    Ey[c] = (ym - yp) * s;
-    Ez[c] = (zm - zp) * s;
+    Ex[c] = df_pack(df_of_double((xm - xp) * s));
+    Ey[c] = df_pack(df_of_double((ym - yp) * s));
+    Ez[c] = df_pack(df_of_double((zm - zp) * s));
   }
 }
 
@@ -356,87 +440,97 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// S6: CIC gather of E and leapfrog push; then the new cell key and in-cell
-// rank (counts must be zero on entry) for the next sort. drift == 0 gives the
-// closing half-kick only (no key update).
+// S6: CIC gather of E and leapfrog push (Eqs. 3-4), in double-float; then the
+// new cell key and in-cell rank (counts must be zero on entry) for the next
+// sort. drift == 0 gives the closing half-kick only (no key update).
+//   kick_qm = -kick (q/m = -1), dth = dt / h, both double-float (hi, lo).
+// The ranks come from one atomic per group of lanes with equal keys (the
+// particles are in cell order, so a warp covers a few cells).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const double* __restrict__ Ex,
-                                                     const double* __restrict__ Ey, const double* __restrict__ Ez,
-                                                     Grid g, double kick_qm, double dt, int drift, uint32_t* keys,
+__global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const float2* __restrict__ Ex,
+                                                     const float2* __restrict__ Ey, const float2* __restrict__ Ez,
+                                                     Grid g, float2 kick_qm, float2 dth, int drift, uint32_t* keys,
                                                      uint32_t* ranks, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  double2* rec = reinterpret_cast<double2*>(P + p);
-  const double2 r0 = rec[0], r1 = rec[1], r2 = rec[2];
-  const uint4 r3 = reinterpret_cast<const uint4*>(rec)[3];
-  double x = r0.x, y = r0.y, z = r1.x;
-  const int N = g.N;
-  // the cell of the current position, kept in the record since its key was
-  // computed (integer decode instead of three FP64 floors)
-  const uint32_t key = r3.y;
-  const int ix = (int)(key % (uint32_t)N), iy = (int)((key / (uint32_t)N) % (uint32_t)N),
-            iz = (int)(key / ((uint32_t)N * (uint32_t)N));
-  const double fx = fma(x, g.inv_h, -(double)ix), fy = fma(y, g.inv_h, -(double)iy),
-               fz = fma(z, g.inv_h, -(double)iz);
-  const double gx = 1.0 - fx, gy = 1.0 - fy, gz = 1.0 - fz;
-  const double w00 = gy * gz, w10 = fy * gz, w01 = gy * fz, w11 = fy * fz;
-  const double w[8] = {gx * w00, fx * w00, gx * w10, fx * w10, gx * w01, fx * w01, gx * w11, fx * w11};
-  const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
-  const size_t Ns = N;
-  const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
-  const size_t idx[8] = {z0 + y0 + ix, z0 + y0 + jx, z0 + y1 + ix, z0 + y1 + jx,
-                         z1 + y0 + ix, z1 + y0 + jx, z1 + y1 + ix, z1 + y1 + jx};
-  double ex = 0.0, ey = 0.0, ez = 0.0;
+  const bool valid = p < np;
+  uint32_t kk = 0xFFFFFFFFu;
+  if (valid) {
+    ulonglong2* rec = reinterpret_cast<ulonglong2*>(P + p);
+    const ulonglong2 r0 = rec[0];
+    const ulonglong2 r1 = rec[1];
+    const float4 r2 = reinterpret_cast<const float4*>(rec)[2];
+    const uint4 r3 = reinterpret_cast<const uint4*>(rec)[3];
+    uint64_t fx = r0.x, fy = r0.y, fz = r1.x;
+    df vx = {__uint_as_float((uint32_t)r1.y), __uint_as_float((uint32_t)(r1.y >> 32))};
+    df vy = {r2.x, r2.y}, vz = {r2.z, r2.w};
+    int ix = (int)(r3.z & 0xFFFFu), iy = (int)(r3.z >> 16), iz = (int)(r3.w & 0xFFFFu);
+    const int N = g.N;
+    // CIC weights prod_d (f_d or 1 - f_d) of the 8 corners
+    const df ax = frac_df(fx), ay = frac_df(fy), az = frac_df(fz);
+    const df bx = one_minus_frac_df(fx), by = one_minus_frac_df(fy), bz = one_minus_frac_df(fz);
+    const df w00 = df_mul(by, bz), w10 = df_mul(ay, bz), w01 = df_mul(by, az), w11 = df_mul(ay, az);
+    const df w[8] = {df_mul(bx, w00), df_mul(ax, w00), df_mul(bx, w10), df_mul(ax, w10),
+                     df_mul(bx, w01), df_mul(ax, w01), df_mul(bx, w11), df_mul(ax, w11)};
+    const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
+    const size_t Ns = N;
+    const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
+    const size_t idx[8] = {z0 + y0 + ix, z0 + y0 + jx, z0 + y1 + ix, z0 + y1 + jx,
+                           z1 + y0 + ix, z1 + y0 + jx, z1 + y1 + ix, z1 + y1 + jx};
+    DfAcc ex, ey, ez;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    ex = fma(w[c], __ldg(Ex + idx[c]), ex);
-    ey = fma(w[c], __ldg(Ey + idx[c]), ey);
-    ez = fma(w[c], __ldg(Ez + idx[c]), ez);
+    for (int c = 0; c < 8; ++c) {
+      ex.add_mul(w[c], df_from(__ldg(Ex + idx[c])));
+      ey.add_mul(w[c], df_from(__ldg(Ey + idx[c])));
+      ez.add_mul(w[c], df_from(__ldg(Ez + idx[c])));
+    }
+    const df kq = dfc(kick_qm);
+    vx = df_add(vx, df_mul(kq, ex.value()));
+    vy = df_add(vy, df_mul(kq, ey.value()));
+    vz = df_add(vz, df_mul(kq, ez.value()));
+    reinterpret_cast<float4*>(rec)[2] = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
+    // vx as the second 8-byte word of the record's second 16 bytes
+    const unsigned long long vxw =
+        (unsigned long long)__float_as_uint(vx.hi) | ((unsigned long long)__float_as_uint(vx.lo) << 32);
+    if (!drift) {
+      rec[1] = make_ulonglong2(fz, vxw);
+    } else {
+      const df s = dfc(dth);
+      move_coord(fx, ix, df_mul(vx, s), N);
+      move_coord(fy, iy, df_mul(vy, s), N);
+      move_coord(fz, iz, df_mul(vz, s), N);
+      rec[0] = make_ulonglong2(fx, fy);
+      rec[1] = make_ulonglong2(fz, vxw);
+      kk = cell_key(ix, iy, iz, N);
+      reinterpret_cast<uint4*>(rec)[3] =
+          make_uint4(r3.x, kk, (uint32_t)ix | ((uint32_t)iy << 16), (uint32_t)iz | (r3.w & 0xFFFF0000u));
+    }
   }
-  double vx = fma(kick_qm, ex, r1.y);
-  double vy = fma(kick_qm, ey, r2.x);
-  double vz = fma(kick_qm, ez, r2.y);
-  rec[2] = make_double2(vy, vz);
-  if (!drift) {
-    rec[1] = make_double2(z, vx);
-    return;
-  }
-  const double L = g.L;
-  x = fma(dt, vx, x);
-  y = fma(dt, vy, y);
-  z = fma(dt, vz, z);
-  // periodic wrap into [0, L); a value that rounds to L becomes 0. Only the
-  // few particles that left the box take the full sequence; for the others
-  // it is the identity (same result, fewer FP64 operations).
-  if (x < 0.0 || x >= L) {
-    x = x >= L ? x - L : x; x = x < 0.0 ? x + L : x; x = x >= L ? 0.0 : x;
-  }
-  if (y < 0.0 || y >= L) {
-    y = y >= L ? y - L : y; y = y < 0.0 ? y + L : y; y = y >= L ? 0.0 : y;
-  }
-  if (z < 0.0 || z >= L) {
-    z = z >= L ? z - L : z; z = z < 0.0 ? z + L : z; z = z >= L ? 0.0 : z;
-  }
-  rec[0] = make_double2(x, y);
-  rec[1] = make_double2(z, vx);
-  const uint32_t kk = key_of(x, y, z, g);
-  reinterpret_cast<uint4*>(rec)[3] = make_uint4(r3.x, kk, 0u, 0u);
+  if (!drift) return;  // uniform over the launch: no lane is left in the match below
+  // one atomic per group of lanes with the same key
+  const unsigned peers = __match_any_sync(0xffffffffu, kk);
+  if (!valid) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&counts[kk], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
   keys[p] = kk;
-  ranks[p] = atomicAdd(&counts[kk], 1u);
+  ranks[p] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// Copy particles back to the original order: out[q * np + id[p]] = field q of p.
-__global__ void k_unsort(const PRec* P, uint64_t np, double* out) {
+// Copy particles back to the original order, in FP64: out[q * np + id[p]] =
+// field q of p (x, y, z, vx, vy, vz).
+__global__ void k_unsort(const PRec* P, uint64_t np, Grid g, double* out) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const PRec r = P[p];
   const uint64_t d = r.id;
-  out[d] = r.x;
-  out[np + d] = r.y;
-  out[2 * np + d] = r.z;
-  out[3 * np + d] = r.vx;
-  out[4 * np + d] = r.vy;
-  out[5 * np + d] = r.vz;
+  out[d] = from_cell_offset(r.ix, r.fx, g);
+  out[np + d] = from_cell_offset(r.iy, r.fy, g);
+  out[2 * np + d] = from_cell_offset(r.iz, r.fz, g);
+  out[3 * np + d] = double_of_df(df_from(r.vx));
+  out[4 * np + d] = double_of_df(df_from(r.vy));
+  out[5 * np + d] = double_of_df(df_from(r.vz));
 }
 
 }  // namespace pic
