@@ -441,9 +441,10 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   return PIC_ENOCONV;
 }
 
+// E_x, E_y, E_z and the double-float copy of phi (4 n double-float values).
 int ensure_E(pic_ctx* c) {
   if (c->E) return PIC_OK;
-  return dalloc(&c->E, 3 * c->n);
+  return dalloc(&c->E, 4 * c->n);
 }
 
 // A double-float constant (hi, lo) for the particle kernels.
@@ -456,7 +457,11 @@ int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift
   int e;
   if ((e = ensure_E(c))) return e;
   const int sb = streaming_blocks(c);
-  launch(c, k_gradient, sb, 256, 0, phi, c->E, c->E + c->n, c->E + 2 * c->n, c->grid);
+  float2* phid = c->E + 3 * c->n;
+  launch(c, k_phi_df, sb, 256, 0, phi, phid, c->n);
+  const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
+  launch(c, k_gradient, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)phid, c->E, c->E + c->n,
+         c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
@@ -608,7 +613,7 @@ int pic_deposit(pic_ctx* c, double* rho) {
     launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
     launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
     launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
-    const unsigned sblocks = (unsigned)((c->np / 2 + 255) / 256);
+    const unsigned sblocks = (unsigned)(((c->np + 31) / 32 * 32 + 255) / 256);
     launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
            (const uint32_t*)c->ranks,
                                               c->offsets);

@@ -17,6 +17,7 @@ struct MgLevel {
   int N = 0;
   float *x = nullptr, *r = nullptr, *t = nullptr, *res = nullptr;
   bool streamed = false;          // N % 4 == 0: plane-streamed kernels
+  bool tall = false;              // N >= 512: one 1024-thread block per SM
   StreamGeo geo[kNumMgKer]{};
   size_t smem[kNumMgKer]{};
 };
@@ -38,6 +39,35 @@ void mg_state_free(MgState* s) {
 }
 
 namespace {
+
+#ifndef MG_TALL_PROLONG
+#define MG_TALL_PROLONG 0
+#endif
+
+// Whether kernel k of level L runs in the tall-block form.
+bool tall_form(const MgLevel& L, MgKer k) {
+  const bool prolong = k == kResidProlong || k == kSmoothProlong;
+  return L.tall && (!prolong || MG_TALL_PROLONG);
+}
+
+// The plane-streamed kernel k in its small- or tall-block form.
+const void* mg_kernel(MgKer k, bool tall) {
+  switch (k) {
+    case kPre: return tall ? (const void*)mg::k_mg_pre<true> : (const void*)mg::k_mg_pre<false>;
+    case kResid:
+      return tall ? (const void*)mg::k_mg_stencil<mg::kResid, false, true>
+                  : (const void*)mg::k_mg_stencil<mg::kResid, false, false>;
+    case kResidProlong:
+      return tall ? (const void*)mg::k_mg_stencil<mg::kResid, true, true>
+                  : (const void*)mg::k_mg_stencil<mg::kResid, true, false>;
+    case kSmoothProlong:
+      return tall ? (const void*)mg::k_mg_stencil<mg::kSmooth, true, true>
+                  : (const void*)mg::k_mg_stencil<mg::kSmooth, true, false>;
+    default:
+      return tall ? (const void*)mg::k_mg_stencil<mg::kSmooth, false, true>
+                  : (const void*)mg::k_mg_stencil<mg::kSmooth, false, false>;
+  }
+}
 
 int grid_for(const pic_ctx* c, size_t n) {
   size_t b = (n + 255) / 256;
@@ -78,27 +108,30 @@ int ensure_state(pic_ctx* c) {
   }
   // slab geometry of every streamed level; each kernel's shared-memory limit
   // ends at the largest size any level launches it with
-  void* kers[kNumMgKer] = {(void*)mg::k_mg_pre, (void*)mg::k_mg_stencil<mg::kResid, false>,
-                           (void*)mg::k_mg_stencil<mg::kResid, true>, (void*)mg::k_mg_stencil<mg::kSmooth, true>,
-                           (void*)mg::k_mg_stencil<mg::kSmooth, false>};
-  size_t smax[kNumMgKer] = {};
+  size_t smax[2][kNumMgKer] = {};
   for (int l = 0; l < b && !e; ++l) {
     MgLevel& L = s->lev[l];
     L.streamed = L.N % 4 == 0;
     if (!L.streamed) continue;
-    // coarse levels are latency-bound: more blocks with fewer planes each
+    // the tall block re-reads fewer halo rows on large grids (as for the CG
+    // direction kernel); coarse levels are latency-bound: more blocks with
+    // fewer planes each
+    L.tall = L.N >= 512;
     const int min_planes = L.N >= 256 ? 4 : (L.N >= 128 ? 2 : 1);
     for (int k = 0; k < kNumMgKer && !e; ++k) {
-      e = slab_geometry<float, float, float, 1>(c, L.N, (const void*)kers[k], &L.geo[k], &L.smem[k], false,
+      const bool t = tall_form(L, (MgKer)k);
+      e = slab_geometry<float, float, float, 1>(c, L.N, mg_kernel((MgKer)k, t), &L.geo[k], &L.smem[k], t,
                                                 min_planes);
-      if (L.smem[k] > smax[k]) smax[k] = L.smem[k];
+      size_t& m = smax[t][k];
+      if (L.smem[k] > m) m = L.smem[k];
     }
   }
-  for (int k = 0; k < kNumMgKer && !e; ++k) {
-    if (smax[k] && cudaFuncSetAttribute(kers[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax[k]) !=
-                       cudaSuccess)
-      e = PIC_ECUDA;
-  }
+  for (int t = 0; t < 2; ++t)
+    for (int k = 0; k < kNumMgKer && !e; ++k) {
+      if (smax[t][k] && cudaFuncSetAttribute(mg_kernel((MgKer)k, t != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smax[t][k]) != cudaSuccess)
+        e = PIC_ECUDA;
+    }
   // the small levels (first one = lev[b])
   mg::SmallLevels& S = s->small;
   S.n = nl - b;
@@ -159,13 +192,13 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     if (l == 0 && learned) {
       if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
     } else if (L.streamed) {
-      slab(L, kPre, PIC_KER_MG_PRE, mg::k_mg_pre, rl(l), xl(l));
+      slab(L, kPre, PIC_KER_MG_PRE, tall_form(L, kPre) ? mg::k_mg_pre<true> : mg::k_mg_pre<false>, rl(l), xl(l));
     } else {
       launch(c, mg::k_mg_jacobi, g, 256, 0, nul, rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
     }
     if (L.streamed) {
-      slab(L, kResid, PIC_KER_MG_RESID, mg::k_mg_stencil<mg::kResid, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
+      slab(L, kResid, PIC_KER_MG_RESID, tall_form(L, kResid) ? mg::k_mg_stencil<mg::kResid, false, true> : mg::k_mg_stencil<mg::kResid, false, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
       const int Nc = L.N / 2;
       const unsigned per_plane = (unsigned)(Nc / 2) * (unsigned)Nc;
       const unsigned bx = (per_plane + 255) / 256;
@@ -189,7 +222,7 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     if (l == 0 && learned) {
       // x' = x + P e_c (into t), res = r - A^ x', x = x' + K res
       if (L.streamed) {
-        slab(L, kResidProlong, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_stencil<mg::kResid, true>, (const float*)xl(0), rl(0), L.res, L.t, ec);
+        slab(L, kResidProlong, PIC_KER_MG_PROLONG_SMOOTH, tall_form(L, kResidProlong) ? mg::k_mg_stencil<mg::kResid, true, true> : mg::k_mg_stencil<mg::kResid, true, false>, (const float*)xl(0), rl(0), L.res, L.t, ec);
       } else {
         launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(0), ec, L.N / 2, done);
         launch(c, mg::k_mg_copy, grid_for(c, n), 256, 0, (const float*)xl(0), L.t, n, done);
@@ -198,8 +231,8 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
       if ((e = cnn_apply(c, L.res, xl(0), nullptr, n))) return e;
       launch(c, mg::k_mg_add, grid_for(c, n / 4), 256, 0, xl(0), (const float*)L.t, n / 4, done);
     } else if (L.streamed) {
-      slab(L, kSmoothProlong, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_stencil<mg::kSmooth, true>, (const float*)xl(l), rl(l), L.t, nulw, ec);
-      slab(L, kSmooth, PIC_KER_MG_SMOOTH, mg::k_mg_stencil<mg::kSmooth, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
+      slab(L, kSmoothProlong, PIC_KER_MG_PROLONG_SMOOTH, tall_form(L, kSmoothProlong) ? mg::k_mg_stencil<mg::kSmooth, true, true> : mg::k_mg_stencil<mg::kSmooth, true, false>, (const float*)xl(l), rl(l), L.t, nulw, ec);
+      slab(L, kSmooth, PIC_KER_MG_SMOOTH, tall_form(L, kSmooth) ? mg::k_mg_stencil<mg::kSmooth, false, true> : mg::k_mg_stencil<mg::kSmooth, false, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
     } else {
       launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), ec, L.N / 2, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);

@@ -53,35 +53,39 @@ __device__ __forceinline__ float apply_hat(const float* __restrict__ x, int N, i
 // Plane-streamed kernels (N % 4 == 0)
 // ---------------------------------------------------------------------------
 
-// v += (P e_c) on the 4 cells at stage offset e of plane z (fine grid s.N,
-// coarse Nc = s.N / 2 even): fine x = 2I is coarse I, fine x = 2I+1 the mean
-// of I and I+1; likewise in y and z, so the 4 cells need coarse x-nodes
-// I0, I0+1, I0+2 (I0 = x0 / 2 even) summed over the 1, 2 or 4 (J, K) pairs.
-__device__ __forceinline__ void add_prolonged(V4<float>& v, const float* __restrict__ ec, const Slab& s, size_t e,
-                                              int z) {
-  const int N = s.N, Nc = N >> 1;
-  const unsigned sr = (unsigned)e / (unsigned)N;
-  const int i0 = (int)((unsigned)e - sr * (unsigned)N);
-  const int j = (s.TY == N) ? (int)sr : wrapi(s.j0 - 1 + (int)sr, N);
-  const int I0 = i0 >> 1;
+// The coarse values that the prolongation adds to 4 fine cells (x0..x0+3,
+// x0 % 4 == 0) of fine row j, plane z (fine grid N, coarse Nc = N / 2 even):
+// fine x = 2I is coarse I, fine x = 2I+1 the mean of I and I+1, likewise in y
+// and z, so the cells need coarse x-nodes I0, I0+1, I0+2 (I0 = x0 / 2) of the
+// 1, 2 or 4 coarse (row, plane) pairs around (j / 2, z / 2). Loaded into
+// registers (q = 0..3: (J0, K0), (J1, K0), (J0, K1), (J1, K1); unused pairs
+// stay zero) so that the loads of the next plane can be issued early.
+struct CoarseRows {
+  float2 a[4];  // coarse I0, I0 + 1
+  float b[4];   // coarse I0 + 2 (periodic)
+};
+
+__device__ __forceinline__ void coarse_rows_load(CoarseRows& R, const float* __restrict__ ec, int Nc, int x0, int j,
+                                                 int z) {
+  const int I0 = x0 >> 1;
   const int I2 = (I0 + 2 == Nc) ? 0 : I0 + 2;
   const int J0 = j >> 1, K0 = z >> 1;
   const int J1 = (J0 + 1 == Nc) ? 0 : J0 + 1;
   const int K1 = (K0 + 1 == Nc) ? 0 : K0 + 1;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  auto acc = [&](int J, int K) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool use = (!(q & 1) || (j & 1)) && (!(q & 2) || (z & 1));
+    const int J = (q & 1) ? J1 : J0, K = (q & 2) ? K1 : K0;
     const float* row = ec + ((size_t)K * Nc + J) * Nc;
-    const float2 a = __ldg(reinterpret_cast<const float2*>(row + I0));
-    s0 += a.x;
-    s1 += a.y;
-    s2 += __ldg(row + I2);
-  };
-  acc(J0, K0);
-  if (j & 1) acc(J1, K0);
-  if (z & 1) {
-    acc(J0, K1);
-    if (j & 1) acc(J1, K1);
+    R.a[q] = use ? __ldg(reinterpret_cast<const float2*>(row + I0)) : make_float2(0.f, 0.f);
+    R.b[q] = use ? __ldg(row + I2) : 0.f;
   }
+}
+
+__device__ __forceinline__ void coarse_rows_add(V4<float>& v, const CoarseRows& R, int j, int z) {
+  const float s0 = (R.a[0].x + R.a[1].x) + (R.a[2].x + R.a[3].x);
+  const float s1 = (R.a[0].y + R.a[1].y) + (R.a[2].y + R.a[3].y);
+  const float s2 = (R.b[0] + R.b[1]) + (R.b[2] + R.b[3]);
   const float wyz = ((j & 1) ? 0.5f : 1.f) * ((z & 1) ? 0.5f : 1.f);
   v.v[0] += wyz * s0;
   v.v[1] += wyz * (0.5f * (s0 + s1));
@@ -89,10 +93,21 @@ __device__ __forceinline__ void add_prolonged(V4<float>& v, const float* __restr
   v.v[3] += wyz * (0.5f * (s1 + s2));
 }
 
+// Global row of stage offset e (stage rows are the slab's rows plus one halo
+// row each side, or the whole plane when TY == N) and the x of its first cell.
+__device__ __forceinline__ void stage_row_x(const Slab& s, size_t e, int& j, int& x0) {
+  const int N = s.N;
+  const unsigned sr = (unsigned)e / (unsigned)N;
+  x0 = (int)((unsigned)e - sr * (unsigned)N);
+  j = (s.TY == N) ? (int)sr : wrapi(s.j0 - 1 + (int)sr, N);
+}
+
 // Pre-smoothing, nu1 = 2 damped sweeps from x = 0 in one pass:
 // x1 = w r, x2 = x1 + w (r - A^ x1) = w (2 r - w A^ r), w = omega / 6.
-__global__ void __launch_bounds__(kStreamSmall) k_mg_pre(const float* __restrict__ r, float* __restrict__ x, int* err,
-                                                         StreamGeo g, const int* done) {
+template <bool TALL>
+__global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_mg_pre(const float* __restrict__ r,
+                                                                            float* __restrict__ x, int* err,
+                                                                            StreamGeo g, const int* done) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (done && *done) return;
@@ -117,11 +132,10 @@ enum : int { kResid = 0, kSmooth = 1 };
 //   kResid : out = r - A^ x'        (and xout = x' when PROLONG)
 //   kSmooth: out = x' + w (r - A^ x')
 // out and xout must not alias x (other blocks read x's halo rows).
-template <int MODE, bool PROLONG>
-__global__ void __launch_bounds__(kStreamSmall) k_mg_stencil(const float* __restrict__ x, const float* __restrict__ r,
-                                                             float* __restrict__ out, float* __restrict__ xout,
-                                                             const float* __restrict__ ec, int* err, StreamGeo g,
-                                                             const int* done) {
+template <int MODE, bool PROLONG, bool TALL>
+__global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_mg_stencil(
+    const float* __restrict__ x, const float* __restrict__ r, float* __restrict__ out, float* __restrict__ xout,
+    const float* __restrict__ ec, int* err, StreamGeo g, const int* done) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (done && *done) return;
@@ -129,9 +143,30 @@ __global__ void __launch_bounds__(kStreamSmall) k_mg_stencil(const float* __rest
   const float w = kOmega / 6.0f;
   V4<float> cb;
   auto start = [&](const Slab& s) { cb = ldg4(r + cell_offset(s, 0)); };
+  // the coarse values of the thread's own cells for the next plane are
+  // loaded while the current plane is processed (halo rows load on demand)
+  CoarseRows next;
+  int next_z = -1, next_j = -1;
+  const int Nc = g.N >> 1;
   auto ingest = [&](int st, size_t e, const Slab& s, int z) {
     V4<float> v = ld4(lay.v0(smem, st) + e);
-    if (PROLONG) add_prolonged(v, ec, s, e, z);
+    if (PROLONG) {
+      int j, x0;
+      stage_row_x(s, e, j, x0);
+      const bool own = e == (size_t)s.srow * s.N + s.x0;
+      if (own && z == next_z && j == next_j) {
+        coarse_rows_add(v, next, j, z);
+      } else {
+        CoarseRows now;
+        coarse_rows_load(now, ec, Nc, x0, j, z);
+        coarse_rows_add(v, now, j, z);
+      }
+      if (own) {
+        next_z = z + 1 == s.N ? 0 : z + 1;
+        next_j = j;
+        coarse_rows_load(next, ec, Nc, x0, j, next_z);
+      }
+    }
     return v;
   };
   auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,

@@ -104,6 +104,17 @@ __device__ __forceinline__ df one_minus_frac_df(uint64_t f) {
   return frac_df(0ull - f);
 }
 
+// |x| 2^64 truncated to an integer, for |x| < 1, with two 32-bit
+// conversions (a 64-bit float-to-integer conversion would run on GB300's
+// FP64 pipe): a = |x| 2^32 < 2^32 splits exactly into its integer part and
+// its fraction, and the fraction times 2^32 is the low word.
+__device__ __forceinline__ uint64_t abs_times_2p64(float x) {
+  const float a = __fmul_rn(fabsf(x), 0x1p32f);
+  const float h = truncf(a);
+  const float l = __fmul_rn(__fsub_rn(a, h), 0x1p32f);
+  return ((uint64_t)__float2uint_rz(h) << 32) | __float2uint_rz(l);
+}
+
 // Moves one coordinate by d cells (double-float): the offset takes the
 // fraction of d in exact 64-bit arithmetic, the carries and the integer part
 // of d move the cell index, which wraps periodically. Needs |d| < 2^20.
@@ -113,19 +124,12 @@ __device__ __forceinline__ df one_minus_frac_df(uint64_t f) {
 __device__ __forceinline__ void move_coord(uint64_t& f, int& i, df d, int N) {
   const float n = truncf(d.hi);
   const float r = __fsub_rn(d.hi, n);  // exact, |r| < 1, sign of d.hi
-  uint64_t f1;
-  int carry;
-  if (r >= 0.0f) {
-    f1 = f + __float2ull_rn(__fmul_rn(r, 0x1p64f));
-    carry = f1 < f ? 1 : 0;
-  } else {
-    f1 = f - __float2ull_rn(__fmul_rn(-r, 0x1p64f));
-    carry = f1 > f ? -1 : 0;
-  }
-  const int64_t B = __float2ll_rn(__fmul_rn(d.lo, 0x1p64f));
-  const uint64_t f2 = f1 + (uint64_t)B;
-  if (B >= 0) carry += f2 < f1 ? 1 : 0;
-  else carry -= f2 > f1 ? 1 : 0;
+  const uint64_t A = abs_times_2p64(r), B = abs_times_2p64(d.lo);
+  const bool ra = r >= 0.0f, ba = d.lo >= 0.0f;
+  const uint64_t f1 = ra ? f + A : f - A;
+  int carry = ra ? (f1 < f ? 1 : 0) : (f1 > f ? -1 : 0);
+  const uint64_t f2 = ba ? f1 + B : f1 - B;
+  carry += ba ? (f2 < f1 ? 1 : 0) : (f2 > f1 ? -1 : 0);
   f = f2;
   int t = i + (int)n + carry;
   if (t < 0 || t >= N) {
@@ -282,33 +286,34 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
   if (base + 16 >= n && base < n) offsets[n] = run;  // the thread holding the last count
 }
 
-// Move particle p to offsets[key] + rank (the other buffer). Each thread
-// moves 2 consecutive particles, 64 bytes each as four 16-byte vectors, so
-// every destination is written in whole sectors (np % 2 == 0).
+// Move particle p to offsets[key] + rank (the other buffer). Each warp moves
+// 32 consecutive particles; lane l holds 16-byte word (l & 3) of particles
+// 8k + (l >> 2), k = 0..3, so every load and every store instruction of the
+// warp covers 8 whole 64-byte records (whole sectors at both ends).
 __global__ void __launch_bounds__(256) k_scatter(const PRec* __restrict__ src, PRec* __restrict__ dst, uint64_t np,
                                                  const uint32_t* __restrict__ keys,
                                                  const uint32_t* __restrict__ ranks,
                                                  const uint32_t* __restrict__ offsets) {
-  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (2 * q >= np) return;
-  const uint2 k2 = __ldg(reinterpret_cast<const uint2*>(keys) + q);
-  const uint2 r2 = __ldg(reinterpret_cast<const uint2*>(ranks) + q);
-  const uint64_t d0 = (uint64_t)__ldg(offsets + k2.x) + r2.x;
-  const uint64_t d1 = (uint64_t)__ldg(offsets + k2.y) + r2.y;
-  const uint4* s0 = reinterpret_cast<const uint4*>(src + 2 * q);
-  const uint4* s1 = reinterpret_cast<const uint4*>(src + 2 * q + 1);
-  uint4 a[4], b[4];
+  const uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  if (base >= np) return;  // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  const uint64_t p = base + lane;
+  uint64_t d = 0;
+  if (p < np) d = (uint64_t)__ldg(offsets + __ldg(keys + p)) + __ldg(ranks + p);
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  const int word = lane & 3;
+  uint4 v[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    a[i] = __ldg(s0 + i);
-    b[i] = __ldg(s1 + i);
+  for (int k = 0; k < 4; ++k) {
+    const uint64_t q = base + 8 * k + (lane >> 2);
+    if (q < np) v[k] = __ldg(s4 + q * 4 + word);
   }
-  uint4* t0 = reinterpret_cast<uint4*>(dst + d0);
-  uint4* t1 = reinterpret_cast<uint4*>(dst + d1);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    t0[i] = a[i];
-    t1[i] = b[i];
+  for (int k = 0; k < 4; ++k) {
+    const int ql = 8 * k + (lane >> 2);
+    const uint64_t dq = __shfl_sync(0xffffffffu, d, ql);
+    if (base + ql < np) d4[dq * 4 + word] = v[k];
   }
 }
 
@@ -385,28 +390,37 @@ __global__ void __launch_bounds__(256) k_deposit_nodes(const float2* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// S5: E = -grad phi, central differences, periodic (Eq. 2). Ex = (phi[i-1] -
-// phi[i+1]) / 2h in FP64, stored as double-float for the gather.
+// S5: E = -grad phi, central differences, periodic (Eq. 2):
+// Ex = (phi[i-1] - phi[i+1]) / 2h. phi is converted to double-float once per
+// node (FP64 operations), the differences run in double-float.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gradient(const double* __restrict__ phi, float2* __restrict__ Ex,
-                                                  float2* __restrict__ Ey, float2* __restrict__ Ez, Grid g) {
-  const int N = g.N;
-  const size_t Ns = N, n = Ns * Ns * Ns;
-  const double s = 0.5 * g.inv_h;
+__global__ void __launch_bounds__(256) k_phi_df(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
-    const int ix = (int)(c % Ns), iy = (int)((c / Ns) % Ns), iz = (int)(c / (Ns * Ns));
-    const size_t row = c - ix, pl = c - (size_t)iy * Ns;
-    const double xm = __ldg(phi + row + (ix == 0 ? N - 1 : ix - 1));
-    const double xp = __ldg(phi + row + (ix == N - 1 ? 0 : ix + 1));
-    const double ym = __ldg(phi + pl + (size_t)(iy == 0 ? N - 1 : iy - 1) * Ns);
-    const double yp = __ldg(phi + pl + (size_t)(iy == N - 1 ? 0 : iy + 1) * Ns);
-    const size_t col = c - (size_t)iz * Ns * Ns;
-    const double zm = __ldg(phi + col + (size_t)(iz == 0 ? N - 1 : iz - 1) * Ns * Ns);
-    const double zp = __ldg(phi + col + (size_t)(iz == N - 1 ? 0 : iz + 1) * Ns * Ns);
-    Ex[c] = df_pack(df_of_double((xm - xp) * s));
-    Ey[c] = df_pack(df_of_double((ym - yp) * s));
-    Ez[c] = df_pack(df_of_double((zm - zp) * s));
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
+    out[c] = df_pack(df_of_double(__ldg(phi + c)));
+}
+
+__global__ void __launch_bounds__(256) k_gradient(const float2* __restrict__ phi, float2* __restrict__ Ex,
+                                                  float2* __restrict__ Ey, float2* __restrict__ Ez, int N,
+                                                  float2 half_inv_h) {
+  const size_t Ns = N;
+  const int k = blockIdx.y;
+  const unsigned per_plane = (unsigned)N * (unsigned)N;
+  const df s = dfc(half_inv_h);
+  const int km = k == 0 ? N - 1 : k - 1, kp = k == N - 1 ? 0 : k + 1;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < per_plane; t += gridDim.x * blockDim.x) {
+    const int j = (int)(t / (unsigned)N), i = (int)(t - (unsigned)j * (unsigned)N);
+    const int im = i == 0 ? N - 1 : i - 1, ip = i == N - 1 ? 0 : i + 1;
+    const int jm = j == 0 ? N - 1 : j - 1, jp = j == N - 1 ? 0 : j + 1;
+    const size_t pl = (size_t)k * per_plane, row = pl + (size_t)j * Ns;
+    const df xm = df_from(__ldg(phi + row + im)), xp = df_from(__ldg(phi + row + ip));
+    const df ym = df_from(__ldg(phi + pl + (size_t)jm * Ns + i)), yp = df_from(__ldg(phi + pl + (size_t)jp * Ns + i));
+    const df zm = df_from(__ldg(phi + (size_t)km * per_plane + (size_t)j * Ns + i));
+    const df zp = df_from(__ldg(phi + (size_t)kp * per_plane + (size_t)j * Ns + i));
+    const size_t c = row + i;
+    Ex[c] = df_pack(df_mul(df_sub(xm, xp), s));
+    Ey[c] = df_pack(df_mul(df_sub(ym, yp), s));
+    Ez[c] = df_pack(df_mul(df_sub(zm, zp), s));
   }
 }
 
@@ -444,24 +458,28 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 // new cell key and in-cell rank (counts must be zero on entry) for the next
 // sort. drift == 0 gives the closing half-kick only (no key update).
 //   kick_qm = -kick (q/m = -1), dth = dt / h, both double-float (hi, lo).
-// The ranks come from one atomic per group of lanes with equal keys (the
+// Each thread reads and writes its own 64-byte record (four 16-byte words).
+// The ranks come from one atomic per run of equal keys in a warp (the
 // particles are in cell order, so a warp covers a few cells).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const float2* __restrict__ Ex,
-                                                     const float2* __restrict__ Ey, const float2* __restrict__ Ez,
-                                                     Grid g, float2 kick_qm, float2 dth, int drift, uint32_t* keys,
-                                                     uint32_t* ranks, uint32_t* counts) {
-  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kPushThreads = 256;
+
+__global__ void __launch_bounds__(kPushThreads) k_gather_push(PRec* P, uint64_t np, const float2* __restrict__ Ex,
+                                                              const float2* __restrict__ Ey,
+                                                              const float2* __restrict__ Ez, Grid g, float2 kick_qm,
+                                                              float2 dth, int drift, uint32_t* keys, uint32_t* ranks,
+                                                              uint32_t* counts) {
+  const uint64_t base = (uint64_t)blockIdx.x * kPushThreads;
+  const uint64_t p = base + threadIdx.x;
   const bool valid = p < np;
   uint32_t kk = 0xFFFFFFFFu;
   if (valid) {
-    ulonglong2* rec = reinterpret_cast<ulonglong2*>(P + p);
-    const ulonglong2 r0 = rec[0];
-    const ulonglong2 r1 = rec[1];
-    const float4 r2 = reinterpret_cast<const float4*>(rec)[2];
-    const uint4 r3 = reinterpret_cast<const uint4*>(rec)[3];
-    uint64_t fx = r0.x, fy = r0.y, fz = r1.x;
-    df vx = {__uint_as_float((uint32_t)r1.y), __uint_as_float((uint32_t)(r1.y >> 32))};
+    uint4* rec = reinterpret_cast<uint4*>(P + p);
+    const uint4 r0 = rec[0], r1 = rec[1], r3 = rec[3];
+    const float4 r2 = *reinterpret_cast<const float4*>(rec + 2);
+    uint64_t fx = ((uint64_t)r0.y << 32) | r0.x, fy = ((uint64_t)r0.w << 32) | r0.z;
+    uint64_t fz = ((uint64_t)r1.y << 32) | r1.x;
+    df vx = {__uint_as_float(r1.z), __uint_as_float(r1.w)};
     df vy = {r2.x, r2.y}, vz = {r2.z, r2.w};
     int ix = (int)(r3.z & 0xFFFFu), iy = (int)(r3.z >> 16), iz = (int)(r3.w & 0xFFFFu);
     const int N = g.N;
@@ -487,35 +505,35 @@ __global__ void __launch_bounds__(256) k_gather_push(PRec* P, uint64_t np, const
     vx = df_add(vx, df_mul(kq, ex.value()));
     vy = df_add(vy, df_mul(kq, ey.value()));
     vz = df_add(vz, df_mul(kq, ez.value()));
-    reinterpret_cast<float4*>(rec)[2] = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
-    // vx as the second 8-byte word of the record's second 16 bytes
-    const unsigned long long vxw =
-        (unsigned long long)__float_as_uint(vx.hi) | ((unsigned long long)__float_as_uint(vx.lo) << 32);
-    if (!drift) {
-      rec[1] = make_ulonglong2(fz, vxw);
-    } else {
+    *reinterpret_cast<float4*>(rec + 2) = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
+    if (drift) {
       const df s = dfc(dth);
       move_coord(fx, ix, df_mul(vx, s), N);
       move_coord(fy, iy, df_mul(vy, s), N);
       move_coord(fz, iz, df_mul(vz, s), N);
-      rec[0] = make_ulonglong2(fx, fy);
-      rec[1] = make_ulonglong2(fz, vxw);
+      rec[0] = make_uint4((uint32_t)fx, (uint32_t)(fx >> 32), (uint32_t)fy, (uint32_t)(fy >> 32));
       kk = cell_key(ix, iy, iz, N);
-      reinterpret_cast<uint4*>(rec)[3] =
-          make_uint4(r3.x, kk, (uint32_t)ix | ((uint32_t)iy << 16), (uint32_t)iz | (r3.w & 0xFFFF0000u));
+      rec[3] = make_uint4(r3.x, kk, (uint32_t)ix | ((uint32_t)iy << 16), (uint32_t)iz | (r3.w & 0xFFFF0000u));
     }
+    rec[1] = make_uint4((uint32_t)fz, (uint32_t)(fz >> 32), __float_as_uint(vx.hi), __float_as_uint(vx.lo));
   }
-  if (!drift) return;  // uniform over the launch: no lane is left in the match below
-  // one atomic per group of lanes with the same key
-  const unsigned peers = __match_any_sync(0xffffffffu, kk);
-  if (!valid) return;
+  if (!drift) return;  // uniform over the launch: every lane reaches the warp collectives below
+  // runs of equal keys: the first lane of a run takes the run's ranks with one atomic
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&counts[kk], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  keys[p] = kk;
-  ranks[p] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, kk, 1);
+  const bool start = lane == 0 || prev != kk;
+  const unsigned starts = __ballot_sync(0xffffffffu, start);
+  const unsigned upto = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+  const int run0 = 31 - __clz(starts & upto);
+  const unsigned after = starts & ~upto;
+  const int run1 = after ? __ffs(after) - 1 : 32;
+  uint32_t b = 0;
+  if (start && valid) b = atomicAdd(&counts[kk], (uint32_t)(run1 - run0));
+  b = __shfl_sync(0xffffffffu, b, run0);
+  if (valid) {
+    keys[p] = kk;
+    ranks[p] = b + (uint32_t)(lane - run0);
+  }
 }
 
 // Copy particles back to the original order, in FP64: out[q * np + id[p]] =
