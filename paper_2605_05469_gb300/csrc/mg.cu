@@ -40,14 +40,12 @@ void mg_state_free(MgState* s) {
 
 namespace {
 
-#ifndef MG_TALL_PROLONG
-#define MG_TALL_PROLONG 0
-#endif
-
-// Whether kernel k of level L runs in the tall-block form.
+// Whether kernel k of level L runs in the tall-block form: the kernels with
+// the prolongation keep the small block (their coarse-value registers would
+// spill at the tall block's 64-register limit; measured no faster at 512^3).
 bool tall_form(const MgLevel& L, MgKer k) {
   const bool prolong = k == kResidProlong || k == kSmoothProlong;
-  return L.tall && (!prolong || MG_TALL_PROLONG);
+  return L.tall && !prolong;
 }
 
 // The plane-streamed kernel k in its small- or tall-block form.
