@@ -40,6 +40,11 @@ void mg_state_free(MgState* s) {
 
 namespace {
 
+// Shared memory of a small V-cycle block (the CG kernels' budget: three
+// blocks an SM; measured, four blocks with fewer stages were slower, the
+// kernels spilling at the 64-register limit that four blocks impose).
+constexpr size_t kMgSmemBudget = 72 * 1024;
+
 // Whether kernel k of level L runs in the tall-block form: the kernels with
 // the prolongation keep the small block (their coarse-value registers would
 // spill at the tall block's 64-register limit; measured no faster at 512^3).
@@ -118,8 +123,13 @@ int ensure_state(pic_ctx* c) {
     const int min_planes = L.N >= 256 ? 4 : (L.N >= 128 ? 2 : 1);
     for (int k = 0; k < kNumMgKer && !e; ++k) {
       const bool t = tall_form(L, (MgKer)k);
-      e = slab_geometry<float, float, float, 1>(c, L.N, mg_kernel((MgKer)k, t), &L.geo[k], &L.smem[k], t,
-                                                min_planes);
+      // pre-smoothing streams r alone, the others x and r
+      if (k == kPre)
+        e = slab_geometry<float, float, float, 1>(c, L.N, mg_kernel((MgKer)k, t), &L.geo[k], &L.smem[k], t,
+                                                  min_planes, kMgSmemBudget);
+      else
+        e = slab_geometry<float, float, float, 2>(c, L.N, mg_kernel((MgKer)k, t), &L.geo[k], &L.smem[k], t,
+                                                  min_planes, kMgSmemBudget);
       size_t& m = smax[t][k];
       if (L.smem[k] > m) m = L.smem[k];
     }

@@ -53,39 +53,32 @@ __device__ __forceinline__ float apply_hat(const float* __restrict__ x, int N, i
 // Plane-streamed kernels (N % 4 == 0)
 // ---------------------------------------------------------------------------
 
-// The coarse values that the prolongation adds to 4 fine cells (x0..x0+3,
-// x0 % 4 == 0) of fine row j, plane z (fine grid N, coarse Nc = N / 2 even):
-// fine x = 2I is coarse I, fine x = 2I+1 the mean of I and I+1, likewise in y
-// and z, so the cells need coarse x-nodes I0, I0+1, I0+2 (I0 = x0 / 2) of the
-// 1, 2 or 4 coarse (row, plane) pairs around (j / 2, z / 2). Loaded into
-// registers (q = 0..3: (J0, K0), (J1, K0), (J0, K1), (J1, K1); unused pairs
-// stay zero) so that the loads of the next plane can be issued early.
-struct CoarseRows {
-  float2 a[4];  // coarse I0, I0 + 1
-  float b[4];   // coarse I0 + 2 (periodic)
-};
-
-__device__ __forceinline__ void coarse_rows_load(CoarseRows& R, const float* __restrict__ ec, int Nc, int x0, int j,
-                                                 int z) {
+// v += (P e_c) on the 4 fine cells x0..x0+3 (x0 % 4 == 0) of fine row j,
+// plane z (fine grid N, coarse Nc = N / 2 even): fine x = 2I is coarse I, fine
+// x = 2I+1 the mean of I and I+1, likewise in y and z, so the cells need
+// coarse x-nodes I0, I0+1, I0+2 (I0 = x0 / 2) summed over the 1, 2 or 4
+// coarse (row, plane) pairs around (j / 2, z / 2).
+__device__ __forceinline__ void add_prolonged(V4<float>& v, const float* __restrict__ ec, int Nc, int x0, int j,
+                                              int z) {
   const int I0 = x0 >> 1;
   const int I2 = (I0 + 2 == Nc) ? 0 : I0 + 2;
   const int J0 = j >> 1, K0 = z >> 1;
   const int J1 = (J0 + 1 == Nc) ? 0 : J0 + 1;
   const int K1 = (K0 + 1 == Nc) ? 0 : K0 + 1;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const bool use = (!(q & 1) || (j & 1)) && (!(q & 2) || (z & 1));
-    const int J = (q & 1) ? J1 : J0, K = (q & 2) ? K1 : K0;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  auto acc = [&](int J, int K) {
     const float* row = ec + ((size_t)K * Nc + J) * Nc;
-    R.a[q] = use ? __ldg(reinterpret_cast<const float2*>(row + I0)) : make_float2(0.f, 0.f);
-    R.b[q] = use ? __ldg(row + I2) : 0.f;
+    const float2 a = __ldg(reinterpret_cast<const float2*>(row + I0));
+    s0 += a.x;
+    s1 += a.y;
+    s2 += __ldg(row + I2);
+  };
+  acc(J0, K0);
+  if (j & 1) acc(J1, K0);
+  if (z & 1) {
+    acc(J0, K1);
+    if (j & 1) acc(J1, K1);
   }
-}
-
-__device__ __forceinline__ void coarse_rows_add(V4<float>& v, const CoarseRows& R, int j, int z) {
-  const float s0 = (R.a[0].x + R.a[1].x) + (R.a[2].x + R.a[3].x);
-  const float s1 = (R.a[0].y + R.a[1].y) + (R.a[2].y + R.a[3].y);
-  const float s2 = (R.b[0] + R.b[1]) + (R.b[2] + R.b[3]);
   const float wyz = ((j & 1) ? 0.5f : 1.f) * ((z & 1) ? 0.5f : 1.f);
   v.v[0] += wyz * s0;
   v.v[1] += wyz * (0.5f * (s0 + s1));
@@ -132,6 +125,9 @@ enum : int { kResid = 0, kSmooth = 1 };
 //   kResid : out = r - A^ x'        (and xout = x' when PROLONG)
 //   kSmooth: out = x' + w (r - A^ x')
 // out and xout must not alias x (other blocks read x's halo rows).
+// x streams through the slab stages together with r (r's own cells are
+// kept in a two-deep register queue at ingest: the body of plane t runs one
+// arriving plane later).
 template <int MODE, bool PROLONG, bool TALL>
 __global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_mg_stencil(
     const float* __restrict__ x, const float* __restrict__ r, float* __restrict__ out, float* __restrict__ xout,
@@ -139,50 +135,36 @@ __global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_mg_stenci
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStages];
   if (done && *done) return;
-  const StageLayout<float, float, 1> lay(g.rows, g.N);
+  const StageLayout<float, float, 2> lay(g.rows, g.N);
   const float w = kOmega / 6.0f;
-  V4<float> cb;
-  auto start = [&](const Slab& s) { cb = ldg4(r + cell_offset(s, 0)); };
-  // the coarse values of the thread's own cells for the next plane are
-  // loaded while the current plane is processed (halo rows load on demand)
-  CoarseRows next;
-  int next_z = -1, next_j = -1;
   const int Nc = g.N >> 1;
+  V4<float> r_prev, r_cur;
+  auto start = [&](const Slab&) {};
   auto ingest = [&](int st, size_t e, const Slab& s, int z) {
     V4<float> v = ld4(lay.v0(smem, st) + e);
     if (PROLONG) {
       int j, x0;
       stage_row_x(s, e, j, x0);
-      const bool own = e == (size_t)s.srow * s.N + s.x0;
-      if (own && z == next_z && j == next_j) {
-        coarse_rows_add(v, next, j, z);
-      } else {
-        CoarseRows now;
-        coarse_rows_load(now, ec, Nc, x0, j, z);
-        coarse_rows_add(v, now, j, z);
-      }
-      if (own) {
-        next_z = z + 1 == s.N ? 0 : z + 1;
-        next_j = j;
-        coarse_rows_load(next, ec, Nc, x0, j, next_z);
-      }
+      add_prolonged(v, ec, Nc, x0, j, z);
+    }
+    if (e == (size_t)s.srow * s.N + s.x0) {
+      r_prev = r_cur;
+      r_cur = ld4(lay.v1(smem, st) + e);
     }
     return v;
   };
   auto body = [&](const Slab& s, int t, const float* pb, const V4<float>& zm, const V4<float>& c,
                   const V4<float>& zp) {
-    V4<float> nb = cb;
-    if (t + 1 < s.ZC) nb = ldg4(r + cell_offset(s, t + 1));
     const V4<float> ax = stencil_q(pb, s, zm, c, zp);
     const size_t off = cell_offset(s, t);
     V4<float> o;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) o.v[i] = MODE == kResid ? cb.v[i] - ax.v[i] : c.v[i] + w * (cb.v[i] - ax.v[i]);
-    cb = nb;
+    for (int i = 0; i < 4; ++i)
+      o.v[i] = MODE == kResid ? r_prev.v[i] - ax.v[i] : c.v[i] + w * (r_prev.v[i] - ax.v[i]);
     st4(out + off, o);
     if (PROLONG && MODE == kResid) st4(xout + off, c);
   };
-  stream_slab<float, float, float, 1>(g, smem, bars, x, (const float*)nullptr, err, start, ingest, body);
+  stream_slab<float, float, float, 2>(g, smem, bars, x, r, err, start, ingest, body);
 }
 
 // rc = 4 R res onto the coarse grid Nf/2 (Nf % 4 == 0): each thread the

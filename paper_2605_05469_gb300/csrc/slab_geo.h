@@ -20,13 +20,15 @@ constexpr size_t kSmemMax = 226 * 1024;
 // as the budget allows (at least three, at most kMaxStages). The persistent
 // grid is the resident blocks of `kernel`, but at least `min_planes` planes
 // per block. Sets the kernel's dynamic shared-memory limit to the size
-// returned in *smem.
+// returned in *smem. budget_bytes (0: the defaults above) replaces the
+// shared-memory budget of a small block.
 template <typename TP, typename A, typename B, int NV, typename K>
 int slab_geometry(pic_ctx* c, int N, K kernel, StreamGeo* out, size_t* smem, bool tall = false,
-                  int min_planes = 4) {
+                  int min_planes = 4, size_t budget_bytes = 0) {
   if (N < 4 || N % 4) return PIC_EINVAL;
   const int cap = tall ? kStreamTall : kStreamSmall;
-  const size_t budget = tall ? kSmemTall : (sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32);
+  const size_t budget = tall ? kSmemTall
+                             : (budget_bytes ? budget_bytes : (sizeof(TP) == 8 ? kSmemBudget64 : kSmemBudget32));
   StreamGeo g{};
   bool found = false;
   for (int pass = 0; pass < 2 && !found; ++pass) {
