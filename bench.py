@@ -63,6 +63,18 @@ MG_BYTES = {
 # with the learned smoother the prolongation slot is the residual of x + P e_c:
 # read x, e_c, r; write res and x + P e_c
 MG_BYTES_PROLONG_RESID = 16.5
+# algorithmic bytes of the particle kernels: per particle, and per grid node
+PARTICLE_BYTES = {
+    # scatter: read and write the 64-byte record, read its key and rank, one
+    # offset per particle (cached: counted once per cell)
+    "scatter": (136, 4),
+    # deposit: the record's first 32-byte sector (offsets), 8 corner sums per
+    # cell written and read back (8 B each), the cell offsets, rho written
+    "deposit": (32, 64 + 64 + 4 + 8),
+    # push: read and write the 64-byte record, its key and rank; E (3 x 8 B) read
+    # once per node
+    "push": (136, 24),
+}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
 
@@ -351,7 +363,22 @@ def run_ours(args):
             vcycle = {"avg_us": round(avg_ms * 1e3, 2), "samples": prof["ker_samples"]["precond"],
                       "bytes_per_fine_cell": round(bpc, 3), "gbs": round(bpc * n / (avg_ms * 1e-3) / 1e9, 1),
                       "note": "one V-cycle, every level; bytes of the plane-streamed levels"}
-    dom = max(rows, key=lambda k: rows[k]["avg_us"]) if rows else None
+    # the particle kernels (one launch each per step)
+    np_ = 0 if solve_only else ppc * n
+    for k, (bp, bn) in PARTICLE_BYTES.items():
+        if not np_ or not prof["ker_samples"].get(k):
+            continue
+        avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
+        b = bp * np_ + bn * n
+        rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "bytes_per_particle": bp,
+                   "bytes_per_node": bn, "gbs": b / (avg_ms * 1e-3) / 1e9, "launches_per_step": 1}
+    # the dominant kernel: the largest device time per step (solver kernels
+    # run once per iteration)
+    it_mean = statistics.mean(i["iters"] for i in infos) if infos else 1
+
+    def per_step(k):
+        return rows[k]["avg_us"] * rows[k].get("launches_per_step", it_mean)
+    dom = max(rows, key=per_step) if rows else None
     kname = {("pap", 1): "k_cg_pap<float>", ("update", 1): "k_fcg_update32", ("dot", 1): "k_fcg_dot",
              ("pap", 0): "k_cg_pap<double,true>", ("update", 0): "k_cg_update64",
              ("mg_pre", 1): "k_mg_pre (finest level)", ("mg_resid", 1): "k_mg_stencil<kResid> (finest level)",
@@ -378,6 +405,16 @@ def run_ours(args):
                 "frac": round(r["tflops"] / FP32_PEAK_TFLOPS, 4),
                 "peak_source": "measured FP32 FMA loop (no FP32 figure in MEASURED_PEAKS.json)",
                 "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n, "avg_launch_us": round(r["avg_us"], 2)}
+    elif dom in PARTICLE_BYTES:
+        r = rows[dom]
+        b = r["bytes_per_particle"] * np_ + r["bytes_per_node"] * n
+        roof = {"kernel": {"scatter": "k_scatter (sort: 64-byte records to their cells)",
+                           "deposit": "k_deposit_cells + k_deposit_nodes (CIC scatter)",
+                           "push": "k_gather_push (CIC gather + leapfrog, double-float)"}[dom],
+                "bound": "hbm", "achieved": round(r["gbs"], 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(r["gbs"] / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "algorithmic_bytes": b, "avg_launch_us": round(r["avg_us"], 2),
+                "note": "dominant kernel of the whole step (device time per step)"}
     elif dom is not None:
         r = rows[dom]
         if kp == 1:

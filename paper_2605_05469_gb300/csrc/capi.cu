@@ -464,9 +464,11 @@ int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift
          c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
          (const float2*)(c->E + c->n), (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
          df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts);
+  if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -614,9 +616,10 @@ int pic_deposit(pic_ctx* c, double* rho) {
     launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
     launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
     const unsigned sblocks = (unsigned)(((c->np + 31) / 32 * 32 + 255) / 256);
+    const int slot = c->prof_on ? c->ker[PIC_KER_SCATTER].begin(c->stream) : -1;
     launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
-           (const uint32_t*)c->ranks,
-                                              c->offsets);
+           (const uint32_t*)c->ranks, (const uint32_t*)c->offsets);
+    if (c->prof_on) c->ker[PIC_KER_SCATTER].end(slot, c->stream);
     CK(cudaGetLastError());
     c->cur ^= 1;
     c->sorted = true;
@@ -626,11 +629,13 @@ int pic_deposit(pic_ctx* c, double* rho) {
   if (!c->dep && (e = dalloc(&c->dep, 8 * c->n))) return e;
   const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
   const unsigned cblocks = (unsigned)((c->n + 255) / 256);
+  const int slot = c->prof_on ? c->ker[PIC_KER_DEPOSIT].begin(c->stream) : -1;
   launch(c, k_deposit_cells, cblocks, 256, 0, (const PRec*)c->prec[c->cur], (const uint32_t*)c->offsets, c->dep,
          c->n);
   const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
   launch(c, k_deposit_nodes, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)c->dep, rho, c->N,
          qscale);
+  if (c->prof_on) c->ker[PIC_KER_DEPOSIT].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
 }
