@@ -16,4 +16,7 @@ pic      Landau initial condition, CIC scatter, 7-point FD operator,
          leapfrog push, field energy, and the full PIC loop.
 cnn      3x3x3 conv3d forward/backward by direct loops, the 4-layer CNN
          preconditioner, its loss, Adam, and flexible CG (FCG(1)).
+mg       geometric multigrid V-cycle preconditioner (textbook, beyond the
+         paper): transfers, damped Jacobi, the cycle.
+fft      FFT pseudo-spectral periodic Poisson solve (Sec. 3.1): phi and E.
 """
