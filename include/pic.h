@@ -140,6 +140,29 @@ int pic_sync_velocity(pic_ctx *c, const double *phi, double dt);
  * central differences, d = x, y, z. `out_w` is host memory; synchronises. */
 int pic_field_energy(pic_ctx *c, const double *phi, double out_w[3]);
 
+/* The FFT pseudo-spectral periodic solve (Sec. 3.1), the paper's other
+ * solver: phi = F^-1(rho_hat / k^2) and, when E is not NULL,
+ * E_d = F^-1(-i k_d rho_hat / k^2), k = 2 pi m / L (3-D FP64 transforms by
+ * cuFFT). The k = 0 mode is zero (rho's mean is removed; phi has mean zero);
+ * for the derivative along d its Nyquist mode m_d = N/2 is zero. rho, phi:
+ * device FP64 [N^3], x fastest (rho is not modified); E: device FP64
+ * [3 N^3] (E_x, E_y, E_z) or NULL. The context keeps the transform plans and
+ * two complex buffers of N^2 (N/2 + 1) values. Returns PIC_ECUDA if cuFFT
+ * fails (including out of memory for its plans). */
+int pic_fft_solve(pic_ctx *c, const double *rho, double *phi, double *E);
+
+/* S6 with a given node field instead of -grad phi (the FFT scheme's spectral
+ * field): E device FP64 [3 N^3] (E_x, E_y, E_z). Same leapfrog as
+ * pic_gather_push. */
+int pic_gather_push_field(pic_ctx *c, const double *E, double dt);
+
+/* pic_sync_velocity with a given node field E (device FP64 [3 N^3]). */
+int pic_sync_velocity_field(pic_ctx *c, const double *E, double dt);
+
+/* S7 from a given node field: out_w[d] = h^3 sum_i E_{d,i}^2 (host memory;
+ * synchronises). */
+int pic_field_energy_E(pic_ctx *c, const double *E, double out_w[3]);
+
 /* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
  * the ORIGINAL particle order (index p of pic_init), to device memory
  * (on_device = 1) or host memory (0; synchronises). `half_step` (may be

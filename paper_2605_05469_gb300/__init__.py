@@ -9,7 +9,10 @@ Module-level functions carry the C names (``pic_create``, ``pic_init``,
 ``pic_deposit``, ``poisson_solve``, ``poisson_solve_ex``, ``pic_gather_push``,
 ``pic_sync_velocity``, ``pic_field_energy``, ``pic_get_particles``,
 ``pic_apply_laplacian``, ``pic_profile_enable``, ``pic_profile_read``,
-``pic_destroy``); ``Context`` bundles them.
+``pic_destroy``); ``Context`` bundles them, and calls the other entry points
+(the spectral solve ``pic_fft_solve``, ``pic_gather_push_field``,
+``pic_sync_velocity_field``, ``pic_field_energy_E``, the learned
+preconditioner's and the V-cycle's) as methods.
 """
 import ctypes
 import os
@@ -114,6 +117,10 @@ _SIGS = {
     "pic_cnn_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_cnn_set_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_mg_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "pic_fft_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_gather_push_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    "pic_sync_velocity_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    "pic_field_energy_E": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pic_cnn_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                        ctypes.c_int]),
     "pic_cnn_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
@@ -296,6 +303,23 @@ class Context:
 
     def field_energy(self, phi):
         return pic_field_energy(self.h, phi, self.n)
+
+    def fft_solve(self, rho, phi, E=None):
+        """FFT pseudo-spectral solve: phi (and E [3 N^3] if given) from rho."""
+        _check(lib().pic_fft_solve(self.h, _dptr(rho, "float64", self.n, "rho"), _dptr(phi, "float64", self.n, "phi"),
+                                   None if E is None else _dptr(E, "float64", 3 * self.n, "E")), "pic_fft_solve")
+
+    def gather_push_field(self, E, dt):
+        _check(lib().pic_gather_push_field(self.h, _dptr(E, "float64", 3 * self.n, "E"), dt), "pic_gather_push_field")
+
+    def sync_velocity_field(self, E, dt):
+        _check(lib().pic_sync_velocity_field(self.h, _dptr(E, "float64", 3 * self.n, "E"), dt),
+               "pic_sync_velocity_field")
+
+    def field_energy_E(self, E):
+        out = (ctypes.c_double * 3)()
+        _check(lib().pic_field_energy_E(self.h, _dptr(E, "float64", 3 * self.n, "E"), out), "pic_field_energy_E")
+        return np.array(list(out))
 
     def particles(self):
         return pic_get_particles(self.h, self.num_particles)

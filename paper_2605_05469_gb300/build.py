@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills"]
-UNITS = ["capi.cu", "cnn.cu", "mg.cu", "noalloc.cu"]
+UNITS = ["capi.cu", "cnn.cu", "mg.cu", "fft.cu", "noalloc.cu"]
 
 
 def nvcc():
@@ -50,7 +50,8 @@ def build(verbose=False):
         results = list(ex.map(lambda u: _compile(u, verbose), UNITS))
     objs = [o for o, _ in results]
     tmp = OUT + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft", "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

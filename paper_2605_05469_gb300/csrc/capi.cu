@@ -7,6 +7,7 @@
 
 #include "cnn.h"
 #include "mg.h"
+#include "fft.h"
 #include "ctx.h"
 #include "particle_kernels.cuh"
 #include "slab_geo.h"
@@ -453,15 +454,21 @@ float2 df_const(double x) {
   return make_float2(hi, (float)(x - (double)hi));
 }
 
-int launch_push(pic_ctx* c, const double* phi, double kick, double dt, int drift) {
+// The push with the node field -grad phi by central differences (phi), or a
+// given node field (Efield: 3 n FP64, E_x, E_y, E_z; phi == nullptr).
+int launch_push(pic_ctx* c, const double* phi, const double* Efield, double kick, double dt, int drift) {
   int e;
   if ((e = ensure_E(c))) return e;
   const int sb = streaming_blocks(c);
-  float2* phid = c->E + 3 * c->n;
-  launch(c, k_phi_df, sb, 256, 0, phi, phid, c->n);
-  const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
-  launch(c, k_gradient, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)phid, c->E, c->E + c->n,
-         c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
+  if (phi) {
+    float2* phid = c->E + 3 * c->n;
+    launch(c, k_phi_df, sb, 256, 0, phi, phid, c->n);
+    const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
+    launch(c, k_gradient, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)phid, c->E, c->E + c->n,
+           c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
+  } else {
+    launch(c, k_phi_df, sb, 256, 0, Efield, c->E, 3 * c->n);
+  }
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
@@ -553,6 +560,7 @@ void pic_destroy(pic_ctx* c) {
   }
   cnn_state_free(c->cnn);
   mg_state_free(c->mg);
+  fft_state_free(c->fft);
   delete c;
 }
 
@@ -683,7 +691,20 @@ int pic_gather_push(pic_ctx* c, const double* phi, double dt) {
   const double kick = c->half_step ? dt : 0.5 * dt;
   PhaseScope ps(c, PIC_PHASE_PUSH);
   int e;
-  if ((e = launch_push(c, phi, kick, dt, 1))) return e;
+  if ((e = launch_push(c, phi, nullptr, kick, dt, 1))) return e;
+  c->half_step = true;
+  c->keys_valid = true;
+  c->sorted = false;
+  return PIC_OK;
+}
+
+int pic_gather_push_field(pic_ctx* c, const double* E, double dt) {
+  if (!c || !dev_ptr_ok(E) || !isfinite(dt)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  const double kick = c->half_step ? dt : 0.5 * dt;
+  PhaseScope ps(c, PIC_PHASE_PUSH);
+  int e;
+  if ((e = launch_push(c, nullptr, E, kick, dt, 1))) return e;
   c->half_step = true;
   c->keys_valid = true;
   c->sorted = false;
@@ -695,8 +716,35 @@ int pic_sync_velocity(pic_ctx* c, const double* phi, double dt) {
   if (!c->has_grid || c->np == 0) return PIC_ESTATE;
   if (!c->half_step) return PIC_OK;
   int e;
-  if ((e = launch_push(c, phi, 0.5 * dt, dt, 0))) return e;
+  if ((e = launch_push(c, phi, nullptr, 0.5 * dt, dt, 0))) return e;
   c->half_step = false;
+  return PIC_OK;
+}
+
+int pic_sync_velocity_field(pic_ctx* c, const double* E, double dt) {
+  if (!c || !dev_ptr_ok(E) || !isfinite(dt)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  if (!c->half_step) return PIC_OK;
+  int e;
+  if ((e = launch_push(c, nullptr, E, 0.5 * dt, dt, 0))) return e;
+  c->half_step = false;
+  return PIC_OK;
+}
+
+int pic_field_energy_E(pic_ctx* c, const double* E, double out_w[3]) {
+  if (!c || !dev_ptr_ok(E) || !out_w) return PIC_EINVAL;
+  if (!c->has_grid) return PIC_ESTATE;
+  const int sb = streaming_blocks(c);
+  {
+    PhaseScope ps(c, PIC_PHASE_ENERGY);
+    launch(c, k_field_energy_E, sb, 256, 0, E, c->n, c->grid.h * c->grid.h * c->grid.h, c->out3, c->partials,
+           c->counter);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->out3_host, c->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int e;
+  if ((e = sync_status(c))) return e;
+  for (int d = 0; d < 3; ++d) out_w[d] = c->out3_host[d];
   return PIC_OK;
 }
 

@@ -7,6 +7,7 @@ namespace pic {
 
 struct CnnState;  // learned-preconditioner state, see cnn.cu
 struct MgState;   // multigrid hierarchy, see mg.cu
+struct FftState;  // spectral solve plans and buffers, see fft.cu
 
 struct SolverWs {
   // FP64 judge
@@ -110,6 +111,7 @@ struct pic_ctx {
   int cnn_apply_mode = 0;  // PIC_CNN_APPLY_*
   // multigrid preconditioner (level buffers)
   pic::MgState* mg = nullptr;
+  pic::FftState* fft = nullptr;
 };
 
 namespace pic {

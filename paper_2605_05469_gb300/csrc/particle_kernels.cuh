@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(256) k_deposit_nodes(const float2* __restrict_
 // Ex = (phi[i-1] - phi[i+1]) / 2h. phi is converted to double-float once per
 // node (FP64 operations), the differences run in double-float.
 // ---------------------------------------------------------------------------
+// (also converts a given 3 n node field)
 __global__ void __launch_bounds__(256) k_phi_df(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
@@ -421,6 +422,26 @@ __global__ void __launch_bounds__(256) k_gradient(const float2* __restrict__ phi
     Ex[c] = df_pack(df_mul(df_sub(xm, xp), s));
     Ey[c] = df_pack(df_mul(df_sub(ym, yp), s));
     Ez[c] = df_pack(df_mul(df_sub(zm, zp), s));
+  }
+}
+
+// S7 for a given node field (the spectral solve's): W_d = h^3 sum E_d^2.
+__global__ void __launch_bounds__(256) k_field_energy_E(const double* __restrict__ E, size_t n, double h3,
+                                                        double* out3, double* partials, unsigned* counter) {
+  double a[3] = {0.0, 0.0, 0.0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double v = __ldg(E + (size_t)d * n + c);
+      a[d] = fma(v, v, a[d]);
+    }
+  }
+  double tot[3];
+  if (grid_reduce_last<3>(a, partials, counter, tot) && threadIdx.x == 0) {
+    out3[0] = h3 * tot[0];
+    out3[1] = h3 * tot[1];
+    out3[2] = h3 * tot[2];
   }
 }
 
