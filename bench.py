@@ -117,12 +117,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn"], default="mg",
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "fft"], default="mg",
                     help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
                          "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
                          "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
-                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge. The learned "
-                         "solvers are always trained and timed in the solve comparison as well")
+                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; fft: the "
+                         "paper's other scheme, the FFT pseudo-spectral solve (cuFFT FP64) with the spectral field "
+                         "pushed to the particles. The learned solvers are always trained and timed in the solve "
+                         "comparison as well")
     ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
@@ -237,16 +239,30 @@ def run_ours(args):
         rho = torch.empty(n, dtype=torch.float64, device="cuda")
     infos = []
 
+    use_fft = args.solver == "fft"
+    E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda") if use_fft else None
+
+    def solve_into(rho_, phi_):
+        if use_fft:
+            # direct solve: no iterations or residual; its time is the solve phase's
+            c.fft_solve(rho_, phi_, E3)
+            return {"iters": 0, "t_ms": None, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
+        return c.solve(rho_, phi_, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
+
     def step(record):
         if solve_only:
             phi.zero_()
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
+            info = solve_into(rho, phi)
             W = None
         else:
             c.deposit(rho)
-            info = c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
-            W = c.field_energy(phi)
-            c.gather_push(phi, DT)
+            info = solve_into(rho, phi)
+            if use_fft:
+                W = c.field_energy_E(E3)
+                c.gather_push_field(E3, DT)
+            else:
+                W = c.field_energy(phi)
+                c.gather_push(phi, DT)
         if record:
             infos.append(info)
         return W
@@ -305,7 +321,7 @@ def run_ours(args):
     for _ in range(reps):
         rho.copy_(rho_host, non_blocking=True)
         phi.zero_()
-        c.solve(rho, phi, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
+        solve_into(rho, phi)
         phi_host.copy_(phi, non_blocking=True)
     torch.cuda.synchronize()
     e2e_solve = {"value": reps / (time.perf_counter() - t0), "unit": "solves/s (cold start)",
@@ -431,7 +447,8 @@ def run_ours(args):
                     "algorithmic_bytes": r["bytes_per_cell"] * n, "avg_launch_us": round(r["avg_us"], 2)}
 
     iters = [i["iters"] for i in infos]
-    solve_ms = [i["t_ms"] for i in infos]
+    solve_ms = ([i["t_ms"] for i in infos] if not use_fft else
+                [prof["phase_ms"]["solve"] / max(1, prof["phase_calls"]["solve"])])
     out = {
         "metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
@@ -440,13 +457,15 @@ def run_ours(args):
                   "f64 particles/grid; solve f32 vectors + f64 reductions" +
                   ((f"; {'bf16 tensor-core' if args.cnn_apply == 'tc' else args.cnn_apply} "
                     "9^3 learned preconditioner") if pc == pg.PC_CNN else "") +
-                  ("; f32 multigrid V-cycle" if pc == pg.PC_MG else "") +
+                  ("; f32 multigrid V-cycle" if pc == pg.PC_MG and not use_fft else "") +
+                  ("; FP64 spectral solve (cuFFT)" if use_fft else "") +
                   ("; f32 multigrid V-cycle, learned finest-level smoother" if pc == pg.PC_MG_CNN else "")),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
                                (f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc ({ppc * n} particles), "
-                                f"solve to rel-res {TOL:g}, dt {DT}"),
+                                + ("FFT pseudo-spectral solve with the spectral field" if use_fft else
+                                   f"solve to rel-res {TOL:g}") + f", dt {DT}"),
                    "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
                    "warm_start": True, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
@@ -536,7 +555,40 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
             learned_roof = tc_roofline(prof, n)
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
                      "converged": bool(best["converged"])}
+    # the paper's FFT scheme: the spectral solve of the same right-hand side
+    # (phi and the three spectral field components), cold, CUDA-event timed
+    E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    c.fft_solve(rho, phi, E3)  # plans
+    best = None
+    for _ in range(max(1, reps)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.fft_solve(rho, phi, E3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None or t < best else best
+    res["fft_spectral_phi_and_E"] = {"s": best, "note": "direct solve of the continuous-symbol equation "
+                                                        "(Sec. 3.1), not the finite-difference system"}
+    best = None
+    for _ in range(max(1, reps)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.fft_solve(rho, phi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None or t < best else best
+    res["fft_spectral_phi"] = {"s": best, "note": "phi alone: one forward and one inverse transform"}
+    del E3
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
+    res["fp64_pcg_vs_fft_time_ratio"] = res["fp64_jacobi_pcg"]["s"] / res["fft_spectral_phi_and_E"]["s"]
     res["speedup_multigrid_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_multigrid"]["s"]
     if with_cnn:
         res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
@@ -583,6 +635,13 @@ def oracle_iteration_seconds(N, solver):
     h = L / Ns
     b = inputs.landau_noise_rhs(Ns, 1)
     x0 = np.zeros(Ns ** 3)
+    if solver == "fft":
+        from oracle import fft as offt
+        h = L / N
+        b = inputs.landau_noise_rhs(N, 1)
+        t0 = time.perf_counter()
+        offt.spectral_solve(b, N, L)
+        return time.perf_counter() - t0, f"one spectral solve (numpy FFT, phi and E) on the full {N}^3 grid"
     if solver in ("mg", "cnn", "mg_cnn"):
         ws = ocnn.init_weights(0)
 
@@ -620,6 +679,8 @@ def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", reference_iters=None, 
     n = N ** 3
     t_cg, cg_desc = oracle_iteration_seconds(N, solver)
     it = reference_iters if reference_iters else iters_per_solve
+    if solver == "fft":
+        it = 1  # a direct solve
     if ppc == 0:
         step_s = t_cg * it
         return {"value": 1.0 / step_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
