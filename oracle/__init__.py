@@ -19,4 +19,6 @@ cnn      3x3x3 conv3d forward/backward by direct loops, the 4-layer CNN
 mg       geometric multigrid V-cycle preconditioner (textbook, beyond the
          paper): transfers, damped Jacobi, the cycle.
 fft      FFT pseudo-spectral periodic Poisson solve (Sec. 3.1): phi and E.
+ssor     red-black SSOR preconditioner (the paper's PCG configuration,
+         Sec. 4.1).
 """
