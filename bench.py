@@ -117,11 +117,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "fft"], default="mg",
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft"], default="mg",
                     help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
                          "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
                          "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
-                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; fft: the "
+                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; ssor: the "
+                         "paper's PCG configuration (red-black SSOR, 4 inner, 2 outer, damping pi/2); fft: the "
                          "paper's other scheme, the FFT pseudo-spectral solve (cuFFT FP64) with the spectral field "
                          "pushed to the particles. The learned solvers are always trained and timed in the solve "
                          "comparison as well")
@@ -219,7 +220,8 @@ def run_ours(args):
     N, ppc = args.N, args.ppc
     n = N ** 3
     prec = pg.PREC_FP64 if args.solver == "fp64" else pg.PREC_MIXED
-    pc = {"cnn": pg.PC_CNN, "mg": pg.PC_MG, "mg_cnn": pg.PC_MG_CNN}.get(args.solver, pg.PC_JACOBI)
+    pc = {"cnn": pg.PC_CNN, "mg": pg.PC_MG, "mg_cnn": pg.PC_MG_CNN, "ssor": pg.PC_SSOR}.get(args.solver,
+                                                                                          pg.PC_JACOBI)
     stream = torch.cuda.current_stream()
     solve_only = args.workload == "solve"
     weights, train_info = None, None
@@ -528,7 +530,8 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
     timed region."""
     res = {}
     cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI),
-             ("mixed_fcg_multigrid", pg.PREC_MIXED, pg.PC_MG)]
+             ("mixed_fcg_multigrid", pg.PREC_MIXED, pg.PC_MG),
+             ("mixed_cg_ssor_paper_configuration", pg.PREC_MIXED, pg.PC_SSOR)]
     if with_cnn:
         cases.append(("mixed_fcg_learned", pg.PREC_MIXED, pg.PC_CNN))
         cases.append(("mixed_fcg_learned_fp32", pg.PREC_MIXED, pg.PC_CNN))
@@ -590,6 +593,7 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
     res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
     res["fp64_pcg_vs_fft_time_ratio"] = res["fp64_jacobi_pcg"]["s"] / res["fft_spectral_phi_and_E"]["s"]
     res["speedup_multigrid_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_multigrid"]["s"]
+    res["speedup_ssor_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_cg_ssor_paper_configuration"]["s"]
     if with_cnn:
         res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
         res["speedup_learned_fp32_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned_fp32"]["s"]
@@ -631,7 +635,7 @@ def oracle_iteration_seconds(N, solver):
     from paper_2605_05469_gb300 import inputs
 
     L = 4.0 * np.pi
-    Ns = min(N, {"mg": 128, "cnn": 32, "mg_cnn": 32}.get(solver, N))
+    Ns = min(N, {"mg": 128, "cnn": 32, "mg_cnn": 32, "ssor": 64}.get(solver, N))
     h = L / Ns
     b = inputs.landau_noise_rhs(Ns, 1)
     x0 = np.zeros(Ns ** 3)
@@ -642,21 +646,24 @@ def oracle_iteration_seconds(N, solver):
         t0 = time.perf_counter()
         offt.spectral_solve(b, N, L)
         return time.perf_counter() - t0, f"one spectral solve (numpy FFT, phi and E) on the full {N}^3 grid"
-    if solver in ("mg", "cnn", "mg_cnn"):
+    if solver in ("mg", "cnn", "mg_cnn", "ssor"):
+        from oracle import ssor as ossor
         ws = ocnn.init_weights(0)
 
         def net(q):
             return h * h * ocnn.forward(q.reshape(Ns, Ns, Ns), ws)[0].reshape(-1)
         prec = {"mg": lambda r: omg.vcycle(r, Ns, h),
                 "cnn": lambda r: ocnn.precondition(r, ws, Ns, h),
-                "mg_cnn": lambda r: omg.vcycle(r, Ns, h, smoother=net)}[solver]
+                "mg_cnn": lambda r: omg.vcycle(r, Ns, h, smoother=net),
+                "ssor": lambda r: ossor.ssor(r, Ns, h)}[solver]
         k_it = 1
         t0 = time.perf_counter()
         ocnn.fcg(b, x0, Ns, h, 0.0, k_it, prec)   # k_it iterations + the initial preconditioning
         dt = (time.perf_counter() - t0) / (k_it + 1)
         what = {"mg": "flexible-CG iterations with the multigrid V-cycle",
                 "cnn": "flexible-CG iterations with the network preconditioner",
-                "mg_cnn": "flexible-CG iterations with the V-cycle and network smoother"}[solver]
+                "mg_cnn": "flexible-CG iterations with the V-cycle and network smoother",
+                "ssor": "CG iterations with the red-black SSOR preconditioner"}[solver]
     else:
         k_it = 3
         t0 = time.perf_counter()

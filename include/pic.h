@@ -66,8 +66,10 @@ enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 };
  * conclusion, Sec. 5, sets PCG beside the multigrid solvers of a cited
  * comparison; requires PIC_PREC_MIXED): MG smooths every level with
  * damped Jacobi, MG_CNN smooths the finest level with the learned network
- * (requires weights). See pic_mg_apply for the cycle. */
-enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1, PIC_PC_MG = 2, PIC_PC_MG_CNN = 3 };
+ * (requires weights). See pic_mg_apply for the cycle. SSOR is the paper's
+ * PCG configuration (Sec. 4.1, red-black ordering, 4 inner and 2 outer
+ * iterations, damping pi/2; requires PIC_PREC_MIXED); see pic_ssor_apply. */
+enum { PIC_PC_JACOBI = 0, PIC_PC_CNN = 1, PIC_PC_MG = 2, PIC_PC_MG_CNN = 3, PIC_PC_SSOR = 4 };
 
 typedef struct {
   int precision;         /* PIC_PREC_* */
@@ -139,6 +141,13 @@ int pic_sync_velocity(pic_ctx *c, const double *phi, double dt);
 /* S7 (Fig. 2 diagnostic): out_w[d] = h^3 sum_i E_{d,i}^2, E = -grad phi by
  * central differences, d = x, y, z. `out_w` is host memory; synchronises. */
 int pic_field_energy(pic_ctx *c, const double *phi, double out_w[3]);
+
+/* The red-black SSOR preconditioner by itself: z = M r on the scaled system
+ * (h^2 A) z = r, r and z device FP32 [N^3] (z is overwritten; r is not). From
+ * z = 0, two outer iterations of four forward SOR sweeps (red nodes, then
+ * black; red when i + j + k is even) and four backward sweeps (black, then
+ * red), damping pi/2 (Sec. 4.1); FP32. Enqueued on the context stream. */
+int pic_ssor_apply(pic_ctx *c, const float *r, float *z);
 
 /* The FFT pseudo-spectral periodic solve (Sec. 3.1), the paper's other
  * solver: phi = F^-1(rho_hat / k^2) and, when E is not NULL,

@@ -37,6 +37,7 @@ PC_JACOBI = 0
 PC_CNN = 1
 PC_MG = 2
 PC_MG_CNN = 3
+PC_SSOR = 4
 CNN_APPLY_TC = 0
 CNN_APPLY_FP32 = 1
 CNN_APPLY_LAYERS = 2
@@ -118,6 +119,7 @@ _SIGS = {
     "pic_cnn_set_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_mg_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "pic_fft_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_ssor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_gather_push_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "pic_sync_velocity_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "pic_field_energy_E": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -303,6 +305,11 @@ class Context:
 
     def field_energy(self, phi):
         return pic_field_energy(self.h, phi, self.n)
+
+    def ssor_apply(self, r, z):
+        """z = M r of the red-black SSOR preconditioner (FP32, scaled units)."""
+        _check(lib().pic_ssor_apply(self.h, _dptr(r, "float32", self.n, "r"), _dptr(z, "float32", self.n, "z")),
+               "pic_ssor_apply")
 
     def fft_solve(self, rho, phi, E=None):
         """FFT pseudo-spectral solve: phi (and E [3 N^3] if given) from rho."""

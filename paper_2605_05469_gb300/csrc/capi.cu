@@ -8,6 +8,7 @@
 #include "cnn.h"
 #include "mg.h"
 #include "fft.h"
+#include "ssor.h"
 #include "ctx.h"
 #include "particle_kernels.cuh"
 #include "slab_geo.h"
@@ -300,6 +301,7 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   // z = M r for the chosen preconditioner (enqueued on the context stream)
   auto precond = [&](const float* r, float* z, bool sample) -> int {
     if (pc == PIC_PC_CNN) return cnn_apply(c, r, z, &c->sc->rr, c->n);
+    if (pc == PIC_PC_SSOR) return ssor_apply(c, r, z, &c->sc->done);
     return mg_apply(c, r, z, pc == PIC_PC_MG_CNN, &c->sc->done, sample);
   };
   if (!w.xm[0]) {
@@ -655,7 +657,7 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   if (!(tol >= 0.0) || maxit < 0) return PIC_EINVAL;
   pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
   if (o) opts = *o;
-  if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_MG_CNN) return PIC_EINVAL;
+  if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_SSOR) return PIC_EINVAL;
   // status-check cadence: the multigrid solve converges in about ten
   // iterations, so its batches are single iterations (each iteration
   // launched past convergence still costs the launches of its kernels)
