@@ -75,6 +75,11 @@ PARTICLE_BYTES = {
     # once per node
     "push": (136, 24),
 }
+# DRAM traffic per particle of one launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over the particle count) measured by ncu on the
+# 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
+# count): it stands for the same kernels at other sizes
+MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.70, "scatter": 133.72}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
 
@@ -430,7 +435,11 @@ def run_ours(args):
                            "deposit": "k_deposit_cells + k_deposit_nodes (CIC scatter)",
                            "push": "k_gather_push (CIC gather + leapfrog, double-float)"}[dom],
                 "bound": "hbm", "achieved": round(r["gbs"], 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(r["gbs"] / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs", "traffic": None,
+                "frac": round(r["gbs"] / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": (round(MEASURED_TRAFFIC_PER_PARTICLE[dom] * np_) if dom in MEASURED_TRAFFIC_PER_PARTICLE
+                            else None),
+                "traffic_source": ("ncu DRAM bytes per particle at 128^3 x 8 ppc, scaled by the particle count"
+                                   if dom in MEASURED_TRAFFIC_PER_PARTICLE else None),
                 "algorithmic_bytes": b, "avg_launch_us": round(r["avg_us"], 2),
                 "note": "dominant kernel of the whole step (device time per step)"}
     elif dom is not None:
