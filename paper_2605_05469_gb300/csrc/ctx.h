@@ -153,6 +153,11 @@ void launch(pic_ctx* c, void (*kernel)(KArgs...), dim3 grid, unsigned block, siz
   kernel<<<grid, block, smem, c->stream>>>(args...);
   ++c->launches;
 }
+template <typename... KArgs, typename... Args>
+void launch(pic_ctx* c, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  kernel<<<grid, block, smem, c->stream>>>(args...);
+  ++c->launches;
+}
 
 // Phase timer around one public call (no-op unless profiling is on).
 struct PhaseScope {

@@ -18,6 +18,7 @@ struct MgLevel {
   float *x = nullptr, *r = nullptr, *t = nullptr, *res = nullptr;
   bool streamed = false;          // N % 4 == 0: plane-streamed kernels
   bool tall = false;              // N >= 512: one 1024-thread block per SM
+  bool zmarch = false;            // N % 128 == 0: z-marching pre-smoothing, residual, smoothing
   StreamGeo geo[kNumMgKer]{};
   size_t smem[kNumMgKer]{};
 };
@@ -116,6 +117,7 @@ int ensure_state(pic_ctx* c) {
     MgLevel& L = s->lev[l];
     L.streamed = L.N % 4 == 0;
     if (!L.streamed) continue;
+    L.zmarch = L.N % 128 == 0;
     // the tall block re-reads fewer halo rows on large grids (as for the CG
     // direction kernel); coarse levels are latency-bound: more blocks with
     // fewer planes each
@@ -183,6 +185,20 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
   // plane-streamed kernel k of level L; the finest level's launches are
   // timed into event pool `pool` when sampling
   sample = sample && c->prof_on;
+  // the z-marching form (levels whose size is a multiple of 128) of the
+  // pre-smoothing, residual and plain smoothing kernels
+  auto zmarch = [&](const MgLevel& L, int pool, auto kernel, const float* field, const float* aux, float* out,
+                    const float* ec_in = nullptr, float* xout = nullptr) {
+    const bool t = sample && &L == &s->lev[0];
+    const int slot = t ? c->ker[pool].begin(c->stream) : -1;
+    const unsigned tiles = (unsigned)(L.N / 128) * (unsigned)(L.N / 8);
+    // the longest chunk (a power of two dividing N) that still gives about
+    // four blocks an SM
+    int zc = mg::kZChunkMax;
+    while (zc > 4 && (long)tiles * (L.N / zc) < 4L * c->sms) zc /= 2;
+    launch(c, kernel, dim3(tiles, L.N / zc), dim3(32, 8), 0, field, aux, out, L.N, zc, done, ec_in, xout);
+    if (t) c->ker[pool].end(slot, c->stream);
+  };
   auto slab = [&](const MgLevel& L, MgKer k, int pool, auto kernel, auto... args) {
     const StreamGeo& g = L.geo[k];
     const bool t = sample && &L == &s->lev[0];
@@ -199,6 +215,8 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     const int g = grid_for(c, n);
     if (l == 0 && learned) {
       if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
+    } else if (L.zmarch) {
+      zmarch(L, PIC_KER_MG_PRE, mg::k_mg_zmarch<mg::kZPre, false>, rl(l), nul, xl(l));
     } else if (L.streamed) {
       slab(L, kPre, PIC_KER_MG_PRE, tall_form(L, kPre) ? mg::k_mg_pre<true> : mg::k_mg_pre<false>, rl(l), xl(l));
     } else {
@@ -206,7 +224,10 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
     }
     if (L.streamed) {
-      slab(L, kResid, PIC_KER_MG_RESID, tall_form(L, kResid) ? mg::k_mg_stencil<mg::kResid, false, true> : mg::k_mg_stencil<mg::kResid, false, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
+      if (L.zmarch)
+        zmarch(L, PIC_KER_MG_RESID, mg::k_mg_zmarch<mg::kZResid, false>, (const float*)xl(l), rl(l), L.res);
+      else
+        slab(L, kResid, PIC_KER_MG_RESID, tall_form(L, kResid) ? mg::k_mg_stencil<mg::kResid, false, true> : mg::k_mg_stencil<mg::kResid, false, false>, (const float*)xl(l), rl(l), L.res, nulw, nul);
       const int Nc = L.N / 2;
       const unsigned per_plane = (unsigned)(Nc / 2) * (unsigned)Nc;
       const unsigned bx = (per_plane + 255) / 256;
@@ -229,7 +250,10 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     const float* ec = xl(l + 1);
     if (l == 0 && learned) {
       // x' = x + P e_c (into t), res = r - A^ x', x = x' + K res
-      if (L.streamed) {
+      if (L.zmarch) {
+        zmarch(L, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_zmarch<mg::kZResid, true>, (const float*)xl(0), rl(0), L.res,
+               ec, L.t);
+      } else if (L.streamed) {
         slab(L, kResidProlong, PIC_KER_MG_PROLONG_SMOOTH, tall_form(L, kResidProlong) ? mg::k_mg_stencil<mg::kResid, true, true> : mg::k_mg_stencil<mg::kResid, true, false>, (const float*)xl(0), rl(0), L.res, L.t, ec);
       } else {
         launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(0), ec, L.N / 2, done);
@@ -238,6 +262,9 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
       }
       if ((e = cnn_apply(c, L.res, xl(0), nullptr, n))) return e;
       launch(c, mg::k_mg_add, grid_for(c, n / 4), 256, 0, xl(0), (const float*)L.t, n / 4, done);
+    } else if (L.zmarch) {
+      zmarch(L, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, true>, (const float*)xl(l), rl(l), L.t, ec);
+      zmarch(L, PIC_KER_MG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, false>, (const float*)L.t, rl(l), xl(l));
     } else if (L.streamed) {
       slab(L, kSmoothProlong, PIC_KER_MG_PROLONG_SMOOTH, tall_form(L, kSmoothProlong) ? mg::k_mg_stencil<mg::kSmooth, true, true> : mg::k_mg_stencil<mg::kSmooth, true, false>, (const float*)xl(l), rl(l), L.t, nulw, ec);
       slab(L, kSmooth, PIC_KER_MG_SMOOTH, tall_form(L, kSmooth) ? mg::k_mg_stencil<mg::kSmooth, false, true> : mg::k_mg_stencil<mg::kSmooth, false, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);

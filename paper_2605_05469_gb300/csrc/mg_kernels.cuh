@@ -167,6 +167,101 @@ __global__ void __launch_bounds__(TALL ? kStreamTall : kStreamSmall) k_mg_stenci
   stream_slab<float, float, float, 2>(g, smem, bars, x, r, err, start, ingest, body);
 }
 
+// ---------------------------------------------------------------------------
+// z-marching kernels (N % 128 == 0): a block is 32 x 8 threads over a tile of
+// 128 x-cells by 8 rows; each thread owns 4 x-cells of one row and marches up
+// a chunk of ZC planes, keeping the field at planes z-1, z, z+1 in registers
+// (the next plane's load is issued a plane ahead). x-neighbours come from the
+// adjacent lanes (each warp is one row of the tile; lanes 0 and 31 load the
+// cell beyond the tile), y-neighbours are loads of the adjacent rows (L1 hits
+// within the tile). No shared memory and no barriers.
+//   kZPre   : field r:  out = w (2 r - w A^ r)      (both pre-sweeps from 0)
+//   kZResid : field x:  out = aux - A^ x             (aux = r)
+//   kZSmooth: field x:  out = x + w (aux - A^ x)
+// ---------------------------------------------------------------------------
+//   with PROLONG the field is x' = x + P e_c (formed for every value loaded:
+//   own column, adjacent rows, the cells beyond the tile), and kZResid also
+//   writes x' to xout.
+enum : int { kZPre = 0, kZResid = 1, kZSmooth = 2 };
+constexpr int kZChunkMax = 16;  // planes a block marches (fewer on small grids, for more blocks)
+
+// (P e_c) at one fine node (i, j, z): the mean of the 1, 2, 4 or 8 coarse
+// nodes around it (coarse grid Nc = N / 2).
+__device__ __forceinline__ float prolonged_at(const float* __restrict__ ec, int Nc, int i, int j, int z) {
+  const int I0 = i >> 1, J0 = j >> 1, K0 = z >> 1;
+  const int I1 = (i & 1) ? (I0 + 1 == Nc ? 0 : I0 + 1) : I0;
+  const int J1 = (j & 1) ? (J0 + 1 == Nc ? 0 : J0 + 1) : J0;
+  const int K1 = (z & 1) ? (K0 + 1 == Nc ? 0 : K0 + 1) : K0;
+  auto e = [&](int I, int J, int K) { return __ldg(ec + ((size_t)K * Nc + J) * Nc + I); };
+  const float s = ((e(I0, J0, K0) + e(I1, J0, K0)) + (e(I0, J1, K0) + e(I1, J1, K0))) +
+                  ((e(I0, J0, K1) + e(I1, J0, K1)) + (e(I0, J1, K1) + e(I1, J1, K1)));
+  return 0.125f * s;
+}
+
+template <int MODE, bool PROLONG = false>
+__global__ void __launch_bounds__(256) k_mg_zmarch(const float* __restrict__ field, const float* __restrict__ aux,
+                                                   float* __restrict__ out, int N, int zc, const int* done,
+                                                   const float* __restrict__ ec, float* __restrict__ xout) {
+  if (done && *done) return;
+  const int tiles_x = N >> 7;
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int lane = threadIdx.x;
+  const int i0 = (tx << 7) + 4 * lane;
+  const int j = ty * 8 + threadIdx.y;
+  const int jm = j == 0 ? N - 1 : j - 1, jp = j == N - 1 ? 0 : j + 1;
+  const int z0 = blockIdx.y * zc;
+  const size_t NN = (size_t)N * N;
+  const int il = i0 == 0 ? N - 1 : i0 - 1, ir = i0 + 4 == N ? 0 : i0 + 4;
+  const float w = kOmega / 6.0f;
+  const int Nc = N >> 1;
+  auto at = [&](int z, int jj) { return (size_t)z * NN + (size_t)jj * N; };
+  auto ld = [&](const float* p, size_t off) { return __ldg(reinterpret_cast<const float4*>(p + off)); };
+  // the field's float4 at (z, row jj) (x' when PROLONG)
+  auto fld = [&](int z, int jj) {
+    float4 v = ld(field, at(z, jj) + i0);
+    if (PROLONG) {
+      V4<float> u = {{v.x, v.y, v.z, v.w}};
+      add_prolonged(u, ec, Nc, i0, jj, z);
+      v = make_float4(u.v[0], u.v[1], u.v[2], u.v[3]);
+    }
+    return v;
+  };
+  const int zb = z0 == 0 ? N - 1 : z0 - 1;
+  float4 cm = fld(zb, j);
+  float4 c0 = fld(z0, j);
+#pragma unroll 1
+  for (int t = 0; t < zc; ++t) {
+    const int z = z0 + t;
+    const int zn = z + 1 == N ? 0 : z + 1;
+    const float4 cp = fld(zn, j);
+    const size_t row = at(z, j);
+    const float4 ym = fld(z, jm), yp = fld(z, jp);
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODE != kZPre) a = ld(aux, row + i0);
+    float xl = __shfl_up_sync(0xffffffffu, c0.w, 1);
+    float xr = __shfl_down_sync(0xffffffffu, c0.x, 1);
+    if (lane == 0) xl = __ldg(field + row + il) + (PROLONG ? prolonged_at(ec, Nc, il, j, z) : 0.f);
+    if (lane == 31) xr = __ldg(field + row + ir) + (PROLONG ? prolonged_at(ec, Nc, ir, j, z) : 0.f);
+    const float c[4] = {c0.x, c0.y, c0.z, c0.w};
+    const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
+    const float zmv[4] = {cm.x, cm.y, cm.z, cm.w}, zpv[4] = {cp.x, cp.y, cp.z, cp.w};
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float l = q == 0 ? xl : c[q - 1];
+      const float r = q == 3 ? xr : c[q + 1];
+      const float s = ((l + r) + (ymv[q] + ypv[q])) + (zmv[q] + zpv[q]);
+      const float ax = 6.0f * c[q] - s;
+      o[q] = MODE == kZPre ? w * (2.0f * c[q] - w * ax) : (MODE == kZResid ? av[q] - ax : c[q] + w * (av[q] - ax));
+    }
+    *reinterpret_cast<float4*>(out + row + i0) = make_float4(o[0], o[1], o[2], o[3]);
+    if (PROLONG && MODE == kZResid) *reinterpret_cast<float4*>(xout + row + i0) = c0;
+    cm = c0;
+    c0 = cp;
+  }
+}
+
 // rc = 4 R res onto the coarse grid Nf/2 (Nf % 4 == 0): each thread the
 // coarse pair (2P, 2P+1) of row J of plane K = blockIdx.y, from the fine
 // float4 at x = 4P and the scalar at 4P - 1 of each of the 9 fine rows.

@@ -35,13 +35,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("N", [8, 16, 32, 40, 48, 64, 72, 96])
+@pytest.mark.parametrize("N", [8, 16, 32, 40, 48, 64, 72, 96, 128, 256])
 def test_vcycle_matches_oracle(pg, N):
     """16^3 and below run entirely in the one-block kernel; 32^3, 64^3 and
     96^3 add plane-streamed full-grid levels (whole-plane blocks at 32^3,
     slabs with halo rows above); 48^3 coarsens 48 -> 24 -> 12 -> 6 -> 3 (odd
     coarsest); 40^3 has a 20^3 streamed level; 72^3 coarsens to 36^3 and then
-    18^3, a size not a multiple of 4, which takes the per-cell kernels."""
+    18^3, a size not a multiple of 4, which takes the per-cell kernels; 128^3
+    and 256^3 have levels that take the z-marching kernels."""
     h = L / N
     r = np.random.default_rng(N).normal(size=N ** 3)
     r -= r.mean()
