@@ -45,7 +45,7 @@ KER_BYTES = {
     (0, "pap"): 32,      # read r, p_in; write p, q (FP64)
     (0, "update"): 48,   # read x, r, p, q; write x, r (FP64)
 }
-# FP64 operations per cell of one launch (the FP64 judge is FP64-pipe bound)
+# FP64 operations per cell of one launch (the FP64 reference solve is FP64-pipe bound)
 KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
 # learned preconditioner applied as its composed 9^3 kernel: 729 FMA per cell
 PRECOND_FLOP_PER_CELL = 2 * 729
@@ -126,7 +126,7 @@ def parse():
                     help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
                          "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
                          "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
-                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the Jacobi-PCG judge; ssor: the "
+                         "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the FP64 Jacobi-PCG reference; ssor: the "
                          "paper's PCG configuration (red-black SSOR, 4 inner, 2 outer, damping pi/2); fft: the "
                          "paper's other scheme, the FFT pseudo-spectral solve (cuFFT FP64) with the spectral field "
                          "pushed to the particles. The learned solvers are always trained and timed in the solve "
@@ -157,7 +157,7 @@ def peaks():
 
 def fp64_peak_tflops():
     """FP64 FMA peak of GB300: 1.2 TFLOP/s measured with a dependent-chain-free
-    DFMA loop on this machine's GB300 (152 SMs, ~2 GHz); see the FP64 note in the design doc."""
+    DFMA loop on this machine's GB300 (152 SMs, ~2 GHz); the FP64 rate is 1/58 of the FP32 rate."""
     return 1.20
 
 
@@ -533,7 +533,7 @@ def train_preconditioner(pg, torch, N=64, steps=600, val_grid=128, val_every=100
 
 def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
     """Cold-start solves of the same right-hand side (the last deposit): the FP64
-    Jacobi-PCG judge against the mixed-precision solvers (Jacobi-CG, flexible
+    Jacobi-PCG reference against the mixed-precision solvers (Jacobi-CG, flexible
     CG with the multigrid V-cycle, and with the learned preconditioner and the
     V-cycle with the learned smoother when the network is loaded), outside the
     timed region."""

@@ -56,7 +56,7 @@ typedef struct {
   double k;     /* perturbation wavenumber; L = 2 pi / k */
 } pic_params;
 
-/* Solver precision. FP64 = Jacobi-PCG entirely in FP64 (the judge).
+/* Solver precision. FP64 = Jacobi-PCG entirely in FP64 (the reference solve).
  * MIXED = FP32 stencil and vectors, FP64 reductions, FP64 solution and
  * reliable-update residual recomputation in FP64. */
 enum { PIC_PREC_FP64 = 0, PIC_PREC_MIXED = 1 };

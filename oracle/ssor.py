@@ -2,9 +2,9 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Sec. 4.1: the paper's PCG runs with an SSOR preconditioner with four inner
-and two outer iterations and damping factor pi/2. The paper does not define
-the iterations further; this module fixes the reading the GPU library
+Sec. 4.1 configures the paper's PCG with SSOR: 4 inner and 2 outer
+iterations, damping pi/2. The paper does not define the two kinds of
+iteration further; this module fixes the reading the GPU library
 implements (textbook SOR, e.g. Saad, "Iterative Methods for Sparse Linear
 Systems", 2nd ed., sec. 4.1, with the red-black ordering of sec. 12.4):
 

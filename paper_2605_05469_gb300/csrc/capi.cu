@@ -83,7 +83,7 @@ int sync_status(pic_ctx* c) {
 bool dev_ptr_ok(const void* p) { return p != nullptr && ((uintptr_t)p % 16) == 0; }
 
 // --------------------------------------------------------------------------
-// FP64 Jacobi-PCG (the judge)
+// FP64 Jacobi-PCG (the reference solve)
 // --------------------------------------------------------------------------
 int solve_common_setup(pic_ctx* c, const double* rho, const double* phi, double tol, int maxit, double delta,
                        double* xout) {

@@ -10,7 +10,7 @@ struct MgState;   // multigrid hierarchy, see mg.cu
 struct FftState;  // spectral solve plans and buffers, see fft.cu
 
 struct SolverWs {
-  // FP64 judge
+  // FP64 reference solve
   double *x = nullptr, *r = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
   // mixed
   double* xm[2] = {nullptr, nullptr};

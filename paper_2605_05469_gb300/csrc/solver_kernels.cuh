@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_fcg_update32(float* __restrict__ x, flo
 }
 
 // ---------------------------------------------------------------------------
-// Initial FP64 residual of the judge: r = h^2 b - (h^2 A) x, (r, r).
+// Initial FP64 residual of the FP64 reference solve: r = h^2 b - (h^2 A) x, (r, r).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStreamSmall) k_residual64(const double* __restrict__ x, const double* __restrict__ b,
                                                     double* __restrict__ r, Scalars* sc, double* partials,

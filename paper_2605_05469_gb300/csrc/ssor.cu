@@ -1,5 +1,5 @@
 // Red-black SSOR preconditioner, the paper's PCG configuration (Sec. 4.1:
-// four inner and two outer iterations, damping pi/2). z = M r starts from
+// INNER = 4, OUTER = 2, damping w = pi/2). z = M r starts from
 // z = 0 and repeats OUTER times: INNER forward SOR sweeps (red nodes, then
 // black), then INNER backward sweeps (black, then red). Nodes are red when
 // i + j + k is even; every 7-point neighbour of a node has the other colour,

@@ -144,7 +144,7 @@ def fcg_iterations(N=128, seed=21, tol=1e-10, maxit=2000):
 
 def compare_preconditioners(ctx, rho, tol=1e-10, maxit=20000):
     """Cold-start solves of rho with FCG + network and with mixed Jacobi-CG
-    (and the FP64 judge): iterations, device time, true relative residual."""
+    (and the FP64 reference solve): iterations, device time, true relative residual."""
     import torch
     res = {}
     for name, prec, pc in (("fp64_jacobi", PREC_FP64, PC_JACOBI), ("mixed_jacobi", PREC_MIXED, PC_JACOBI),

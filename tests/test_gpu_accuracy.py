@@ -5,7 +5,7 @@ The exact solution of A phi = b - mean(b) comes from the oracle's FFT form of
 the spectral solve (pinned in test_oracle_pic.py against the brute-force DFT,
 the operator and single Fourier modes); the right-hand side is the seeded
 Landau density + N(0, 0.01^2) noise of the solver-only workloads. The solvers
-stop at ||b - A phi|| <= 1e-10 ||b|| (the FP64 judge on its recursive
+stop at ||b - A phi|| <= 1e-10 ||b|| (the FP64 reference solve on its recursive
 residual, the mixed-precision solvers on the true FP64 residual), which bounds
 the relative error by 1e-10 ||b|| / (lambda_min ||phi||); the measured errors
 are asserted below the 1e-9 target.

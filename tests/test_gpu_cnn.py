@@ -232,7 +232,7 @@ def test_adam_matches_oracle_on_gpu_gradients(pg):
 def test_fcg_cnn_solve_reaches_true_residual(pg, N):
     """Flexible CG with the network (random weights: the descent guard keeps
     it convergent) reaches the same true FP64 relative residual 1e-10 as the
-    Jacobi judge."""
+    Jacobi-PCG reference."""
     h = L / N
     _, flat = rounded_weights(4)
     c = ctx_with_weights(pg, flat, N)
@@ -326,7 +326,7 @@ def test_trained_preconditioner_gain(pg, capsys):
     with it solves held-out Landau deposits at 64^3 and 128^3 to the true
     relative residual 1e-10. Asserted: convergence and at least 2x fewer
     iterations than mixed-precision Jacobi-CG; reported: iterations and
-    device time of both and of the FP64 judge."""
+    device time of both and of the FP64 reference solve."""
     from paper_2605_05469_gb300 import train as T
     sets = T.landau_snapshot_sets(64, seeds=[11, 12, 13, 14])
     c = pg.Context().init(64, 0, 0)

@@ -8,8 +8,8 @@ order, FMA contraction and libm vs CUDA sin/cos/log at the ulp level):
   initial particles: 1e-12 absolute (positions are O(L = 12.6));
   deposit: 1e-12 absolute on rho = O(1);
   solve: phi rel-L2 <= 1e-10 against the exact discrete solution at tol 1e-12;
-  40-step loop: particles within 1e-10, field energy rel 1e-8 (north-star
-  figures), with solves at tol 1e-12.
+  40-step loop: particles within 1e-10, field energy rel 1e-8 (the stated
+  accuracy targets), with solves at tol 1e-12.
 """
 import numpy as np
 import pytest
