@@ -317,11 +317,6 @@ __global__ void __launch_bounds__(256) k_scatter(const PRec* __restrict__ src, P
   }
 }
 
-__global__ void k_fill(double* a, size_t n, double v) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = v;
-}
-
 // ---------------------------------------------------------------------------
 // S2: CIC scatter from cell-sorted particles (Eq. 2), in two passes.
 // Cells: one thread per cell sums, over the cell's particles, the corner
