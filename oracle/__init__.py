@@ -21,4 +21,6 @@ mg       geometric multigrid V-cycle preconditioner (textbook, beyond the
 fft      FFT pseudo-spectral periodic Poisson solve (Sec. 3.1): phi and E.
 ssor     red-black SSOR preconditioner (the paper's PCG configuration,
          Sec. 4.1).
+pif      particle-in-Fourier field by direct non-uniform DFT sums (Sec. 3.4,
+         Appendix A).
 """
