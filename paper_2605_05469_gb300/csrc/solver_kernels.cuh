@@ -5,14 +5,15 @@
 // Jacobi diagonal 6/h^2 folded into the scalars, Jacobi-PCG and CG produce
 // the same iterates, so the preconditioner costs nothing per cell.
 //
-// One iteration is two kernels, each a single pass over the grid with its
-// reduction finished on the device by the last block (alpha and beta never
-// leave the GPU):
+// One iteration is two kernels (plus, for flexible CG, the preconditioner and
+// a dot-product kernel), each a single pass over the grid with its reduction
+// finished on the device by the last block (alpha and beta never leave the
+// GPU):
 //   pap   : p = r + beta p_in (on the whole streamed slab incl. halo),
-//           writes p, optionally q = A p, reduces (p, A p) -> alpha;
-//   update: x += alpha p, r -= alpha q (FP64, q stored) or
-//           r -= alpha A p (FP32, stencil recomputed), reduces (r, r) -> beta,
-//           convergence and iteration count.
+//           writes p and q = A p, reduces (p, A p) -> alpha;
+//   update: x += alpha p, r -= alpha q (q stored by pap; FP64, or the FP32
+//           streaming update of the mixed-precision solvers), reduces
+//           (r, r) -> beta, convergence and iteration count.
 #pragma once
 #include "stream.cuh"
 
