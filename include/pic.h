@@ -5,8 +5,10 @@
  * (Sec. 2, Eqs. 1-4) with the particle-in-cell loop of Fig. 1:
  * scatter -> solve -> gather -> push, on one GPU. The solve is a matrix-free
  * preconditioned conjugate gradient on the periodic 7-point finite-difference
- * Laplacian (Sec. 3.2). All calls are plain C: device buffers are passed as
- * raw pointers, sizes as integers, and no C++ exception crosses the boundary.
+ * Laplacian (Sec. 3.2; Jacobi, a learned CNN, a multigrid V-cycle or the
+ * paper's SSOR as the preconditioner), or the FFT pseudo-spectral solve of
+ * Sec. 3.1. All calls are plain C: device buffers are passed as raw
+ * pointers, sizes as integers, and no C++ exception crosses the boundary.
  *
  * Conventions (Sec. 2 and Sec. 2.1):
  *   - plasma units: electrons with q/m = -1, eps0 = 1, mean density 1, so the
@@ -14,7 +16,9 @@
  *     -Delta phi = rho (Eq. 2), E = -grad phi;
  *   - periodic cube [0, L)^3, L = 2 pi / k, N^3 nodes x_i = i h, h = L / N;
  *   - grid arrays are N^3 contiguous values, x fastest: i + N (j + N k);
- *   - particles are stored structure-of-arrays in FP64.
+ *   - particles live in the context as 64-byte records (the cell and a 64-bit
+ *     fixed-point offset inside it per coordinate, double-float velocities);
+ *     pic_get_particles returns them in FP64, structure of arrays.
  *
  * Streams: every call enqueues its work on the context's CUDA stream
  * (given to pic_create) and returns without synchronising, except those that
