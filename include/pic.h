@@ -176,6 +176,21 @@ int pic_sync_velocity_field(pic_ctx *c, const double *E, double dt);
  * synchronises). */
 int pic_field_energy_E(pic_ctx *c, const double *E, double out_w[3]);
 
+/* The particle-in-Fourier field (Sec. 3.4, Appendix A), the paper's third
+ * scheme: the charges go to the Fourier modes K_N (N = the grid size, modes
+ * -N/2..N/2-1) by a type-1 NUFFT, E_hat = -i k rho_hat / (|k|^2 L^3) over
+ * the symmetric modes |m_d| <= N/2 - 1 (k != 0), and the field is evaluated
+ * at the particles by a type-2 NUFFT (exponential-of-semicircle window on a
+ * 2x oversampled grid, FP64 cuFFT; the window width follows the relative
+ * tolerance tol, about 1e-12 for tol = 1e-12). E: device FP64 [3 Np]
+ * (E_x, E_y, E_z) in the ORIGINAL particle order (index p of pic_init). */
+int pic_pif_field(pic_ctx *c, double tol, double *E);
+
+/* One leapfrog step of the particle-in-Fourier scheme: the PIF field at the
+ * particles (no grid deposit or solve), then the kick and drift of
+ * pic_gather_push. */
+int pic_pif_push(pic_ctx *c, double tol, double dt);
+
 /* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
  * the ORIGINAL particle order (index p of pic_init), to device memory
  * (on_device = 1) or host memory (0; synchronises). `half_step` (may be

@@ -10,7 +10,8 @@ Module-level functions carry the C names (``pic_create``, ``pic_init``,
 ``pic_sync_velocity``, ``pic_field_energy``, ``pic_get_particles``,
 ``pic_apply_laplacian``, ``pic_profile_enable``, ``pic_profile_read``,
 ``pic_destroy``); ``Context`` bundles them, and calls the other entry points
-(the spectral solve ``pic_fft_solve``, ``pic_gather_push_field``,
+(the spectral solve ``pic_fft_solve``, the particle-in-Fourier
+``pic_pif_field`` and ``pic_pif_push``, ``pic_gather_push_field``,
 ``pic_sync_velocity_field``, ``pic_field_energy_E``, the learned
 preconditioner's and the V-cycle's) as methods.
 """
@@ -120,6 +121,8 @@ _SIGS = {
     "pic_mg_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "pic_fft_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_ssor_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pic_pif_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "pic_pif_push": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
     "pic_gather_push_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "pic_sync_velocity_field": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "pic_field_energy_E": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
@@ -305,6 +308,13 @@ class Context:
 
     def field_energy(self, phi):
         return pic_field_energy(self.h, phi, self.n)
+
+    def pif_field(self, E, tol=1e-12):
+        """The particle-in-Fourier field at the particles, E [3 Np] in the original order."""
+        _check(lib().pic_pif_field(self.h, tol, _dptr(E, "float64", 3 * self.num_particles, "E")), "pic_pif_field")
+
+    def pif_push(self, dt, tol=1e-12):
+        _check(lib().pic_pif_push(self.h, tol, dt), "pic_pif_push")
 
     def ssor_apply(self, r, z):
         """z = M r of the red-black SSOR preconditioner (FP32, scaled units)."""

@@ -8,6 +8,7 @@
 #include "cnn.h"
 #include "mg.h"
 #include "fft.h"
+#include "pif.h"
 #include "ssor.h"
 #include "ctx.h"
 #include "particle_kernels.cuh"
@@ -29,6 +30,7 @@ void free_particles(pic_ctx* c) {
   dfree(c->chunks);
   dfree(c->E);
   dfree(c->dep);
+  dfree(c->pif_E);
   c->np = 0;
 }
 
@@ -474,9 +476,9 @@ int launch_push(pic_ctx* c, const double* phi, const double* Efield, double kick
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
-  launch(c, k_gather_push, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
+  launch(c, k_gather_push<false>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
          (const float2*)(c->E + c->n), (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
-         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts);
+         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts, (const double*)nullptr);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -563,6 +565,7 @@ void pic_destroy(pic_ctx* c) {
   cnn_state_free(c->cnn);
   mg_state_free(c->mg);
   fft_state_free(c->fft);
+  pif_state_free(c->pif);
   delete c;
 }
 
@@ -763,6 +766,38 @@ int pic_field_energy(pic_ctx* c, const double* phi, double out_w[3]) {
   int e;
   if ((e = sync_status(c))) return e;
   for (int d = 0; d < 3; ++d) out_w[d] = c->out3_host[d];
+  return PIC_OK;
+}
+
+int pic_pif_field(pic_ctx* c, double tol, double* E) {
+  if (!c || !dev_ptr_ok(E) || !(tol > 0.0)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  int e;
+  if (!c->pif_E && (e = dalloc(&c->pif_E, 3 * c->np))) return e;
+  if ((e = pif_field(c, tol, c->pif_E))) return e;
+  const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  launch(c, k_unsort_field, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, (const double*)c->pif_E, E);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int pic_pif_push(pic_ctx* c, double tol, double dt) {
+  if (!c || !(tol > 0.0) || !isfinite(dt)) return PIC_EINVAL;
+  if (!c->has_grid || c->np == 0) return PIC_ESTATE;
+  const double kick = c->half_step ? dt : 0.5 * dt;
+  PhaseScope ps(c, PIC_PHASE_PUSH);
+  int e;
+  if (!c->pif_E && (e = dalloc(&c->pif_E, 3 * c->np))) return e;
+  if ((e = pif_field(c, tol, c->pif_E))) return e;
+  CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
+  const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)nullptr,
+         (const float2*)nullptr, (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
+         c->keys, c->ranks, c->counts, (const double*)c->pif_E);
+  CK(cudaGetLastError());
+  c->half_step = true;
+  c->keys_valid = true;
+  c->sorted = false;
   return PIC_OK;
 }
 

@@ -8,6 +8,7 @@ namespace pic {
 struct CnnState;  // learned-preconditioner state, see cnn.cu
 struct MgState;   // multigrid hierarchy, see mg.cu
 struct FftState;  // spectral solve plans and buffers, see fft.cu
+struct PifState;  // particle-in-Fourier plans and buffers, see pif.cu
 
 struct SolverWs {
   // FP64 reference solve
@@ -112,6 +113,8 @@ struct pic_ctx {
   // multigrid preconditioner (level buffers)
   pic::MgState* mg = nullptr;
   pic::FftState* fft = nullptr;
+  pic::PifState* pif = nullptr;
+  double* pif_E = nullptr;  // 3 np: the particle-in-Fourier field, current particle order
 };
 
 namespace pic {

@@ -482,11 +482,15 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 // ---------------------------------------------------------------------------
 constexpr int kPushThreads = 256;
 
+// GIVEN: the field at the particles is given (Ep: 3 np FP64, E_x, E_y, E_z in
+// the current particle order; the particle-in-Fourier scheme) instead of
+// gathered from the node field.
+template <bool GIVEN>
 __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64_t np, const float2* __restrict__ Ex,
                                                               const float2* __restrict__ Ey,
                                                               const float2* __restrict__ Ez, Grid g, float2 kick_qm,
                                                               float2 dth, int drift, uint32_t* keys, uint32_t* ranks,
-                                                              uint32_t* counts) {
+                                                              uint32_t* counts, const double* __restrict__ Ep) {
   const uint64_t base = (uint64_t)blockIdx.x * kPushThreads;
   const uint64_t p = base + threadIdx.x;
   const bool valid = p < np;
@@ -501,28 +505,37 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
     df vy = {r2.x, r2.y}, vz = {r2.z, r2.w};
     int ix = (int)(r3.z & 0xFFFFu), iy = (int)(r3.z >> 16), iz = (int)(r3.w & 0xFFFFu);
     const int N = g.N;
-    // CIC weights prod_d (f_d or 1 - f_d) of the 8 corners
-    const df ax = frac_df(fx), ay = frac_df(fy), az = frac_df(fz);
-    const df bx = one_minus_frac_df(fx), by = one_minus_frac_df(fy), bz = one_minus_frac_df(fz);
-    const df w00 = df_mul(by, bz), w10 = df_mul(ay, bz), w01 = df_mul(by, az), w11 = df_mul(ay, az);
-    const df w[8] = {df_mul(bx, w00), df_mul(ax, w00), df_mul(bx, w10), df_mul(ax, w10),
-                     df_mul(bx, w01), df_mul(ax, w01), df_mul(bx, w11), df_mul(ax, w11)};
-    const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
-    const size_t Ns = N;
-    const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
-    const size_t idx[8] = {z0 + y0 + ix, z0 + y0 + jx, z0 + y1 + ix, z0 + y1 + jx,
-                           z1 + y0 + ix, z1 + y0 + jx, z1 + y1 + ix, z1 + y1 + jx};
-    DfAcc ex, ey, ez;
+    df ep[3];
+    if (GIVEN) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      ex.add_mul(w[c], df_from(__ldg(Ex + idx[c])));
-      ey.add_mul(w[c], df_from(__ldg(Ey + idx[c])));
-      ez.add_mul(w[c], df_from(__ldg(Ez + idx[c])));
+      for (int d = 0; d < 3; ++d) ep[d] = df_of_double(__ldg(Ep + (size_t)d * np + p));
+    } else {
+      // CIC weights prod_d (f_d or 1 - f_d) of the 8 corners
+      const df ax = frac_df(fx), ay = frac_df(fy), az = frac_df(fz);
+      const df bx = one_minus_frac_df(fx), by = one_minus_frac_df(fy), bz = one_minus_frac_df(fz);
+      const df w00 = df_mul(by, bz), w10 = df_mul(ay, bz), w01 = df_mul(by, az), w11 = df_mul(ay, az);
+      const df w[8] = {df_mul(bx, w00), df_mul(ax, w00), df_mul(bx, w10), df_mul(ax, w10),
+                       df_mul(bx, w01), df_mul(ax, w01), df_mul(bx, w11), df_mul(ax, w11)};
+      const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
+      const size_t Ns = N;
+      const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
+      const size_t idx[8] = {z0 + y0 + ix, z0 + y0 + jx, z0 + y1 + ix, z0 + y1 + jx,
+                             z1 + y0 + ix, z1 + y0 + jx, z1 + y1 + ix, z1 + y1 + jx};
+      DfAcc ex, ey, ez;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        ex.add_mul(w[c], df_from(__ldg(Ex + idx[c])));
+        ey.add_mul(w[c], df_from(__ldg(Ey + idx[c])));
+        ez.add_mul(w[c], df_from(__ldg(Ez + idx[c])));
+      }
+      ep[0] = ex.value();
+      ep[1] = ey.value();
+      ep[2] = ez.value();
     }
     const df kq = dfc(kick_qm);
-    vx = df_add(vx, df_mul(kq, ex.value()));
-    vy = df_add(vy, df_mul(kq, ey.value()));
-    vz = df_add(vz, df_mul(kq, ez.value()));
+    vx = df_add(vx, df_mul(kq, ep[0]));
+    vy = df_add(vy, df_mul(kq, ep[1]));
+    vz = df_add(vz, df_mul(kq, ep[2]));
     *reinterpret_cast<float4*>(rec + 2) = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
     if (drift) {
       const df s = dfc(dth);
@@ -552,6 +565,15 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
     keys[p] = kk;
     ranks[p] = b + (uint32_t)(lane - run0);
   }
+}
+
+// A per-particle field (3 np, current order) back to the original order.
+__global__ void k_unsort_field(const PRec* P, uint64_t np, const double* Ep, double* out) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const uint64_t d = P[p].id;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) out[q * np + d] = Ep[q * np + p];
 }
 
 // Copy particles back to the original order, in FP64: out[q * np + id[p]] =
