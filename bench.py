@@ -18,6 +18,7 @@ GPU); value = steps of all ranks / max time over ranks.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -79,6 +80,17 @@ PARTICLE_BYTES = {
 # dram__bytes_write.sum over the particle count) measured by ncu on the
 # 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
 # count): it stands for the same kernels at other sizes
+# particle-in-Fourier window sums: a multiply and an atomic add (spreading)
+# or one FMA (interpolation) per window point and particle
+PIF_FLOP_PER_POINT = 2
+
+
+def pif_width(tol):
+    """Window width of the particle-in-Fourier NUFFTs for a relative tolerance
+    (about one digit per point at oversampling 2), clamped to [4, 16]."""
+    return min(16, max(4, int(math.ceil(-math.log10(tol))) + 1))
+
+
 MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.70, "scatter": 133.72}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
@@ -122,15 +134,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft"], default="mg",
+    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft", "pif"], default="mg",
                     help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
                          "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
                          "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
                          "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the FP64 Jacobi-PCG reference; ssor: the "
                          "paper's PCG configuration (red-black SSOR, 4 inner, 2 outer, damping pi/2); fft: the "
                          "paper's other scheme, the FFT pseudo-spectral solve (cuFFT FP64) with the spectral field "
-                         "pushed to the particles. The learned solvers are always trained and timed in the solve "
-                         "comparison as well")
+                         "pushed to the particles; pif: the particle-in-Fourier scheme (NUFFTs, no grid deposit "
+                         "or solve). The learned solvers are always trained and timed in the solve comparison as "
+                         "well")
+    ap.add_argument("--pif-tol", type=float, default=1e-4,
+                    help="relative tolerance of the particle-in-Fourier NUFFTs (sets the window width; 1e-4 as in the paper's runs)")
     ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
@@ -247,6 +262,7 @@ def run_ours(args):
     infos = []
 
     use_fft = args.solver == "fft"
+    use_pif = args.solver == "pif"
     E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda") if use_fft else None
 
     def solve_into(rho_, phi_):
@@ -260,6 +276,10 @@ def run_ours(args):
         if solve_only:
             phi.zero_()
             info = solve_into(rho, phi)
+            W = None
+        elif use_pif:
+            c.pif_push(DT, tol=args.pif_tol)
+            info = {"iters": 0, "t_ms": 0.0, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
             W = None
         else:
             c.deposit(rho)
@@ -320,6 +340,8 @@ def run_ours(args):
            "note": "wall clock through the Python binding; per step the field energy is read to host"}
 
     # solver-only end to end: rho from pinned host memory, phi back to host
+    if use_pif:
+        c.deposit(rho)  # the particle-in-Fourier step has no grid charge of its own
     rho_host = rho.cpu().pin_memory()
     phi_host = torch.empty_like(rho_host).pin_memory()
     barrier()
@@ -395,6 +417,19 @@ def run_ours(args):
         b = bp * np_ + bn * n
         rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "bytes_per_particle": bp,
                    "bytes_per_node": bn, "gbs": b / (avg_ms * 1e-3) / 1e9, "launches_per_step": 1}
+    # particle-in-Fourier: the spreading kernel (the charge) and the
+    # interpolation kernel (the three field components at once), one launch
+    # each a step; FP64 window sums over w^3 grid points a particle
+    if use_pif:
+        w_pif = pif_width(args.pif_tol)
+        for k, comps in (("pif_spread", 1), ("pif_gather", 3)):
+            if not prof["ker_samples"].get(k):
+                continue
+            avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
+            flop = PIF_FLOP_PER_POINT * comps * w_pif ** 3 * np_
+            rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "window_points": w_pif ** 3,
+                       "components": comps, "fp64_flop": flop, "tflops": flop / (avg_ms * 1e-3) / 1e12,
+                       "launches_per_step": 1}
     # the dominant kernel: the largest device time per step (solver kernels
     # run once per iteration)
     it_mean = statistics.mean(i["iters"] for i in infos) if infos else 1
@@ -410,7 +445,17 @@ def run_ours(args):
                                         "k_mg_stencil<kResid, prolong> (finest level)"),
              ("mg_smooth", 1): "k_mg_stencil<kSmooth> (finest level)"}
     roof = None
-    if dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):
+    if dom in ("pif_spread", "pif_gather"):
+        r = rows[dom]
+        roof = {"kernel": {"pif_spread": "k_pif_spread (type-1 NUFFT spreading, FP64 atomics)",
+                           "pif_gather": "k_pif_gather3 (type-2 NUFFT interpolation, three components)"}[dom],
+                "bound": "alu", "achieved": round(r["tflops"], 4), "peak": fp64_peak_tflops(),
+                "unit": "FP64 TFLOP/s", "frac": round(r["tflops"] / fp64_peak_tflops(), 4),
+                "peak_source": "measured FP64 FMA loop", "traffic": None, "algorithmic_flop": r["fp64_flop"],
+                "avg_launch_us": round(r["avg_us"], 2),
+                "note": "window sums: 2 FP64 flops per window point, component and particle (window "
+                        "evaluation not counted)"}
+    elif dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):
         r = rows[dom]
         _, _, pk = peaks()
         peak = pk.get("bf16_tflops_sustained", 1700.0)
@@ -470,13 +515,15 @@ def run_ours(args):
                     "9^3 learned preconditioner") if pc == pg.PC_CNN else "") +
                   ("; f32 multigrid V-cycle" if pc == pg.PC_MG and not use_fft else "") +
                   ("; FP64 spectral solve (cuFFT)" if use_fft else "") +
+                  (f"; FP64 particle-in-Fourier NUFFTs (tol {args.pif_tol:g})" if use_pif else "") +
                   ("; f32 multigrid V-cycle, learned finest-level smoother" if pc == pg.PC_MG_CNN else "")),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
                                (f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc ({ppc * n} particles), "
                                 + ("FFT pseudo-spectral solve with the spectral field" if use_fft else
-                                   f"solve to rel-res {TOL:g}") + f", dt {DT}"),
+                                   f"particle-in-Fourier field ({N}^3 modes, NUFFT tol {args.pif_tol:g})"
+                                   if use_pif else f"solve to rel-res {TOL:g}") + f", dt {DT}"),
                    "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
                    "warm_start": True, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
@@ -503,7 +550,8 @@ def run_ours(args):
         if learned_roof is not None:
             out["roofline_learned_preconditioner"] = learned_roof
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters), args.solver)
+        out["cpu_baseline"] = (cpu_baseline_pif(N, ppc) if use_pif else
+                               cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters), args.solver))
     if dist is not None:
         dist.destroy_process_group()
     c.close()
@@ -720,6 +768,31 @@ def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", reference_iters=None, 
             "host_cpus": os.cpu_count(),
             "sample": f"{cg_desc} (scaled by {it:.0f} iterations/solve), "
                       f"deposit+gather+push of {ns} of {ppc * n} particles (scaled linearly), one field energy"}
+
+
+def cpu_baseline_pif(N, ppc, Ns=16, ns=16384):
+    """The CPU oracle's particle-in-Fourier field (direct type-1/type-2 sums)
+    and push timed on ns particles with Ns^3 modes, scaled to the step by
+    particles x modes (the direct sums cost one term per particle and mode)."""
+    from oracle import pic as opic
+    from oracle import pif as opif
+
+    L = 4.0 * np.pi
+    rng = np.random.default_rng(3)
+    pos = rng.random((3, ns)) * L
+    vel = rng.normal(size=(3, ns))
+    q = np.full(ns, -L ** 3 / ns)
+    t0 = time.perf_counter()
+    Er, _ = opif.field_at_particles(pos, q, Ns, L)
+    t_field = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    opic.push(pos, vel, Er, DT, L, kick=DT)
+    t_push = time.perf_counter() - t0
+    npart = ppc * N ** 3
+    step_s = t_field * (npart / ns) * (N / Ns) ** 3 + t_push * (npart / ns)
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cpus": os.cpu_count(),
+            "sample": f"direct-sum field of {ns} particles on {Ns}^3 modes (scaled by particles x modes "
+                      f"to {npart} x {N}^3) and their push (scaled by particles)"}
 
 
 def run_reference(args):

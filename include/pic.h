@@ -315,8 +315,8 @@ enum { PIC_PHASE_DEPOSIT = 0, PIC_PHASE_SOLVE = 1, PIC_PHASE_PUSH = 2, PIC_PHASE
  * products, and the finest-level kernels of the multigrid V-cycle (two-sweep
  * pre-smoothing, residual, restriction, prolongation + first post-sweep,
  * second post-sweep; with the learned smoother the residual after the
- * prolongation counts as the prolongation slot), and the particle kernels
- * (every launch). */
+ * prolongation counts as the prolongation slot), the particle kernels and the
+ * particle-in-Fourier spreading and interpolation kernels (every launch). */
 enum {
   PIC_KER_PAP = 0, PIC_KER_UPDATE = 1, PIC_KER_PRECOND = 2, PIC_KER_DOT = 3,
   PIC_KER_MG_PRE = 4, PIC_KER_MG_RESID = 5, PIC_KER_MG_RESTRICT = 6, PIC_KER_MG_PROLONG_SMOOTH = 7,
@@ -324,7 +324,9 @@ enum {
   PIC_KER_SCATTER = 9,  /* the sort's record scatter (every pic_deposit that sorts) */
   PIC_KER_DEPOSIT = 10, /* the two deposit passes (cells, then nodes) */
   PIC_KER_PUSH = 11,    /* the gather + push kernel */
-  PIC_NKER = 12
+  PIC_KER_PIF_SPREAD = 12, /* particle-in-Fourier: spreading the charges to the oversampled grid */
+  PIC_KER_PIF_GATHER = 13, /* particle-in-Fourier: interpolating one field component (3 per field) */
+  PIC_NKER = 14
 };
 typedef struct {
   int64_t launches;           /* kernels launched by the context (counted always) */

@@ -63,13 +63,13 @@ class pic_solve_opts(ctypes.Structure):
 
 class pic_profile_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("phase_calls", ctypes.c_int * 4), ("phase_ms", ctypes.c_double * 4),
-                ("ker_samples", ctypes.c_int * 12), ("ker_ms", ctypes.c_double * 12),
-                ("ker_precision", ctypes.c_int * 12)]
+                ("ker_samples", ctypes.c_int * 14), ("ker_ms", ctypes.c_double * 14),
+                ("ker_precision", ctypes.c_int * 14)]
 
     def as_dict(self):
         phases = ("deposit", "solve", "push", "energy")
         kers = ("pap", "update", "precond", "dot", "mg_pre", "mg_resid", "mg_restrict", "mg_prolong_smooth",
-                "mg_smooth", "scatter", "deposit", "push")
+                "mg_smooth", "scatter", "deposit", "push", "pif_spread", "pif_gather")
         return {
             "launches": int(self.launches),
             "phase_calls": {p: self.phase_calls[i] for i, p in enumerate(phases)},

@@ -614,31 +614,39 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
 
 int64_t pic_num_particles(const pic_ctx* c) { return c ? (int64_t)c->np : 0; }
 
+// Counting sort of the particle records by cell key (a no-op when they are
+// sorted): keys and in-cell ranks (from the last push, else counted here), an
+// exclusive scan of the per-cell counts, and the scatter of the records into
+// the other buffer.
+static int sort_particles(pic_ctx* c) {
+  if (c->sorted) return PIC_OK;
+  const unsigned pblocks = (unsigned)((c->np + 255) / 256);
+  if (!c->keys_valid) {
+    CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
+    launch(c, k_count_keys, pblocks, 256, 0, pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
+  }
+  const int nchunks = (int)((c->n + kScanChunk - 1) / kScanChunk);
+  launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
+  launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
+  launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
+  const unsigned sblocks = (unsigned)(((c->np + 31) / 32 * 32 + 255) / 256);
+  const int slot = c->prof_on ? c->ker[PIC_KER_SCATTER].begin(c->stream) : -1;
+  launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
+         (const uint32_t*)c->ranks, (const uint32_t*)c->offsets);
+  if (c->prof_on) c->ker[PIC_KER_SCATTER].end(slot, c->stream);
+  CK(cudaGetLastError());
+  c->cur ^= 1;
+  c->sorted = true;
+  c->keys_valid = false;
+  return PIC_OK;
+}
+
 int pic_deposit(pic_ctx* c, double* rho) {
   if (!c || !dev_ptr_ok(rho)) return PIC_EINVAL;
   if (!c->has_grid || c->np == 0) return PIC_ESTATE;
   PhaseScope ps(c, PIC_PHASE_DEPOSIT);
-  if (!c->sorted) {
-    const unsigned pblocks = (unsigned)((c->np + 255) / 256);
-    if (!c->keys_valid) {
-      CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
-      launch(c, k_count_keys, pblocks, 256, 0, pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
-    }
-    const int nchunks = (int)((c->n + kScanChunk - 1) / kScanChunk);
-    launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
-    launch(c, k_scan_chunk_sums, 1, 1024, 0, c->chunks, nchunks);
-    launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
-    const unsigned sblocks = (unsigned)(((c->np + 31) / 32 * 32 + 255) / 256);
-    const int slot = c->prof_on ? c->ker[PIC_KER_SCATTER].begin(c->stream) : -1;
-    launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
-           (const uint32_t*)c->ranks, (const uint32_t*)c->offsets);
-    if (c->prof_on) c->ker[PIC_KER_SCATTER].end(slot, c->stream);
-    CK(cudaGetLastError());
-    c->cur ^= 1;
-    c->sorted = true;
-    c->keys_valid = false;
-  }
   int e;
+  if ((e = sort_particles(c))) return e;
   if (!c->dep && (e = dalloc(&c->dep, 8 * c->n))) return e;
   const double qscale = -(double)c->n / (double)c->np;  // q_p / h^3 = -N^3 / Np
   const unsigned cblocks = (unsigned)((c->n + 255) / 256);
@@ -774,6 +782,7 @@ int pic_pif_field(pic_ctx* c, double tol, double* E) {
   if (!c->has_grid || c->np == 0) return PIC_ESTATE;
   int e;
   if (!c->pif_E && (e = dalloc(&c->pif_E, 3 * c->np))) return e;
+  if ((e = sort_particles(c))) return e;  // cell order: neighbouring threads share window points
   if ((e = pif_field(c, tol, c->pif_E))) return e;
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   launch(c, k_unsort_field, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, (const double*)c->pif_E, E);
@@ -788,12 +797,15 @@ int pic_pif_push(pic_ctx* c, double tol, double dt) {
   PhaseScope ps(c, PIC_PHASE_PUSH);
   int e;
   if (!c->pif_E && (e = dalloc(&c->pif_E, 3 * c->np))) return e;
+  if ((e = sort_particles(c))) return e;  // cell order: neighbouring threads share window points
   if ((e = pif_field(c, tol, c->pif_E))) return e;
   CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
+  const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)nullptr,
          (const float2*)nullptr, (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
          c->keys, c->ranks, c->counts, (const double*)c->pif_E);
+  if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   c->half_step = true;
   c->keys_valid = true;

@@ -31,7 +31,8 @@ struct PifState {
   double beta = 0.0;
   cufftHandle fwd = 0, inv = 0;
   bool have_fwd = false, have_inv = false;
-  double* G = nullptr;                 // M^3 spread charge, then each field component
+  double* G = nullptr;                 // M^3 spread charge, then the field's x component
+  double* Gyz[2] = {nullptr, nullptr}; // M^3 each: the field's y and z components
   cufftDoubleComplex* Gh = nullptr;    // M x M x (M/2 + 1)
   cufftDoubleComplex* F = nullptr;     // M x M x (M/2 + 1)
   double* phihat = nullptr;            // window transform at the signed modes -N/2 .. N/2 - 1
@@ -42,6 +43,8 @@ void pif_state_free(PifState* s) {
   if (s->have_fwd) cufftDestroy(s->fwd);
   if (s->have_inv) cufftDestroy(s->inv);
   cudaFree(s->G);
+  cudaFree(s->Gyz[0]);
+  cudaFree(s->Gyz[1]);
   cudaFree(s->Gh);
   cudaFree(s->F);
   cudaFree(s->phihat);
@@ -50,7 +53,7 @@ void pif_state_free(PifState* s) {
 
 namespace {
 
-constexpr int kPifMaxW = 16;
+constexpr int kPifMinW = 4, kPifMaxW = 16;
 
 __host__ __device__ inline double es_window(double z, double beta) {
   return fabs(z) <= 1.0 ? exp(beta * (sqrt(1.0 - z * z) - 1.0)) : 0.0;
@@ -111,36 +114,45 @@ __device__ __forceinline__ void grid_units(const PRec* P, uint64_t p, double u[3
   for (int d = 0; d < 3; ++d) u[d] = 2.0 * ((double)c[d] + (double)(f[d] >> 11) * (1.0 / 9007199254740992.0));
 }
 
-// The window's w weights along one axis and the first grid index (mod M).
-__device__ __forceinline__ int axis_weights(double u, int w, double beta, int M, double* wt) {
-  const int g0 = (int)ceil(u - 0.5 * w);
-  for (int a = 0; a < w; ++a) wt[a] = es_window(2.0 * (u - (double)(g0 + a)) / w, beta);
-  int g = g0 % M;
-  return g < 0 ? g + M : g;
+// First grid index of the window along one axis (unwrapped: may be negative)
+// and its W weights.
+template <int W>
+__device__ __forceinline__ int axis_weights(double u, double beta, double* wt) {
+  const int g0 = (int)ceil(u - 0.5 * W);
+#pragma unroll
+  for (int a = 0; a < W; ++a) wt[a] = es_window(2.0 * (u - (double)(g0 + a)) / W, beta);
+  return g0;
 }
 
-// Type-1 spreading: G[g] += q phi_x phi_y phi_z over the w^3 window of each particle.
-__global__ void __launch_bounds__(128) k_pif_spread(const PRec* __restrict__ P, uint64_t np, int M, int w,
-                                                    double beta, double q, double* G) {
+// Index g in [-M, 2M) reduced to [0, M).
+__device__ __forceinline__ int wrap_m(int g, int M) { return g < 0 ? g + M : (g >= M ? g - M : g); }
+
+// Type-1 spreading: G[g] += q phi_x phi_y phi_z over the W^3 window of each
+// particle (FP64 atomics; the particles are in cell order, so the threads of
+// a warp update neighbouring points).
+template <int W>
+__global__ void __launch_bounds__(128) k_pif_spread(const PRec* __restrict__ P, uint64_t np, int M, double beta,
+                                                    double q, double* G) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   double u[3];
   grid_units(P, p, u);
-  double wx[kPifMaxW], wy[kPifMaxW], wz[kPifMaxW];
-  const int gx = axis_weights(u[0], w, beta, M, wx), gy = axis_weights(u[1], w, beta, M, wy),
-            gz = axis_weights(u[2], w, beta, M, wz);
+  double wx[W], wy[W];
+  const int gx = axis_weights<W>(u[0], beta, wx), gy = axis_weights<W>(u[1], beta, wy);
+  const int gz = (int)ceil(u[2] - 0.5 * W);
   const size_t Ms = M;
-  for (int c = 0; c < w; ++c) {
-    const int z = gz + c < M ? gz + c : gz + c - M;
-    const double qz = q * wz[c];
-    for (int b = 0; b < w; ++b) {
-      const int y = gy + b < M ? gy + b : gy + b - M;
+  int xs[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) xs[a] = wrap_m(gx + a, M);
+  for (int c = 0; c < W; ++c) {
+    const int z = wrap_m(gz + c, M);
+    const double qz = q * es_window(2.0 * (u[2] - (double)(gz + c)) / W, beta);
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
       const double qzy = qz * wy[b];
-      double* row = G + ((size_t)z * Ms + y) * Ms;
-      for (int a = 0; a < w; ++a) {
-        const int x = gx + a < M ? gx + a : gx + a - M;
-        atomicAdd(row + x, qzy * wx[a]);
-      }
+      double* row = G + ((size_t)z * Ms + wrap_m(gy + b, M)) * Ms;
+#pragma unroll
+      for (int a = 0; a < W; ++a) atomicAdd(row + xs[a], qzy * wx[a]);
     }
   }
 }
@@ -172,41 +184,75 @@ __global__ void __launch_bounds__(256) k_pif_modes(const cufftDoubleComplex* __r
   }
 }
 
-// Type-2 interpolation of one field component: Ep[p] = sum over the window of f[g] phi.
-__global__ void __launch_bounds__(128) k_pif_gather(const PRec* __restrict__ P, uint64_t np, int M, int w, double beta,
-                                                    const double* __restrict__ f, double* __restrict__ Ep) {
+// Type-2 interpolation of the three field components at once (the window
+// weights and the particle's record are shared): Ep[d np + p] = sum over the
+// window of f_d[g] phi_x phi_y phi_z.
+template <int W>
+__global__ void __launch_bounds__(128) k_pif_gather3(const PRec* __restrict__ P, uint64_t np, int M, double beta,
+                                                     const double* __restrict__ f0, const double* __restrict__ f1,
+                                                     const double* __restrict__ f2, double* __restrict__ Ep) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   double u[3];
   grid_units(P, p, u);
-  double wx[kPifMaxW], wy[kPifMaxW], wz[kPifMaxW];
-  const int gx = axis_weights(u[0], w, beta, M, wx), gy = axis_weights(u[1], w, beta, M, wy),
-            gz = axis_weights(u[2], w, beta, M, wz);
+  double wx[W], wy[W];
+  const int gx = axis_weights<W>(u[0], beta, wx), gy = axis_weights<W>(u[1], beta, wy);
+  const int gz = (int)ceil(u[2] - 0.5 * W);
   const size_t Ms = M;
-  double acc = 0.0;
-  for (int c = 0; c < w; ++c) {
-    const int z = gz + c < M ? gz + c : gz + c - M;
-    double sz = 0.0;
-    for (int b = 0; b < w; ++b) {
-      const int y = gy + b < M ? gy + b : gy + b - M;
-      const double* row = f + ((size_t)z * Ms + y) * Ms;
-      double sy = 0.0;
-      for (int a = 0; a < w; ++a) {
-        const int x = gx + a < M ? gx + a : gx + a - M;
-        sy = fma(__ldg(row + x), wx[a], sy);
+  int xs[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) xs[a] = wrap_m(gx + a, M);
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+  for (int c = 0; c < W; ++c) {
+    const int z = wrap_m(gz + c, M);
+    const double wz = es_window(2.0 * (u[2] - (double)(gz + c)) / W, beta);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      const size_t row = ((size_t)z * Ms + wrap_m(gy + b, M)) * Ms;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        t0 = fma(__ldg(f0 + row + xs[a]), wx[a], t0);
+        t1 = fma(__ldg(f1 + row + xs[a]), wx[a], t1);
+        t2 = fma(__ldg(f2 + row + xs[a]), wx[a], t2);
       }
-      sz = fma(sy, wy[b], sz);
+      s0 = fma(t0, wy[b], s0);
+      s1 = fma(t1, wy[b], s1);
+      s2 = fma(t2, wy[b], s2);
     }
-    acc = fma(sz, wz[c], acc);
+    acc0 = fma(s0, wz, acc0);
+    acc1 = fma(s1, wz, acc1);
+    acc2 = fma(s2, wz, acc2);
   }
-  Ep[p] = acc;
+  Ep[p] = acc0;
+  Ep[np + p] = acc1;
+  Ep[2 * np + p] = acc2;
 }
+
+// Launch kernel template K<W> for the runtime width w (kPifMinW..kPifMaxW).
+#define PIF_DISPATCH_W(w, KER, ...)                              \
+  switch (w) {                                                   \
+    case 4: launch(c, KER<4>, __VA_ARGS__); break;               \
+    case 5: launch(c, KER<5>, __VA_ARGS__); break;               \
+    case 6: launch(c, KER<6>, __VA_ARGS__); break;               \
+    case 7: launch(c, KER<7>, __VA_ARGS__); break;               \
+    case 8: launch(c, KER<8>, __VA_ARGS__); break;               \
+    case 9: launch(c, KER<9>, __VA_ARGS__); break;               \
+    case 10: launch(c, KER<10>, __VA_ARGS__); break;             \
+    case 11: launch(c, KER<11>, __VA_ARGS__); break;             \
+    case 12: launch(c, KER<12>, __VA_ARGS__); break;             \
+    case 13: launch(c, KER<13>, __VA_ARGS__); break;             \
+    case 14: launch(c, KER<14>, __VA_ARGS__); break;             \
+    case 15: launch(c, KER<15>, __VA_ARGS__); break;             \
+    default: launch(c, KER<16>, __VA_ARGS__); break;             \
+  }
 
 // The window width for a relative tolerance (about one digit per point with
 // sigma = 2), 4 <= w <= kPifMaxW.
 int width_for(double tol) {
   int w = (int)ceil(-log10(tol > 0.0 ? tol : 1e-16)) + 1;
-  if (w < 4) w = 4;
+  if (w < kPifMinW) w = kPifMinW;
   if (w > kPifMaxW) w = kPifMaxW;
   return w;
 }
@@ -224,6 +270,8 @@ int ensure_pif(pic_ctx* c, int w) {
   const size_t M = s->M, nr = M * M * M, nc = M * M * (M / 2 + 1);
   int e = PIC_OK;
   if (cudaMalloc(reinterpret_cast<void**>(&s->G), nr * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&s->Gyz[0]), nr * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&s->Gyz[1]), nr * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->Gh), nc * sizeof(cufftDoubleComplex)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->F), nc * sizeof(cufftDoubleComplex)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->phihat), (size_t)s->N * sizeof(double)) != cudaSuccess) {
@@ -254,8 +302,12 @@ int ensure_pif(pic_ctx* c, int w) {
 
 int pif_field(pic_ctx* c, double tol, double* Ep) {
   if (c->np == 0) return PIC_ESTATE;
+  const int w = width_for(tol);
+  // the window must fit in one period of the oversampled grid (w <= M = 2N),
+  // which also keeps every window index within [-M, 2M) for wrap_m
+  if (w > 2 * c->N) return PIC_EINVAL;
   int e;
-  if ((e = ensure_pif(c, width_for(tol)))) return e;
+  if ((e = ensure_pif(c, w))) return e;
   PifState* s = c->pif;
   if (cufftSetStream(s->fwd, c->stream) != CUFFT_SUCCESS || cufftSetStream(s->inv, c->stream) != CUFFT_SUCCESS)
     return PIC_ECUDA;
@@ -264,20 +316,26 @@ int pif_field(pic_ctx* c, double tol, double* Ep) {
   const PRec* P = c->prec[c->cur];
   const unsigned pb = (unsigned)((c->np + 127) / 128);
   CK(cudaMemsetAsync(s->G, 0, nr * sizeof(double), c->stream));
-  launch(c, k_pif_spread, pb, 128, 0, P, c->np, s->M, s->w, s->beta, -L * L * L / (double)c->np, s->G);
+  int slot = c->prof_on ? c->ker[PIC_KER_PIF_SPREAD].begin(c->stream) : -1;
+  PIF_DISPATCH_W(s->w, k_pif_spread, pb, 128, 0, P, c->np, s->M, s->beta, -L * L * L / (double)c->np, s->G);
+  if (c->prof_on) c->ker[PIC_KER_PIF_SPREAD].end(slot, c->stream);
   if (cufftExecD2Z(s->fwd, s->G, s->Gh) != CUFFT_SUCCESS) return PIC_ECUDA;
   size_t b = (nc + 255) / 256;
   const size_t cap = (size_t)c->sms * 16;
   const unsigned grid = (unsigned)(b < cap ? b : cap);
   const double pi = 3.14159265358979323846;
+  // G is free again after the forward transform: it takes the x component
+  double* comp[3] = {s->G, s->Gyz[0], s->Gyz[1]};
   for (int d = 0; d < 3; ++d) {
     launch(c, k_pif_modes, grid, 256, 0, (const cufftDoubleComplex*)s->Gh, s->F, s->N, s->M,
            (const double*)s->phihat, 2.0 * pi / L, 1.0 / (L * L * L), d);
-    // the complex-to-real transform overwrites F; G is free again after the forward transform
-    if (cufftExecZ2D(s->inv, s->F, s->G) != CUFFT_SUCCESS) return PIC_ECUDA;
-    launch(c, k_pif_gather, pb, 128, 0, P, c->np, s->M, s->w, s->beta, (const double*)s->G,
-           Ep + (size_t)d * c->np);
+    // the complex-to-real transform overwrites F, which the next component rebuilds
+    if (cufftExecZ2D(s->inv, s->F, comp[d]) != CUFFT_SUCCESS) return PIC_ECUDA;
   }
+  slot = c->prof_on ? c->ker[PIC_KER_PIF_GATHER].begin(c->stream) : -1;
+  PIF_DISPATCH_W(s->w, k_pif_gather3, pb, 128, 0, P, c->np, s->M, s->beta, (const double*)comp[0],
+                 (const double*)comp[1], (const double*)comp[2], Ep);
+  if (c->prof_on) c->ker[PIC_KER_PIF_GATHER].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
 }

@@ -2,9 +2,12 @@
 against the CPU oracle's direct non-uniform DFT sums (oracle/pif.py): the
 field at the particles, and a few leapfrog steps with it.
 
-The GPU evaluates the sums by NUFFTs (window width from the tolerance, FP64
-cuFFT); at tol = 1e-12 they match the direct sums to ~1e-12 of the field's
-maximum (checked at 1e-9)."""
+The GPU evaluates the sums by NUFFTs (window width w = ceil(-log10 tol) + 1,
+FP64 cuFFT); their error follows the tolerance: about 1.0-1.3 tol of the
+field's maximum for tol = 1e-4 (the tolerance of the paper's runs, w = 5),
+1e-6 and 1e-12, so the bounds below are 5 tol, and 1e-9 where FP64 rounding
+of the sums dominates (tol <= 1e-12; tol = 1e-15 takes the widest window,
+w = 16, which spans the whole oversampled grid at N = 8)."""
 import numpy as np
 import pytest
 
@@ -25,17 +28,22 @@ def pg():
     return pg
 
 
-@pytest.mark.parametrize("N,ppc", [(8, 1), (16, 1)])
-def test_pif_field_matches_direct_sums(pg, N, ppc):
+@pytest.mark.parametrize("N,ppc,tol,bound", [(8, 1, 1e-12, 1e-9), (16, 1, 1e-12, 1e-9), (8, 1, 1e-15, 1e-9),
+                                             (16, 2, 1e-4, 5e-4), (16, 1, 1e-6, 5e-6)])
+def test_pif_field_matches_direct_sums(pg, N, ppc, tol, bound):
     c = pg.Context().init(N, ppc, 21)
     npart = ppc * N ** 3
     E = torch.full((3 * npart,), float("nan"), dtype=torch.float64, device="cuda")
-    c.pif_field(E, tol=1e-12)
+    c.pif_field(E, tol=tol)
     pos, _ = opic.init_particles(N, ppc, 21)
     ref, imag = opif.field_at_particles(pos, np.full(npart, -L ** 3 / npart), N, L)
     got = E.cpu().numpy().reshape(3, -1)
-    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= bound * np.max(np.abs(ref))
     assert np.max(np.abs(imag)) <= 1e-12 * np.max(np.abs(ref))
+    # a second evaluation finds the particles already in cell order
+    E2 = torch.full_like(E, float("nan"))
+    c.pif_field(E2, tol=tol)
+    assert torch.allclose(E2, E, rtol=0.0, atol=1e-12 * float(np.max(np.abs(ref))))
 
 
 def test_pif_steps_match_the_oracle(pg):
