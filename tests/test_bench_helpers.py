@@ -27,3 +27,23 @@ def test_particle_kernel_bytes():
 def test_whole_job_rate_and_ranks():
     assert bench.whole_job_rate(4, 10, 2.0) == 20.0
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+
+
+def test_pif_window_width():
+    # about one digit a window point at oversampling 2: w = ceil(-log10 tol) + 1 in [4, 16]
+    assert bench.pif_width(1e-4) == 5
+    assert bench.pif_width(1e-6) == 7
+    assert bench.pif_width(1e-12) == 13
+    assert bench.pif_width(1e-2) == 4
+    assert bench.pif_width(1e-20) == 16
+    # flops of the window sums: a multiply and an add per point, component and particle
+    assert bench.PIF_FLOP_PER_POINT == 2
+
+
+def test_pif_cpu_baseline_scales_by_particles_and_modes():
+    # the direct sums cost one term per (particle, mode): the sampled rate of a
+    # 2x larger grid (8x the modes, 8x the particles at the same ppc) is ~64x lower
+    a = bench.cpu_baseline_pif(16, 1, Ns=8, ns=1024)
+    b = bench.cpu_baseline_pif(32, 1, Ns=8, ns=1024)
+    assert a["kind"] == "oracle" and a["unit"] == bench.UNIT
+    assert 16 < a["value"] / b["value"] < 256
