@@ -62,3 +62,17 @@ def test_pif_steps_match_the_oracle(pg):
     d = np.abs(got[:3] - pos)
     assert np.max(np.minimum(d, L - d)) <= 1e-9
     assert np.max(np.abs(got[3:] - vel)) <= 1e-9
+
+
+def test_pif_rejects_bad_arguments(pg):
+    # checked before any launch: a solver-only context has no particles, and
+    # the tolerance and time step must be positive and finite
+    c = pg.Context().init(8, 0, 0)
+    with pytest.raises(pg.PicError) as e:
+        c.pif_push(0.05, tol=1e-4)
+    assert e.value.code == pg.PIC_ESTATE
+    c = pg.Context().init(8, 1, 0)
+    for tol, dt in ((0.0, 0.05), (float("nan"), 0.05), (1e-4, float("inf"))):
+        with pytest.raises(pg.PicError) as e:
+            c.pif_push(dt, tol=tol)
+        assert e.value.code == pg.PIC_EINVAL
