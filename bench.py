@@ -770,7 +770,7 @@ def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", reference_iters=None, 
                       f"deposit+gather+push of {ns} of {ppc * n} particles (scaled linearly), one field energy"}
 
 
-def cpu_baseline_pif(N, ppc, Ns=16, ns=16384):
+def cpu_baseline_pif(N, ppc, Ns=16, ns=65536):
     """The CPU oracle's particle-in-Fourier field (direct type-1/type-2 sums)
     and push timed on ns particles with Ns^3 modes, scaled to the step by
     particles x modes (the direct sums cost one term per particle and mode)."""
