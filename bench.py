@@ -6,10 +6,14 @@ the library's C ABI: sort by cell + CIC scatter (pic_deposit), the Poisson
 solve to relative residual 1e-10 (poisson_solve_ex), the field energy
 (pic_field_energy) and E = -grad phi + CIC gather + leapfrog push
 (pic_gather_push). Default workload: 256^3 periodic grid, 8 particles per cell
-(134,217,728 particles, 64-byte FP64 records, 8.6 GB), Landau initial condition
-(k = 0.5, alpha = 0.05), dt = 0.05, warm-started solves.
+(134,217,728 particles, 64-byte records: fixed-point positions, double-float
+velocities; 8.6 GB), Landau initial condition (k = 0.5, alpha = 0.05),
+dt = 0.05, warm-started solves preconditioned by the multigrid V-cycle.
+--solver selects the solve (mg, mg_cnn, cnn, ssor, mixed, fp64), the FFT-PIC
+step (fft: spectral phi and E) or the particle-in-Fourier step (pif: NUFFTs,
+no grid deposit or solve).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver cnn|mixed|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver ...]
   python bench.py --impl reference      # the CPU oracle on a bounded sample
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own
