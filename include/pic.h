@@ -180,15 +180,20 @@ int pic_field_energy_E(pic_ctx *c, const double *E, double out_w[3]);
  * scheme: the charges go to the Fourier modes K_N (N = the grid size, modes
  * -N/2..N/2-1) by a type-1 NUFFT, E_hat = -i k rho_hat / (|k|^2 L^3) over
  * the symmetric modes |m_d| <= N/2 - 1 (k != 0), and the field is evaluated
- * at the particles by a type-2 NUFFT (exponential-of-semicircle window on a
- * 2x oversampled grid, FP64 cuFFT; the window width follows the relative
- * tolerance tol, about 1e-12 for tol = 1e-12). E: device FP64 [3 Np]
- * (E_x, E_y, E_z) in the ORIGINAL particle order (index p of pic_init). */
+ * at the particles by a type-2 NUFFT (exponential-of-semicircle window of
+ * w = ceil(-log10 tol) + 1 points, 4 <= w <= 16, on a 2x oversampled grid,
+ * FP64 arithmetic and cuFFT; the error is about tol relative to the field's
+ * maximum, down to ~1e-12). The particles are first sorted by cell (as by
+ * pic_deposit). E: device FP64 [3 Np] (E_x, E_y, E_z) in the ORIGINAL
+ * particle order (index p of pic_init). The oversampled grids take about
+ * 320 bytes per Fourier mode (kept between calls with the same N and w).
+ * PIC_EINVAL for tol <= 0 or NaN, PIC_ESTATE without particles. */
 int pic_pif_field(pic_ctx *c, double tol, double *E);
 
 /* One leapfrog step of the particle-in-Fourier scheme: the PIF field at the
  * particles (no grid deposit or solve), then the kick and drift of
- * pic_gather_push. */
+ * pic_gather_push (the first step after pic_init kicks by dt/2). PIC_EINVAL
+ * for tol <= 0 or NaN or a non-finite dt, PIC_ESTATE without particles. */
 int pic_pif_push(pic_ctx *c, double tol, double dt);
 
 /* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
