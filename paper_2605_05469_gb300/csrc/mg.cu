@@ -45,6 +45,8 @@ namespace {
 // blocks an SM; measured, four blocks with fewer stages were slower, the
 // kernels spilling at the 64-register limit that four blocks impose).
 constexpr size_t kMgSmemBudget = 72 * 1024;
+// damped-Jacobi sweeps before and after the coarse-grid correction (even, >= 2)
+constexpr int kMgNu = 2;
 
 // Whether kernel k of level L runs in the tall-block form: the kernels with
 // the prolongation keep the small block (their coarse-value registers would
@@ -208,6 +210,25 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
   };
   const float* nul = nullptr;
   float* nulw = nullptr;
+  // damped-Jacobi sweeps before and after the coarse correction (even); the
+  // first two are fused (from zero before, with the prolongation after) and
+  // every further pair ping-pongs x -> t -> x
+  const int nu = kMgNu;
+  auto sweep_pair = [&](MgLevel& L) {
+    const int l = (int)(&L - s->lev);
+    if (L.zmarch) {
+      zmarch(L, PIC_KER_MG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, false>, (const float*)xl(l), rl(l), L.t);
+      zmarch(L, PIC_KER_MG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, false>, (const float*)L.t, rl(l), xl(l));
+    } else if (L.streamed) {
+      auto k = tall_form(L, kSmooth) ? mg::k_mg_stencil<mg::kSmooth, false, true> : mg::k_mg_stencil<mg::kSmooth, false, false>;
+      slab(L, kSmooth, PIC_KER_MG_SMOOTH, k, (const float*)xl(l), rl(l), L.t, nulw, nul);
+      slab(L, kSmooth, PIC_KER_MG_SMOOTH, k, (const float*)L.t, rl(l), xl(l), nulw, nul);
+    } else {
+      const int g = grid_for(c, (size_t)L.N * L.N * L.N);
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);
+      launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
+    }
+  };
   // down: pre-smooth, residual, restrict
   for (int l = 0; l < B; ++l) {
     MgLevel& L = s->lev[l];
@@ -217,11 +238,14 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
       if ((e = cnn_apply(c, rl(0), xl(0), nullptr, n))) return e;
     } else if (L.zmarch) {
       zmarch(L, PIC_KER_MG_PRE, mg::k_mg_zmarch<mg::kZPre, false>, rl(l), nul, xl(l));
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     } else if (L.streamed) {
       slab(L, kPre, PIC_KER_MG_PRE, tall_form(L, kPre) ? mg::k_mg_pre<true> : mg::k_mg_pre<false>, rl(l), xl(l));
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     } else {
       launch(c, mg::k_mg_jacobi, g, 256, 0, nul, rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     }
     if (L.streamed) {
       if (L.zmarch)
@@ -241,7 +265,7 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     }
   }
   // the small levels in one CTA
-  launch(c, mg::k_mg_small, 1, mg::kSmallThreads, s->small_smem, rl(B), xl(B), s->small, 2, done);
+  launch(c, mg::k_mg_small, 1, mg::kSmallThreads, s->small_smem, rl(B), xl(B), s->small, nu, done);
   // up: prolong-add, post-smooth
   for (int l = B - 1; l >= 0; --l) {
     MgLevel& L = s->lev[l];
@@ -265,13 +289,16 @@ int mg_apply(pic_ctx* c, const float* r, float* z, bool learned, const int* done
     } else if (L.zmarch) {
       zmarch(L, PIC_KER_MG_PROLONG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, true>, (const float*)xl(l), rl(l), L.t, ec);
       zmarch(L, PIC_KER_MG_SMOOTH, mg::k_mg_zmarch<mg::kZSmooth, false>, (const float*)L.t, rl(l), xl(l));
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     } else if (L.streamed) {
       slab(L, kSmoothProlong, PIC_KER_MG_PROLONG_SMOOTH, tall_form(L, kSmoothProlong) ? mg::k_mg_stencil<mg::kSmooth, true, true> : mg::k_mg_stencil<mg::kSmooth, true, false>, (const float*)xl(l), rl(l), L.t, nulw, ec);
       slab(L, kSmooth, PIC_KER_MG_SMOOTH, tall_form(L, kSmooth) ? mg::k_mg_stencil<mg::kSmooth, false, true> : mg::k_mg_stencil<mg::kSmooth, false, false>, (const float*)L.t, rl(l), xl(l), nulw, nul);
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     } else {
       launch(c, mg::k_mg_prolong_add, g, 256, 0, xl(l), ec, L.N / 2, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)xl(l), rl(l), L.t, L.N, done);
       launch(c, mg::k_mg_jacobi, g, 256, 0, (const float*)L.t, rl(l), xl(l), L.N, done);
+      for (int k = 2; k < nu; k += 2) sweep_pair(L);
     }
   }
   CK(cudaGetLastError());
