@@ -524,10 +524,9 @@ def run_ours(args):
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
-                               (f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc ({ppc * n} particles), "
-                                + ("FFT pseudo-spectral solve with the spectral field" if use_fft else
-                                   f"particle-in-Fourier field ({N}^3 modes, NUFFT tol {args.pif_tol:g})"
-                                   if use_pif else f"solve to rel-res {TOL:g}") + f", dt {DT}"),
+                               pic_workload(N, ppc, "FFT pseudo-spectral solve with the spectral field" if use_fft
+                                            else f"particle-in-Fourier field ({N}^3 modes, NUFFT tol "
+                                                 f"{args.pif_tol:g})" if use_pif else None),
                    "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
                    "warm_start": True, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
@@ -799,6 +798,13 @@ def cpu_baseline_pif(N, ppc, Ns=16, ns=65536):
                       f"to {npart} x {N}^3) and their push (scaled by particles)"}
 
 
+def pic_workload(N, ppc, field=None):
+    """The name of the PIC-step workload (both arms): grid, particles, how the
+    field is obtained (default: the Poisson solve to the bench tolerance)."""
+    return (f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc ({ppc * N ** 3} particles), "
+            + (field or f"solve to rel-res {TOL:g}") + f", dt {DT}")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -819,16 +825,17 @@ def run_reference(args):
     for _ in range(max(1, args.steps)):
         base = cpu_baseline(N, ppc, iters)
     total = time.perf_counter() - t0
+    value = float(f"{base['value']:.6g}")
     out = {
-        "metric": METRIC, "value": round(base["value"], 6), "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(1e3 / base["value"], 1), "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: seeded Landau density + particles", "impl": "reference",
-        "config": {"workload": f"Landau PIC step, {N}^3 periodic grid x {ppc} ppc, solve to rel-res {TOL:g}",
+        "config": {"workload": pic_workload(N, ppc),
                    "N": N, "ppc": ppc, "iters_per_solve_est": iters},
-        "cpu_baseline": {"value": base["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": base["sample"] + f"; {args.steps} samples in {total:.1f} s"},
-        "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return out
 
