@@ -341,6 +341,14 @@ class Context:
     def particles(self):
         return pic_get_particles(self.h, self.num_particles)
 
+    def particles_into(self, out):
+        """The particles into a device FP64 tensor of 6 Np (x, y, z, vx, vy, vz
+        blocks, original order); returns whether velocities lag by dt/2."""
+        half = ctypes.c_int()
+        _check(lib().pic_get_particles(self.h, _dptr(out, "float64", 6 * self.num_particles, "out"), 1,
+                                       ctypes.byref(half)), "pic_get_particles")
+        return bool(half.value)
+
     def apply_laplacian(self, x, y):
         pic_apply_laplacian(self.h, x, y, self.n)
 

@@ -14,9 +14,10 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    # the guard-band bounds checks run after every parity test, so that a
-    # stopped run (-x) still reports the parity of all kernels
-    items.sort(key=lambda it: "test_gpu_canaries" in it.nodeid)
+    # the small-size parity tests first, then the guard-band bounds checks,
+    # then the full-size checks (the longest), so that a stopped run (-x)
+    # still reports the parity of every kernel
+    items.sort(key=lambda it: 1 if "test_gpu_canaries" in it.nodeid else 2 if "test_gpu_fullsize" in it.nodeid else 0)
     try:
         import torch
         have_gpu = torch.cuda.is_available()
