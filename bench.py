@@ -132,7 +132,7 @@ def whole_job_rate(world, steps_per_rank, seconds):
     return world * steps_per_rank / seconds
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
@@ -162,7 +162,7 @@ def parse():
     ap.add_argument("--compare-reps", type=int, default=2, help="cold solves per solver in the comparison (best kept)")
     ap.add_argument("--compare-maxit", type=int, default=MAXIT,
                     help="iteration cap of the comparison solves (mixed Jacobi-CG stagnates at 1024^3)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -524,9 +524,7 @@ def run_ours(args):
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
         "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
                                 f"cold start, rel-res {TOL:g}") if solve_only else
-                               pic_workload(N, ppc, "FFT pseudo-spectral solve with the spectral field" if use_fft
-                                            else f"particle-in-Fourier field ({N}^3 modes, NUFFT tol "
-                                                 f"{args.pif_tol:g})" if use_pif else None),
+                               pic_workload(N, ppc, field_name(args)),
                    "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
                    "warm_start": True, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
@@ -798,6 +796,16 @@ def cpu_baseline_pif(N, ppc, Ns=16, ns=65536):
                       f"to {npart} x {N}^3) and their push (scaled by particles)"}
 
 
+def field_name(args):
+    """How the step obtains its field when it is not the bench's Poisson solve
+    (None for the solve)."""
+    if args.solver == "fft":
+        return "FFT pseudo-spectral solve with the spectral field"
+    if args.solver == "pif":
+        return f"particle-in-Fourier field ({args.N}^3 modes, NUFFT tol {args.pif_tol:g})"
+    return None
+
+
 def pic_workload(N, ppc, field=None):
     """The name of the PIC-step workload (both arms): grid, particles, how the
     field is obtained (default: the Poisson solve to the bench tolerance)."""
@@ -810,20 +818,27 @@ def run_reference(args):
     if rank != 0:
         return None
     N, ppc = args.N, args.ppc
-    # iterations per warm-started solve: the oracle's Jacobi-PCG on this workload
-    # needs the same count as any exact-arithmetic CG; measured once at 64^3 and
-    # scaled by N (CG iterations grow like sqrt(kappa) ~ N).
-    from oracle import pic as opic
-    N0 = 64
-    pos, _ = opic.init_particles(N0, ppc, SEED)
-    L = 4.0 * np.pi
-    rho = opic.deposit(pos, N0, L)
-    _, it0, _, _ = opic.pcg_jacobi(rho, np.zeros(N0 ** 3), N0, L / N0, TOL, MAXIT)
-    iters = it0 * N / N0
+    iters = None
+    if args.solver not in ("fft", "pif"):
+        # iterations per warm-started solve: the oracle's Jacobi-PCG on this
+        # workload needs the same count as any exact-arithmetic CG; measured once
+        # at 64^3 and scaled by N (CG iterations grow like sqrt(kappa) ~ N).
+        from oracle import pic as opic
+        N0 = 64
+        pos, _ = opic.init_particles(N0, ppc, SEED)
+        L = 4.0 * np.pi
+        rho = opic.deposit(pos, N0, L)
+        _, it0, _, _ = opic.pcg_jacobi(rho, np.zeros(N0 ** 3), N0, L / N0, TOL, MAXIT)
+        iters = it0 * N / N0
     t0 = time.perf_counter()
     base = None
     for _ in range(max(1, args.steps)):
-        base = cpu_baseline(N, ppc, iters)
+        if args.solver == "pif":
+            base = cpu_baseline_pif(N, ppc)
+        elif args.solver == "fft":
+            base = cpu_baseline(N, ppc, 1, "fft")
+        else:
+            base = cpu_baseline(N, ppc, iters)
     total = time.perf_counter() - t0
     value = float(f"{base['value']:.6g}")
     out = {
@@ -831,7 +846,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: seeded Landau density + particles", "impl": "reference",
-        "config": {"workload": pic_workload(N, ppc),
+        "config": {"workload": pic_workload(N, ppc, field_name(args)), "solver": args.solver,
                    "N": N, "ppc": ppc, "iters_per_solve_est": iters},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": base["sample"] + f"; {args.steps} samples in {total:.1f} s"},

@@ -9,10 +9,14 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_json_line():
+import pytest
+
+
+@pytest.mark.parametrize("solver", ["mg", "pif"])
+def test_reference_arm_json_line(solver):
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--N", "16", "--ppc", "2",
-                          "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600,
-                         check=True).stdout
+                          "--steps", "1", "--warmup", "0", "--solver", solver], cwd=ROOT, capture_output=True,
+                         text=True, timeout=600, check=True).stdout
     lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     r = json.loads(lines[0])
@@ -21,7 +25,8 @@ def test_reference_arm_json_line():
     assert r["impl"] == "reference" and "unavailable" not in r
     assert r["metric"] == bench.METRIC and r["unit"] == bench.UNIT and r["higher_is_better"] is True
     assert r["value"] > 0 and r["steps"] == 1 and r["warmup"] == 0
-    assert r["config"]["workload"] == bench.pic_workload(16, 2)
+    args = bench.parse(["--N", "16", "--ppc", "2", "--solver", solver])
+    assert r["config"]["workload"] == bench.pic_workload(16, 2, bench.field_name(args))
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
