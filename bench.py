@@ -5,15 +5,20 @@ One step is one pass of the whole hot path of the PIC loop (Fig. 1) through
 the library's C ABI: sort by cell + CIC scatter (pic_deposit), the Poisson
 solve to relative residual 1e-10 (poisson_solve_ex), the field energy
 (pic_field_energy) and E = -grad phi + CIC gather + leapfrog push
-(pic_gather_push). Default workload: 256^3 periodic grid, 8 particles per cell
-(134,217,728 particles, 64-byte records: fixed-point positions, double-float
-velocities; 8.6 GB), Landau initial condition (k = 0.5, alpha = 0.05),
-dt = 0.05, warm-started solves preconditioned by the multigrid V-cycle.
---solver selects the solve (mg, mg_cnn, cnn, ssor, mixed, fp64), the FFT-PIC
-step (fft: spectral phi and E) or the particle-in-Fourier step (pif: NUFFTs,
-no grid deposit or solve).
+(pic_gather_push). Default workload: the full PIC run with the learned part,
+512^3 periodic grid, 8 particles per cell (1,073,741,824 particles, 64-byte
+records: fixed-point positions, double-float velocities), Landau initial
+condition (k = 0.5, alpha = 0.05), dt = 0.05, warm-started solves by
+mixed-precision flexible CG with the learned preconditioner (trained on the
+GPU before timing). The same particles then take timed steps with the
+multigrid-preconditioned solve, and cold solves of the last deposit (512^3)
+and of a 1024^3 Landau density + noise right-hand side compare the FP64
+Jacobi-PCG reference with every solver. --solver selects the step's solve
+(cnn, mg, mg_cnn, ssor, mixed, fp64), the FFT-PIC step (fft: spectral phi
+and E) or the particle-in-Fourier step (pif: NUFFTs, no grid deposit or
+solve).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver ...]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--solver ...] [--N ...]
   python bench.py --impl reference      # the CPU oracle on a bounded sample
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs its own
@@ -41,6 +46,16 @@ SEED = 0x5EED
 DT = 0.05
 TOL = 1e-10
 MAXIT = 20000
+SOLVERS = ["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft", "pif"]
+# the full-PIC configuration with the learned part: 512^3 periodic grid x 8
+# particles per cell (1.07e9 particles), flexible CG with the learned
+# preconditioner, warm-started solves to rel-res 1e-10
+DEFAULT_N = 512
+DEFAULT_SOLVER = "cnn"
+# also timed on the same particles: the multigrid-preconditioned step
+DEFAULT_ALT_SOLVERS = ("mg",)
+# cold solves of the largest solver-only grid, after the particles are freed
+DEFAULT_COMPARE_GRIDS = (1024,)
 
 # algorithmic bytes per cell of one launch of the two CG kernels
 KER_BYTES = {
@@ -68,22 +83,23 @@ MG_BYTES = {
 # with the learned smoother the prolongation slot is the residual of x + P e_c:
 # read x, e_c, r; write res and x + P e_c
 MG_BYTES_PROLONG_RESID = 16.5
-# algorithmic bytes of the particle kernels: per particle, and per grid node
+# algorithmic bytes of the particle kernels, per particle and per grid node,
+# counted on the particle state itself (three FP64 positions and three FP64
+# velocities, 48 B), not on the library's record layout
 PARTICLE_BYTES = {
-    # scatter: read and write the 64-byte record, read its key and rank, one
-    # offset per particle (cached: counted once per cell)
-    "scatter": (136, 4),
-    # deposit: the record's first 32-byte sector (offsets), 8 corner sums per
-    # cell written and read back (8 B each), the cell offsets, rho written
-    "deposit": (32, 64 + 64 + 4 + 8),
-    # push: read and write the 64-byte record, its key and rank; E (3 x 8 B) read
-    # once per node
-    "push": (136, 24),
+    # sort: the state read and written once, and the particle's cell key read
+    "scatter": (100, 0),
+    # deposit: read the positions (24 B), write rho (8 B a node)
+    "deposit": (24, 8),
+    # gather + push: read and write positions and velocities (96 B), E read
+    # once per node (3 x 8 B)
+    "push": (96, 24),
 }
-# DRAM traffic per particle of one launch (dram__bytes_read.sum +
-# dram__bytes_write.sum over the particle count) measured by ncu on the
-# 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
-# count): it stands for the same kernels at other sizes
+# bytes per particle the library's kernels move by design: the 64-byte record
+# (cell index and 64-bit fixed-point offsets, double-float velocities, id and
+# key) read and written, plus the 4-byte key and rank arrays (the deposit
+# reads the record's first 32-byte sector)
+PARTICLE_IMPL_BYTES = {"scatter": 136, "deposit": 32, "push": 136}
 # particle-in-Fourier window sums: a multiply and an atomic add (spreading)
 # or one FMA (interpolation) per window point and particle
 PIF_FLOP_PER_POINT = 2
@@ -95,6 +111,10 @@ def pif_width(tol):
     return min(16, max(4, int(math.ceil(-math.log10(tol))) + 1))
 
 
+# DRAM traffic per particle of one launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over the particle count) measured by ncu on the
+# 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
+# count): it stands for the same kernels at other sizes
 MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.70, "scatter": 133.72}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
@@ -138,10 +158,10 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft", "pif"], default="mg",
-                    help="mg (default, the fastest): mixed-precision flexible CG with a multigrid V-cycle (damped "
-                         "Jacobi smoothing); cnn: flexible CG with the learned preconditioner (trained on the GPU "
-                         "before timing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
+    ap.add_argument("--solver", choices=SOLVERS, default=DEFAULT_SOLVER,
+                    help="cnn (default): mixed-precision flexible CG with the learned preconditioner (trained on "
+                         "the GPU before timing); mg: flexible CG with a multigrid V-cycle (damped Jacobi "
+                         "smoothing); mg_cnn: the V-cycle with the learned network smoothing the finest level; "
                          "mixed: FP32 Jacobi-CG + FP64 reliable updates; fp64: the FP64 Jacobi-PCG reference; ssor: the "
                          "paper's PCG configuration (red-black SSOR, 4 inner, 2 outer, damping pi/2); fft: the "
                          "paper's other scheme, the FFT pseudo-spectral solve (cuFFT FP64) with the spectral field "
@@ -155,11 +175,18 @@ def parse(argv=None):
                          "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
     ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
                     help="pic: full PIC step; solve: one cold-start Poisson solve of a Landau density + noise rhs")
-    ap.add_argument("--N", type=int, default=256)
+    ap.add_argument("--N", type=int, default=DEFAULT_N)
     ap.add_argument("--ppc", type=int, default=8)
+    ap.add_argument("--alt-solvers", default=",".join(DEFAULT_ALT_SOLVERS),
+                    help="comma-separated solvers whose PIC steps are also timed, after the main run, on the "
+                         "same particles (extra keys; empty = none)")
+    ap.add_argument("--compare-grids", default=",".join(str(g) for g in DEFAULT_COMPARE_GRIDS),
+                    help="comma-separated grid sizes of extra cold-solve comparisons on a Landau density + "
+                         "N(0, 0.01^2) noise right-hand side, run after the PIC context is freed (empty = none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-vs-mixed solve comparison")
-    ap.add_argument("--compare-reps", type=int, default=2, help="cold solves per solver in the comparison (best kept)")
+    ap.add_argument("--compare-reps", type=int, default=2,
+                    help="cold solves per solver in the comparison (best kept; solves longer than 2 s run once)")
     ap.add_argument("--compare-maxit", type=int, default=MAXIT,
                     help="iteration cap of the comparison solves (mixed Jacobi-CG stagnates at 1024^3)")
     return ap.parse_args(argv)
@@ -227,6 +254,142 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- ours
+def particle_roofline(rows, k, np_, n, hbm, peak_kind):
+    """HBM roofline of a particle kernel from its sampled launches: the
+    algorithmic bytes of the FP64 particle state (and the grid) over the
+    average CUDA-event duration, with the ncu DRAM traffic beside them."""
+    r = rows[k]
+    b = r["bytes_per_particle"] * np_ + r["bytes_per_node"] * n
+    traffic = round(MEASURED_TRAFFIC_PER_PARTICLE[k] * np_) if k in MEASURED_TRAFFIC_PER_PARTICLE else None
+    return {"kernel": {"scatter": "k_scatter (sort: 64-byte records to their cells)",
+                       "deposit": "k_deposit_cells + k_deposit_nodes (CIC scatter)",
+                       "push": "k_gather_push (CIC gather + leapfrog, double-float)"}[k],
+            "bound": "hbm", "achieved": round(r["gbs"], 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(r["gbs"] / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": traffic,
+            "traffic_source": ("ncu DRAM bytes per particle at 128^3 x 8 ppc, scaled by the particle count"
+                               if traffic is not None else None),
+            "traffic_over_algorithmic": round(traffic / b, 3) if traffic is not None else None,
+            "algorithmic_bytes": b, "algorithmic_bytes_per_particle": r["bytes_per_particle"],
+            "impl_bytes_per_particle": r["impl_bytes_per_particle"], "avg_launch_us": round(r["avg_us"], 2)}
+
+
+def mem_available_bytes():
+    """MemAvailable of the host (0 if unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrier, torch, unit, solve_into):
+    """The metric end to end through the public API on the host's wall clock,
+    with the step's inputs copied in from host memory and its result read back
+    every step: the PIC step's particle state (48 B a particle each way, via
+    pic_set_particles / pic_get_particles, page-locked host memory) and its
+    field energy; a solve's rho in and phi out."""
+    if solve_only:
+        rho_h = rho.cpu().pin_memory()
+        phi_h = torch.empty_like(rho_h).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            rho.copy_(rho_h, non_blocking=True)
+            phi.zero_()
+            solve_into(rho, phi)
+            phi_h.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n, "note": "rho from pinned host memory, phi back to it, every solve"}
+    state_bytes = 48 * np_
+    avail = mem_available_bytes()
+    if avail < 2 * state_bytes + (48 << 30):
+        # not enough host memory for the state: the device-resident loop, the
+        # field energy read back every step
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step(False)
+        torch.cuda.synchronize()
+        barrier()
+        s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 24,
+                "note": f"host memory too small for the particle state ({avail / 2**30:.0f} GiB available): "
+                        "particles stay on the device, the field energy is read back every step"}
+    state = torch.empty(6 * np_, dtype=torch.float64)
+    cudart = torch._C._cudart
+    registered = cudart.cudaHostRegister(state.data_ptr(), state_bytes, 0) == cudart.cudaError.success
+    try:
+        half = c.particles_to_host(state)  # the state starts on the host (untimed)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            c.set_particles(state, half)
+            step(False)  # reads the field energy back
+            half = c.particles_to_host(state)
+        torch.cuda.synchronize()
+        barrier()
+        s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    finally:
+        if registered:
+            cudart.cudaHostUnregister(state.data_ptr())
+        del state
+    return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": state_bytes,
+            "d2h_bytes_per_step": state_bytes + 24,
+            "note": ("every step: the particle state (FP64 x, y, z, vx, vy, vz) in from "
+                     + ("page-locked" if registered else "pageable") + " host memory (pic_set_particles), "
+                     "the step, its field energy read back, the state out to host memory (pic_get_particles)")}
+
+
+def solver_modes(pg, solver):
+    """(precision, preconditioner) of a --solver name."""
+    prec = pg.PREC_FP64 if solver == "fp64" else pg.PREC_MIXED
+    pc = {"cnn": pg.PC_CNN, "mg": pg.PC_MG, "mg_cnn": pg.PC_MG_CNN, "ssor": pg.PC_SSOR}.get(solver, pg.PC_JACOBI)
+    return prec, pc
+
+
+def dtype_label(pg, solver, cnn_apply="tc", pif_tol=1e-4, solve_only=False):
+    """What the step computes in: particle state and arithmetic, grid fields,
+    the solve's vectors and reductions, the preconditioner."""
+    parts = [] if solve_only else ["particles: 64-bit fixed-point positions + double-float velocities"]
+    if solver == "pif":
+        return "; ".join(parts + [f"FP64 particle-in-Fourier NUFFTs (tol {pif_tol:g}) and cuFFT"])
+    parts.append("rho, phi FP64")
+    if solver == "fft":
+        return "; ".join(parts + ["FP64 spectral solve (cuFFT)"])
+    if solver == "fp64":
+        return "; ".join(parts + ["solve FP64 throughout"])
+    parts.append("solve FP32 vectors + FP64 reductions and residual recomputation")
+    if solver == "cnn":
+        parts.append({"tc": "BF16 tensor-core", "tc_fused": "BF16 tensor-core (fused)", "fp32": "FP32",
+                      "layers": "BF16 four-conv"}[cnn_apply] + " learned preconditioner (composed 9^3 kernel)")
+    elif solver == "mg":
+        parts.append("FP32 multigrid V-cycle")
+    elif solver == "mg_cnn":
+        parts.append("FP32 multigrid V-cycle, BF16 learned finest-level smoother")
+    elif solver == "ssor":
+        parts.append("FP32 red-black SSOR")
+    return "; ".join(parts)
+
+
+def l2_note(N, ppc, solve_only):
+    """How the timed steps relate to the 129 MB L2: every input is larger."""
+    n = N ** 3
+    cells = f"grid vectors {n * 4 / 1e6:.0f} MB (FP32) to {n * 8 / 1e6:.0f} MB (FP64) each"
+    if max(n * 8, 0 if solve_only else ppc * n * 64) < 129e6:
+        return "small case: inputs fit in the 129 MB L2, no flush between steps"
+    if solve_only:
+        return f"inputs larger than L2 ({cells})"
+    return (f"inputs larger than L2 (particle records {ppc * n * 64 / 1e9:.1f} GB; {cells})")
+
+
 def run_ours(args):
     import torch
     import paper_2605_05469_gb300 as pg
@@ -243,18 +406,20 @@ def run_ours(args):
 
     N, ppc = args.N, args.ppc
     n = N ** 3
-    prec = pg.PREC_FP64 if args.solver == "fp64" else pg.PREC_MIXED
-    pc = {"cnn": pg.PC_CNN, "mg": pg.PC_MG, "mg_cnn": pg.PC_MG_CNN, "ssor": pg.PC_SSOR}.get(args.solver,
-                                                                                          pg.PC_JACOBI)
+    prec, pc = solver_modes(pg, args.solver)
     stream = torch.cuda.current_stream()
     solve_only = args.workload == "solve"
+    alt_solvers = [] if solve_only else [s for s in args.alt_solvers.split(",") if s and s != args.solver]
+    for s_ in alt_solvers:
+        if s_ not in SOLVERS:
+            raise SystemExit(f"unknown solver in --alt-solvers: {s_}")
     weights, train_info = None, None
-    if args.solver in ("cnn", "mg_cnn") or not args.no_compare:
+    if any(s_ in ("cnn", "mg_cnn") for s_ in [args.solver] + alt_solvers) or not args.no_compare:
         weights, train_info = train_preconditioner(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
     apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
                   "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
-    if weights is not None and pc in (pg.PC_CNN, pg.PC_MG_CNN):
+    if weights is not None:
         c.cnn_set_weights(weights)
         c.cnn_set_apply(apply_mode)
     phi = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -263,50 +428,60 @@ def run_ours(args):
         rho = inputs.landau_noise_rhs_torch(N, 0xC0FFEE + rank, "cuda")
     else:
         rho = torch.empty(n, dtype=torch.float64, device="cuda")
-    infos = []
+    E3 = None
 
-    use_fft = args.solver == "fft"
-    use_pif = args.solver == "pif"
-    E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda") if use_fft else None
+    def make_step(solver, infos):
+        """One step of the workload with the given solver; appends the solve's
+        info to `infos` when recording."""
+        nonlocal E3
+        s_prec, s_pc = solver_modes(pg, solver)
+        use_fft, use_pif = solver == "fft", solver == "pif"
+        if use_fft and E3 is None:
+            E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda")
 
-    def solve_into(rho_, phi_):
-        if use_fft:
-            # direct solve: no iterations or residual; its time is the solve phase's
-            c.fft_solve(rho_, phi_, E3)
-            return {"iters": 0, "t_ms": None, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
-        return c.solve(rho_, phi_, tol=TOL, maxit=MAXIT, precision=prec, precond=pc)
-
-    def step(record):
-        if solve_only:
-            phi.zero_()
-            info = solve_into(rho, phi)
-            W = None
-        elif use_pif:
-            c.pif_push(DT, tol=args.pif_tol)
-            info = {"iters": 0, "t_ms": 0.0, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
-            W = None
-        else:
-            c.deposit(rho)
-            info = solve_into(rho, phi)
+        def solve_into(rho_, phi_):
             if use_fft:
-                W = c.field_energy_E(E3)
-                c.gather_push_field(E3, DT)
-            else:
-                W = c.field_energy(phi)
-                c.gather_push(phi, DT)
-        if record:
-            infos.append(info)
-        return W
+                # direct solve: no iterations or residual; its time is the solve phase's
+                c.fft_solve(rho_, phi_, E3)
+                return {"iters": 0, "t_ms": None, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
+            return c.solve(rho_, phi_, tol=TOL, maxit=MAXIT, precision=s_prec, precond=s_pc)
 
-    for _ in range(args.warmup):
-        step(False)
-    c.profile(True)
-    c.profile_read(reset=True)
+        def step(record):
+            if solve_only:
+                phi.zero_()
+                info = solve_into(rho, phi)
+                W = None
+            elif use_pif:
+                c.pif_push(DT, tol=args.pif_tol)
+                info = {"iters": 0, "t_ms": 0.0, "rel_res": 0.0, "reliable_updates": 0, "converged": True}
+                W = None
+            else:
+                c.deposit(rho)
+                info = solve_into(rho, phi)
+                if use_fft:
+                    W = c.field_energy_E(E3)
+                    c.gather_push_field(E3, DT)
+                else:
+                    W = c.field_energy(phi)
+                    c.gather_push(phi, DT)
+            if record:
+                infos.append(info)
+            return W
+        step.solve_into = solve_into
+        return step
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    infos = []
+    step = make_step(args.solver, infos)
+    use_fft, use_pif = args.solver == "fft", args.solver == "pif"
+    for _ in range(args.warmup):
+        step(False)
+    c.profile(True)
+    c.profile_read(reset=True)
 
     barrier()
     clocks = ClockSampler(local)
@@ -328,20 +503,41 @@ def run_ours(args):
     unit = "solves/s" if solve_only else UNIT
     metric = ("Poisson solves/s to rel-res 1e-10 (7-point FD, cold start)" if solve_only else METRIC)
 
-    # end to end through the public API, host wall clock: per step the host
-    # reads back the step's result (field energy, 3 doubles) and the solver's
-    # status; the particle state is device resident by design.
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step(False)
-    torch.cuda.synchronize()
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
-    e2e = {"value": whole_job_rate(world, args.steps, e2e_s), "unit": unit, "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": 0 if solve_only else 24,
-           "note": "wall clock through the Python binding; per step the field energy is read to host"}
+    # end to end through the public API, host wall clock. PIC step: the
+    # particle state (FP64 positions and velocities, 48 B a particle) lives in
+    # page-locked host memory; every step copies it in (pic_set_particles),
+    # runs the step, reads the field energy and copies the state back out
+    # (pic_get_particles). Solver-only: rho in from host memory, phi back.
+    np_ = 0 if solve_only else ppc * n
+    e2e = end_to_end(c, step, np_, n, rho, phi, args.steps, solve_only, world, dist, barrier, torch, unit,
+                     step.solve_into)
+
+    # the other solvers' PIC steps on the same particles (extra keys)
+    alt = {}
+    for s_ in alt_solvers:
+        alt_infos = []
+        st_ = make_step(s_, alt_infos)
+        for _ in range(max(1, args.warmup // 2)):
+            st_(False)
+        c.profile(True)
+        c.profile_read(reset=True)
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            st_(True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        a_ms = max_over_ranks(a0.elapsed_time(a1), dist, "cuda")
+        a_prof = c.profile_read(reset=True)
+        c.profile(False)
+        alt[s_] = {"value": round(whole_job_rate(world, args.steps, a_ms / 1e3), 4), "unit": unit,
+                   "ms_per_step": round(a_ms / args.steps, 3), "steps": args.steps,
+                   "dtype": dtype_label(pg, s_, args.cnn_apply, args.pif_tol),
+                   "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in a_prof["phase_ms"].items()},
+                   "solve_iters_mean": (statistics.mean(i["iters"] for i in alt_infos) if alt_infos else None)}
 
     # solver-only end to end: rho from pinned host memory, phi back to host
     if use_pif:
@@ -354,11 +550,12 @@ def run_ours(args):
     for _ in range(reps):
         rho.copy_(rho_host, non_blocking=True)
         phi.zero_()
-        solve_into(rho, phi)
+        step.solve_into(rho, phi)
         phi_host.copy_(phi, non_blocking=True)
     torch.cuda.synchronize()
     e2e_solve = {"value": reps / (time.perf_counter() - t0), "unit": "solves/s (cold start)",
                  "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+    del rho_host, phi_host
 
     if rank != 0:
         if dist is not None:
@@ -412,15 +609,17 @@ def run_ours(args):
             vcycle = {"avg_us": round(avg_ms * 1e3, 2), "samples": prof["ker_samples"]["precond"],
                       "bytes_per_fine_cell": round(bpc, 3), "gbs": round(bpc * n / (avg_ms * 1e-3) / 1e9, 1),
                       "note": "one V-cycle, every level; bytes of the plane-streamed levels"}
-    # the particle kernels (one launch each per step)
-    np_ = 0 if solve_only else ppc * n
+    # the particle kernels (one launch each per step): algorithmic bytes of
+    # the FP64 particle state, and the bytes the record layout moves
     for k, (bp, bn) in PARTICLE_BYTES.items():
         if not np_ or not prof["ker_samples"].get(k):
             continue
         avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
         b = bp * np_ + bn * n
         rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "bytes_per_particle": bp,
-                   "bytes_per_node": bn, "gbs": b / (avg_ms * 1e-3) / 1e9, "launches_per_step": 1}
+                   "bytes_per_node": bn, "gbs": b / (avg_ms * 1e-3) / 1e9, "launches_per_step": 1,
+                   "impl_bytes_per_particle": PARTICLE_IMPL_BYTES[k],
+                   "impl_gbs": (PARTICLE_IMPL_BYTES[k] * np_ + bn * n) / (avg_ms * 1e-3) / 1e9}
     # particle-in-Fourier: the spreading kernel (the charge) and the
     # interpolation kernel (the three field components at once), one launch
     # each a step; FP64 window sums over w^3 grid points a particle
@@ -478,19 +677,7 @@ def run_ours(args):
                 "peak_source": "measured FP32 FMA loop (no FP32 figure in MEASURED_PEAKS.json)",
                 "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n, "avg_launch_us": round(r["avg_us"], 2)}
     elif dom in PARTICLE_BYTES:
-        r = rows[dom]
-        b = r["bytes_per_particle"] * np_ + r["bytes_per_node"] * n
-        roof = {"kernel": {"scatter": "k_scatter (sort: 64-byte records to their cells)",
-                           "deposit": "k_deposit_cells + k_deposit_nodes (CIC scatter)",
-                           "push": "k_gather_push (CIC gather + leapfrog, double-float)"}[dom],
-                "bound": "hbm", "achieved": round(r["gbs"], 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(r["gbs"] / hbm, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": (round(MEASURED_TRAFFIC_PER_PARTICLE[dom] * np_) if dom in MEASURED_TRAFFIC_PER_PARTICLE
-                            else None),
-                "traffic_source": ("ncu DRAM bytes per particle at 128^3 x 8 ppc, scaled by the particle count"
-                                   if dom in MEASURED_TRAFFIC_PER_PARTICLE else None),
-                "algorithmic_bytes": b, "avg_launch_us": round(r["avg_us"], 2),
-                "note": "dominant kernel of the whole step (device time per step)"}
+        roof = particle_roofline(rows, dom, np_, n, hbm, peak_kind)
     elif dom is not None:
         r = rows[dom]
         if kp == 1:
@@ -513,21 +700,9 @@ def run_ours(args):
         "metric": metric, "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": ("f64" if prec == pg.PREC_FP64 else
-                  "f64 particles/grid; solve f32 vectors + f64 reductions" +
-                  ((f"; {'bf16 tensor-core' if args.cnn_apply == 'tc' else args.cnn_apply} "
-                    "9^3 learned preconditioner") if pc == pg.PC_CNN else "") +
-                  ("; f32 multigrid V-cycle" if pc == pg.PC_MG and not use_fft else "") +
-                  ("; FP64 spectral solve (cuFFT)" if use_fft else "") +
-                  (f"; FP64 particle-in-Fourier NUFFTs (tol {args.pif_tol:g})" if use_pif else "") +
-                  ("; f32 multigrid V-cycle, learned finest-level smoother" if pc == pg.PC_MG_CNN else "")),
+        "dtype": dtype_label(pg, args.solver, args.cnn_apply, args.pif_tol, solve_only),
         "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
-        "config": {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
-                                f"cold start, rel-res {TOL:g}") if solve_only else
-                               pic_workload(N, ppc, field_name(args)),
-                   "N": N, "ppc": ppc, "particles": ppc * n, "solver": args.solver, "tol": TOL, "dt": DT,
-                   "warm_start": True, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (particle records 8.6 GB; solver vectors 4 x 67-134 MB per iteration)"},
+        "config": pic_config(args, world),
         "clocks": clk,
         "e2e": e2e,
         "e2e_solve": e2e_solve,
@@ -541,21 +716,53 @@ def run_ours(args):
         "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in prof["phase_ms"].items()},
         "impl": "ours",
     }
+    if alt:
+        out["pic_steps_other_solvers"] = alt
+    if roof is not None and dom != "push" and "push" in rows:
+        out["roofline_push"] = particle_roofline(rows, "push", np_, n, hbm, peak_kind)
     if train_info is not None:
         out["preconditioner_training"] = train_info
     if not args.no_compare:
+        cmp_ = {}
         if weights is not None:
             c.cnn_set_weights(weights)
-        out["solve_compare"], learned_roof = compare_solvers(c, rho, n, pg, torch, with_cnn=weights is not None,
-                                                             reps=args.compare_reps, maxit=args.compare_maxit)
+        cmp_[str(N)], learned_roof = compare_solvers(
+            c, rho, n, pg, torch, with_cnn=weights is not None, reps=args.compare_reps, maxit=args.compare_maxit,
+            rhs=("Landau density + N(0, 0.01^2) noise, mean removed" if solve_only else
+                 f"CIC deposit of the last step ({np_} particles)"))
         if learned_roof is not None:
             out["roofline_learned_preconditioner"] = learned_roof
+        out["solve_compare"] = cmp_
+    grids = [] if args.no_compare else [int(g) for g in args.compare_grids.split(",") if g and int(g) != N]
+    if grids:
+        # free the particles and the step's grids before the larger solves
+        c.close()
+        c = None
+        del rho, phi, E3
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        from paper_2605_05469_gb300 import inputs
+        for G in grids:
+            cg = pg.Context(stream).init(G, 0, 0)
+            if weights is not None:
+                cg.cnn_set_weights(weights)
+                cg.cnn_set_apply(apply_mode)
+            rho_g = inputs.landau_noise_rhs_torch(G, 0xC0FFEE, "cuda")
+            out["solve_compare"][str(G)], _ = compare_solvers(
+                cg, rho_g, G ** 3, pg, torch, with_cnn=weights is not None, reps=args.compare_reps,
+                maxit=args.compare_maxit, rhs="Landau density + N(0, 0.01^2) noise, mean removed",
+                skip=LARGE_GRID_SKIP if G >= 1024 else ())
+            cg.close()
+            del rho_g
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = (cpu_baseline_pif(N, ppc) if use_pif else
                                cpu_baseline(N, 0 if solve_only else ppc, statistics.mean(iters), args.solver))
     if dist is not None:
         dist.destroy_process_group()
-    c.close()
+    if c is not None:
+        c.close()
     return out
 
 
@@ -580,13 +787,25 @@ def train_preconditioner(pg, torch, N=64, steps=600, val_grid=128, val_every=100
                "seconds": round(time.perf_counter() - t0, 2)}
 
 
-def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
-    """Cold-start solves of the same right-hand side (the last deposit): the FP64
-    Jacobi-PCG reference against the mixed-precision solvers (Jacobi-CG, flexible
-    CG with the multigrid V-cycle, and with the learned preconditioner and the
-    V-cycle with the learned smoother when the network is loaded), outside the
-    timed region."""
-    res = {}
+# solvers left out of the cold-solve comparison on grids of 1024^3 and more,
+# with the reason (each would take minutes)
+LARGE_GRID_SKIP = {
+    "mixed_fp32_fp64": "not run: FP32 Jacobi-CG with FP64 reliable updates stagnates above rel-res 1e-10 at "
+                       "1024^3 (4.0e-10 after 8000 iterations, 61 s)",
+    "mixed_cg_ssor_paper_configuration": "not run: about 30-60 s at 1024^3 (32 half-sweeps an application)",
+    "mixed_fcg_learned_fp32": "not run: the CUDA-core form of the learned preconditioner, about 25 s at 1024^3",
+}
+
+
+def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT, rhs="", skip=()):
+    """Cold-start solves of the same right-hand side: the FP64 Jacobi-PCG
+    reference against the mixed-precision solvers (Jacobi-CG, flexible CG with
+    the multigrid V-cycle, the paper's SSOR configuration, and with the
+    learned preconditioner and the V-cycle with the learned smoother when the
+    network is loaded) and the FFT pseudo-spectral solve, outside the timed
+    region. The best of `reps` solves is kept (one solve when it takes more
+    than 2 s)."""
+    res = {"N": round(n ** (1.0 / 3.0)), "rhs": rhs, "tol": TOL}
     cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI),
              ("mixed_fcg_multigrid", pg.PREC_MIXED, pg.PC_MG),
              ("mixed_cg_ssor_paper_configuration", pg.PREC_MIXED, pg.PC_SSOR)]
@@ -596,6 +815,9 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
         cases.append(("mixed_fcg_multigrid_learned_smoother", pg.PREC_MIXED, pg.PC_MG_CNN))
     learned_roof = None
     for name, prec, pc in cases:
+        if name in skip:
+            res[name] = {"skipped": skip[name]}
+            continue
         if with_cnn:
             c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
         best = None
@@ -605,58 +827,46 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT):
         if sample:
             c.profile(True)
             c.profile_read(reset=True)
-        for _ in range(max(1, reps)):
+        for r_ in range(max(1, reps)):
             phi = torch.zeros(n, dtype=torch.float64, device="cuda")
             info = c.solve(rho, phi, tol=TOL, maxit=maxit, precision=prec, precond=pc, raise_on_error=False)
             if best is None or info["t_ms"] < best["t_ms"]:
                 best = info
+            if info["t_ms"] > 2000.0:
+                break
+            del phi
         if sample:
             prof = c.profile_read(reset=True)
             c.profile(False)
             learned_roof = tc_roofline(prof, n)
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
                      "converged": bool(best["converged"])}
+        if name != "fp64_jacobi_pcg" and "fp64_jacobi_pcg" in res and "s" in res["fp64_jacobi_pcg"]:
+            res[name]["speedup_vs_fp64_jacobi_pcg"] = round(res["fp64_jacobi_pcg"]["s"] / res[name]["s"], 3)
     # the paper's FFT scheme: the spectral solve of the same right-hand side
     # (phi and the three spectral field components), cold, CUDA-event timed
-    E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda")
-    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
-    c.fft_solve(rho, phi, E3)  # plans
-    best = None
-    for _ in range(max(1, reps)):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        stream = torch.cuda.current_stream()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        c.fft_solve(rho, phi, E3)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        best = t if best is None or t < best else best
-    res["fft_spectral_phi_and_E"] = {"s": best, "note": "direct solve of the continuous-symbol equation "
-                                                        "(Sec. 3.1), not the finite-difference system"}
-    best = None
-    for _ in range(max(1, reps)):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        c.fft_solve(rho, phi)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        best = t if best is None or t < best else best
-    res["fft_spectral_phi"] = {"s": best, "note": "phi alone: one forward and one inverse transform"}
-    del E3
-    res["speedup_mixed_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fp32_fp64"]["s"]
-    res["fp64_pcg_vs_fft_time_ratio"] = res["fp64_jacobi_pcg"]["s"] / res["fft_spectral_phi_and_E"]["s"]
-    res["speedup_multigrid_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_multigrid"]["s"]
-    res["speedup_ssor_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_cg_ssor_paper_configuration"]["s"]
-    if with_cnn:
-        res["speedup_learned_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned"]["s"]
-        res["speedup_learned_fp32_vs_fp64"] = res["fp64_jacobi_pcg"]["s"] / res["mixed_fcg_learned_fp32"]["s"]
-        res["speedup_multigrid_learned_vs_fp64"] = (res["fp64_jacobi_pcg"]["s"] /
-                                                     res["mixed_fcg_multigrid_learned_smoother"]["s"])
+    stream = torch.cuda.current_stream()
+    for name, with_E in (("fft_spectral_phi_and_E", True), ("fft_spectral_phi", False)):
+        E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda") if with_E else None
+        phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+        c.fft_solve(rho, phi, E3)  # plans
+        best = None
+        for _ in range(max(1, reps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c.fft_solve(rho, phi, E3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None or t < best else best
+        res[name] = {"s": best, "note": ("direct solve of the continuous-symbol equation (Sec. 3.1), not the "
+                                         "finite-difference system" if with_E else
+                                         "phi alone: one forward and one inverse transform")}
+        del E3, phi
+    judge = res["fp64_jacobi_pcg"]["s"]
+    res["fp64_pcg_vs_fft_time_ratio"] = judge / res["fft_spectral_phi_and_E"]["s"]
     return res, learned_roof
 
 
@@ -681,29 +891,35 @@ def tc_roofline(prof, n):
 
 
 # --------------------------------------------------------------------------- oracle
-def oracle_iteration_seconds(N, solver):
+# sample grids of the oracle timings (the oracle's cost per cell and per
+# particle does not depend on the grid size, so samples scale by cells)
+ORACLE_SOLVE_GRID = {"mg": 128, "cnn": 32, "mg_cnn": 32, "ssor": 64, "fft": 128, "mixed": 128, "fp64": 128}
+ORACLE_PARTICLE_GRID = 64
+
+
+def oracle_iteration_seconds(N, solver, Ns=None):
     """Seconds of one solver iteration of the CPU oracle (as it stands) on an
     N^3 grid, with the same algorithm as the GPU solver: Jacobi-PCG for the
-    mixed and FP64 solvers (timed on the full grid), flexible CG with the
-    V-cycle or with the network (timed on a smaller grid and scaled by the
-    cell count, the oracle's cost being linear in it)."""
+    mixed and FP64 solvers, flexible CG with the V-cycle, the network or SSOR
+    for the others, and one spectral solve for fft; timed on an Ns^3 grid and
+    scaled by the cell count (the FFT by cells x log cells)."""
     from oracle import cnn as ocnn
     from oracle import mg as omg
     from oracle import pic as opic
     from paper_2605_05469_gb300 import inputs
 
     L = 4.0 * np.pi
-    Ns = min(N, {"mg": 128, "cnn": 32, "mg_cnn": 32, "ssor": 64}.get(solver, N))
+    Ns = min(N, Ns or ORACLE_SOLVE_GRID.get(solver, 128))
     h = L / Ns
     b = inputs.landau_noise_rhs(Ns, 1)
     x0 = np.zeros(Ns ** 3)
     if solver == "fft":
         from oracle import fft as offt
-        h = L / N
-        b = inputs.landau_noise_rhs(N, 1)
         t0 = time.perf_counter()
-        offt.spectral_solve(b, N, L)
-        return time.perf_counter() - t0, f"one spectral solve (numpy FFT, phi and E) on the full {N}^3 grid"
+        offt.spectral_solve(b, Ns, L)
+        scale = (N / Ns) ** 3 * math.log(N) / math.log(Ns)
+        return ((time.perf_counter() - t0) * scale,
+                f"one spectral solve (numpy FFT, phi and E) on a {Ns}^3 grid (scaled by cells x log cells)")
     if solver in ("mg", "cnn", "mg_cnn", "ssor"):
         from oracle import ssor as ossor
         ws = ocnn.init_weights(0)
@@ -733,48 +949,101 @@ def oracle_iteration_seconds(N, solver):
     return dt * scale, desc
 
 
-def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", reference_iters=None, budget_s=20.0):
-    """The CPU oracle (numpy, FP64, as it stands) timed on a bounded sample of
-    the same step: solver iterations of the same algorithm as the GPU solve
-    and the particle kernels on a subset of particles, scaled to one step."""
+def cpu_sample(N, ppc, iters_per_solve, solver, Ns_solve=None, Ns_part=None):
+    """Seconds of one step of the CPU oracle (numpy, FP64, as it stands) on
+    one core, from a bounded sample: solver iterations of the same algorithm
+    (scaled by cells and by the iterations per solve), and init-free
+    deposit + gather + push + field energy of ppc particles per cell on an
+    Ns_part^3 grid (scaled by cells: the oracle's particle work is linear in
+    the particle count at fixed ppc). Returns (seconds, description)."""
     from oracle import pic as opic
 
-    L = 4.0 * np.pi
-    h = L / N
-    n = N ** 3
-    t_cg, cg_desc = oracle_iteration_seconds(N, solver)
-    it = reference_iters if reference_iters else iters_per_solve
-    if solver == "fft":
-        it = 1  # a direct solve
+    if solver == "pif":
+        return cpu_sample_pif(N, ppc, Ns_solve or 16, Ns_part or 65536)
+    t_cg, cg_desc = oracle_iteration_seconds(N, solver, Ns_solve)
+    it = 1 if solver == "fft" else iters_per_solve
     if ppc == 0:
-        step_s = t_cg * it
-        return {"value": 1.0 / step_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "host_cpus": os.cpu_count(),
-                "sample": f"{cg_desc}, scaled by {it:.0f} iterations/solve"}
-    ns = min(ppc * n, 1 << 21)
+        return t_cg * it, f"{cg_desc}, scaled by {it:.0f} iterations/solve"
+    Np_ = min(N, Ns_part or ORACLE_PARTICLE_GRID)
+    L = 4.0 * np.pi
+    ns = ppc * Np_ ** 3
     rng = np.random.default_rng(3)
     pos = rng.random((3, ns)) * L
     vel = rng.normal(size=(3, ns))
-    phi = np.zeros(n)
+    phi = inputs_rhs(Np_)
     t0 = time.perf_counter()
-    opic.deposit(pos, N, L)
-    Ep = opic.gather(opic.gradient(phi, N, h), pos, N, L)
+    opic.deposit(pos, Np_, L)
+    Ep = opic.gather(opic.gradient(phi, Np_, L / Np_), pos, Np_, L)
     opic.push(pos, vel, Ep, DT, L, kick=DT)
-    t_part = (time.perf_counter() - t0) * (ppc * n / ns)
-    t0 = time.perf_counter()
-    opic.field_energy(phi, N, h)
-    t_en = time.perf_counter() - t0
-    step_s = t_cg * it + t_part + t_en
-    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+    opic.field_energy(phi, Np_, L / Np_)
+    t_part = (time.perf_counter() - t0) * (N / Np_) ** 3
+    return (t_cg * it + t_part,
+            f"{cg_desc} (scaled by {it:.0f} iterations/solve); deposit + gather + push + field energy of "
+            f"{ns} particles on a {Np_}^3 grid (scaled by cells x{(N / Np_) ** 3:g})")
+
+
+def inputs_rhs(N):
+    from paper_2605_05469_gb300 import inputs
+    return inputs.landau_noise_rhs(N, 1)
+
+
+_ORACLE_BARRIER = None
+
+
+def _oracle_worker_init(barrier):
+    global _ORACLE_BARRIER
+    _ORACLE_BARRIER = barrier
+
+
+def _oracle_worker_task(spec):
+    _ORACLE_BARRIER.wait()   # all workers start their samples together
+    return cpu_sample(*spec)
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core (spawned, so it can
+    start after CUDA is initialised). Each round runs the same sample on
+    every process at once; the host's throughput is procs / the slowest
+    process's scaled step time (the cores share memory bandwidth, which the
+    concurrent run includes)."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        ctx = mp.get_context("spawn")
+        self.barrier = ctx.Barrier(self.procs)
+        self.pool = ctx.Pool(self.procs, initializer=_oracle_worker_init, initargs=(self.barrier,))
+
+    def step_seconds(self, spec):
+        res = self.pool.map(_oracle_worker_task, [spec] * self.procs, chunksize=1)
+        return max(r[0] for r in res) / self.procs, res[0][1]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(N, ppc, iters_per_solve, solver="mixed", procs=None):
+    """The CPU oracle (numpy, FP64, as it stands) on every host core: the
+    bounded sample of cpu_sample run by one process per core at once."""
+    pool = OraclePool(procs)
+    try:
+        step_s, desc = pool.step_seconds((N, ppc, iters_per_solve, solver))
+    finally:
+        pool.close()
+    return {"value": 1.0 / step_s, "unit": "solves/s" if ppc == 0 else UNIT, "cores": pool.procs, "kind": "oracle",
             "host_cpus": os.cpu_count(),
-            "sample": f"{cg_desc} (scaled by {it:.0f} iterations/solve), "
-                      f"deposit+gather+push of {ns} of {ppc * n} particles (scaled linearly), one field energy"}
+            "sample": f"per process: {desc}; {pool.procs} single-threaded processes at once, "
+                      f"throughput = processes / slowest scaled step"}
 
 
-def cpu_baseline_pif(N, ppc, Ns=16, ns=65536):
-    """The CPU oracle's particle-in-Fourier field (direct type-1/type-2 sums)
-    and push timed on ns particles with Ns^3 modes, scaled to the step by
-    particles x modes (the direct sums cost one term per particle and mode)."""
+def cpu_sample_pif(N, ppc, Ns=16, ns=65536):
+    """Seconds of one particle-in-Fourier step of the CPU oracle on one core:
+    its direct type-1/type-2 sums and push timed on ns particles with Ns^3
+    modes, scaled to the step by particles x modes (the direct sums cost one
+    term per particle and mode). Returns (seconds, description)."""
     from oracle import pic as opic
     from oracle import pif as opif
 
@@ -790,10 +1059,22 @@ def cpu_baseline_pif(N, ppc, Ns=16, ns=65536):
     opic.push(pos, vel, Er, DT, L, kick=DT)
     t_push = time.perf_counter() - t0
     npart = ppc * N ** 3
-    step_s = t_field * (npart / ns) * (N / Ns) ** 3 + t_push * (npart / ns)
-    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle", "host_cpus": os.cpu_count(),
-            "sample": f"direct-sum field of {ns} particles on {Ns}^3 modes (scaled by particles x modes "
-                      f"to {npart} x {N}^3) and their push (scaled by particles)"}
+    return (t_field * (npart / ns) * (N / Ns) ** 3 + t_push * (npart / ns),
+            f"direct-sum field of {ns} particles on {Ns}^3 modes (scaled by particles x modes to {npart} x {N}^3) "
+            f"and their push (scaled by particles)")
+
+
+def cpu_baseline_pif(N, ppc, Ns=16, ns=65536, procs=None):
+    """The particle-in-Fourier step of the CPU oracle on every host core (one
+    process per core running the sample of cpu_sample_pif at once)."""
+    pool = OraclePool(procs)
+    try:
+        step_s, desc = pool.step_seconds((N, ppc, 0, "pif", Ns, ns))
+    finally:
+        pool.close()
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": pool.procs, "kind": "oracle", "host_cpus": os.cpu_count(),
+            "sample": f"per process: {desc}; {pool.procs} single-threaded processes at once, "
+                      f"throughput = processes / slowest scaled step"}
 
 
 def field_name(args):
@@ -806,6 +1087,17 @@ def field_name(args):
     return None
 
 
+def pic_config(args, world):
+    """The `config` block of both arms' JSON lines."""
+    solve_only = getattr(args, "workload", "pic") == "solve"
+    N, ppc = args.N, args.ppc
+    return {"workload": (f"Poisson solve, {N}^3 periodic grid, Landau density + N(0, 0.01^2) noise rhs, "
+                         f"cold start, rel-res {TOL:g}") if solve_only else pic_workload(N, ppc, field_name(args)),
+            "N": N, "ppc": 0 if solve_only else ppc, "particles": 0 if solve_only else ppc * N ** 3,
+            "solver": args.solver, "tol": TOL, "dt": None if solve_only else DT, "warm_start": not solve_only,
+            "parallelism": f"replicas x{world}", "l2": l2_note(N, ppc, solve_only)}
+
+
 def pic_workload(N, ppc, field=None):
     """The name of the PIC-step workload (both arms): grid, particles, how the
     field is obtained (default: the Poisson solve to the bench tolerance)."""
@@ -813,43 +1105,86 @@ def pic_workload(N, ppc, field=None):
             + (field or f"solve to rel-res {TOL:g}") + f", dt {DT}")
 
 
+def oracle_iters_per_solve(N, ppc, solver):
+    """Iterations of a warm-started solve of the PIC step for the CPU oracle:
+    two steps of the oracle's loop on an N0^3 grid (deposit, cold solve,
+    push, deposit, solve warm-started from the previous phi), the second
+    solve's iterations with the step's algorithm, scaled to N^3 by the
+    algorithm's growth: CG with a fixed-stencil preconditioner (Jacobi; the
+    learned network, whose untrained oracle weights are exactly the Jacobi
+    direction) like sqrt(kappa) ~ N, SSOR-CG like N^(1/2), multigrid FCG not
+    at all. Returns (iterations, description)."""
+    from oracle import cnn as ocnn
+    from oracle import mg as omg
+    from oracle import pic as opic
+    from oracle import ssor as ossor
+    if solver in ("fft", "pif"):
+        return 1, "direct solve"
+    N0 = min(N, 32)
+    L = 4.0 * np.pi
+    h = L / N0
+    pos, vel = opic.init_particles(N0, ppc, SEED)
+    jac = solver in ("mixed", "fp64", "cnn")
+
+    def solve(b, x0):
+        if jac:
+            x, it, _, _ = opic.pcg_jacobi(b, x0, N0, h, TOL, MAXIT)
+            return x, it
+        prec = {"mg": lambda r: omg.vcycle(r, N0, h), "mg_cnn": lambda r: omg.vcycle(r, N0, h),
+                "ssor": lambda r: ossor.ssor(r, N0, h)}[solver]
+        out = ocnn.fcg(b, x0, N0, h, TOL, MAXIT, prec)
+        return out[0], out[1]
+    rho = opic.deposit(pos, N0, L)
+    b = rho - rho.mean()
+    phi, _ = solve(b, np.zeros(N0 ** 3))
+    Ep = opic.gather(opic.gradient(phi, N0, h), pos, N0, L)
+    pos, vel = opic.push(pos, vel, Ep, DT, L, kick=0.5 * DT)
+    rho = opic.deposit(pos, N0, L)
+    _, it0 = solve(rho - rho.mean(), phi)
+    growth = {"ssor": (N / N0) ** 0.5, "mg": 1.0, "mg_cnn": 1.0}.get(solver, N / N0)
+    what = "Jacobi-PCG" if jac else {"mg": "multigrid FCG", "mg_cnn": "multigrid FCG (Jacobi-smoothed)",
+                                     "ssor": "SSOR-CG"}[solver]
+    return (max(1.0, it0 * growth),
+            f"{it0} iterations of a warm-started {what} solve at {N0}^3 x {ppc} ppc, scaled x{growth:g} to {N}^3")
+
+
 def run_reference(args):
+    """The CPU oracle, as it stands, on this arm's workload: every step is one
+    round of the bounded sample of cpu_sample on one process per host core
+    (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     N, ppc = args.N, args.ppc
-    iters = None
-    if args.solver not in ("fft", "pif"):
-        # iterations per warm-started solve: the oracle's Jacobi-PCG on this
-        # workload needs the same count as any exact-arithmetic CG; measured once
-        # at 64^3 and scaled by N (CG iterations grow like sqrt(kappa) ~ N).
-        from oracle import pic as opic
-        N0 = 64
-        pos, _ = opic.init_particles(N0, ppc, SEED)
-        L = 4.0 * np.pi
-        rho = opic.deposit(pos, N0, L)
-        _, it0, _, _ = opic.pcg_jacobi(rho, np.zeros(N0 ** 3), N0, L / N0, TOL, MAXIT)
-        iters = it0 * N / N0
+    iters, it_desc = oracle_iters_per_solve(N, ppc, args.solver)
+    # a small sample per step keeps the whole run within a few minutes
+    spec = ((N, ppc, 0, "pif", 8, 16384) if args.solver == "pif" else
+            (N, ppc, iters, args.solver, min(64, ORACLE_SOLVE_GRID.get(args.solver, 64)), 32))
+    pool = OraclePool()
     t0 = time.perf_counter()
-    base = None
-    for _ in range(max(1, args.steps)):
-        if args.solver == "pif":
-            base = cpu_baseline_pif(N, ppc)
-        elif args.solver == "fft":
-            base = cpu_baseline(N, ppc, 1, "fft")
-        else:
-            base = cpu_baseline(N, ppc, iters)
+    try:
+        for _ in range(max(0, args.warmup)):
+            pool.step_seconds(spec)
+        secs = []
+        for _ in range(max(1, args.steps)):
+            s_, desc = pool.step_seconds(spec)
+            secs.append(s_)
+    finally:
+        pool.close()
     total = time.perf_counter() - t0
-    value = float(f"{base['value']:.6g}")
+    value = float(f"{len(secs) / sum(secs):.6g}")
+    cfg = pic_config(args, 1)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 / value, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic: seeded Landau density + particles", "impl": "reference",
-        "config": {"workload": pic_workload(N, ppc, field_name(args)), "solver": args.solver,
-                   "N": N, "ppc": ppc, "iters_per_solve_est": iters},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": base["sample"] + f"; {args.steps} samples in {total:.1f} s"},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (numpy)",
+        "data": "synthetic: seeded Landau initial condition (Philox4x32-10, inverse CDF, Box-Muller)",
+        "impl": "reference", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                         "host_cpus": os.cpu_count(),
+                         "sample": f"per step and process: {desc}; iterations per solve: {it_desc}; "
+                                   f"{pool.procs} single-threaded processes at once, throughput = processes / "
+                                   f"slowest scaled step; {args.warmup} + {len(secs)} rounds in {total:.1f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return out

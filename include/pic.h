@@ -198,9 +198,28 @@ int pic_pif_push(pic_ctx *c, double tol, double dt);
 
 /* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
  * the ORIGINAL particle order (index p of pic_init), to device memory
- * (on_device = 1) or host memory (0; synchronises). `half_step` (may be
- * NULL) receives 1 when velocities lag positions by dt/2. */
+ * (on_device = 1) or host memory (0; pageable or pinned; converted and copied
+ * in chunks of 2^24 particles through a context-owned 805 MB device staging
+ * buffer; synchronises). `half_step` (may be NULL) receives 1 when
+ * velocities lag positions by dt/2. */
 int pic_get_particles(pic_ctx *c, double *out, int on_device, int *half_step);
+
+/* Replace the particle state (the phase-space sample f of Sec. 2 that the
+ * loop of Fig. 1 advances) by caller data, the inverse of pic_get_particles:
+ * `in` holds 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz), Np =
+ * pic_num_particles; element p becomes particle p. Positions are wrapped
+ * into [0, L) (any finite value is accepted); velocities are stored as
+ * double-float pairs (~48-bit significand), positions as the cell and a
+ * 64-bit fixed-point offset. `half_step` = 1 states that the velocities lag
+ * the positions by dt/2 (the next push kicks by dt), 0 that they are
+ * synchronous (the next push kicks by dt/2). From device memory (on_device =
+ * 1, 8-byte aligned, read only) or host memory (0; pageable or pinned; copied
+ * in chunks of 2^24 particles through the staging buffer of
+ * pic_get_particles). Synchronises. Returns PIC_EINVAL for a null pointer, a
+ * half_step other than 0/1, or a non-finite value in `in` (the state is then
+ * replaced with those particles at the origin at rest: set it again),
+ * PIC_ESTATE for a context without particles. */
+int pic_set_particles(pic_ctx *c, const double *in, int on_device, int half_step);
 
 /* Number of particles of the context (0 for a solver-only context). */
 int64_t pic_num_particles(const pic_ctx *c);
@@ -356,9 +375,10 @@ int pic_profile_read(pic_ctx *c, pic_profile_stats *out, int reset);
  * scratch is a fixed 48.25 KiB file-scope device array that every GPU loading
  * the library keeps until exit; all calls on a device share it, so calls that
  * overlap on the GPU (different streams) race and must be serialised by the
- * caller. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Returns PIC_OK, PIC_EINVAL or PIC_ECUDA. */
+ * caller. Every call looks up the array's device address in the current
+ * device's context (cudaGetSymbolAddress, which allocates nothing); the first
+ * call on a device also loads the library's module there, so make it before
+ * any stream capture. Returns PIC_OK, PIC_EINVAL or PIC_ECUDA. */
 int pic_field_energy_noalloc(const double *phi, int N, double k, double *out_w, void *cuda_stream);
 
 #ifdef __cplusplus

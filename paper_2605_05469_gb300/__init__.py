@@ -108,6 +108,7 @@ _SIGS = {
     "pic_field_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pic_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
+    "pic_set_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "pic_num_particles": (ctypes.c_int64, [ctypes.c_void_p]),
     "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pic_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -348,6 +349,32 @@ class Context:
         _check(lib().pic_get_particles(self.h, _dptr(out, "float64", 6 * self.num_particles, "out"), 1,
                                        ctypes.byref(half)), "pic_get_particles")
         return bool(half.value)
+
+    def particles_to_host(self, out):
+        """The particles into a host FP64 tensor of 6 Np (pinned or pageable; x,
+        y, z, vx, vy, vz blocks, original order); returns whether velocities lag
+        by dt/2."""
+        import torch
+        if not isinstance(out, torch.Tensor) or out.is_cuda or out.dtype != torch.float64 or \
+                not out.is_contiguous() or out.numel() != 6 * self.num_particles:
+            raise ValueError("out: expected a contiguous host float64 tensor of 6 Np elements")
+        half = ctypes.c_int()
+        _check(lib().pic_get_particles(self.h, ctypes.c_void_p(out.data_ptr()), 0, ctypes.byref(half)),
+               "pic_get_particles")
+        return bool(half.value)
+
+    def set_particles(self, state, half_step):
+        """Replace the particle state by a FP64 tensor of 6 Np (x, y, z, vx, vy,
+        vz blocks), on the device or on the host; `half_step`: velocities lag
+        the positions by dt/2."""
+        import torch
+        if isinstance(state, np.ndarray):
+            state = torch.from_numpy(np.ascontiguousarray(state, dtype=np.float64).reshape(-1))
+        if not isinstance(state, torch.Tensor) or state.dtype != torch.float64 or not state.is_contiguous() or \
+                state.numel() != 6 * self.num_particles:
+            raise ValueError("state: expected a contiguous float64 tensor of 6 Np elements")
+        _check(lib().pic_set_particles(self.h, ctypes.c_void_p(state.data_ptr()), 1 if state.is_cuda else 0,
+                                       1 if half_step else 0), "pic_set_particles")
 
     def apply_laplacian(self, x, y):
         pic_apply_laplacian(self.h, x, y, self.n)

@@ -31,7 +31,18 @@ void free_particles(pic_ctx* c) {
   dfree(c->E);
   dfree(c->dep);
   dfree(c->pif_E);
+  dfree(c->stage);
   c->np = 0;
+}
+
+// Particles per chunk of a host transfer (6 FP64 blocks: 805 MB of staging).
+constexpr uint64_t kStageParticles = 1ull << 24;
+
+int ensure_stage(pic_ctx* c) {
+  int e;
+  if (!c->stage && (e = dalloc(&c->stage, 6 * kStageParticles))) return e;
+  if (!c->io_flag && (e = dalloc(&c->io_flag, 1))) return e;
+  return PIC_OK;
 }
 
 void free_solver(pic_ctx* c) {
@@ -546,6 +557,7 @@ void pic_destroy(pic_ctx* c) {
   dfree(c->sc);
   dfree(c->counter);
   dfree(c->err);
+  dfree(c->io_flag);
   dfree(c->out3);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->err_host) cudaFreeHost(c->err_host);
@@ -823,14 +835,57 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
     CK(cudaGetLastError());
     return PIC_OK;
   }
-  double* tmp = nullptr;
+  // host: the records in the original order in the sort's scratch buffer
+  // (free between calls), then converted and copied in chunks
   int e;
-  if ((e = dalloc(&tmp, 6 * c->np))) return e;
-  launch(c, k_unsort, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, c->grid, tmp);
-  cudaError_t ce = cudaMemcpyAsync(out, tmp, 6 * c->np * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
-  cudaFree(tmp);
-  return ce == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  if ((e = ensure_stage(c))) return e;
+  PRec* orig = pptrs(c, c->cur ^ 1);
+  launch(c, k_unsort_records, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), orig, c->np);
+  for (uint64_t base = 0; base < c->np; base += kStageParticles) {
+    const uint64_t cnt = c->np - base < kStageParticles ? c->np - base : kStageParticles;
+    launch(c, k_records_to_soa, (unsigned)((cnt + 255) / 256), 256, 0, (const PRec*)orig, base, cnt, c->grid,
+           c->stage, cnt);
+    for (int q = 0; q < 6; ++q)
+      CK(cudaMemcpyAsync(out + q * c->np + base, c->stage + q * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step) {
+  if (!c || !in || (half_step != 0 && half_step != 1)) return PIC_EINVAL;
+  if (on_device && ((uintptr_t)in % 8) != 0) return PIC_EINVAL;
+  if (c->np == 0) return PIC_ESTATE;
+  int e;
+  if ((e = ensure_stage(c))) return e;
+  CK(cudaMemsetAsync(c->io_flag, 0, sizeof(int), c->stream));
+  PRec* P = pptrs(c, c->cur);
+  if (on_device) {
+    launch(c, k_set_particles, (unsigned)((c->np + 255) / 256), 256, 0, in, c->np, c->np, (uint64_t)0, P, c->grid,
+           c->io_flag);
+  } else {
+    for (uint64_t base = 0; base < c->np; base += kStageParticles) {
+      const uint64_t cnt = c->np - base < kStageParticles ? c->np - base : kStageParticles;
+      for (int q = 0; q < 6; ++q)
+        CK(cudaMemcpyAsync(c->stage + q * cnt, in + q * c->np + base, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream));
+      launch(c, k_set_particles, (unsigned)((cnt + 255) / 256), 256, 0, (const double*)c->stage, cnt, cnt, base, P,
+             c->grid, c->io_flag);
+    }
+  }
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(c->err_host, c->io_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  flag = *c->err_host;
+  // the records are in the caller's order: keys and ranks are recounted by
+  // the next sort
+  c->keys_valid = false;
+  c->sorted = false;
+  c->half_step = half_step != 0;
+  return (flag & DEV_ERR_NONFINITE) ? PIC_EINVAL : PIC_OK;
 }
 
 int pic_residual(pic_ctx* c, const double* rho, const double* phi, double* r) {

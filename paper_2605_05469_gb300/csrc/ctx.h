@@ -115,6 +115,10 @@ struct pic_ctx {
   pic::FftState* fft = nullptr;
   pic::PifState* pif = nullptr;
   double* pif_E = nullptr;  // 3 np: the particle-in-Fourier field, current particle order
+  // host <-> device particle transfers: FP64 staging of up to kStageParticles
+  // particles (6 blocks) and a device flag for rejected input
+  double* stage = nullptr;
+  int* io_flag = nullptr;
 };
 
 namespace pic {

@@ -13,8 +13,6 @@
 // library keeps until the process exits.
 #include <math.h>
 
-#include <mutex>
-
 #include "common.cuh"
 
 using namespace pic;
@@ -28,28 +26,19 @@ constexpr size_t kNoAllocScratchBytes = kNoAllocPartialBytes + 256;  // + counte
 // Shared by every call on a device; holds the last call's partial sums.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};  // device address per device, set once
-
-// Device address of the scratch array on the current device. The name
-// g_noalloc_scratch in host code is only a host-side stand-in, so the address
-// is looked up with cudaGetSymbolAddress once per device (with that device
-// current) and cached.
+// Device address of the scratch array in the current device's context. The
+// name g_noalloc_scratch in host code is only a host-side stand-in, so the
+// address is looked up with cudaGetSymbolAddress, with the device current, on
+// every call: the lookup allocates nothing, and a cached address would go
+// stale when the module is reloaded at another address (after
+// cudaDeviceReset, or under another driver context).
 int scratch_for_current_device(unsigned char** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return PIC_EINVAL;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return PIC_ECUDA;
-    }
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return PIC_ECUDA;
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return PIC_OK;
 }
 

@@ -591,4 +591,71 @@ __global__ void k_unsort(const PRec* P, uint64_t np, Grid g, double* out) {
   out[5 * np + d] = double_of_df(df_from(r.vz));
 }
 
+// Particles from caller data (FP64 structure of arrays, blocks of `ld`
+// values: x, y, z, vx, vy, vz): particle base + i takes element i of each
+// block, for i < count. Positions are wrapped into [0, L); a non-finite value
+// sets DEV_ERR_NONFINITE in *flag and the particle is stored at the origin at
+// rest.
+__global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint64_t count, uint64_t base, PRec* P,
+                                Grid g, int* flag) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double v[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) v[q] = in[q * ld + i];
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) ok = ok && isfinite(v[q]);
+  if (!ok) {
+    atomicOr(flag, DEV_ERR_NONFINITE);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double x = fmod(v[q], g.L);  // exact; |x| < L
+    if (x < 0.0) x += g.L;       // may round to L, which to_cell_offset wraps to 0
+    v[q] = x;
+  }
+  PRec rec;
+  int ix, iy, iz;
+  to_cell_offset(v[0], g, ix, rec.fx);
+  to_cell_offset(v[1], g, iy, rec.fy);
+  to_cell_offset(v[2], g, iz, rec.fz);
+  rec.vx = df_pack(df_of_double(v[3]));
+  rec.vy = df_pack(df_of_double(v[4]));
+  rec.vz = df_pack(df_of_double(v[5]));
+  rec.id = (uint32_t)(base + i);
+  rec.key = cell_key(ix, iy, iz, g.N);
+  rec.ix = (uint16_t)ix;
+  rec.iy = (uint16_t)iy;
+  rec.iz = (uint16_t)iz;
+  rec.pad = 0;
+  P[base + i] = rec;
+}
+
+// The records back in the original order: dst[id] = src[p] (a permutation).
+__global__ void __launch_bounds__(256) k_unsort_records(const PRec* __restrict__ src, PRec* __restrict__ dst,
+                                                        uint64_t np) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const PRec r = src[p];
+  dst[r.id] = r;
+}
+
+// Records base .. base + count - 1 of an array in the original order to FP64
+// structure of arrays (blocks of `ld` values: x, y, z, vx, vy, vz).
+__global__ void k_records_to_soa(const PRec* __restrict__ P, uint64_t base, uint64_t count, Grid g, double* out,
+                                 uint64_t ld) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const PRec r = P[base + i];
+  out[i] = from_cell_offset(r.ix, r.fx, g);
+  out[ld + i] = from_cell_offset(r.iy, r.fy, g);
+  out[2 * ld + i] = from_cell_offset(r.iz, r.fz, g);
+  out[3 * ld + i] = double_of_df(df_from(r.vx));
+  out[4 * ld + i] = double_of_df(df_from(r.vy));
+  out[5 * ld + i] = double_of_df(df_from(r.vz));
+}
+
 }  // namespace pic

@@ -17,7 +17,12 @@ def pytest_collection_modifyitems(config, items):
     # the small-size parity tests first, then the guard-band bounds checks,
     # then the full-size checks (the longest), so that a stopped run (-x)
     # still reports the parity of every kernel
-    items.sort(key=lambda it: 1 if "test_gpu_canaries" in it.nodeid else 2 if "test_gpu_fullsize" in it.nodeid else 0)
+    # and the allocation-free entry point's file after everything else
+    def order(it):
+        if "test_zz_no_alloc" in it.nodeid:
+            return 3
+        return 1 if "test_gpu_canaries" in it.nodeid else 2 if "test_gpu_fullsize" in it.nodeid else 0
+    items.sort(key=order)
     try:
         import torch
         have_gpu = torch.cuda.is_available()

@@ -17,11 +17,28 @@ def test_vcycle_bytes_per_cell():
 
 
 def test_particle_kernel_bytes():
-    # record read and written (128 B), key and rank (8 B)
-    assert bench.PARTICLE_BYTES["push"][0] == 136
-    assert bench.PARTICLE_BYTES["scatter"][0] == 136
+    # algorithmic: the FP64 state (x, y, z, vx, vy, vz: 48 B) read and written
+    # by the push, positions read by the deposit, E read once per node
+    assert bench.PARTICLE_BYTES["push"] == (96, 24)
+    assert bench.PARTICLE_BYTES["deposit"] == (24, 8)
+    # the library's record layout: 64-byte record read and written, key and rank
+    assert bench.PARTICLE_IMPL_BYTES["push"] == 136
+    assert bench.PARTICLE_IMPL_BYTES["scatter"] == 136
     for k in ("push", "scatter"):
         assert abs(bench.MEASURED_TRAFFIC_PER_PARTICLE[k] - 136) < 5
+
+
+def test_particle_roofline_counts_algorithmic_bytes():
+    # 256^3 x 8 ppc, push at 4991.4 us: 96 B a particle + 24 B a node
+    n, np_ = 256 ** 3, 8 * 256 ** 3
+    b = 96 * np_ + 24 * n
+    rows = {"push": {"avg_us": 4991.4, "bytes_per_particle": 96, "bytes_per_node": 24,
+                     "gbs": b / 4991.4e-6 / 1e9, "impl_bytes_per_particle": 136}}
+    r = bench.particle_roofline(rows, "push", np_, n, 6787.2, "measured")
+    assert r["algorithmic_bytes"] == b
+    assert abs(r["frac"] - b / 4991.4e-6 / 1e9 / 6787.2) < 1e-4
+    assert abs(r["frac"] - 0.392) < 0.002
+    assert abs(r["traffic_over_algorithmic"] - 136.70 * np_ / b) < 1e-3
 
 
 def test_whole_job_rate_and_ranks():
@@ -40,10 +57,24 @@ def test_pif_window_width():
     assert bench.PIF_FLOP_PER_POINT == 2
 
 
-def test_pif_cpu_baseline_scales_by_particles_and_modes():
-    # the direct sums cost one term per (particle, mode): the sampled rate of a
-    # 2x larger grid (8x the modes, 8x the particles at the same ppc) is ~64x lower
-    a = bench.cpu_baseline_pif(16, 1, Ns=8, ns=1024)
-    b = bench.cpu_baseline_pif(32, 1, Ns=8, ns=1024)
-    assert a["kind"] == "oracle" and a["unit"] == bench.UNIT
-    assert 16 < a["value"] / b["value"] < 256
+def test_pif_cpu_sample_scales_by_particles_and_modes():
+    # the direct sums cost one term per (particle, mode): the sampled time of a
+    # 2x larger grid (8x the modes, 8x the particles at the same ppc) is ~64x higher
+    a, _ = bench.cpu_sample_pif(16, 1, Ns=8, ns=1024)
+    b, _ = bench.cpu_sample_pif(32, 1, Ns=8, ns=1024)
+    assert 16 < b / a < 256
+
+
+def test_cpu_baseline_uses_every_core():
+    r = bench.cpu_baseline(16, 2, 5, "mixed", procs=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0
+    assert "Jacobi-PCG" in r["sample"] and "2 single-threaded processes" in r["sample"]
+
+
+def test_dtype_label_names_the_arithmetic():
+    import types
+    pg = types.SimpleNamespace()
+    d = bench.dtype_label(pg, "cnn")
+    assert "64-bit fixed-point positions + double-float velocities" in d
+    assert "rho, phi FP64" in d and "FP32 vectors + FP64 reductions" in d and "BF16 tensor-core" in d
+    assert "particles" not in bench.dtype_label(pg, "mg", solve_only=True)

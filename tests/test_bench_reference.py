@@ -1,18 +1,21 @@
 """bench.py's reference arm (the CPU oracle, as it stands) prints the contract's
-JSON line on a small case, on the same metric, unit and workload as the GPU
-arm (no GPU needed)."""
+JSON line on a small case, on the same metric, unit, workload and config block
+as the GPU arm, timing the step's own algorithm on every host core (no GPU
+needed)."""
 import json
 import os
 import subprocess
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
-
 import pytest
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-@pytest.mark.parametrize("solver", ["mg", "pif"])
+# what the sample description must name for each solver
+ALGORITHM = {"mg": "multigrid", "ssor": "SSOR", "mixed": "Jacobi-PCG", "pif": "direct-sum"}
+
+
+@pytest.mark.parametrize("solver", ["mg", "ssor", "mixed", "pif"])
 def test_reference_arm_json_line(solver):
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--N", "16", "--ppc", "2",
                           "--steps", "1", "--warmup", "0", "--solver", solver], cwd=ROOT, capture_output=True,
@@ -26,7 +29,11 @@ def test_reference_arm_json_line(solver):
     assert r["metric"] == bench.METRIC and r["unit"] == bench.UNIT and r["higher_is_better"] is True
     assert r["value"] > 0 and r["steps"] == 1 and r["warmup"] == 0
     args = bench.parse(["--N", "16", "--ppc", "2", "--solver", solver])
-    assert r["config"]["workload"] == bench.pic_workload(16, 2, bench.field_name(args))
+    assert r["config"] == bench.pic_config(args, 1)
     cb = r["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == r["value"] and cb["sample"]
+    assert cb["cores"] == os.cpu_count() and cb["cores"] >= 1
+    assert ALGORITHM[solver] in cb["sample"], cb["sample"]
+    if solver != "pif":
+        assert "warm-started" in cb["sample"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
