@@ -415,12 +415,13 @@ def run_ours(args):
             raise SystemExit(f"unknown solver in --alt-solvers: {s_}")
     weights, train_info = None, None
     if any(s_ in ("cnn", "mg_cnn") for s_ in [args.solver] + alt_solvers) or not args.no_compare:
-        weights, train_info = train_preconditioner(pg, torch)
+        weights, train_info = train_networks(pg, torch)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
     apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
                   "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
+    nets = Networks(c, weights)
     if weights is not None:
-        c.cnn_set_weights(weights)
+        nets.use(pc if pc in weights else pg.PC_CNN)
         c.cnn_set_apply(apply_mode)
     phi = torch.zeros(n, dtype=torch.float64, device="cuda")
     if solve_only:
@@ -435,11 +436,13 @@ def run_ours(args):
         info to `infos` when recording."""
         nonlocal E3
         s_prec, s_pc = solver_modes(pg, solver)
+        nets.use(s_pc)
         use_fft, use_pif = solver == "fft", solver == "pif"
         if use_fft and E3 is None:
             E3 = torch.empty(3 * n, dtype=torch.float64, device="cuda")
 
         def solve_into(rho_, phi_):
+            nets.use(s_pc)
             if use_fft:
                 # direct solve: no iterations or residual; its time is the solve phase's
                 c.fft_solve(rho_, phi_, E3)
@@ -721,13 +724,11 @@ def run_ours(args):
     if roof is not None and dom != "push" and "push" in rows:
         out["roofline_push"] = particle_roofline(rows, "push", np_, n, hbm, peak_kind)
     if train_info is not None:
-        out["preconditioner_training"] = train_info
+        out["network_training"] = train_info
     if not args.no_compare:
         cmp_ = {}
-        if weights is not None:
-            c.cnn_set_weights(weights)
         cmp_[str(N)], learned_roof = compare_solvers(
-            c, rho, n, pg, torch, with_cnn=weights is not None, reps=args.compare_reps, maxit=args.compare_maxit,
+            c, rho, n, pg, torch, nets=nets, reps=args.compare_reps, maxit=args.compare_maxit,
             rhs=("Landau density + N(0, 0.01^2) noise, mean removed" if solve_only else
                  f"CIC deposit of the last step ({np_} particles)"))
         if learned_roof is not None:
@@ -744,12 +745,9 @@ def run_ours(args):
         from paper_2605_05469_gb300 import inputs
         for G in grids:
             cg = pg.Context(stream).init(G, 0, 0)
-            if weights is not None:
-                cg.cnn_set_weights(weights)
-                cg.cnn_set_apply(apply_mode)
             rho_g = inputs.landau_noise_rhs_torch(G, 0xC0FFEE, "cuda")
             out["solve_compare"][str(G)], _ = compare_solvers(
-                cg, rho_g, G ** 3, pg, torch, with_cnn=weights is not None, reps=args.compare_reps,
+                cg, rho_g, G ** 3, pg, torch, nets=Networks(cg, weights), reps=args.compare_reps,
                 maxit=args.compare_maxit, rhs="Landau density + N(0, 0.01^2) noise, mean removed",
                 skip=LARGE_GRID_SKIP if G >= 1024 else ())
             cg.close()
@@ -766,25 +764,43 @@ def run_ours(args):
     return out
 
 
-def train_preconditioner(pg, torch, N=64, steps=600, val_grid=128, val_every=100):
-    """Train the learned preconditioner on the GPU before timing (the library's
-    own kernels: Jacobi-PCG snapshots of four 64^3 Landau deposits, 600 Adam
-    steps on 32^3 crops); the weights kept are those with the fewest
-    flexible-CG iterations, scored every 100 steps on a held-out 128^3
-    deposit (another seed)."""
-    from paper_2605_05469_gb300 import train as T
+def train_networks(pg, torch):
+    """Train the network twice on the GPU before timing, each by one
+    pic_cnn_train call (the library's own solves for the data, its kernels
+    for forward, loss, backward and Adam): as flexible CG's preconditioner
+    (Jacobi-PCG snapshots of four 64^3 Landau deposits, 600 Adam steps on
+    32^3 crops, kept by the flexible-CG iterations of a held-out 128^3
+    deposit) and as the V-cycle's finest-level smoother (white-noise errors,
+    kept by the multigrid-FCG iterations of the same deposit). Returns the
+    weights per preconditioner and the training records."""
     t0 = time.perf_counter()
-    sets = T.landau_snapshot_sets(N, seeds=[11, 12, 13, 14])
-    c = pg.Context().init(N, 0, 0)
-    val = T.fcg_iterations(val_grid)
-    losses = T.train(c, sets, steps, B=8, D=32, lr=2e-3, seed=0, validate=val, validate_every=val_every)
-    w = c.cnn_get_weights()
+    c = pg.Context().init(64, 0, 0)
+    info_p = c.cnn_train(pg.TRAIN_PRECONDITIONER)
+    w_p = c.cnn_get_weights()
+    info_s = c.cnn_train(pg.TRAIN_SMOOTHER)
+    w_s = c.cnn_get_weights()
     c.close()
-    del sets, val
     torch.cuda.synchronize()
-    return w, {"grid": N, "steps": steps, "loss_first": float(losses[:10].mean()),
-               "loss_last": float(losses[-50:].mean()), "selected_by": f"FCG iterations on a {val_grid}^3 deposit",
-               "seconds": round(time.perf_counter() - t0, 2)}
+    rec = {k: {"loss_first": round(v["loss_first"], 4), "loss_last": round(v["loss_last"], 4),
+               "kept_adam_step": v["adam_steps"], "validation_iters": v["best_iters"], "seconds": round(v["seconds"], 2)}
+           for k, v in (("preconditioner", info_p), ("smoother", info_s))}
+    rec.update({"grid": 64, "steps": 600, "selected_by": "flexible-CG iterations on a 128^3 deposit",
+                "seconds": round(time.perf_counter() - t0, 2)})
+    return {pg.PC_CNN: w_p, pg.PC_MG_CNN: w_s}, rec
+
+
+class Networks:
+    """The trained weights of the context's network, switched to the ones a
+    preconditioner was trained for before a solve that uses the network."""
+
+    def __init__(self, c, weights):
+        self.c, self.w, self.cur = c, weights, None
+
+    def use(self, pc):
+        if self.w is None or pc not in self.w or pc == self.cur:
+            return
+        self.c.cnn_set_weights(self.w[pc])
+        self.cur = pc
 
 
 # solvers left out of the cold-solve comparison on grids of 1024^3 and more,
@@ -797,7 +813,7 @@ LARGE_GRID_SKIP = {
 }
 
 
-def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT, rhs="", skip=()):
+def compare_solvers(c, rho, n, pg, torch, nets=None, reps=2, maxit=MAXIT, rhs="", skip=()):
     """Cold-start solves of the same right-hand side: the FP64 Jacobi-PCG
     reference against the mixed-precision solvers (Jacobi-CG, flexible CG with
     the multigrid V-cycle, the paper's SSOR configuration, and with the
@@ -806,6 +822,7 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT, r
     region. The best of `reps` solves is kept (one solve when it takes more
     than 2 s)."""
     res = {"N": round(n ** (1.0 / 3.0)), "rhs": rhs, "tol": TOL}
+    with_cnn = nets is not None and nets.w is not None
     cases = [("fp64_jacobi_pcg", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_fp32_fp64", pg.PREC_MIXED, pg.PC_JACOBI),
              ("mixed_fcg_multigrid", pg.PREC_MIXED, pg.PC_MG),
              ("mixed_cg_ssor_paper_configuration", pg.PREC_MIXED, pg.PC_SSOR)]
@@ -819,6 +836,7 @@ def compare_solvers(c, rho, n, pg, torch, with_cnn=False, reps=2, maxit=MAXIT, r
             res[name] = {"skipped": skip[name]}
             continue
         if with_cnn:
+            nets.use(pc)
             c.cnn_set_apply(pg.CNN_APPLY_FP32 if name.endswith("_fp32") else pg.CNN_APPLY_TC)
         best = None
         # the tensor-core preconditioner's launches are sampled in the first

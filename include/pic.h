@@ -135,7 +135,10 @@ int poisson_solve_ex(pic_ctx *c, const double *rho, double *phi, double tol, int
  * v += (q/m) kick E(x), x = wrap(x + dt v), where kick = dt/2 on the first
  * push after pic_init / pic_sync_velocity and dt otherwise (kick-drift-kick
  * with the two half-kicks at each step boundary merged). `phi` is device
- * FP64 [N^3]. */
+ * FP64 [N^3]. PIC_EINVAL for a non-finite dt. A particle whose kick is not
+ * finite (a non-finite phi near it) is left unchanged and the context records
+ * the fault: its next synchronising call returns PIC_EBREAKDOWN, and so do
+ * the later ones (destroy the context). */
 int pic_gather_push(pic_ctx *c, const double *phi, double dt);
 
 /* Closing half-kick v += (q/m) (dt/2) E(x): makes velocities synchronous
@@ -195,6 +198,18 @@ int pic_pif_field(pic_ctx *c, double tol, double *E);
  * pic_gather_push (the first step after pic_init kicks by dt/2). PIC_EINVAL
  * for tol <= 0 or NaN or a non-finite dt, PIC_ESTATE without particles. */
 int pic_pif_push(pic_ctx *c, double tol, double dt);
+
+/* Self-test of the library's bounded device-side waits (the mbarrier waits of
+ * the streaming solver kernels and of the tensor-core preconditioner, which
+ * give up after about two seconds instead of hanging): one warp waits on an
+ * mbarrier of one expected arrival, with a wall-time budget of budget_ns
+ * (1 <= budget_ns <= 2e9). With producer = 1 a lane arrives and the call
+ * returns PIC_OK; with producer = 0 nothing arrives (no copy is issued), the
+ * wait runs out and the call returns PIC_ETIMEOUT; the context keeps the
+ * timeout recorded, as after any expired wait: its later synchronising
+ * calls return PIC_ETIMEOUT, so destroy it. Synchronises. PIC_EINVAL for a
+ * budget or producer out of range. */
+int pic_selftest_bounded_wait(pic_ctx *c, uint64_t budget_ns, int producer);
 
 /* Copy particles out as 6 SoA blocks of Np doubles (x, y, z, vx, vy, vz) in
  * the ORIGINAL particle order (index p of pic_init), to device memory
@@ -320,6 +335,84 @@ int pic_cnn_make_batch(pic_ctx *c, const double *r, const double *a, const doubl
  * residual norm). Writes the loss to *loss_host and its gradient with respect
  * to y to gy (device FP32 [B][D^3]). */
 int pic_cnn_loss(pic_ctx *c, const float *y, const float *t, int B, int D, float *gy, double *loss_host);
+
+/* ------------------------------------------------------------------------
+ * Training of the network behind one call. The paper has no learned part;
+ * this follows the learned-preconditioner pattern the library adds to the
+ * PCG solve of Sec. 3.2: (residual, error) pairs, random crops, the loss of
+ * pic_cnn_loss, Adam, and selection of the kept weights by the flexible-CG
+ * iterations of a held-out solve.
+ *   PIC_TRAIN_PRECONDITIONER: the pairs come from the library's own FP64
+ *     Jacobi-PCG solves of the CIC deposits of `sets` seeded Landau initial
+ *     conditions (grid^3 x 8 ppc, seeds seed .. seed + sets - 1): the
+ *     converged phi* (tol 1e-12) and the iterates after 1, 2, 4, ..., 128
+ *     iterations from zero; scored by PIC_PC_CNN solves.
+ *   PIC_TRAIN_SMOOTHER: white-noise errors e (Philox4x32-10 normals, seeds
+ *     as above) and r = A e, for the finest-level smoother of the multigrid
+ *     V-cycle (PIC_PC_MG_CNN); scored by PIC_PC_MG_CNN solves.
+ * Each Adam step draws a set, a snapshot and `batch` crop origins from a
+ * Philox4x32-10 stream keyed by `seed` whose counter is the Adam step count,
+ * so a training resumed from a weights file (resume = 1, after pic_cnn_load)
+ * continues the stream. Without resume the weights start from the Jacobi
+ * direction plus seeded noise. With validate_every > 0 the training state is
+ * scored every validate_every steps and at the end (flexible CG to rel-res
+ * 1e-10 of the CIC deposit of a val_grid^3 x 8 ppc Landau initial condition
+ * with seed val_seed), and the best scored state (weights, Adam moments and
+ * step count) is the one the context keeps; with 0 the last state is kept.
+ * The training runs in contexts of its own on the context's device and
+ * stream (the training grid, the validation grid); the context `c` only
+ * receives the result, so it may be of any size or a solver-only context.
+ * Synchronises. PIC_EINVAL for options out of range (32 <= grid <= 256,
+ * grid % 16 == 0, 16 <= crop <= grid, crop % 16 == 0, 1 <= batch, sets <= 64,
+ * lr > 0, val_grid % 32 == 0 in [32, 512]); PIC_ESTATE for resume without
+ * weights.
+ * ------------------------------------------------------------------------ */
+enum { PIC_TRAIN_PRECONDITIONER = 0, PIC_TRAIN_SMOOTHER = 1 };
+typedef struct {
+  int target;          /* PIC_TRAIN_PRECONDITIONER or PIC_TRAIN_SMOOTHER */
+  int grid;            /* training grid (64) */
+  int sets;            /* training right-hand sides (4) */
+  int steps;           /* Adam steps of this call (600) */
+  int batch;           /* crops per step (8) */
+  int crop;            /* crop edge D (32) */
+  double lr;           /* Adam step size (2e-3) */
+  uint64_t seed;       /* data, crop-origin and initial-weight seed (11) */
+  int validate_every;  /* steps between scorings (100; 0 = keep the last state) */
+  int val_grid;        /* validation grid (128) */
+  uint64_t val_seed;   /* validation seed (21) */
+  int resume;          /* 1 = continue from the context's weights, Adam moments and step */
+} pic_train_opts;
+typedef struct {
+  int steps;           /* Adam steps taken by this call */
+  int adam_steps;      /* Adam step count of the kept state */
+  int best_step;       /* step of this call whose state was kept */
+  int best_iters;      /* its validation iterations (-1 without validation) */
+  double loss_first;   /* mean loss of the first 10 steps */
+  double loss_last;    /* mean loss of the last 50 steps */
+  double seconds;      /* wall time of the call */
+} pic_train_info;
+int pic_cnn_train(pic_ctx *c, const pic_train_opts *o, pic_train_info *info);
+
+/* The network's training state in a file: a 32-byte header (magic
+ * "PICCNN1\n", format version 1, weight count, Adam step count, FNV-1a
+ * 64-bit hash of the payload) and the payload of FP32 master weights, Adam's
+ * m and v (PIC_CNN_WEIGHTS floats each, little-endian). pic_cnn_load
+ * restores all of it (so training can resume) and rebuilds the inference
+ * kernels; PIC_EINVAL for an unreadable, truncated, foreign or corrupted
+ * file, PIC_ESTATE from pic_cnn_save without weights. Both synchronise. */
+int pic_cnn_save(pic_ctx *c, const char *path);
+int pic_cnn_load(pic_ctx *c, const char *path);
+
+/* Arithmetic of the training passes (pic_cnn_forward, pic_cnn_backward):
+ * PIC_CNN_TRAIN_BF16 (default) runs the convolutions on the tensor cores
+ * with BF16 weights and activations and FP32 accumulation;
+ * PIC_CNN_TRAIN_FP32 is a test mode that runs every convolution of both
+ * passes on the CUDA cores in FP32 (FP32 activations and data gradients,
+ * the FP32 master weights), so that the gradients can be compared with an
+ * FP64 reference element by element. A backward pass must follow a forward
+ * pass in the same mode (PIC_ESTATE otherwise). PIC_EINVAL for another mode. */
+enum { PIC_CNN_TRAIN_BF16 = 0, PIC_CNN_TRAIN_FP32 = 1 };
+int pic_cnn_set_train_precision(pic_ctx *c, int mode);
 
 /* One convolution of the packed network without epilogue, for tests: which =
  * 0..3 forward layers 1..4, 4..6 data-gradient convs of layers 4, 3, 2.

@@ -60,6 +60,12 @@ def field_at_particles(pos, q, N, L):
     above): (1/L^3) sum over the symmetric nonzero modes of
     -i k / |k|^2 rho_hat(k) exp(i k.x_j); returned real (the imaginary part is
     zero to rounding over the symmetric mode set)."""
+    return field_at(pos, q, N, L, pos)
+
+
+def field_at(pos, q, N, L, at):
+    """The field of the charges q at pos (as in field_at_particles) evaluated
+    at the points `at` (3, M): type 1 over every charge, type 2 at `at` only."""
     m = mode_numbers(N)
     rho_hat = nudft_type1(pos, q, N, L)
     k = 2.0 * np.pi * m / L
@@ -73,6 +79,6 @@ def field_at_particles(pos, q, N, L):
     phi_hat = rho_hat * inv / L ** 3
     E = []
     for kd in (kx, ky, kz):
-        E.append(nudft_type2(-1j * kd * phi_hat, pos, N, L))
+        E.append(nudft_type2(-1j * kd * phi_hat, at, N, L))
     E = np.stack(E)
     return E.real, E.imag

@@ -44,6 +44,8 @@ CNN_APPLY_FP32 = 1
 CNN_APPLY_LAYERS = 2
 CNN_APPLY_TC_FUSED = 3
 CNN_WEIGHTS = 14688
+CNN_TRAIN_BF16 = 0
+CNN_TRAIN_FP32 = 1
 
 
 class PicError(RuntimeError):
@@ -80,6 +82,26 @@ class pic_profile_stats(ctypes.Structure):
         }
 
 
+TRAIN_PRECONDITIONER = 0
+TRAIN_SMOOTHER = 1
+
+
+class pic_train_opts(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_int), ("grid", ctypes.c_int), ("sets", ctypes.c_int), ("steps", ctypes.c_int),
+                ("batch", ctypes.c_int), ("crop", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("validate_every", ctypes.c_int), ("val_grid", ctypes.c_int), ("val_seed", ctypes.c_uint64),
+                ("resume", ctypes.c_int)]
+
+
+class pic_train_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("adam_steps", ctypes.c_int), ("best_step", ctypes.c_int),
+                ("best_iters", ctypes.c_int), ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class pic_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("fallbacks", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
@@ -108,6 +130,7 @@ _SIGS = {
     "pic_field_energy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pic_get_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]),
+    "pic_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
     "pic_set_particles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "pic_num_particles": (ctypes.c_int64, [ctypes.c_void_p]),
     "pic_apply_laplacian": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -136,6 +159,10 @@ _SIGS = {
                                           ctypes.c_void_p, ctypes.c_double]),
     "pic_cnn_loss": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pic_cnn_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_train_opts), ctypes.POINTER(pic_train_info)]),
+    "pic_cnn_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "pic_cnn_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "pic_cnn_set_train_precision": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pic_cnn_conv_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_int]),
     "pic_field_energy_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
@@ -350,6 +377,10 @@ class Context:
                                        ctypes.byref(half)), "pic_get_particles")
         return bool(half.value)
 
+    def selftest_bounded_wait(self, budget_ns, producer):
+        """Status code of the bounded-wait self-test (PIC_OK or PIC_ETIMEOUT)."""
+        return lib().pic_selftest_bounded_wait(self.h, int(budget_ns), 1 if producer else 0)
+
     def particles_to_host(self, out):
         """The particles into a host FP64 tensor of 6 Np (pinned or pageable; x,
         y, z, vx, vy, vz blocks, original order); returns whether velocities lag
@@ -411,6 +442,30 @@ class Context:
     def cnn_apply(self, r, z):
         _check(lib().pic_cnn_apply(self.h, _dptr(r, "float32", self.n, "r"), _dptr(z, "float32", self.n, "z")),
                "pic_cnn_apply")
+
+    def cnn_train(self, target=TRAIN_PRECONDITIONER, grid=64, sets=4, steps=600, batch=8, crop=32, lr=2e-3,
+                  seed=11, validate_every=100, val_grid=128, val_seed=21, resume=False, raise_on_error=True):
+        """pic_cnn_train: trains the network in the library and keeps the
+        result in this context; returns the training info (and its code)."""
+        o = pic_train_opts(int(target), grid, sets, steps, batch, crop, lr, seed, validate_every, val_grid, val_seed,
+                           1 if resume else 0)
+        info = pic_train_info()
+        code = lib().pic_cnn_train(self.h, ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error:
+            _check(code, "pic_cnn_train")
+        d = info.as_dict()
+        d["code"] = code
+        return d
+
+    def cnn_save(self, path):
+        _check(lib().pic_cnn_save(self.h, os.fsencode(path)), "pic_cnn_save")
+
+    def cnn_load(self, path):
+        _check(lib().pic_cnn_load(self.h, os.fsencode(path)), "pic_cnn_load")
+
+    def cnn_set_train_precision(self, mode):
+        _check(lib().pic_cnn_set_train_precision(self.h, int(mode)), "pic_cnn_set_train_precision")
+        return self
 
     def cnn_forward(self, x, y, B, D):
         n = B * D ** 3

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills"]
-UNITS = ["capi.cu", "cnn.cu", "mg.cu", "fft.cu", "ssor.cu", "pif.cu", "noalloc.cu"]
+UNITS = ["capi.cu", "cnn.cu", "mg.cu", "fft.cu", "ssor.cu", "pif.cu", "train.cu", "noalloc.cu"]
 
 
 def nvcc():

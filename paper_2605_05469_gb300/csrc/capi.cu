@@ -81,8 +81,9 @@ int ensure_partials(pic_ctx* c, size_t need) {
 }
 
 int check_dev_err(pic_ctx* c) {
-  // caller has synchronised
+  // caller has synchronised; the faults stay recorded for the context's life
   if (*c->err_host & DEV_ERR_TIMEOUT) return PIC_ETIMEOUT;
+  if (*c->err_host & DEV_ERR_NONFINITE) return PIC_EBREAKDOWN;  // a push met a non-finite field
   return PIC_OK;
 }
 
@@ -489,7 +490,7 @@ int launch_push(pic_ctx* c, const double* phi, const double* Efield, double kick
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push<false>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
          (const float2*)(c->E + c->n), (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
-         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts, (const double*)nullptr);
+         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts, (const double*)nullptr, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -816,7 +817,7 @@ int pic_pif_push(pic_ctx* c, double tol, double dt) {
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)nullptr,
          (const float2*)nullptr, (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
-         c->keys, c->ranks, c->counts, (const double*)c->pif_E);
+         c->keys, c->ranks, c->counts, (const double*)c->pif_E, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   c->half_step = true;
@@ -852,6 +853,13 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return PIC_OK;
+}
+
+int pic_selftest_bounded_wait(pic_ctx* c, uint64_t budget_ns, int producer) {
+  if (!c || budget_ns == 0 || budget_ns > kWaitBudgetNs || (producer != 0 && producer != 1)) return PIC_EINVAL;
+  launch(c, k_selftest_wait, 1, 32, 0, budget_ns, producer, c->err);
+  CK(cudaGetLastError());
+  return sync_status(c);
 }
 
 int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step) {

@@ -2,6 +2,8 @@
 // the C ABI (include/pic.h). The network and its kernels are described in
 // cnn_kernels.cuh; this file owns the buffers and sequences the launches.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -20,6 +22,10 @@ struct CnnState {
   // training: activations of the last forward (B x D^3 cells)
   size_t train_cells = 0;
   __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *ga = nullptr, *gb = nullptr;
+  // the FP32 test mode of the training convs (PIC_CNN_TRAIN_FP32)
+  int train_prec = 0;
+  size_t f32_cells = 0;
+  float *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *fa = nullptr, *fb = nullptr;
   const float* last_x = nullptr;
   int last_B = 0, last_D = 0;
   // inference ping-pong activations at N^3
@@ -79,6 +85,28 @@ int ensure_train(pic_ctx* c, size_t cells) {
   return PIC_OK;
 }
 
+int ensure_train_f32(pic_ctx* c, size_t cells) {
+  CnnState* s = c->cnn;
+  if (s->f32_cells >= cells) return PIC_OK;
+  dfree(s->f1); dfree(s->f2); dfree(s->f3); dfree(s->fa); dfree(s->fb);
+  s->f32_cells = 0;
+  int e;
+  if ((e = dalloc(&s->f1, 16 * cells)) || (e = dalloc(&s->f2, 16 * cells)) || (e = dalloc(&s->f3, 16 * cells)) ||
+      (e = dalloc(&s->fa, 16 * cells)) || (e = dalloc(&s->fb, 16 * cells)))
+    return e;
+  s->f32_cells = cells;
+  return PIC_OK;
+}
+
+template <int CIN, int COUT, bool ADJ>
+int conv_f32(pic_ctx* c, const float* in, float* out, int layer, int D, int B) {
+  const long cells = (long)B * D * D * D;
+  launch(c, k_conv_f32<CIN, COUT, ADJ>, (unsigned)((cells * COUT + 255) / 256), 256, 0, in, out,
+         (const float*)(c->cnn->w + kLayerOff[layer]), D, cells);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
 int ensure_batch(pic_ctx* c, int B) {
   CnnState* s = c->cnn;
   if (s->bmax >= B) return PIC_OK;
@@ -119,10 +147,10 @@ int conv(pic_ctx* c, const void* in, void* out, const unsigned char* w, int mode
   return PIC_OK;
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool F32 = false>
 int wgrad(pic_ctx* c, const void* gz, const void* a, int D, int B, float* dW) {
   const long tiles = (long)(D / TX) * (D / TY) * (D / ZT) * B;
-  launch(c, k_wgrad<CIN, COUT>, (unsigned)tiles, 256, 0, gz, a, D, D, D, dW);
+  launch(c, k_wgrad<CIN, COUT, F32>, (unsigned)tiles, 256, 0, gz, a, D, D, D, dW);
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -145,6 +173,7 @@ void cnn_state_free(CnnState* s) {
   if (!s) return;
   dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K); dfree(s->Bt);
   dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
+  dfree(s->f1); dfree(s->f2); dfree(s->f3); dfree(s->fa); dfree(s->fb);
   dfree(s->i1); dfree(s->i2);
   dfree(s->sums); dfree(s->origins); dfree(s->q);
   if (s->sums_host) cudaFreeHost(s->sums_host);
@@ -235,7 +264,60 @@ int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) 
                   inv_n, SCALE_SQRT);
 }
 
+int cnn_state_get(pic_ctx* c, float* dev3, int* adam_t) {
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  CK(cudaMemcpyAsync(dev3, s->w, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(dev3 + kWeights, s->m, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(dev3 + 2 * kWeights, s->v, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  *adam_t = s->adam_t;
+  return PIC_OK;
+}
+
+int cnn_state_set(pic_ctx* c, const float* dev3, int adam_t) {
+  int e;
+  if ((e = ensure_state(c))) return e;
+  CnnState* s = c->cnn;
+  CK(cudaMemcpyAsync(s->w, dev3, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(s->m, dev3 + kWeights, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(s->v, dev3 + 2 * kWeights, kWeights * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemsetAsync(s->g, 0, kWeights * 4, c->stream));
+  s->adam_t = adam_t;
+  if ((e = repack(c))) return e;
+  s->has_weights = true;
+  return PIC_OK;
+}
+
 }  // namespace pic
+
+namespace {
+
+// Weights file: a 32-byte header (magic, format version, weight count, Adam
+// step count, FNV-1a 64-bit hash of the payload) and the payload: the FP32
+// master weights, then Adam's m and v, PIC_CNN_WEIGHTS floats each,
+// little-endian.
+constexpr char kFileMagic[8] = {'P', 'I', 'C', 'C', 'N', 'N', '1', '\n'};
+constexpr uint32_t kFileVersion = 1;
+
+struct FileHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t count;
+  int64_t adam_t;
+  uint64_t hash;
+};
+static_assert(sizeof(FileHeader) == 32, "weights file header");
+
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+}  // namespace
 
 // ==========================================================================
 // C ABI
@@ -303,6 +385,17 @@ int pic_cnn_forward(pic_ctx* c, const float* x, float* y, int B, int D) {
   CnnState* s = c->cnn;
   const size_t cells = (size_t)B * D * D * D;
   int e;
+  if (s->train_prec == PIC_CNN_TRAIN_FP32) {
+    if ((e = ensure_train_f32(c, cells))) return e;
+    if ((e = conv_f32<1, 16, false>(c, x, s->f1, 0, D, B))) return e;
+    if ((e = conv_f32<16, 16, false>(c, s->f1, s->f2, 1, D, B))) return e;
+    if ((e = conv_f32<16, 16, false>(c, s->f2, s->f3, 2, D, B))) return e;
+    if ((e = conv_f32<16, 1, false>(c, s->f3, y, 3, D, B))) return e;
+    s->last_x = x;
+    s->last_B = B;
+    s->last_D = D;
+    return PIC_OK;
+  }
   if ((e = ensure_train(c, cells))) return e;
   if ((e = conv<1>(c, x, s->a1, s->packed + kPackFwd1, OUT_BF16, D, D, D, B))) return e;
   if ((e = conv<16>(c, s->a1, s->a2, s->packed + kPackFwd2, OUT_BF16, D, D, D, B))) return e;
@@ -326,6 +419,19 @@ int pic_cnn_backward(pic_ctx* c, const float* gy, int B, int D) {
   int e;
   // the activations are the identity, so each data gradient is the adjoint
   // conv of the layer's own gradient; weight gradients per layer, then tied
+  if (s->train_prec == PIC_CNN_TRAIN_FP32) {
+    if (s->f32_cells < (size_t)B * D * D * D) return PIC_ESTATE;
+    if ((e = wgrad<16, 1, true>(c, gy, s->f3, D, B, g4))) return e;
+    if ((e = conv_f32<1, 16, true>(c, gy, s->fa, 3, D, B))) return e;
+    if ((e = wgrad<16, 16, true>(c, s->fa, s->f2, D, B, g3))) return e;
+    if ((e = conv_f32<16, 16, true>(c, s->fa, s->fb, 2, D, B))) return e;
+    if ((e = wgrad<16, 16, true>(c, s->fb, s->f1, D, B, g2))) return e;
+    if ((e = conv_f32<16, 16, true>(c, s->fb, s->fa, 1, D, B))) return e;
+    if ((e = wgrad<1, 16, true>(c, s->fa, s->last_x, D, B, g1))) return e;
+    launch(c, k_tie_grads, 27, 256, 0, s->g);
+    CK(cudaGetLastError());
+    return PIC_OK;
+  }
   if ((e = wgrad<16, 1>(c, gy, s->a3, D, B, g4))) return e;
   if ((e = conv<1>(c, gy, s->ga, s->packed + kPackBwd4, OUT_BF16, D, D, D, B))) return e;
   if ((e = wgrad<16, 16>(c, s->ga, s->a2, D, B, g3))) return e;
@@ -335,6 +441,90 @@ int pic_cnn_backward(pic_ctx* c, const float* gy, int B, int D) {
   if ((e = wgrad<1, 16>(c, s->ga, s->last_x, D, B, g1))) return e;
   launch(c, k_tie_grads, 27, 256, 0, s->g);
   CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int pic_cnn_save(pic_ctx* c, const char* path) {
+  if (!c || !path) return PIC_EINVAL;
+  if (!cnn_ready(c)) return PIC_ESTATE;
+  CnnState* s = c->cnn;
+  float* host = static_cast<float*>(malloc(3 * kWeights * sizeof(float)));
+  if (!host) return PIC_ENOMEM;
+  cudaError_t ce = cudaMemcpyAsync(host, s->w, kWeights * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(host + kWeights, s->m, kWeights * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(host + 2 * kWeights, s->v, kWeights * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    free(host);
+    return PIC_ECUDA;
+  }
+  FileHeader hd;
+  memcpy(hd.magic, kFileMagic, 8);
+  hd.version = kFileVersion;
+  hd.count = kWeights;
+  hd.adam_t = s->adam_t;
+  hd.hash = fnv1a64(reinterpret_cast<const unsigned char*>(host), 3 * kWeights * sizeof(float));
+  FILE* f = fopen(path, "wb");
+  int rc = PIC_OK;
+  if (!f) {
+    rc = PIC_EINVAL;
+  } else {
+    if (fwrite(&hd, sizeof(hd), 1, f) != 1 || fwrite(host, sizeof(float), 3 * kWeights, f) != 3 * (size_t)kWeights)
+      rc = PIC_EINVAL;
+    if (fclose(f) != 0) rc = PIC_EINVAL;
+  }
+  free(host);
+  return rc;
+}
+
+int pic_cnn_load(pic_ctx* c, const char* path) {
+  if (!c || !path) return PIC_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return PIC_EINVAL;
+  FileHeader hd;
+  float* host = static_cast<float*>(malloc(3 * kWeights * sizeof(float)));
+  int rc = PIC_OK;
+  if (!host) {
+    rc = PIC_ENOMEM;
+  } else if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kFileMagic, 8) != 0 ||
+             hd.version != kFileVersion || hd.count != (uint32_t)kWeights || hd.adam_t < 0 ||
+             hd.adam_t > 0x7fffffff || fread(host, sizeof(float), 3 * kWeights, f) != 3 * (size_t)kWeights ||
+             fnv1a64(reinterpret_cast<const unsigned char*>(host), 3 * kWeights * sizeof(float)) != hd.hash) {
+    rc = PIC_EINVAL;
+  }
+  fclose(f);
+  if (rc != PIC_OK) {
+    free(host);
+    return rc;
+  }
+  int e;
+  if ((e = ensure_state(c))) {
+    free(host);
+    return e;
+  }
+  CnnState* s = c->cnn;
+  cudaError_t ce = cudaMemcpyAsync(s->w, host, kWeights * 4, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->m, host + kWeights, kWeights * 4, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(s->v, host + 2 * kWeights, kWeights * 4, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->g, 0, kWeights * 4, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);  // the host buffer is freed next
+  free(host);
+  if (ce != cudaSuccess) return PIC_ECUDA;
+  s->adam_t = (int)hd.adam_t;
+  if ((e = repack(c))) return e;
+  CK(cudaStreamSynchronize(c->stream));
+  s->has_weights = true;
+  return PIC_OK;
+}
+
+int pic_cnn_set_train_precision(pic_ctx* c, int mode) {
+  if (!c || (mode != PIC_CNN_TRAIN_BF16 && mode != PIC_CNN_TRAIN_FP32)) return PIC_EINVAL;
+  int e;
+  if ((e = ensure_state(c))) return e;
+  c->cnn->train_prec = mode;
+  c->cnn->last_x = nullptr;  // a backward pass needs a forward pass in the same mode
   return PIC_OK;
 }
 

@@ -24,5 +24,11 @@ bool cnn_fused_ok(const pic_ctx* c);
 int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x);
 // z = N r, only if a reliable update replaced r in this iteration.
 int cnn_apply_redo(pic_ctx* c, const float* r, float* z);
+// The training state: FP32 master weights, Adam moments m and v (three
+// blocks of PIC_CNN_WEIGHTS floats in device memory) and the Adam step count.
+// cnn_state_set also clears the gradients and rebuilds the packed and
+// composed inference kernels. Both enqueue on the context stream.
+int cnn_state_get(pic_ctx* c, float* dev3, int* adam_t);
+int cnn_state_set(pic_ctx* c, const float* dev3, int adam_t);
 
 }  // namespace pic

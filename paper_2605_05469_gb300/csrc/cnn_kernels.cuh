@@ -817,7 +817,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 0) {
       if (*abort_flag) return false;
-      if (global_timer_ns() - t0 > 2000000000ull) {
+      if (global_timer_ns() - t0 > kWaitBudgetNs) {
         atomicOr(err, DEV_ERR_TIMEOUT);
         *abort_flag = 1;
         return false;
@@ -1044,12 +1044,48 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
 }
 
 // ---------------------------------------------------------------------------
+// One layer of the network in FP32 on the CUDA cores (the training test mode):
+// periodic within each D^3 crop of the batch, activations FP32 (one value a
+// cell for one channel, 16 channel-last values a cell for sixteen), weights
+// the FP32 master copy w[out][in][tz][ty][tx]. ADJ applies the layer's
+// adjoint (the data gradient): channels transposed and taps flipped,
+//   forward  out[o][p] = sum_{c,t} w[o][c][t] in[c][p + t - 1],
+//   adjoint  out[c][p] = sum_{o,t} w[o][c][t] in[o][p - t + 1],
+// with CIN / COUT the channels this call reads / writes. One thread per
+// output value.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, bool ADJ>
+__global__ void __launch_bounds__(256) k_conv_f32(const float* __restrict__ in, float* __restrict__ out,
+                                                  const float* __restrict__ w, int D, long cells) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells * COUT) return;
+  const int o = (int)(t % COUT);
+  const long cell = t / COUT;
+  const long D3 = (long)D * D * D;
+  const long b = cell / D3, r = cell % D3;
+  const int x = (int)(r % D), y = (int)((r / D) % D), z = (int)(r / ((long)D * D));
+  float acc = 0.f;
+  for (int tz = 0; tz < 3; ++tz)
+    for (int ty = 0; ty < 3; ++ty)
+      for (int tx = 0; tx < 3; ++tx) {
+        const int dz = ADJ ? 1 - tz : tz - 1, dy = ADJ ? 1 - ty : ty - 1, dx = ADJ ? 1 - tx : tx - 1;
+        const long src = b * D3 + ((long)wrap(z + dz, D) * D + wrap(y + dy, D)) * D + wrap(x + dx, D);
+        const int tap = (tz * 3 + ty) * 3 + tx;
+        for (int c = 0; c < CIN; ++c) {
+          const float wv = ADJ ? w[(c * COUT + o) * 27 + tap] : w[(o * CIN + c) * 27 + tap];
+          acc = fmaf(wv, in[src * CIN + c], acc);
+        }
+      }
+  out[cell * COUT + o] = acc;
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient on CUDA cores, FP32:
 //   dW[o][c][tap] += sum_cells gz[cell][o] * a[cell + tap - 1][c]
 // gz: COUT channels (f32 if COUT == 1 else bf16 x16); a: CIN channels (f32 if
 // CIN == 1 else bf16 x16). One CTA per 8 x 16 x 4 tile; 4 x 4 register blocks.
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool F32 = false>
 __global__ void __launch_bounds__(256) k_wgrad(const void* __restrict__ gz_, const void* __restrict__ a_, int NX,
                                                int NY, int NZ, float* __restrict__ dW) {
   constexpr int CP = CIN < 4 ? 4 : CIN, OP = COUT < 4 ? 4 : COUT;
@@ -1069,6 +1105,9 @@ __global__ void __launch_bounds__(256) k_wgrad(const void* __restrict__ gz_, con
     if (CIN == 1) {
       sa[c * CP] = reinterpret_cast<const float*>(a_)[cell];
       sa[c * CP + 1] = sa[c * CP + 2] = sa[c * CP + 3] = 0.f;
+    } else if (F32) {
+      const float* ap = reinterpret_cast<const float*>(a_) + 16 * cell;
+      for (int i = 0; i < 16; ++i) sa[c * CP + i] = ap[i];
     } else {
       const __nv_bfloat16* ap = reinterpret_cast<const __nv_bfloat16*>(a_) + 16 * cell;
       for (int i = 0; i < 16; ++i) sa[c * CP + i] = __bfloat162float(ap[i]);
@@ -1080,6 +1119,9 @@ __global__ void __launch_bounds__(256) k_wgrad(const void* __restrict__ gz_, con
     if (COUT == 1) {
       sg[c * OP] = reinterpret_cast<const float*>(gz_)[cell];
       sg[c * OP + 1] = sg[c * OP + 2] = sg[c * OP + 3] = 0.f;
+    } else if (F32) {
+      const float* gp = reinterpret_cast<const float*>(gz_) + 16 * cell;
+      for (int i = 0; i < 16; ++i) sg[c * OP + i] = gp[i];
     } else {
       const __nv_bfloat16* gp = reinterpret_cast<const __nv_bfloat16*>(gz_) + 16 * cell;
       for (int i = 0; i < 16; ++i) sg[c * OP + i] = __bfloat162float(gp[i]);

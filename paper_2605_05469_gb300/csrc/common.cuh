@@ -102,14 +102,19 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-// Wait for the phase with the given parity to complete. Gives up after about
-// two seconds of wall time, records DEV_ERR_TIMEOUT and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+// Wall-time budget of every bounded device-side wait.
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;
+
+// Wait for the phase with the given parity to complete. Gives up after
+// budget_ns of wall time (about two seconds by default), records
+// DEV_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  uint64_t budget_ns = kWaitBudgetNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 0 && global_timer_ns() - t0 > 2000000000ull) {
+    if ((i & 255u) == 0 && global_timer_ns() - t0 > budget_ns) {
       atomicOr(err, DEV_ERR_TIMEOUT);
       return false;
     }

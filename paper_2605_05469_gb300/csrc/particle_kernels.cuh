@@ -122,7 +122,7 @@ __device__ __forceinline__ uint64_t abs_times_2p64(float x) {
 // exact (its bits are a subset of d.hi's), which d.hi - floor(d.hi) is not
 // for negative d.hi (-0.3 + 1 needs one more bit than 0.7 has).
 __device__ __forceinline__ void move_coord(uint64_t& f, int& i, df d, int N) {
-  const float n = truncf(d.hi);
+  const float n = fminf(fmaxf(truncf(d.hi), -1048576.0f), 1048576.0f);  // keeps the index arithmetic in range
   const float r = __fsub_rn(d.hi, n);  // exact, |r| < 1, sign of d.hi
   const uint64_t A = abs_times_2p64(r), B = abs_times_2p64(d.lo);
   const bool ra = r >= 0.0f, ba = d.lo >= 0.0f;
@@ -490,7 +490,8 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
                                                               const float2* __restrict__ Ey,
                                                               const float2* __restrict__ Ez, Grid g, float2 kick_qm,
                                                               float2 dth, int drift, uint32_t* keys, uint32_t* ranks,
-                                                              uint32_t* counts, const double* __restrict__ Ep) {
+                                                              uint32_t* counts, const double* __restrict__ Ep,
+                                                              int* err) {
   const uint64_t base = (uint64_t)blockIdx.x * kPushThreads;
   const uint64_t p = base + threadIdx.x;
   const bool valid = p < np;
@@ -533,11 +534,22 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
       ep[2] = ez.value();
     }
     const df kq = dfc(kick_qm);
-    vx = df_add(vx, df_mul(kq, ep[0]));
-    vy = df_add(vy, df_mul(kq, ep[1]));
-    vz = df_add(vz, df_mul(kq, ep[2]));
+    const df ux = df_add(vx, df_mul(kq, ep[0]));
+    const df uy = df_add(vy, df_mul(kq, ep[1]));
+    const df uz = df_add(vz, df_mul(kq, ep[2]));
+    // a non-finite field at the particle: record the fault and leave the
+    // particle as it is (its key and rank are still written below)
+    const bool fin = isfinite(ux.hi) && isfinite(uy.hi) && isfinite(uz.hi) && isfinite(ux.lo) &&
+                     isfinite(uy.lo) && isfinite(uz.lo);
+    if (fin) {
+      vx = ux;
+      vy = uy;
+      vz = uz;
+    } else {
+      atomicOr(err, DEV_ERR_NONFINITE);
+    }
     *reinterpret_cast<float4*>(rec + 2) = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
-    if (drift) {
+    if (drift && fin) {
       const df s = dfc(dth);
       move_coord(fx, ix, df_mul(vx, s), N);
       move_coord(fy, iy, df_mul(vy, s), N);
@@ -545,6 +557,8 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
       rec[0] = make_uint4((uint32_t)fx, (uint32_t)(fx >> 32), (uint32_t)fy, (uint32_t)(fy >> 32));
       kk = cell_key(ix, iy, iz, N);
       rec[3] = make_uint4(r3.x, kk, (uint32_t)ix | ((uint32_t)iy << 16), (uint32_t)iz | (r3.w & 0xFFFF0000u));
+    } else if (drift) {
+      kk = cell_key(ix, iy, iz, N);
     }
     rec[1] = make_uint4((uint32_t)fz, (uint32_t)(fz >> 32), __float_as_uint(vx.hi), __float_as_uint(vx.lo));
   }

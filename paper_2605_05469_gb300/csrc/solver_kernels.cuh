@@ -446,4 +446,21 @@ __global__ void __launch_bounds__(kStreamSmall) k_apply64(const double* __restri
   stream_slab<double, double, double, 1>(g, smem, bars, x, (const double*)nullptr, err, start, ingest, body);
 }
 
+// Self-test of the bounded device wait (mbar_wait_bounded): one warp waits on
+// an mbarrier of one expected arrival; with `producer` lane 1 arrives, else
+// nothing does and the wait gives up after budget_ns, recording
+// DEV_ERR_TIMEOUT. No copy is ever issued, so nothing is in flight when the
+// warp leaves.
+__global__ void k_selftest_wait(uint64_t budget_ns, int producer, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  if (producer && threadIdx.x == 1)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  mbar_wait_bounded(&bar, 0, err, budget_ns);
+}
+
 }  // namespace pic

@@ -32,20 +32,13 @@ def pg():
 
 @pytest.mark.parametrize("N", [256, 512])
 def test_solver_errors_against_exact_solution(pg, N, capsys):
-    from paper_2605_05469_gb300 import train as T
     h = L / N
     b = inputs.landau_noise_rhs(N, 3)
     exact = opic.spectral_solve_fft(b, N, h)
     enorm = np.linalg.norm(exact)
     # the learned preconditioner, trained as the benchmark trains it
-    sets = T.landau_snapshot_sets(64, seeds=[11, 12, 13, 14])
-    ct = pg.Context().init(64, 0, 0)
-    T.train(ct, sets, 600, B=8, D=32, lr=2e-3, seed=0)
-    w = ct.cnn_get_weights()
-    ct.close()
-    del sets
     c = pg.Context().init(N, 0, 0)
-    c.cnn_set_weights(w)
+    c.cnn_train(pg.TRAIN_PRECONDITIONER)
     bt = torch.from_numpy(b).cuda()
     errs = {}
     for name, prec, pc in (("fp64_jacobi", pg.PREC_FP64, pg.PC_JACOBI), ("mixed_jacobi", pg.PREC_MIXED, pg.PC_JACOBI),

@@ -8,8 +8,10 @@ tolerance is 1e-5 relative. The full network stores BF16 activations between
 layers, so forward values and the loss are compared at BF16 tolerance (2e-2
 relative), and weight gradients by direction (cosine >= 0.995) and magnitude
 (1e-1 relative L2): they are sums over all cells of products whose signs
-cancel, which magnifies the BF16 rounding of the data gradients. Adam is compared exactly on the
-GPU's own gradients.
+cancel, which magnifies the BF16 rounding of the data gradients. The FP32
+test mode of the training passes pins every weight gradient element by element
+(1e-2 of its value plus 1e-4 of the layer's largest). Adam is compared exactly
+on the GPU's own gradients.
 """
 import numpy as np
 import pytest
@@ -209,6 +211,61 @@ def test_network_forward_loss_and_gradients_match_oracle(pg):
         assert cos >= 0.995 and r_err <= 0.1, report
 
 
+def test_network_gradients_fp32_mode_match_oracle_elementwise(pg):
+    """The training passes in the FP32 test mode (every convolution on the
+    CUDA cores in FP32): the forward values, the loss and every weight
+    gradient (which carries the whole chain of data gradients) against the
+    oracle's FP64 network on the same crops, element by element. Bound per
+    weight: 1e-2 of its own value plus 1e-4 of the layer's largest gradient
+    (a gradient is a sum over 8192 cells whose terms can cancel to far below
+    their magnitudes, where FP32 accumulation of ~5e-6 of the sum of |terms|
+    dominates)."""
+    N, D, B = 32, 16, 2
+    h = L / N
+    ws, flat = rounded_weights(2)
+    c = ctx_with_weights(pg, flat, N)
+    c.cnn_set_train_precision(pg.CNN_TRAIN_FP32)
+    r = inputs.noise_field(N, 5)
+    a = inputs.noise_field(N, 6)
+    b = inputs.noise_field(N, 7)
+    origins = np.array([[0, 3, 5], [20, 31, 9]], dtype=np.int32)
+    x = torch.empty(B * D ** 3, dtype=torch.float32, device="cuda")
+    t = torch.empty_like(x)
+    c.cnn_make_batch(torch.from_numpy(r).cuda(), torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
+                     origins, D, x, t, h * h)
+
+    def crop(f, o):
+        g = f.reshape(N, N, N)
+        return g[np.ix_((o[2] + np.arange(D)) % N, (o[1] + np.arange(D)) % N, (o[0] + np.arange(D)) % N)]
+    r_cr = [crop(r, o) for o in origins]
+    e_cr = [crop(a - b, o) for o in origins]
+    y = torch.empty_like(x)
+    c.cnn_forward(x, y, B, D)
+    ys = y.cpu().numpy().reshape(B, D, D, D)
+    for i in range(B):
+        ref, _ = ocnn.forward(r_cr[i] / np.sqrt(np.mean(r_cr[i] ** 2)), ws)
+        assert np.max(np.abs(ys[i] - ref)) <= 1e-5 * np.max(np.abs(ref))
+    gy = torch.empty_like(x)
+    loss = c.cnn_loss(y, t, B, D, gy)
+    ref_loss, ref_grads = ocnn.loss_and_grads(ws, r_cr, e_cr, h)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    c.cnn_backward(gy, B, D)
+    g = c.cnn_get_grads()
+    off = 0
+    for layer, rg in enumerate(ref_grads):
+        gl = g[off:off + rg.size].reshape(rg.shape).astype(np.float64)
+        off += rg.size
+        err = np.abs(gl - rg)
+        bound = 1e-2 * np.abs(rg) + 1e-4 * np.max(np.abs(rg))
+        assert np.all(err <= bound), (layer, float(np.max(err / bound)), float(np.median(err / np.abs(rg))))
+    # a backward pass in the other mode needs its own forward pass
+    c.cnn_set_train_precision(pg.CNN_TRAIN_BF16)
+    with pytest.raises(pg.PicError) as ex:
+        c.cnn_backward(gy, B, D)
+    assert ex.value.code == pg.PIC_ESTATE
+    c.close()
+
+
 def test_adam_matches_oracle_on_gpu_gradients(pg):
     ws, flat = rounded_weights(3)
     c = ctx_with_weights(pg, flat, 16)
@@ -320,18 +377,19 @@ def test_cnn_requires_weights_and_mixed_precision(pg):
 def test_trained_preconditioner_gain(pg, capsys):
     """What the trained network gains over the method without it.
 
-    The network is trained on the GPU (600 Adam steps on 32^3 crops of
-    (residual, error) pairs from Jacobi-PCG snapshots of four 64^3 Landau
-    deposits, forward/backward by the library's kernels), then flexible CG
-    with it solves held-out Landau deposits at 64^3 and 128^3 to the true
-    relative residual 1e-10. Asserted: convergence and at least 2x fewer
-    iterations than mixed-precision Jacobi-CG; reported: iterations and
-    device time of both and of the FP64 reference solve."""
-    from paper_2605_05469_gb300 import train as T
-    sets = T.landau_snapshot_sets(64, seeds=[11, 12, 13, 14])
+    The network is trained on the GPU by pic_cnn_train (600 Adam steps on
+    32^3 crops of (residual, error) pairs from Jacobi-PCG snapshots of four
+    64^3 Landau deposits, forward/backward by the library's kernels, the
+    weights scored on a held-out 128^3 deposit), then flexible CG with it
+    solves other held-out Landau deposits at 64^3 and 128^3 to the true
+    relative residual 1e-10. Asserted: the loss falls, convergence, no
+    descent-guard fallback, and at least 2x fewer iterations than
+    mixed-precision Jacobi-CG; reported: iterations and device time of both
+    and of the FP64 reference solve."""
     c = pg.Context().init(64, 0, 0)
-    losses = T.train(c, sets, 600, B=8, D=32, lr=2e-3, seed=0)
-    assert losses[-50:].mean() < 0.7 * losses[:10].mean()
+    info = c.cnn_train(pg.TRAIN_PRECONDITIONER)
+    assert info["loss_last"] < 0.7 * info["loss_first"], info
+    assert 0 < info["best_iters"] < 2001 and info["adam_steps"] <= 600, info
     w = c.cnn_get_weights()
     report = {}
     for N in (64, 128):
@@ -339,12 +397,21 @@ def test_trained_preconditioner_gain(pg, capsys):
         rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
         ce.deposit(rho)
         ce.cnn_set_weights(w)
-        res = T.compare_preconditioners(ce, rho)
+        res = {}
+        for name, prec, pc in (("fp64_jacobi", pg.PREC_FP64, pg.PC_JACOBI),
+                               ("mixed_jacobi", pg.PREC_MIXED, pg.PC_JACOBI),
+                               ("mixed_fcg_cnn", pg.PREC_MIXED, pg.PC_CNN)):
+            best = None
+            for _ in range(2):
+                phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+                r = ce.solve(rho, phi, tol=1e-10, maxit=20000, precision=prec, precond=pc)
+                best = r if best is None or r["t_ms"] < best["t_ms"] else best
+            res[name] = best
         cnn, jac = res["mixed_fcg_cnn"], res["mixed_jacobi"]
         assert cnn["converged"] and cnn["rel_res"] <= 1e-10 and cnn["fallbacks"] == 0, cnn
         assert cnn["iters"] * 2 <= jac["iters"], (cnn, jac)
         report[N] = {k: (v["iters"], round(v["t_ms"], 2)) for k, v in res.items()}
         ce.close()
+    c.close()
     with capsys.disabled():
-        print("\npreconditioner gain (iterations, device ms):", report)
-
+        print("\npreconditioner gain (iterations, device ms):", report, "training:", info)

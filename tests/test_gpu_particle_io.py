@@ -3,7 +3,8 @@ context through the C ABI, from and to device and host memory (the host path
 converts and copies in chunks of 2^24 particles), against the oracle's push
 of the same caller-given state.
 
-Tolerances: velocities round-trip exactly (FP64 -> double-float -> FP64);
+Tolerances: velocities that came out of the context round-trip exactly
+(double-float -> FP64 -> double-float), others keep 48 significant bits;
 positions within 1e-15 L (the fixed-point offset keeps 53 bits of a cell);
 one push of a caller-given state matches the oracle's to 1e-12 (the
 particle parity tolerance of the PIC tests)."""
@@ -65,11 +66,12 @@ def test_caller_state_is_wrapped_and_pushed_like_the_oracle(pg):
     c.set_particles(np.concatenate([pos, vel]), False)
     got, half = c.particles()
     assert half is False
-    wrapped = opic.wrap(pos, L)
+    wrapped = np.mod(pos, L)  # the periodic image in [0, L)
     d = np.abs(got[:3] - wrapped)
     d = np.minimum(d, L - d)  # a wrapped value may land on either side of 0 == L
     assert np.max(d) <= 1e-12
-    assert np.array_equal(got[3:], vel)
+    # velocities are kept as double-float pairs (two 24-bit significands)
+    assert np.max(np.abs(got[3:] - vel) / np.maximum(np.abs(vel), 1e-300)) <= 2.0 ** -46
     # deposit, solve, push from this state against the oracle
     rho = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
     c.deposit(rho)
@@ -108,9 +110,9 @@ def test_non_finite_state_is_rejected(pg):
 
 
 def test_host_round_trip_spans_several_chunks(pg):
-    """128^3 x 16 ppc = 33.6 M particles: three 2^24-particle chunks, the last
+    """128^3 x 20 ppc = 41.9 M particles: three 2^24-particle chunks, the last
     one ragged, in both directions."""
-    N, ppc = 128, 16
+    N, ppc = 128, 20
     c = pg.Context().init(N, ppc, 11)
     np_ = c.num_particles
     assert np_ > 2 * (1 << 24)

@@ -258,3 +258,54 @@ def test_full_size_step_properties_256cubed(pg):
     c.gather_push(phi, 0.05)
     c.deposit(rho)
     assert abs(host(rho).sum()) * h ** 3 <= 1e-6 * L ** 3
+
+
+# ------------------------------------------------------- Landau damping on the GPU
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return dict((r[0], float(r[1])) for r in rows)
+
+
+@pytest.mark.parametrize("solver", ["fp64_judge", "mixed_mg"])
+def test_landau_damping_rate_on_the_gpu_path(pg, solver):
+    """Fig. 2's check on the GPU path (Sec. 2.1, 3D Landau damping): 32^3 x 8
+    ppc, dt = 0.05, 190 steps (t = 9.5) through pic_deposit, the solve
+    (poisson_solve, the FP64 Jacobi-PCG, or the mixed-precision multigrid
+    FCG of the benchmark) and pic_gather_push. The amplitude of the three
+    k = 0.5 Fourier modes of phi peaks every pi / omega_r; a log-linear fit of
+    the peaks before t = 8.5 gives the damping rate, within 10 % of the
+    dispersion relation's gamma = -0.1534, and the period within 10 %."""
+    g = _golden("landau_linear.txt")
+    N, ppc, dt, steps = 32, 8, 0.05, 190
+    n = N ** 3
+    c = pg.Context().init(N, ppc, 0x5EED)
+    rho = torch.empty(n, dtype=torch.float64, device="cuda")
+    phi = torch.zeros(n, dtype=torch.float64, device="cuda")
+    amp = []
+    for _ in range(steps):
+        c.deposit(rho)
+        if solver == "fp64_judge":
+            assert pg.poisson_solve(c.h, rho, phi, 1e-10, 5000, n) == pg.PIC_OK
+        else:
+            c.solve(rho, phi, tol=1e-10, maxit=200, precision=pg.PREC_MIXED, precond=pg.PC_MG)
+        F = np.fft.fftn(host(phi).reshape(N, N, N))
+        amp.append(abs(F[0, 0, 1]) + abs(F[0, 1, 0]) + abs(F[1, 0, 0]))
+        c.gather_push(phi, dt)
+    c.close()
+    a = np.array(amp)
+    t = np.arange(a.size) * dt
+    pk = [i for i in range(1, a.size - 1) if a[i] > a[i - 1] and a[i] >= a[i + 1] and t[i] < 8.5]
+    assert len(pk) >= 3
+    gamma = np.polyfit(t[pk], np.log(a[pk]), 1)[0]
+    assert abs(gamma - g["gamma"]) < 0.1 * abs(g["gamma"]), gamma
+    period = np.mean(np.diff(t[pk]))
+    assert abs(period - np.pi / g["omega_r"]) < 0.1 * np.pi / g["omega_r"], period
+    print(f"\nGPU Landau damping ({solver}): gamma {gamma:.4f} (theory {g['gamma']}), "
+          f"period {period:.3f} (theory {np.pi / g['omega_r']:.3f})")

@@ -46,6 +46,26 @@ def test_pif_field_matches_direct_sums(pg, N, ppc, tol, bound):
     assert torch.allclose(E2, E, rtol=0.0, atol=1e-12 * float(np.max(np.abs(ref))))
 
 
+def test_pif_field_at_sampled_particles_with_32cubed_modes(pg):
+    """32^3 modes (a 64^3 oversampled grid: the window kernels over many
+    blocks and cells), 32 768 particles: the field at 1024 sampled particles
+    against the oracle's direct sums from every charge, at the paper's
+    tolerance 1e-4 and at 1e-12."""
+    N, ppc = 32, 1
+    npart = ppc * N ** 3
+    c = pg.Context().init(N, ppc, 21)
+    pos, _ = opic.init_particles(N, ppc, 21)
+    idx = np.random.default_rng(4).choice(npart, 1024, replace=False)
+    ref, imag = opif.field_at(pos, np.full(npart, -L ** 3 / npart), N, L, pos[:, idx])
+    assert np.max(np.abs(imag)) <= 1e-12 * np.max(np.abs(ref))
+    for tol, bound in ((1e-4, 5e-4), (1e-12, 1e-9)):
+        E = torch.full((3 * npart,), float("nan"), dtype=torch.float64, device="cuda")
+        c.pif_field(E, tol=tol)
+        got = E.view(3, npart)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= bound * np.max(np.abs(ref)), tol
+    c.close()
+
+
 def test_pif_steps_match_the_oracle(pg):
     N, ppc, steps, dt = 8, 2, 5, 0.05
     npart = ppc * N ** 3
