@@ -323,9 +323,18 @@ def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrie
                 "d2h_bytes_per_step": 24,
                 "note": f"host memory too small for the particle state ({avail / 2**30:.0f} GiB available): "
                         "particles stay on the device, the field energy is read back every step"}
-    state = torch.empty(6 * np_, dtype=torch.float64)
+    state = torch.zeros(6 * np_, dtype=torch.float64)
+    # page-locked in pieces of at most 4 GiB: measured on the Grace host, one
+    # 51.5 GB registration moved 25-36 GB/s, eight 6.4 GB ones 193 GB/s
     cudart = torch._C._cudart
-    registered = cudart.cudaHostRegister(state.data_ptr(), state_bytes, 0) == cudart.cudaError.success
+    piece = min(state_bytes, 4 << 30)
+    pieces = [(a, min(piece, state_bytes - a)) for a in range(0, state_bytes, piece)]
+    done = []
+    for a, b in pieces:
+        if cudart.cudaHostRegister(state.data_ptr() + a, b, 0) != cudart.cudaError.success:
+            break
+        done.append(a)
+    registered = len(done) == len(pieces)
     try:
         half = c.particles_to_host(state)  # the state starts on the host (untimed)
         barrier()
@@ -338,8 +347,8 @@ def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrie
         barrier()
         s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     finally:
-        if registered:
-            cudart.cudaHostUnregister(state.data_ptr())
+        for a in done:
+            cudart.cudaHostUnregister(state.data_ptr() + a)
         del state
     return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": state_bytes,
             "d2h_bytes_per_step": state_bytes + 24,

@@ -103,6 +103,9 @@ typedef struct {
 int pic_create(pic_ctx **out, void *cuda_stream);
 void pic_destroy(pic_ctx *c);
 const char *pic_strerror(int code);
+/* Name of the CUDA runtime error behind the calling thread's most recent
+ * PIC_ECUDA (e.g. "cudaErrorMemoryAllocation"), or "no CUDA error". */
+const char *pic_cuda_error(void);
 
 /* S0 (Sec. 2.1): allocate and sample the Landau initial condition on the
  * device. Particle p draws from Philox4x32-10 (Salmon et al., SC'11) with

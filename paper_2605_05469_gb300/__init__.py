@@ -50,7 +50,13 @@ CNN_TRAIN_FP32 = 1
 
 class PicError(RuntimeError):
     def __init__(self, code, what):
-        super().__init__(f"{what}: {strerror(code)} ({code})")
+        detail = ""
+        if code == PIC_ECUDA:
+            try:
+                detail = f" [{lib().pic_cuda_error().decode()}]"
+            except ImportError:
+                pass
+        super().__init__(f"{what}: {strerror(code)} ({code}){detail}")
         self.code = code
 
 
@@ -116,6 +122,7 @@ _lib = None
 # symbol -> (restype, argtypes)
 _SIGS = {
     "pic_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pic_cuda_error": (ctypes.c_char_p, []),
     "pic_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "pic_destroy": (None, [ctypes.c_void_p]),
     "pic_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(pic_params), ctypes.c_uint64]),

@@ -517,6 +517,10 @@ const char* pic_strerror(int code) {
   }
 }
 
+const char* pic_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorName(g_last_cuda_error);
+}
+
 int pic_create(pic_ctx** out, void* cuda_stream) {
   if (!out) return PIC_EINVAL;
   *out = nullptr;

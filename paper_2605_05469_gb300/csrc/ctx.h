@@ -123,10 +123,19 @@ struct pic_ctx {
 
 namespace pic {
 
+// The CUDA error behind the calling thread's last PIC_ECUDA (pic_cuda_error).
+inline thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+// A failed CUDA call: recorded for pic_cuda_error, and the runtime's own
+// last-error state is cleared so it does not surface in a later call.
 #define CK(call)                                  \
   do {                                            \
     cudaError_t e_ = (call);                      \
-    if (e_ != cudaSuccess) return PIC_ECUDA;      \
+    if (e_ != cudaSuccess) {                      \
+      pic::g_last_cuda_error = e_;                \
+      cudaGetLastError();                         \
+      return PIC_ECUDA;                           \
+    }                                             \
   } while (0)
 
 template <typename T>

@@ -18,6 +18,7 @@
 #include <string.h>
 #include <time.h>
 
+#include <deque>
 #include <vector>
 
 #include "cnn.h"
@@ -101,6 +102,9 @@ void initial_weights(uint64_t seed, float* w) {
 
 struct DevBuf {
   void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;  // owns its allocation: never copied or relocated
+  DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() {
     if (p) cudaFree(p);
   }
@@ -139,7 +143,9 @@ int make_context(cudaStream_t st, int N, int ppc, uint64_t seed, double alpha, d
   return pic_init(g->c, &p, seed);
 }
 
-int dfield(std::vector<DevBuf>& pool, size_t n, double** out) {
+// A device FP64 field of n values owned by `pool` (a deque: its elements stay
+// where they are while it grows).
+int dfield(std::deque<DevBuf>& pool, size_t n, double** out) {
   pool.emplace_back();
   int e = pool.back().alloc(n * sizeof(double));
   *out = pool.back().get<double>();
@@ -200,7 +206,7 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
   }
 
   // training data
-  std::vector<DevBuf> pool;
+  std::deque<DevBuf> pool;
   std::vector<Set> sets(O.sets);
   double* zero = nullptr;
   if ((e = dfield(pool, n, &zero))) return e;
