@@ -778,20 +778,22 @@ def train_networks(pg, torch):
     pic_cnn_train call (the library's own solves for the data, its kernels
     for forward, loss, backward and Adam): as flexible CG's preconditioner
     (Jacobi-PCG snapshots of four 64^3 Landau deposits, 600 Adam steps on
-    32^3 crops, kept by the flexible-CG iterations of a held-out 128^3
-    deposit) and as the V-cycle's finest-level smoother (white-noise errors,
-    kept by the multigrid-FCG iterations of the same deposit). Returns the
-    weights per preconditioner and the training records."""
+    32^3 crops, four restarts, the state kept by the flexible-CG iterations
+    of a held-out 128^3 deposit) and as the V-cycle's finest-level smoother
+    (white-noise errors, kept by the multigrid-FCG iterations of the same
+    deposit). Returns the weights per preconditioner and the training
+    records."""
     t0 = time.perf_counter()
     c = pg.Context().init(64, 0, 0)
-    info_p = c.cnn_train(pg.TRAIN_PRECONDITIONER)
+    info_p = c.cnn_train(pg.TRAIN_PRECONDITIONER, restarts=4)
     w_p = c.cnn_get_weights()
     info_s = c.cnn_train(pg.TRAIN_SMOOTHER)
     w_s = c.cnn_get_weights()
     c.close()
     torch.cuda.synchronize()
     rec = {k: {"loss_first": round(v["loss_first"], 4), "loss_last": round(v["loss_last"], 4),
-               "kept_adam_step": v["adam_steps"], "validation_iters": v["best_iters"], "seconds": round(v["seconds"], 2)}
+               "kept_adam_step": v["adam_steps"], "kept_restart": v["best_restart"],
+               "validation_iters": v["best_iters"], "seconds": round(v["seconds"], 2)}
            for k, v in (("preconditioner", info_p), ("smoother", info_s))}
     rec.update({"grid": 64, "steps": 600, "selected_by": "flexible-CG iterations on a 128^3 deposit",
                 "seconds": round(time.perf_counter() - t0, 2)})

@@ -384,12 +384,16 @@ typedef struct {
   int val_grid;        /* validation grid (128) */
   uint64_t val_seed;   /* validation seed (21) */
   int resume;          /* 1 = continue from the context's weights, Adam moments and step */
+  int restarts;        /* independent trainings from other initial weights and crop streams
+                          (same data), the best validated state kept (1; > 1 needs
+                          validate_every > 0 and resume = 0; at most 16) */
 } pic_train_opts;
 typedef struct {
   int steps;           /* Adam steps taken by this call */
   int adam_steps;      /* Adam step count of the kept state */
   int best_step;       /* step of this call whose state was kept */
   int best_iters;      /* its validation iterations (-1 without validation) */
+  int best_restart;    /* the restart it came from */
   double loss_first;   /* mean loss of the first 10 steps */
   double loss_last;    /* mean loss of the last 50 steps */
   double seconds;      /* wall time of the call */

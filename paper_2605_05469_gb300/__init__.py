@@ -96,12 +96,13 @@ class pic_train_opts(ctypes.Structure):
     _fields_ = [("target", ctypes.c_int), ("grid", ctypes.c_int), ("sets", ctypes.c_int), ("steps", ctypes.c_int),
                 ("batch", ctypes.c_int), ("crop", ctypes.c_int), ("lr", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("validate_every", ctypes.c_int), ("val_grid", ctypes.c_int), ("val_seed", ctypes.c_uint64),
-                ("resume", ctypes.c_int)]
+                ("resume", ctypes.c_int), ("restarts", ctypes.c_int)]
 
 
 class pic_train_info(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("adam_steps", ctypes.c_int), ("best_step", ctypes.c_int),
-                ("best_iters", ctypes.c_int), ("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double),
+                ("best_iters", ctypes.c_int), ("best_restart", ctypes.c_int), ("loss_first", ctypes.c_double),
+                ("loss_last", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
     def as_dict(self):
@@ -451,11 +452,12 @@ class Context:
                "pic_cnn_apply")
 
     def cnn_train(self, target=TRAIN_PRECONDITIONER, grid=64, sets=4, steps=600, batch=8, crop=32, lr=2e-3,
-                  seed=11, validate_every=100, val_grid=128, val_seed=21, resume=False, raise_on_error=True):
+                  seed=11, validate_every=100, val_grid=128, val_seed=21, resume=False, restarts=1,
+                  raise_on_error=True):
         """pic_cnn_train: trains the network in the library and keeps the
         result in this context; returns the training info (and its code)."""
         o = pic_train_opts(int(target), grid, sets, steps, batch, crop, lr, seed, validate_every, val_grid, val_seed,
-                           1 if resume else 0)
+                           1 if resume else 0, restarts)
         info = pic_train_info()
         code = lib().pic_cnn_train(self.h, ctypes.byref(o), ctypes.byref(info))
         if raise_on_error:

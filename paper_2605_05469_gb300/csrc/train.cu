@@ -12,7 +12,9 @@
 // the stream), then runs the library's crop, forward, loss, backward and Adam
 // kernels. Every validate_every steps the weights are scored by the flexible
 // CG iterations of a held-out deposit solve, and the best scored training
-// state (weights, Adam moments, step) is the one the context keeps.
+// state (weights, Adam moments, step) over `restarts` independent trainings
+// (other initial weights and crop streams, the same data) is the one the
+// context keeps.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -177,6 +179,8 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
       O.validate_every < 0 || (O.resume != 0 && O.resume != 1))
     return PIC_EINVAL;
   if (O.validate_every > 0 && (O.val_grid < 32 || O.val_grid > 512 || O.val_grid % 32 != 0)) return PIC_EINVAL;
+  if (O.restarts < 1 || O.restarts > 16 || (O.restarts > 1 && (O.resume || O.validate_every == 0)))
+    return PIC_EINVAL;
   if (O.resume && !cnn_ready(c)) return PIC_ESTATE;
   const timespec t_start = [] {
     timespec t;
@@ -195,14 +199,11 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
   pic_ctx* t = tg.c;
   DevBuf state, best;  // training state (w, m, v) and the best scored one
   if ((e = state.alloc(3 * kWeightsN * sizeof(float))) || (e = best.alloc(3 * kWeightsN * sizeof(float)))) return e;
-  int adam_t = 0;
+  int adam_t0 = 0;  // Adam step count the training starts from
+  DevBuf start;     // resume: the caller's training state
   if (O.resume) {
-    if ((e = cnn_state_get(c, state.get<float>(), &adam_t)) || (e = cnn_state_set(t, state.get<float>(), adam_t)))
+    if ((e = start.alloc(3 * kWeightsN * sizeof(float))) || (e = cnn_state_get(c, start.get<float>(), &adam_t0)))
       return e;
-  } else {
-    std::vector<float> w0(kWeightsN);
-    initial_weights(O.seed, w0.data());
-    if ((e = pic_cnn_set_weights(t, w0.data()))) return e;
   }
 
   // training data
@@ -262,8 +263,9 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
   if ((e = xb.alloc(m * 4)) || (e = tb.alloc(m * 4)) || (e = yb.alloc(m * 4)) || (e = gb.alloc(m * 4))) return e;
   std::vector<int> origins(3 * B);
   std::vector<double> losses;
-  const uint64_t key = O.seed ^ 0xC7A1B5EEDull;
-  int best_iters = 0x7fffffff, best_step = -1, best_t = adam_t;
+  int best_iters = 0x7fffffff, best_step = -1, best_t = adam_t0, best_restart = 0;
+  int restart = 0;
+  std::vector<double> best_losses;
   auto score = [&](int step) -> int {
     int it = 0, ee, tt;
     if ((ee = cnn_state_get(t, state.get<float>(), &tt))) return ee;
@@ -274,11 +276,25 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
       best_iters = it;
       best_step = step;
       best_t = tt;
+      best_restart = restart;
+      best_losses = losses;
       CK(cudaMemcpyAsync(best.get<float>(), state.get<float>(), 3 * kWeightsN * sizeof(float),
                          cudaMemcpyDeviceToDevice, c->stream));
     }
     return PIC_OK;
   };
+  for (restart = 0; restart < O.restarts; ++restart) {
+  // each restart: its own initial weights and crop stream (restart 0 is the plain training)
+  const uint64_t key = (O.seed + 0x9E3779B97F4A7C15ull * (uint64_t)restart) ^ 0xC7A1B5EEDull;
+  if (O.resume) {
+    if ((e = cnn_state_set(t, start.get<float>(), adam_t0))) return e;
+  } else {
+    std::vector<float> w0(kWeightsN);
+    initial_weights(O.seed + 7919ull * (uint64_t)restart, w0.data());
+    if ((e = pic_cnn_set_weights(t, w0.data()))) return e;
+  }
+  const int adam_t = adam_t0;
+  losses.clear();
   for (int step = 0; step < O.steps; ++step) {
     const uint32_t ctr = (uint32_t)(adam_t + step);
     const U4 pick = philox({ctr, 0u, 0u, 0u}, key);
@@ -301,9 +317,11 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
     if (O.validate_every > 0 && (step + 1) % O.validate_every == 0 && step + 1 < O.steps && (e = score(step + 1)))
       return e;
   }
+  if (O.validate_every > 0 && (e = score(O.steps))) return e;
+  }  // restarts
   int final_t = 0;
   if (O.validate_every > 0) {
-    if ((e = score(O.steps))) return e;
+    losses = best_losses;
     if ((e = cnn_state_set(c, best.get<float>(), best_t))) return e;
     final_t = best_t;
   } else {
@@ -320,6 +338,7 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
     for (size_t i = losses.size() - k2; i < losses.size(); ++i) info->loss_last += losses[i] / (double)k2;
     info->best_step = O.validate_every > 0 ? best_step : O.steps;
     info->best_iters = O.validate_every > 0 ? best_iters : -1;
+    info->best_restart = best_restart;
     timespec t_end;
     clock_gettime(CLOCK_MONOTONIC, &t_end);
     info->seconds = (double)(t_end.tv_sec - t_start.tv_sec) + 1e-9 * (double)(t_end.tv_nsec - t_start.tv_nsec);

@@ -307,7 +307,8 @@ def test_fcg_cnn_solve_reaches_true_residual(pg, N):
 def test_fused_fcg_step_matches_the_unfused_one(pg):
     """On a 128^3 grid the tensor-core preconditioner runs with the CG update
     and the direction's dots fused into it (and recomputes z after each
-    reliable update). It must reach the true FP64 relative residual 1e-10
+    reliable update), or with the direction's dots alone in its epilogue (the
+    default form). Each must reach the true FP64 relative residual 1e-10
     (checked with the oracle's operator) in about as many iterations as the
     unfused sequence with the FP32 evaluation of the same composed kernel, and
     its solution must agree with that one to the solve tolerance."""
@@ -319,19 +320,22 @@ def test_fused_fcg_step_matches_the_unfused_one(pg):
     b = inputs.landau_noise_rhs(N, 12)
     bt = torch.from_numpy(b).cuda()
     res = {}
-    for mode in ("tc", "fp32"):
-        c.cnn_set_apply(pg.CNN_APPLY_TC_FUSED if mode == "tc" else pg.CNN_APPLY_FP32)
+    modes = {"tc_fused": pg.CNN_APPLY_TC_FUSED, "tc": pg.CNN_APPLY_TC, "fp32": pg.CNN_APPLY_FP32}
+    for mode, code in modes.items():
+        c.cnn_set_apply(code)
         phi = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
         info = c.solve(bt, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, precond=pg.PC_CNN)
         got = phi.cpu().numpy()
         bp = b - b.mean()
         assert np.linalg.norm(bp - opic.apply_A(got, N, h)) <= 1.05e-10 * np.linalg.norm(bp), (mode, info)
         res[mode] = (info, got)
-    tc, f32 = res["tc"][0], res["fp32"][0]
-    assert tc["reliable_updates"] > 0, tc
-    assert abs(tc["iters"] - f32["iters"]) <= 0.15 * f32["iters"] + 3, (tc, f32)
-    a, r = res["tc"][1], res["fp32"][1]
-    assert np.linalg.norm(a - r) <= 1e-8 * np.linalg.norm(r)
+    f32 = res["fp32"][0]
+    for mode in ("tc_fused", "tc"):
+        tc = res[mode][0]
+        assert tc["reliable_updates"] > 0, (mode, tc)
+        assert abs(tc["iters"] - f32["iters"]) <= 0.15 * f32["iters"] + 3, (mode, tc, f32)
+        a, r = res[mode][1], res["fp32"][1]
+        assert np.linalg.norm(a - r) <= 1e-8 * np.linalg.norm(r), mode
 
 
 def jacobi_network_weights():

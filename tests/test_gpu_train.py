@@ -123,3 +123,16 @@ def test_rejects_bad_options_and_files(pg, tmp_path):
     with pytest.raises(pg.PicError):
         c.cnn_load(str(tmp_path / "missing.piccnn"))
     c.close()
+
+
+def test_restarts_keep_the_best_validated_state(pg):
+    c = pg.Context().init(64, 0, 0)
+    one = c.cnn_train(pg.TRAIN_PRECONDITIONER)
+    many = c.cnn_train(pg.TRAIN_PRECONDITIONER, restarts=3)
+    assert 0 <= many["best_restart"] < 3
+    # restart 0 repeats the plain training (up to the order of FP32 atomics)
+    assert many["best_iters"] <= one["best_iters"] + 2, (one, many)
+    for bad in ({"restarts": 0}, {"restarts": 17}, {"restarts": 2, "validate_every": 0}):
+        assert c.cnn_train(steps=1, raise_on_error=False, **bad)["code"] == pg.PIC_EINVAL, bad
+    assert c.cnn_train(steps=1, restarts=2, resume=True, raise_on_error=False)["code"] == pg.PIC_EINVAL
+    c.close()
