@@ -362,7 +362,6 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   // the dots are recomputed from it by the redo kernels, which return at once
   // otherwise.
   const bool fused = pc == PIC_PC_CNN && cnn_fused_ok(c);
-  const bool dots_in_precond = pc == PIC_PC_CNN && !fused && cnn_tc_ok(c);
   if (fused && !w.r32b && (e = dalloc(&w.r32b, c->n))) return e;
   float* rbuf[2] = {w.r32, w.r32b};
   int rc = 0;
@@ -403,17 +402,13 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
              w.r32, c->sc, c->partials, c->counter, c->err, gr, 1);
       zc ^= 1;
       slot = sample ? c->ker[PIC_KER_PRECOND].begin(c->stream) : -1;
-      // the tensor-core network computes the direction's dot products in its
-      // epilogue; the other preconditioners leave them to k_fcg_dot
-      const int ce = dots_in_precond ? cnn_apply_dots(c, w.r32, w.z32[zc], w.q32) : precond(w.r32, w.z32[zc], sample);
+      const int ce = precond(w.r32, w.z32[zc], sample);
       if (sample) c->ker[PIC_KER_PRECOND].end(slot, c->stream);
       if (ce && !inner_err) inner_err = ce;
-      if (!dots_in_precond) {
-        slot = sample ? c->ker[PIC_KER_DOT].begin(c->stream) : -1;
-        launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4,
-               c->sc, c->partials, c->counter, 0, 0);
-        if (sample) c->ker[PIC_KER_DOT].end(slot, c->stream);
-      }
+      slot = sample ? c->ker[PIC_KER_DOT].begin(c->stream) : -1;
+      launch(c, k_fcg_dot, sb, 256, 0, (const float*)w.r32, (const float*)w.z32[zc], (const float*)w.q32, n4, c->sc,
+             c->partials, c->counter, 0, 0);
+      if (sample) c->ker[PIC_KER_DOT].end(slot, c->stream);
       launch(c, k_fcg_fallback, sb, 256, 0, (const float*)w.r32, w.z32[zc], n4, (const Scalars*)c->sc);
       cur ^= 1;
     }

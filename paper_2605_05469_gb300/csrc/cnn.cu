@@ -190,18 +190,18 @@ bool cnn_fused_ok(const pic_ctx* c) { return c->N % tck::BY == 0 && c->cnn_apply
 
 // The composed kernel on the tensor cores, persistent: one CTA per SM, each a
 // contiguous range of output planes.
-template <int MODE>
+template <bool FUSED>
 int launch_tc(pic_ctx* c, const float* r, float* z, const TcFcg& F) {
   static bool configured = false;
   if (!configured) {
-    CK(cudaFuncSetAttribute((const void*)k_apply_k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)tck::smem_bytes<MODE>()));
+    CK(cudaFuncSetAttribute((const void*)k_apply_k_tc<FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)tck::smem_bytes<FUSED>()));
     configured = true;
   }
   const int N = c->N;
   const long units = (long)(N / tck::BX) * (N / tck::BY) * N;
   const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
-  launch(c, k_apply_k_tc<MODE>, grid, tck::THREADS, tck::smem_bytes<MODE>(), r, z, N,
+  launch(c, k_apply_k_tc<FUSED>, grid, tck::THREADS, tck::smem_bytes<FUSED>(), r, z, N,
          (const unsigned char*)c->cnn->Bt, c->err, F);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -210,7 +210,7 @@ int launch_tc(pic_ctx* c, const float* r, float* z, const TcFcg& F) {
 int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x) {
   if (!cnn_fused_ok(c)) return PIC_EINVAL;
   TcFcg F{q, p, x, r_new, c->sc, c->partials, c->counter, 0};
-  return launch_tc<tck::MODE_FUSED>(c, r, z, F);
+  return launch_tc<true>(c, r, z, F);
 }
 
 int cnn_apply_redo(pic_ctx* c, const float* r, float* z) {
@@ -218,13 +218,7 @@ int cnn_apply_redo(pic_ctx* c, const float* r, float* z) {
   TcFcg F{};
   F.sc = c->sc;
   F.only_redo = 1;
-  return launch_tc<tck::MODE_PLAIN>(c, r, z, F);
-}
-
-int cnn_apply_dots(pic_ctx* c, const float* r, float* z, const float* q) {
-  if (!cnn_tc_ok(c)) return PIC_EINVAL;
-  TcFcg F{q, nullptr, nullptr, nullptr, c->sc, c->partials, c->counter, 0};
-  return launch_tc<tck::MODE_DOTS>(c, r, z, F);
+  return launch_tc<false>(c, r, z, F);
 }
 
 int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) {
@@ -233,7 +227,7 @@ int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) 
   // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
   if (cnn_tc_ok(c)) {
     TcFcg F{};
-    return launch_tc<tck::MODE_PLAIN>(c, r, z, F);
+    return launch_tc<false>(c, r, z, F);
   }
   // grids that are not a multiple of 128 run the FP32 composed kernel in TC mode
   if (N % KX == 0 && c->cnn_apply_mode != PIC_CNN_APPLY_LAYERS) {

@@ -24,10 +24,6 @@ bool cnn_fused_ok(const pic_ctx* c);
 int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x);
 // z = N r, only if a reliable update replaced r in this iteration.
 int cnn_apply_redo(pic_ctx* c, const float* r, float* z);
-// z = N r on the tensor cores with flexible CG's next-direction dot products
-// (r, z), (z, q), (r, q), the descent guard and beta computed in the same
-// kernel (the work of the separate dot kernel).
-int cnn_apply_dots(pic_ctx* c, const float* r, float* z, const float* q);
 // The training state: FP32 master weights, Adam moments m and v (three
 // blocks of PIC_CNN_WEIGHTS floats in device memory) and the Adam step count.
 // cnn_state_set also clears the gradients and rebuilds the packed and

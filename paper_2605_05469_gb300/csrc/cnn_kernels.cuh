@@ -488,25 +488,21 @@ constexpr int PTHREADS = 256;             // producer threads
 constexpr int LOADS = (AROWS * 8 + PTHREADS - 1) / PTHREADS;  // 16-byte pieces per producer per plane (5)
 constexpr int ASLOTS = 4;                 // BF16 A operands (input planes ready for the tensor cores)
 constexpr int TILE_OUT_B = BY * BX * 4;   // 8192: one output plane's 128 x 16 FP32 block
-// Forms of the kernel: PLAIN z = N r; DOTS z = N r and the dot products
-// flexible CG needs next, (r, z), (z, q), (r, q), in the epilogue; FUSED also
-// the CG update in front of the network (below).
-enum { MODE_PLAIN = 0, MODE_DOTS = 1, MODE_FUSED = 2 };
-// the epilogue operands r, q (DOTS) and p, x (FUSED) of one output plane's
-// block, double-buffered (cp.async two planes ahead)
+// the fused form's epilogue operands r, q, p, x of one output plane's block,
+// double-buffered (cp.async two planes ahead)
 constexpr int EPI_PLANE_B = 4 * TILE_OUT_B;
-template <int MODE>
-constexpr int epi_bufs() { return MODE != MODE_PLAIN ? 2 : 0; }
+template <bool FUSED>
+constexpr int epi_bufs() { return FUSED ? 2 : 0; }
 // an output plane's TMEM slots (zeroed by the epilogue after it reads them)
 // are taken again by the output plane TSLOTS later, whose first term comes
 // from the input plane TSLOTS - 8 input planes after the one that completed it
 constexpr int SLOT_REUSE_LAG = TSLOTS - 8;
 constexpr int ERING = 32;                 // plane handshakes between the MMA issuer and the epilogue
-template <int MODE>
+template <bool FUSED>
 constexpr size_t smem_bytes() {
-  return (size_t)B_BYTES + ASLOTS * SLOT_B + TILE_OUT_B + epi_bufs<MODE>() * EPI_PLANE_B;
-}  // 126976 plain, 192512 with the epilogue operands
-static_assert(smem_bytes<MODE_PLAIN>() > 114 * 1024 && smem_bytes<MODE_FUSED>() <= 226 * 1024, "one CTA per SM");
+  return (size_t)B_BYTES + ASLOTS * SLOT_B + TILE_OUT_B + epi_bufs<FUSED>() * EPI_PLANE_B;
+}  // 126976 plain, 192512 fused
+static_assert(smem_bytes<false>() > 114 * 1024 && smem_bytes<true>() <= 226 * 1024, "one CTA per SM");
 static_assert(ERING > SLOT_REUSE_LAG, "the issuer must not lap the epilogue handshakes");
 }  // namespace tck
 
@@ -718,7 +714,6 @@ __device__ __forceinline__ size_t tc_epi_offset(const TcPlane& P, int N, int et,
 // plane that P completes, copied two planes ahead (they do not depend on the
 // MMAs) into one of two shared-memory buffers: [array][f] float4 per buffer,
 // each thread its own pieces. One cp.async group per plane, always committed.
-template <bool FULL>
 __device__ __forceinline__ void tc_epi_fetch(const TcPlane& P, const float* __restrict__ r, int N, const TcFcg& F,
                                              bool x_zero, float4* buf) {
   if (P.z - 4 >= P.pa) {
@@ -729,10 +724,8 @@ __device__ __forceinline__ void tc_epi_fetch(const TcPlane& P, const float* __re
       const size_t off = tc_epi_offset(P, N, et, k);
       cp_async16(buf + f, r + off);
       cp_async16(buf + 512 + f, F.q + off);
-      if (FULL) {
-        cp_async16(buf + 1024 + f, F.p + off);
-        if (!x_zero) cp_async16(buf + 1536 + f, F.x + off);
-      }
+      cp_async16(buf + 1024 + f, F.p + off);
+      if (!x_zero) cp_async16(buf + 1536 + f, F.x + off);
     }
   }
   cp_async_commit();
@@ -750,7 +743,7 @@ __device__ __forceinline__ void tc_epi_barrier() { asm volatile("bar.sync 1, 128
 // all 16 columns (x) of the slot, into a shared-memory tile; the 128
 // epilogue threads then move the plane's 128 x 16 block to and from global
 // memory four threads per 64-byte row segment (coalesced).
-template <int MODE>
+template <bool FUSED>
 __device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict__ z, int N, uint32_t tmem,
                                             long ubegin, const TcFcg& F, float alpha, bool x_zero, TcDots& D,
                                             float4* tile, const float4* ops) {
@@ -785,24 +778,7 @@ __device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict_
     const size_t off = tc_epi_offset(P, N, et, k);
     const float4 zv = tile[tc_tile_idx(f >> 2, f & 3)];
     *reinterpret_cast<float4*>(z + off) = zv;
-    if (MODE == MODE_PLAIN) continue;
-    if (MODE == MODE_DOTS) {
-      const float4 rv = ops[f], qv = ops[512 + f];
-      const float* r4 = &rv.x;
-      const float* q4 = &qv.x;
-      const float* z4 = &zv.x;
-      float prz = 0.f, pzq = 0.f, prq = 0.f;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        prz = fmaf(r4[i], z4[i], prz);
-        pzq = fmaf(z4[i], q4[i], pzq);
-        prq = fmaf(r4[i], q4[i], prq);
-      }
-      D.rz.add(prz);
-      D.zq.add(pzq);
-      D.rq.add(prq);
-      continue;
-    }
+    if (!FUSED) continue;
     float4 rv = ops[f], xv = x_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : ops[1536 + f];
     const float4 qv = ops[512 + f], pv = ops[1024 + f];
     const float* q4 = &qv.x;
@@ -850,12 +826,11 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, int* err
   }
 }
 
-template <int MODE>
+template <bool FUSED>
 __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __restrict__ r, float* __restrict__ z,
                                                                 int N, const unsigned char* __restrict__ Bg,
                                                                 int* err, TcFcg F) {
   using namespace tck;
-  constexpr bool FUSED = MODE == MODE_FUSED, EPI = MODE != MODE_PLAIN;
   if (F.sc) {
     if (F.sc->done) return;
     if (!FUSED && F.only_redo && !F.sc->redo) return;
@@ -953,11 +928,11 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
     constexpr int EB = EPI_PLANE_B / 16;  // float4 per operand buffer
     TcPlane ahead = P;
     bool have_a = have;
-    if (EPI) {
+    if (FUSED) {
       // operands of planes 0 and 1 in flight
       for (int b = 0; b < 2; ++b) {
         if (have_a) {
-          tc_epi_fetch<FUSED>(ahead, r, N, F, x_zero, ebuf + b * EB);
+          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + b * EB);
           have_a = tc_next(uend, N, ahead);
         } else {
           cp_async_commit();
@@ -965,16 +940,16 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
       }
     }
     for (uint32_t j = 0; have; ++j) {
-      if (EPI) cp_async_wait<1>();  // plane j's operands (own pieces)
+      if (FUSED) cp_async_wait<1>();  // plane j's operands (own pieces)
       if (!tc_wait(&acc_full[j % ERING], (j / ERING) & 1u, err, &abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tc_epilogue<MODE>(P, z, N, tmem, ubegin, F, alpha, x_zero, dots, tile, ebuf + (j & 1u) * EB);
+      tc_epilogue<FUSED>(P, z, N, tmem, ubegin, F, alpha, x_zero, dots, tile, ebuf + (j & 1u) * EB);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&acc_empty[j % ERING]);
-      if (EPI) {
+      if (FUSED) {
         // refill the buffer plane j used with plane j + 2
         if (have_a) {
-          tc_epi_fetch<FUSED>(ahead, r, N, F, x_zero, ebuf + (j & 1u) * EB);
+          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + (j & 1u) * EB);
           have_a = tc_next(uend, N, ahead);
         } else {
           cp_async_commit();
@@ -982,7 +957,7 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
       }
       have = tc_next(uend, N, P);
     }
-    if (EPI) cp_async_wait<0>();
+    if (FUSED) cp_async_wait<0>();
   } else {
     // ---- producers: 256 threads, two planes in registers ahead of conversion ----
     const int ptid = tid - PROD_WARP0 * 32;
@@ -1031,26 +1006,6 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
-  if (MODE == MODE_DOTS) {
-    // the next direction: beta = -(z, q) / (p, q), with the descent guard
-    // (the bookkeeping of k_fcg_dot)
-    double v[3] = {dots.rz.value(), dots.zq.value(), dots.rq.value()}, tot[3];
-    if (grid_reduce_last<3>(v, F.partials, F.counter, tot) && threadIdx.x == 0) {
-      Scalars* sc = F.sc;
-      double rz = tot[0], zq = tot[1];
-      sc->fallback_now = 0;
-      if (!(rz > 0.0) || !isfinite(rz) || !isfinite(zq)) {
-        sc->fallback_now = 1;
-        sc->fallbacks += 1;
-        rz = sc->rr / 6.0;
-        zq = tot[2] / 6.0;
-      }
-      sc->beta = -zq / sc->pq;
-      sc->rz = rz;
-      sc->redo = 0;
-      if (!isfinite(sc->beta)) sc->done = 3;
-    }
-  }
   if (FUSED) {
     double v[4] = {dots.rr.value(), dots.rz.value(), dots.zq.value(), dots.rq.value()}, tot[4];
     if (grid_reduce_last<4>(v, F.partials, F.counter, tot) && threadIdx.x == 0) {

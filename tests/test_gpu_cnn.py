@@ -307,8 +307,8 @@ def test_fcg_cnn_solve_reaches_true_residual(pg, N):
 def test_fused_fcg_step_matches_the_unfused_one(pg):
     """On a 128^3 grid the tensor-core preconditioner runs with the CG update
     and the direction's dots fused into it (and recomputes z after each
-    reliable update), or with the direction's dots alone in its epilogue (the
-    default form). Each must reach the true FP64 relative residual 1e-10
+    reliable update), or alone with the update and the dots in their own
+    kernels (the default form). Each must reach the true FP64 relative residual 1e-10
     (checked with the oracle's operator) in about as many iterations as the
     unfused sequence with the FP32 evaluation of the same composed kernel, and
     its solution must agree with that one to the solve tolerance."""
