@@ -52,8 +52,9 @@ SOLVERS = ["mixed", "fp64", "cnn", "mg", "mg_cnn", "ssor", "fft", "pif"]
 # preconditioner, warm-started solves to rel-res 1e-10
 DEFAULT_N = 512
 DEFAULT_SOLVER = "cnn"
-# also timed on the same particles: the multigrid-preconditioned step
-DEFAULT_ALT_SOLVERS = ("mg",)
+# also timed on the same particles: the multigrid-preconditioned step, with
+# Jacobi and with the learned smoother
+DEFAULT_ALT_SOLVERS = ("mg", "mg_cnn")
 # cold solves of the largest solver-only grid, after the particles are freed
 DEFAULT_COMPARE_GRIDS = (1024,)
 
@@ -115,7 +116,7 @@ def pif_width(tol):
 # dram__bytes_write.sum over the particle count) measured by ncu on the
 # 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
 # count): it stands for the same kernels at other sizes
-MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.70, "scatter": 133.72}
+MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.59, "scatter": 133.72}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
 
@@ -184,6 +185,9 @@ def parse(argv=None):
                     help="comma-separated grid sizes of extra cold-solve comparisons on a Landau density + "
                          "N(0, 0.01^2) noise right-hand side, run after the PIC context is freed (empty = none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--weights-dir", default=None,
+                    help="load the trained networks from this directory (pic_cnn_load) when it holds them, else "
+                         "train and save them there (pic_cnn_save)")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64-vs-mixed solve comparison")
     ap.add_argument("--compare-reps", type=int, default=2,
                     help="cold solves per solver in the comparison (best kept; solves longer than 2 s run once)")
@@ -339,22 +343,48 @@ def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrie
         half = c.particles_to_host(state)  # the state starts on the host (untimed)
         barrier()
         t0 = time.perf_counter()
+        marks = []
         for _ in range(steps):
             c.set_particles(state, half)
             step(False)  # reads the field energy back
             half = c.particles_to_host(state)
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         barrier()
         s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        per_step = np.diff([t0] + marks)
     finally:
         for a in done:
             cudart.cudaHostUnregister(state.data_ptr() + a)
         del state
     return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": state_bytes,
             "d2h_bytes_per_step": state_bytes + 24,
+            "step_s": {"min": round(float(per_step.min()), 3), "median": round(float(np.median(per_step)), 3),
+                       "max": round(float(per_step.max()), 3)},
             "note": ("every step: the particle state (FP64 x, y, z, vx, vy, vz) in from "
                      + ("page-locked" if registered else "pageable") + " host memory (pic_set_particles), "
                      "the step, its field energy read back, the state out to host memory (pic_get_particles)")}
+
+
+def vcycle_record(prof, learned, N, hbm):
+    """One V-cycle (every level, the one-block coarse cycle and, with the
+    learned smoother, its two network applications) from the sampled
+    preconditioner launches: bytes of the plane-streamed levels per fine
+    cell over the average duration, against the HBM peak."""
+    k = prof["ker_samples"].get("precond")
+    if not k:
+        return None
+    avg_ms = prof["ker_ms"]["precond"] / k
+    jac = sum(MG_BYTES.values())
+    # learned smoother on the finest level: network r -> x (8), residual,
+    # restriction, residual of x + P e_c, network res -> x (8), x += t (12)
+    fine = jac if not learned else (8 + MG_BYTES["mg_resid"] + MG_BYTES["mg_restrict"] +
+                                    MG_BYTES_PROLONG_RESID + 8 + 12)
+    bpc = fine + jac * (mg_level_fraction(N) - 1.0)
+    gbs = bpc * N ** 3 / (avg_ms * 1e-3) / 1e9
+    return {"avg_us": round(avg_ms * 1e3, 2), "samples": k, "bytes_per_fine_cell": round(bpc, 3),
+            "gbs": round(gbs, 1), "frac_of_hbm": round(gbs / hbm, 4),
+            "note": "one V-cycle, every level; bytes of the plane-streamed levels"}
 
 
 def solver_modes(pg, solver):
@@ -424,7 +454,7 @@ def run_ours(args):
             raise SystemExit(f"unknown solver in --alt-solvers: {s_}")
     weights, train_info = None, None
     if any(s_ in ("cnn", "mg_cnn") for s_ in [args.solver] + alt_solvers) or not args.no_compare:
-        weights, train_info = train_networks(pg, torch)
+        weights, train_info = train_networks(pg, torch, args.weights_dir)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
     apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
                   "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
@@ -545,7 +575,11 @@ def run_ours(args):
         a_ms = max_over_ranks(a0.elapsed_time(a1), dist, "cuda")
         a_prof = c.profile_read(reset=True)
         c.profile(False)
-        alt[s_] = {"value": round(whole_job_rate(world, args.steps, a_ms / 1e3), 4), "unit": unit,
+        if s_ in ("mg", "mg_cnn"):
+            alt_vc = vcycle_record(a_prof, s_ == "mg_cnn", N, peaks()[0])
+        else:
+            alt_vc = None
+        alt[s_] = {"value": round(whole_job_rate(world, args.steps, a_ms / 1e3), 4), "unit": unit, "vcycle": alt_vc,
                    "ms_per_step": round(a_ms / args.steps, 3), "steps": args.steps,
                    "dtype": dtype_label(pg, s_, args.cnn_apply, args.pif_tol),
                    "phases_ms_per_step": {k: round(v / args.steps, 3) for k, v in a_prof["phase_ms"].items()},
@@ -607,20 +641,7 @@ def run_ours(args):
             avg_ms = prof["ker_ms"][k] / prof["ker_samples"][k]
             rows[k] = {"avg_us": avg_ms * 1e3, "samples": prof["ker_samples"][k], "bytes_per_cell": b,
                        "gbs": b * n / (avg_ms * 1e-3) / 1e9}
-        if prof["ker_samples"]["precond"]:
-            # the whole cycle (all levels, the one-block coarse cycle, and with
-            # the learned smoother its two network applications) for context
-            avg_ms = prof["ker_ms"]["precond"] / prof["ker_samples"]["precond"]
-            frac = mg_level_fraction(N)
-            jac = sum(MG_BYTES.values())
-            # learned smoother on the finest level: network r -> x (8), residual,
-            # restriction, residual of x + P e_c, network res -> x (8), x += t (12)
-            fine = jac if pc == pg.PC_MG else (8 + MG_BYTES["mg_resid"] + MG_BYTES["mg_restrict"] +
-                                               MG_BYTES_PROLONG_RESID + 8 + 12)
-            bpc = fine + jac * (frac - 1.0)
-            vcycle = {"avg_us": round(avg_ms * 1e3, 2), "samples": prof["ker_samples"]["precond"],
-                      "bytes_per_fine_cell": round(bpc, 3), "gbs": round(bpc * n / (avg_ms * 1e-3) / 1e9, 1),
-                      "note": "one V-cycle, every level; bytes of the plane-streamed levels"}
+        vcycle = vcycle_record(prof, pc == pg.PC_MG_CNN, N, hbm)
     # the particle kernels (one launch each per step): algorithmic bytes of
     # the FP64 particle state, and the bytes the record layout moves
     for k, (bp, bn) in PARTICLE_BYTES.items():
@@ -773,7 +794,7 @@ def run_ours(args):
     return out
 
 
-def train_networks(pg, torch):
+def train_networks(pg, torch, weights_dir=None):
     """Train the network twice on the GPU before timing, each by one
     pic_cnn_train call (the library's own solves for the data, its kernels
     for forward, loss, backward and Adam): as flexible CG's preconditioner
@@ -785,10 +806,24 @@ def train_networks(pg, torch):
     records."""
     t0 = time.perf_counter()
     c = pg.Context().init(64, 0, 0)
+    files = None if not weights_dir else (os.path.join(weights_dir, "preconditioner.piccnn"),
+                                          os.path.join(weights_dir, "smoother.piccnn"))
+    if files and all(os.path.exists(f) for f in files):
+        c.cnn_load(files[0])
+        w_p = c.cnn_get_weights()
+        c.cnn_load(files[1])
+        w_s = c.cnn_get_weights()
+        c.close()
+        return {pg.PC_CNN: w_p, pg.PC_MG_CNN: w_s}, {"loaded_from": weights_dir}
     info_p = c.cnn_train(pg.TRAIN_PRECONDITIONER, restarts=4)
     w_p = c.cnn_get_weights()
+    if files:
+        os.makedirs(weights_dir, exist_ok=True)
+        c.cnn_save(files[0])
     info_s = c.cnn_train(pg.TRAIN_SMOOTHER)
     w_s = c.cnn_get_weights()
+    if files:
+        c.cnn_save(files[1])
     c.close()
     torch.cuda.synchronize()
     rec = {k: {"loss_first": round(v["loss_first"], 4), "loss_last": round(v["loss_last"], 4),
