@@ -55,6 +55,9 @@ DEFAULT_SOLVER = "cnn"
 # also timed on the same particles: the multigrid-preconditioned step, with
 # Jacobi and with the learned smoother
 DEFAULT_ALT_SOLVERS = ("mg", "mg_cnn")
+# steps of the end-to-end measurement (each copies the whole particle state in
+# and out: 103 GB of host traffic a step at 512^3)
+E2E_STEPS = 5
 # cold solves of the largest solver-only grid, after the particles are freed
 DEFAULT_COMPARE_GRIDS = (1024,)
 
@@ -357,7 +360,7 @@ def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrie
         for a in done:
             cudart.cudaHostUnregister(state.data_ptr() + a)
         del state
-    return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": state_bytes,
+    return {"value": whole_job_rate(world, steps, s), "unit": unit, "steps": steps, "h2d_bytes_per_step": state_bytes,
             "d2h_bytes_per_step": state_bytes + 24,
             "step_s": {"min": round(float(per_step.min()), 3), "median": round(float(np.median(per_step)), 3),
                        "max": round(float(per_step.max()), 3)},
@@ -551,7 +554,8 @@ def run_ours(args):
     # runs the step, reads the field energy and copies the state back out
     # (pic_get_particles). Solver-only: rho in from host memory, phi back.
     np_ = 0 if solve_only else ppc * n
-    e2e = end_to_end(c, step, np_, n, rho, phi, args.steps, solve_only, world, dist, barrier, torch, unit,
+    e2e = end_to_end(c, step, np_, n, rho, phi, min(args.steps, E2E_STEPS), solve_only, world, dist, barrier, torch,
+                     unit,
                      step.solve_into)
 
     # the other solvers' PIC steps on the same particles (extra keys)

@@ -480,16 +480,16 @@ int launch_push(pic_ctx* c, const double* phi, const double* Efield, double kick
     float2* phid = c->E + 3 * c->n;
     launch(c, k_phi_df, sb, 256, 0, phi, phid, c->n);
     const unsigned per_plane = (unsigned)c->N * (unsigned)c->N;
-    launch(c, k_gradient, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)phid, c->E, c->E + c->n,
-           c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
+    launch(c, k_gradient, dim3((per_plane + 255) / 256, c->N), 256, 0, (const float2*)phid,
+           reinterpret_cast<float4*>(c->E), c->E + 2 * c->n, c->N, df_const(0.5 * c->grid.inv_h));
   } else {
-    launch(c, k_phi_df, sb, 256, 0, Efield, c->E, 3 * c->n);
+    launch(c, k_field_df, sb, 256, 0, Efield, reinterpret_cast<float4*>(c->E), c->E + 2 * c->n, c->n);
   }
   if (drift) CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
-  launch(c, k_gather_push<false>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)c->E,
-         (const float2*)(c->E + c->n), (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
+  launch(c, k_gather_push<false>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float4*)c->E,
+         (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
          df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts, (const double*)nullptr, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
@@ -819,8 +819,8 @@ int pic_pif_push(pic_ctx* c, double tol, double dt) {
   CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((c->np + 255) / 256);
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
-  launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float2*)nullptr,
-         (const float2*)nullptr, (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
+  launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float4*)nullptr,
+         (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
          c->keys, c->ranks, c->counts, (const double*)c->pif_E, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());

@@ -87,6 +87,75 @@ struct DfAcc {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Two double-float values at once on Blackwell's packed FP32 instructions
+// (FADD2 / FMUL2 / FFMA2 on float2): lane i of every operation rounds exactly
+// as the scalar _rn operation on lane i would, so a pair computes bit for bit
+// what two scalar double-float computations give, in half the instructions.
+// ---------------------------------------------------------------------------
+struct df2 {
+  float2 hi, lo;  // lane x: first value, lane y: second
+};
+
+__device__ __forceinline__ float2 bcast(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ df2 df2_pair(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ df2 df2_bcast(df a) { return {bcast(a.hi), bcast(a.lo)}; }
+__device__ __forceinline__ df df2_x(const df2& a) { return {a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df df2_y(const df2& a) { return {a.hi.y, a.lo.y}; }
+
+__device__ __forceinline__ df2 two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ df2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ df2 two_prod2(float2 a, float2 b) {
+  const float2 p = mul2(a, b);
+  return {p, fma2(a, b, neg2(p))};
+}
+
+// a + b lane by lane (AccurateDWPlusDW)
+__device__ __forceinline__ df2 df2_add(const df2& a, const df2& b) {
+  const df2 s = two_sum2(a.hi, b.hi);
+  const df2 t = two_sum2(a.lo, b.lo);
+  const df2 v = fast_two_sum2(s.hi, add2(s.lo, t.hi));
+  return fast_two_sum2(v.hi, add2(t.lo, v.lo));
+}
+
+// a b lane by lane (DWTimesDW)
+__device__ __forceinline__ df2 df2_mul(const df2& a, const df2& b) {
+  const df2 p = two_prod2(a.hi, b.hi);
+  float2 t = mul2(a.hi, b.lo);
+  t = fma2(a.lo, b.hi, t);
+  return fast_two_sum2(p.hi, add2(p.lo, t));
+}
+
+// DfAcc on a pair of running sums.
+struct DfAcc2 {
+  float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+  // += w * a (w, a double-float pairs)
+  __device__ __forceinline__ void add_mul(const df2& w, const df2& a) {
+    const df2 p = two_prod2(w.hi, a.hi);
+    float2 t = mul2(w.hi, a.lo);
+    t = fma2(w.lo, a.hi, t);
+    const df2 s = two_sum2(hi, p.hi);
+    hi = s.hi;
+    lo = add2(lo, add2(s.lo, add2(p.lo, t)));
+  }
+  __device__ __forceinline__ df2 value() const { return two_sum2(hi, lo); }
+};
+
 // Double-float of an FP64 value (FP64 operations: for inputs and outputs only).
 __device__ __forceinline__ df df_of_double(double x) {
   const float hi = __double2float_rn(x);

@@ -390,15 +390,27 @@ __global__ void __launch_bounds__(256) k_deposit_nodes(const float2* __restrict_
 // node (FP64 operations), the differences run in double-float.
 // ---------------------------------------------------------------------------
 // (also converts a given 3 n node field)
+// A given FP64 node field (E_x, E_y, E_z blocks of n) into the push's layout.
+__global__ void __launch_bounds__(256) k_field_df(const double* __restrict__ E, float4* __restrict__ Exy,
+                                                  float2* __restrict__ Ez, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) {
+    const df ex = df_of_double(__ldg(E + c)), ey = df_of_double(__ldg(E + n + c));
+    Exy[c] = make_float4(ex.hi, ey.hi, ex.lo, ey.lo);
+    Ez[c] = df_pack(df_of_double(__ldg(E + 2 * n + c)));
+  }
+}
+
 __global__ void __launch_bounds__(256) k_phi_df(const double* __restrict__ phi, float2* __restrict__ out, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride)
     out[c] = df_pack(df_of_double(__ldg(phi + c)));
 }
 
-__global__ void __launch_bounds__(256) k_gradient(const float2* __restrict__ phi, float2* __restrict__ Ex,
-                                                  float2* __restrict__ Ey, float2* __restrict__ Ez, int N,
-                                                  float2 half_inv_h) {
+// E = -grad phi by central differences (Eq. 2) in double-float, into the
+// push's node field: E_x, E_y interleaved {x.hi, y.hi, x.lo, y.lo}, E_z alone.
+__global__ void __launch_bounds__(256) k_gradient(const float2* __restrict__ phi, float4* __restrict__ Exy,
+                                                  float2* __restrict__ Ez, int N, float2 half_inv_h) {
   const size_t Ns = N;
   const int k = blockIdx.y;
   const unsigned per_plane = (unsigned)N * (unsigned)N;
@@ -414,8 +426,8 @@ __global__ void __launch_bounds__(256) k_gradient(const float2* __restrict__ phi
     const df zm = df_from(__ldg(phi + (size_t)km * per_plane + (size_t)j * Ns + i));
     const df zp = df_from(__ldg(phi + (size_t)kp * per_plane + (size_t)j * Ns + i));
     const size_t c = row + i;
-    Ex[c] = df_pack(df_mul(df_sub(xm, xp), s));
-    Ey[c] = df_pack(df_mul(df_sub(ym, yp), s));
+    const df ex = df_mul(df_sub(xm, xp), s), ey = df_mul(df_sub(ym, yp), s);
+    Exy[c] = make_float4(ex.hi, ey.hi, ex.lo, ey.lo);
     Ez[c] = df_pack(df_mul(df_sub(zm, zp), s));
   }
 }
@@ -474,11 +486,13 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 // new cell key and in-cell rank (counts must be zero on entry) for the next
 // sort. drift == 0 gives the closing half-kick only (no key update).
 //   kick_qm = -kick (q/m = -1), dth = dt / h, both double-float (hi, lo).
-// Each thread reads and writes its own 64-byte record (four 16-byte words).
-// The ranks come from one atomic per run of equal keys in a warp (the
-// particles are in cell order, so a warp covers a few cells). Four blocks an
-// SM (64 registers, no spills): measured 12 % faster than the unconstrained
-// 72-register build, which fits three.
+// The node field is E_x and E_y interleaved as one float4 a node
+// {x.hi, y.hi, x.lo, y.lo} and E_z as a float2: the x and y components run
+// as pairs on the packed FP32 instructions (df2), z alone, with the same
+// per-lane rounding as three scalar computations. Each thread reads and
+// writes its own 64-byte record (four 16-byte words). The ranks come from one
+// atomic per run of equal keys in a warp (the particles are in cell order, so
+// a warp covers a few cells). Four blocks an SM (64 registers, no spills).
 // ---------------------------------------------------------------------------
 constexpr int kPushThreads = 256;
 
@@ -486,8 +500,7 @@ constexpr int kPushThreads = 256;
 // the current particle order; the particle-in-Fourier scheme) instead of
 // gathered from the node field.
 template <bool GIVEN>
-__global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64_t np, const float2* __restrict__ Ex,
-                                                              const float2* __restrict__ Ey,
+__global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64_t np, const float4* __restrict__ Exy,
                                                               const float2* __restrict__ Ez, Grid g, float2 kick_qm,
                                                               float2 dth, int drift, uint32_t* keys, uint32_t* ranks,
                                                               uint32_t* counts, const double* __restrict__ Ep,
@@ -502,57 +515,59 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
     const float4 r2 = *reinterpret_cast<const float4*>(rec + 2);
     uint64_t fx = ((uint64_t)r0.y << 32) | r0.x, fy = ((uint64_t)r0.w << 32) | r0.z;
     uint64_t fz = ((uint64_t)r1.y << 32) | r1.x;
-    df vx = {__uint_as_float(r1.z), __uint_as_float(r1.w)};
-    df vy = {r2.x, r2.y}, vz = {r2.z, r2.w};
+    df2 vxy = {make_float2(__uint_as_float(r1.z), r2.x), make_float2(__uint_as_float(r1.w), r2.y)};
+    df vz = {r2.z, r2.w};
     int ix = (int)(r3.z & 0xFFFFu), iy = (int)(r3.z >> 16), iz = (int)(r3.w & 0xFFFFu);
     const int N = g.N;
-    df ep[3];
+    df2 exy;
+    df ez;
     if (GIVEN) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) ep[d] = df_of_double(__ldg(Ep + (size_t)d * np + p));
+      exy = df2_pair(df_of_double(__ldg(Ep + p)), df_of_double(__ldg(Ep + np + p)));
+      ez = df_of_double(__ldg(Ep + 2 * np + p));
     } else {
-      // CIC weights prod_d (f_d or 1 - f_d) of the 8 corners
+      // CIC weights prod_d (f_d or 1 - f_d) of the 8 corners, in pairs
       const df ax = frac_df(fx), ay = frac_df(fy), az = frac_df(fz);
       const df bx = one_minus_frac_df(fx), by = one_minus_frac_df(fy), bz = one_minus_frac_df(fz);
-      const df w00 = df_mul(by, bz), w10 = df_mul(ay, bz), w01 = df_mul(by, az), w11 = df_mul(ay, az);
-      const df w[8] = {df_mul(bx, w00), df_mul(ax, w00), df_mul(bx, w10), df_mul(ax, w10),
-                       df_mul(bx, w01), df_mul(ax, w01), df_mul(bx, w11), df_mul(ax, w11)};
+      const df2 yb = df2_pair(by, ay), xb = df2_pair(bx, ax);
+      const df2 wz0 = df2_mul(yb, df2_bcast(bz)), wz1 = df2_mul(yb, df2_bcast(az));  // (w00, w10), (w01, w11)
+      const df2 w2[4] = {df2_mul(xb, df2_bcast(df2_x(wz0))), df2_mul(xb, df2_bcast(df2_y(wz0))),
+                         df2_mul(xb, df2_bcast(df2_x(wz1))), df2_mul(xb, df2_bcast(df2_y(wz1)))};
       const int jx = ix + 1 == N ? 0 : ix + 1, jy = iy + 1 == N ? 0 : iy + 1, jz = iz + 1 == N ? 0 : iz + 1;
       const size_t Ns = N;
       const size_t z0 = (size_t)iz * Ns * Ns, z1 = (size_t)jz * Ns * Ns, y0 = (size_t)iy * Ns, y1 = (size_t)jy * Ns;
       const size_t idx[8] = {z0 + y0 + ix, z0 + y0 + jx, z0 + y1 + ix, z0 + y1 + jx,
                              z1 + y0 + ix, z1 + y0 + jx, z1 + y1 + ix, z1 + y1 + jx};
-      DfAcc ex, ey, ez;
+      DfAcc2 axy;
+      DfAcc az_;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        ex.add_mul(w[c], df_from(__ldg(Ex + idx[c])));
-        ey.add_mul(w[c], df_from(__ldg(Ey + idx[c])));
-        ez.add_mul(w[c], df_from(__ldg(Ez + idx[c])));
+        const df w = (c & 1) ? df2_y(w2[c >> 1]) : df2_x(w2[c >> 1]);
+        const float4 e = __ldg(Exy + idx[c]);
+        axy.add_mul(df2_bcast(w), {make_float2(e.x, e.y), make_float2(e.z, e.w)});
+        az_.add_mul(w, df_from(__ldg(Ez + idx[c])));
       }
-      ep[0] = ex.value();
-      ep[1] = ey.value();
-      ep[2] = ez.value();
+      exy = axy.value();
+      ez = az_.value();
     }
     const df kq = dfc(kick_qm);
-    const df ux = df_add(vx, df_mul(kq, ep[0]));
-    const df uy = df_add(vy, df_mul(kq, ep[1]));
-    const df uz = df_add(vz, df_mul(kq, ep[2]));
+    const df2 uxy = df2_add(vxy, df2_mul(df2_bcast(kq), exy));
+    const df uz = df_add(vz, df_mul(kq, ez));
     // a non-finite field at the particle: record the fault and leave the
     // particle as it is (its key and rank are still written below)
-    const bool fin = isfinite(ux.hi) && isfinite(uy.hi) && isfinite(uz.hi) && isfinite(ux.lo) &&
-                     isfinite(uy.lo) && isfinite(uz.lo);
+    const bool fin = isfinite(uxy.hi.x) && isfinite(uxy.hi.y) && isfinite(uz.hi) && isfinite(uxy.lo.x) &&
+                     isfinite(uxy.lo.y) && isfinite(uz.lo);
     if (fin) {
-      vx = ux;
-      vy = uy;
+      vxy = uxy;
       vz = uz;
     } else {
       atomicOr(err, DEV_ERR_NONFINITE);
     }
-    *reinterpret_cast<float4*>(rec + 2) = make_float4(vy.hi, vy.lo, vz.hi, vz.lo);
+    *reinterpret_cast<float4*>(rec + 2) = make_float4(vxy.hi.y, vxy.lo.y, vz.hi, vz.lo);
     if (drift && fin) {
       const df s = dfc(dth);
-      move_coord(fx, ix, df_mul(vx, s), N);
-      move_coord(fy, iy, df_mul(vy, s), N);
+      const df2 dxy = df2_mul(vxy, df2_bcast(s));
+      move_coord(fx, ix, df2_x(dxy), N);
+      move_coord(fy, iy, df2_y(dxy), N);
       move_coord(fz, iz, df_mul(vz, s), N);
       rec[0] = make_uint4((uint32_t)fx, (uint32_t)(fx >> 32), (uint32_t)fy, (uint32_t)(fy >> 32));
       kk = cell_key(ix, iy, iz, N);
@@ -560,7 +575,7 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
     } else if (drift) {
       kk = cell_key(ix, iy, iz, N);
     }
-    rec[1] = make_uint4((uint32_t)fz, (uint32_t)(fz >> 32), __float_as_uint(vx.hi), __float_as_uint(vx.lo));
+    rec[1] = make_uint4((uint32_t)fz, (uint32_t)(fz >> 32), __float_as_uint(vxy.hi.x), __float_as_uint(vxy.lo.x));
   }
   if (!drift) return;  // uniform over the launch: every lane reaches the warp collectives below
   // runs of equal keys: the first lane of a run takes the run's ranks with one atomic
