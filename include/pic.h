@@ -54,10 +54,13 @@ typedef struct pic_ctx pic_ctx;
 
 /* Problem description (Sec. 2.1: k = 0.5, alpha = 0.05; Sec. 4.1: 8 ppc). */
 typedef struct {
-  int N;        /* nodes per dimension; 8 <= N <= 1024, N % 8 == 0 */
-  int ppc;      /* particles per cell, Np = ppc * N^3 < 2^32; 0 = solver-only context */
-  double alpha; /* density perturbation amplitude */
-  double k;     /* perturbation wavenumber; L = 2 pi / k */
+  int N;         /* nodes per dimension; 8 <= N <= 1024, N % 8 == 0 */
+  int ppc;       /* particles per cell, Np = ppc * N^3 < 2^32; 0 = solver-only context */
+  double alpha;  /* density perturbation amplitude, |alpha| < 1 (< 1/3 with init_mode 1) */
+  double k;      /* perturbation wavenumber; L = 2 pi / k */
+  double vth;    /* thermal velocity of the Maxwellian (0 selects 1, the paper's units) */
+  int init_mode; /* 0: the paper's density prod_d (1 + alpha cos k x_d);
+                    1: the sum form 1 + alpha sum_d cos k x_d */
 } pic_params;
 
 /* Solver precision. FP64 = Jacobi-PCG entirely in FP64 (the reference solve).
@@ -109,10 +112,13 @@ const char *pic_cuda_error(void);
 
 /* S0 (Sec. 2.1): allocate and sample the Landau initial condition on the
  * device. Particle p draws from Philox4x32-10 (Salmon et al., SC'11) with
- * counters (p_lo, p_hi, j, 0), j = 0..3, and key (seed_lo, seed_hi);
- * positions by per-dimension inverse CDF of (1 + alpha cos k x)/L, velocities
- * by Box-Muller (v_th = 1). Velocities are synchronous with positions. With
- * ppc == 0 only the grid geometry is set (solver-only context). */
+ * counters (p_lo, p_hi, j, 0) and key (seed_lo, seed_hi). init_mode 0:
+ * positions by per-dimension inverse CDF of (1 + alpha cos k x)/L (calls
+ * j = 0, 1); init_mode 1: positions from the sum density by rejection from
+ * the uniform one (trial t uses calls 4 + 2t and 5 + 2t, at most 32 trials).
+ * Velocities: vth times Box-Muller normals (calls 2, 3), synchronous with the
+ * positions. With ppc == 0 only the grid geometry is set (solver-only
+ * context). PIC_EINVAL for parameters out of range. */
 int pic_init(pic_ctx *c, const pic_params *p, uint64_t seed);
 
 /* S1 + S2 (Fig. 1 "scatter", Eq. 2): sort particles by cell, then write

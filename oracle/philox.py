@@ -16,7 +16,8 @@ on its own): particle p uses counters (p_lo, p_hi, j, 0) for j = 0..3 and key
 uniforms in (0, 1) with 53-bit resolution:
     u = ((a >> 5) * 2**26 + (b >> 6) + 0.5) * 2**-53,  u' = same for (c, d).
 Call 0 -> (u_x, u_y); call 1 -> (u_z, unused); call 2 -> Box-Muller pair
-(vx, vy); call 3 -> Box-Muller pair, first value is vz.
+(vx, vy); call 3 -> Box-Muller pair, first value is vz. The sum-form initial
+density takes its rejection trials from calls 4, 5, 6, ... (two a trial).
 """
 import numpy as np
 
@@ -56,16 +57,23 @@ def particle_uniforms(p_index, seed):
 
     Returns an array of shape (4, 2, n): [call j][first/second uniform][particle].
     """
+    return particle_uniforms_calls(p_index, seed, range(4))
+
+
+def particle_uniforms_calls(p_index, seed, calls):
+    """Uniforms of Philox calls ``calls`` (counter c2 = call) of particles
+    ``p_index``: shape (len(calls), 2, n), as particle_uniforms."""
     p = np.asarray(p_index, dtype=np.uint64)
     lo = p & MASK32
     hi = p >> np.uint64(32)
     k0 = np.uint64(seed) & MASK32
     k1 = (np.uint64(seed) >> np.uint64(32)) & MASK32
-    out = np.empty((4, 2, p.size), dtype=np.float64)
-    for j in range(4):
+    calls = list(calls)
+    out = np.empty((len(calls), 2, p.size), dtype=np.float64)
+    for i, j in enumerate(calls):
         a, b, c, d = philox4x32_10(lo, hi, np.full_like(lo, j), np.zeros_like(lo), k0, k1)
-        out[j, 0] = uniform_pair(a, b)
-        out[j, 1] = uniform_pair(c, d)
+        out[i, 0] = uniform_pair(a, b)
+        out[i, 1] = uniform_pair(c, d)
     return out
 
 

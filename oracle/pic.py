@@ -11,7 +11,8 @@ centred), linear index i + N*(j + N*k) (x fastest). Each macro-particle
 carries charge q_p = -L^3/Np.
 
 Readings of the paper used here
-  R1 initial density is the paper's product form (Sec. 2.1).
+  R1 initial density is the paper's product form (Sec. 2.1); the sum form
+     1 + alpha sum_d cos(k x_d) (mode 1) is sampled by rejection.
   R2 CIC cell of a particle is floor(x/h); weights are the trilinear
      (cloud-in-cell) weights to the 8 nodes of that cell.
   R3 the Poisson operator is the 2nd-order central FD Laplacian (Sec. 3.2),
@@ -49,26 +50,63 @@ def inverse_cdf(u, L, alpha, k, newton_steps=12):
     return x
 
 
-def init_particles(N, ppc, seed, alpha=0.05, k=0.5):
+# trials of the rejection sampling of the sum-form density (init_mode 1)
+SUM_FORM_TRIALS = 32
+
+
+def sum_form_positions(p, seed, L, alpha, k, trials=SUM_FORM_TRIALS):
+    """Positions drawn from the sum-form density (1 + alpha sum_d cos(k x_d))/L^3
+    by rejection from the uniform density on [0, L)^3 (reading 1's sum form).
+
+    Trial t of particle p uses Philox calls 4 + 2t -> (u_x, u_y) and
+    5 + 2t -> (u_z, u_accept) of the particle's stream; the proposal
+    x = u L is accepted when u_accept (1 + 3 alpha) <= 1 + alpha sum cos(k x_d)
+    (the density's maximum over the box is 1 + 3 alpha). The first accepted
+    trial is kept; if none of the trials is accepted (probability below
+    (3 alpha / (1 + 3 alpha))^trials) the last proposal is kept.
+    """
+    p = np.asarray(p, dtype=np.uint64)
+    pos = np.empty((3, p.size))
+    done = np.zeros(p.size, dtype=bool)
+    for t in range(trials):
+        U = philox.particle_uniforms_calls(p, seed, (4 + 2 * t, 5 + 2 * t))
+        prop = np.stack([U[0, 0], U[0, 1], U[1, 0]]) * L
+        dens = 1.0 + alpha * np.cos(k * prop).sum(axis=0)
+        acc = U[1, 1] * (1.0 + 3.0 * alpha) <= dens
+        take = ~done & (acc | (t == trials - 1))
+        pos[:, take] = prop[:, take]
+        done |= take
+        if done.all():
+            break
+    return pos
+
+
+def init_particles(N, ppc, seed, alpha=0.05, k=0.5, vth=1.0, mode=0):
     """Particles of the Landau initial condition (Sec. 2.1).
 
-    f(x, v, 0) = (2 pi)^(-3/2) exp(-|v|^2/2) prod_d (1 + alpha cos(k x_d)) on
-    [0, L]^3, L = 2 pi / k. Positions: per-dimension inverse CDF of the
-    separable density; velocities: Box-Muller normals (v_th = 1). Particle p
-    draws from the Philox stream described in ``oracle/philox.py``.
-    Returns (pos[3, Np], vel[3, Np]) as FP64 arrays.
+    mode 0 (the paper's product form): f(x, v, 0) = (2 pi)^(-3/2) exp(-|v|^2/2)
+    prod_d (1 + alpha cos(k x_d)) on [0, L]^3, L = 2 pi / k; positions by the
+    per-dimension inverse CDF of the separable density. mode 1 (the sum form
+    1 + alpha sum_d cos(k x_d)): positions by rejection (sum_form_positions).
+    Velocities: Box-Muller normals times v_th. Particle p draws from the
+    Philox stream described in ``oracle/philox.py``. Returns
+    (pos[3, Np], vel[3, Np]) as FP64 arrays.
     """
     L = 2.0 * np.pi / k
     Np = ppc * N ** 3
-    U = philox.particle_uniforms(np.arange(Np, dtype=np.uint64), seed)
+    p = np.arange(Np, dtype=np.uint64)
+    U = philox.particle_uniforms(p, seed)
     pos = np.empty((3, Np))
-    pos[0] = inverse_cdf(U[0, 0], L, alpha, k)
-    pos[1] = inverse_cdf(U[0, 1], L, alpha, k)
-    pos[2] = inverse_cdf(U[1, 0], L, alpha, k)
+    if mode == 1:
+        pos[:] = sum_form_positions(p, seed, L, alpha, k)
+    else:
+        pos[0] = inverse_cdf(U[0, 0], L, alpha, k)
+        pos[1] = inverse_cdf(U[0, 1], L, alpha, k)
+        pos[2] = inverse_cdf(U[1, 0], L, alpha, k)
     vel = np.empty((3, Np))
     vel[0], vel[1] = philox.box_muller(U[2, 0], U[2, 1])
     vel[2], _ = philox.box_muller(U[3, 0], U[3, 1])
-    return pos, vel
+    return pos, vth * vel
 
 
 # ----------------------------------------------------------------------------

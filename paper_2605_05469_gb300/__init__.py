@@ -61,7 +61,8 @@ class PicError(RuntimeError):
 
 
 class pic_params(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_int), ("ppc", ctypes.c_int), ("alpha", ctypes.c_double), ("k", ctypes.c_double)]
+    _fields_ = [("N", ctypes.c_int), ("ppc", ctypes.c_int), ("alpha", ctypes.c_double), ("k", ctypes.c_double),
+                ("vth", ctypes.c_double), ("init_mode", ctypes.c_int)]
 
 
 class pic_solve_opts(ctypes.Structure):
@@ -238,8 +239,8 @@ def pic_destroy(h):
     lib().pic_destroy(h)
 
 
-def pic_init(h, N, ppc, seed, alpha=0.05, k=0.5):
-    p = pic_params(N, ppc, alpha, k)
+def pic_init(h, N, ppc, seed, alpha=0.05, k=0.5, vth=1.0, init_mode=0):
+    p = pic_params(N, ppc, alpha, k, vth, init_mode)
     _check(lib().pic_init(h, ctypes.byref(p), ctypes.c_uint64(seed)), "pic_init")
 
 
@@ -313,8 +314,8 @@ class Context:
         self.N = 0
         self.n = 0
 
-    def init(self, N, ppc, seed, alpha=0.05, k=0.5):
-        pic_init(self.h, N, ppc, seed, alpha, k)
+    def init(self, N, ppc, seed, alpha=0.05, k=0.5, vth=1.0, init_mode=0):
+        pic_init(self.h, N, ppc, seed, alpha, k, vth, init_mode)
         self.N, self.n = N, N ** 3
         self.L = 2.0 * np.pi / k
         self.h_grid = self.L / N

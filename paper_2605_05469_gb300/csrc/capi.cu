@@ -590,6 +590,10 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
   if (!c || !p) return PIC_EINVAL;
   if (p->N < 8 || p->N > 1024 || p->N % 8 != 0 || p->ppc < 0) return PIC_EINVAL;
   if (!(p->k > 0.0) || !isfinite(p->k) || !isfinite(p->alpha) || fabs(p->alpha) >= 1.0) return PIC_EINVAL;
+  if (p->init_mode != 0 && p->init_mode != 1) return PIC_EINVAL;
+  if (p->init_mode == 1 && !(3.0 * fabs(p->alpha) < 1.0)) return PIC_EINVAL;  // the sum density stays positive
+  const double vth = p->vth == 0.0 ? 1.0 : p->vth;
+  if (!(vth > 0.0) || !isfinite(vth)) return PIC_EINVAL;
   const uint64_t n = (uint64_t)p->N * p->N * p->N;
   const uint64_t np = (uint64_t)p->ppc * n;
   if (np >= (1ull << 32)) return PIC_EINVAL;
@@ -622,8 +626,8 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
   c->np = np;
   CK(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((np + 255) / 256);
-  launch(c, k_init_particles, blocks, 256, 0, pptrs(c, 0), np, seed, p->alpha, p->k, c->grid, c->keys,
-                                                  c->ranks, c->counts);
+  launch(c, k_init_particles, blocks, 256, 0, pptrs(c, 0), np, seed, p->alpha, p->k, vth, p->init_mode, c->grid,
+         c->keys, c->ranks, c->counts);
   CK(cudaGetLastError());
   c->keys_valid = true;
   return PIC_OK;

@@ -144,8 +144,19 @@ __device__ __forceinline__ df dfc(float2 v) { return {v.x, v.y}; }
 
 // S0: sample particle p of the Landau initial condition (FP64), store it as a
 // record, and count its cell.
-__global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alpha, double k, Grid g,
-                                 uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
+// Trials of the rejection sampling of the sum-form density (mode 1).
+constexpr int kSumFormTrials = 32;
+
+// mode 0: the paper's product density prod_d (1 + alpha cos k x_d), exact
+// per-dimension inverse CDF (Philox calls 0 and 1). mode 1: the sum density
+// 1 + alpha sum_d cos k x_d by rejection from the uniform density: trial t
+// takes calls 4 + 2t (u_x, u_y) and 5 + 2t (u_z, u_accept) and accepts x = u L
+// when u_accept (1 + 3 alpha) <= 1 + alpha sum_d cos k x_d; the first accepted
+// trial is kept, the last proposal if none is (probability below
+// (3 alpha / (1 + 3 alpha))^32). Velocities: vth times Box-Muller normals
+// (calls 2 and 3).
+__global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alpha, double k, double vth, int mode,
+                                 Grid g, uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -156,12 +167,26 @@ __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alp
     u[2 * j] = u53(r.x, r.y);
     u[2 * j + 1] = u53(r.z, r.w);
   }
-  const double x = inverse_cdf(u[0], g.L, alpha, k);
-  const double y = inverse_cdf(u[1], g.L, alpha, k);
-  const double z = inverse_cdf(u[2], g.L, alpha, k);
+  double x, y, z;
+  if (mode == 1) {
+    const double top = 1.0 + 3.0 * alpha;
+    for (int t = 0; t < kSumFormTrials; ++t) {
+      const uint4 a = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)(4 + 2 * t), 0u), key);
+      const uint4 b = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), (uint32_t)(5 + 2 * t), 0u), key);
+      x = u53(a.x, a.y) * g.L;
+      y = u53(a.z, a.w) * g.L;
+      z = u53(b.x, b.y) * g.L;
+      const double dens = 1.0 + alpha * (cos(k * x) + cos(k * y) + cos(k * z));
+      if (u53(b.z, b.w) * top <= dens) break;
+    }
+  } else {
+    x = inverse_cdf(u[0], g.L, alpha, k);
+    y = inverse_cdf(u[1], g.L, alpha, k);
+    z = inverse_cdf(u[2], g.L, alpha, k);
+  }
   const double two_pi = 6.283185307179586476925286766559;
   // Box-Muller (Box & Muller 1958)
-  const double r1 = sqrt(-2.0 * log(u[4])), r2 = sqrt(-2.0 * log(u[6]));
+  const double r1 = vth * sqrt(-2.0 * log(u[4])), r2 = vth * sqrt(-2.0 * log(u[6]));
   double s1, c1, s2, c2;
   sincos(two_pi * u[5], &s1, &c1);
   sincos(two_pi * u[7], &s2, &c2);

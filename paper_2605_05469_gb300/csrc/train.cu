@@ -141,7 +141,7 @@ struct Set {
 int make_context(cudaStream_t st, int N, int ppc, uint64_t seed, double alpha, double k, CtxGuard* g) {
   int e;
   if ((e = pic_create(&g->c, st))) return e;
-  pic_params p{N, ppc, alpha, k};
+  pic_params p{N, ppc, alpha, k, 1.0, 0};
   return pic_init(g->c, &p, seed);
 }
 

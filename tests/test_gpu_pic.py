@@ -157,14 +157,34 @@ def test_solve_rejects_bad_arguments(pg):
 
 
 # ------------------------------------------------------------------ particles
-@pytest.mark.parametrize("N,ppc", [(8, 3), (16, 8)])
-def test_init_particles_match_oracle(pg, N, ppc):
-    c = pg.Context().init(N, ppc, 0x5EED)
+@pytest.mark.parametrize("N,ppc,mode,vth,alpha", [(8, 3, 0, 1.0, 0.05), (16, 8, 0, 1.0, 0.05), (16, 8, 1, 1.0, 0.05),
+                                                  (16, 4, 1, 1.7, 0.3), (8, 2, 0, 0.5, 0.3)])
+def test_init_particles_match_oracle(pg, N, ppc, mode, vth, alpha):
+    """Every particle against the oracle's: the paper's product density by
+    inverse CDF (mode 0) and the sum density by rejection (mode 1, the same
+    Philox trials; an accept decision is an FP64 comparison on both sides,
+    so a cos that differs in its last bit could flip one only within
+    ~1e-16 of the boundary), velocities scaled by v_th."""
+    c = pg.Context().init(N, ppc, 0x5EED, alpha=alpha, vth=vth, init_mode=mode)
     got, half = c.particles()
-    pos, vel = opic.init_particles(N, ppc, 0x5EED)
+    pos, vel = opic.init_particles(N, ppc, 0x5EED, alpha=alpha, vth=vth, mode=mode)
     assert not half
     assert np.max(np.abs(got[:3] - pos)) <= 1e-12
-    assert np.max(np.abs(got[3:] - vel)) <= 1e-12
+    assert np.max(np.abs(got[3:] - vel)) <= 1e-12 * vth
+
+
+def test_init_rejects_bad_parameters(pg):
+    c = pg.Context()
+    for kw in ({"init_mode": 2}, {"init_mode": 1, "alpha": 0.4}, {"vth": -1.0}, {"vth": float("nan")},
+               {"alpha": 1.0}):
+        with pytest.raises(pg.PicError) as e:
+            c.init(8, 1, 1, **kw)
+        assert e.value.code == pg.PIC_EINVAL, kw
+    c.init(8, 1, 1, vth=0.0)   # 0 selects v_th = 1
+    got, _ = c.particles()
+    ref_pos, ref_vel = opic.init_particles(8, 1, 1)
+    assert np.max(np.abs(got[3:] - ref_vel)) <= 1e-12
+    c.close()
 
 
 @pytest.mark.parametrize("N,ppc", [(8, 8), (16, 8), (32, 2)])

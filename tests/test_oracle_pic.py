@@ -365,3 +365,32 @@ def test_landau_damping_rate_32cubed():
     assert abs(gamma - g["gamma"]) < 0.1 * abs(g["gamma"])
     period = np.mean(np.diff(t[pk]))
     assert abs(period - np.pi / g["omega_r"]) < 0.1 * np.pi / g["omega_r"]
+
+
+# ------------------------------------------------------ the sum-form initial density
+def test_sum_form_density_moments():
+    """Reading 1's sum form f ~ 1 + alpha sum_d cos(k x_d) against the product
+    form prod_d (1 + alpha cos(k x_d)), by their moments over the box (alpha
+    0.3 to resolve them with 2^18 particles): both have E[cos k x_d] = alpha/2;
+    the sum form's E[cos k x cos k y] is 0, the product form's alpha^2/4;
+    every position lies in [0, L). Tolerances are five standard errors."""
+    N, ppc, alpha, k = 32, 8, 0.3, 0.5
+    L = 2.0 * np.pi / k
+    Np = ppc * N ** 3
+    se = 1.0 / np.sqrt(Np)
+    for mode, cc in ((1, 0.0), (0, alpha ** 2 / 4)):
+        pos, vel = pic.init_particles(N, ppc, 0x5EED, alpha=alpha, k=k, mode=mode)
+        assert np.all((pos >= 0.0) & (pos < L))
+        c = np.cos(k * pos)
+        for d in range(3):
+            assert abs(c[d].mean() - alpha / 2) < 5 * 0.75 * se, (mode, d, c[d].mean())
+        for a, b in ((0, 1), (1, 2), (0, 2)):
+            assert abs((c[a] * c[b]).mean() - cc) < 5 * 0.6 * se, (mode, a, b, (c[a] * c[b]).mean())
+
+
+def test_thermal_velocity_scales_the_maxwellian():
+    pos1, vel1 = pic.init_particles(8, 8, 7)
+    pos2, vel2 = pic.init_particles(8, 8, 7, vth=2.5)
+    assert np.array_equal(pos1, pos2)
+    assert np.array_equal(vel2, 2.5 * vel1)
+    assert abs(vel2.std() - 2.5) < 0.05
