@@ -87,6 +87,10 @@ typedef struct {
                             the learned preconditioner, 0.003 with the V-cycle */
   int check_every;       /* iterations between host reads of the convergence flag;
                             0 = default (1 with the V-cycle, 32 up to 64^3, else 8) */
+  int refine_max;        /* MIXED: at most this many FP64 residual recomputations (the
+                            refinement steps of the inner FP32 solve, each after the FP32
+                            residual fell by reliable_delta, the inner tolerance); when
+                            reached unconverged the solve stops with PIC_ENOCONV; 0 = no cap */
 } pic_solve_opts;
 
 typedef struct {

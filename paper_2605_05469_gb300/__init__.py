@@ -67,7 +67,7 @@ class pic_params(ctypes.Structure):
 
 class pic_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("reliable_delta", ctypes.c_double),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("refine_max", ctypes.c_int)]
 
 
 class pic_profile_stats(ctypes.Structure):
@@ -253,8 +253,8 @@ def poisson_solve(h, rho, phi, tol, maxit, n):
 
 
 def poisson_solve_ex(h, rho, phi, tol, maxit, n, precision=PREC_FP64, precond=PC_JACOBI, reliable_delta=0.0,
-                     check_every=0):
-    o = pic_solve_opts(precision, precond, reliable_delta, check_every)
+                     check_every=0, refine_max=0):
+    o = pic_solve_opts(precision, precond, reliable_delta, check_every, refine_max)
     info = pic_solve_info()
     code = lib().poisson_solve_ex(h, _dptr(rho, "float64", n, "rho"), _dptr(phi, "float64", n, "phi"), tol, maxit,
                                   ctypes.byref(o), ctypes.byref(info))
@@ -329,9 +329,9 @@ class Context:
         pic_deposit(self.h, rho, self.n)
 
     def solve(self, rho, phi, tol=1e-10, maxit=5000, precision=PREC_FP64, precond=PC_JACOBI, reliable_delta=0.0,
-              check_every=0, raise_on_error=True):
+              check_every=0, raise_on_error=True, refine_max=0):
         code, info = poisson_solve_ex(self.h, rho, phi, tol, maxit, self.n, precision, precond, reliable_delta,
-                                      check_every)
+                                      check_every, refine_max)
         info["code"] = code
         if raise_on_error and code not in (PIC_OK,):
             raise PicError(code, "poisson_solve_ex")

@@ -100,11 +100,12 @@ bool dev_ptr_ok(const void* p) { return p != nullptr && ((uintptr_t)p % 16) == 0
 // FP64 Jacobi-PCG (the reference solve)
 // --------------------------------------------------------------------------
 int solve_common_setup(pic_ctx* c, const double* rho, const double* phi, double tol, int maxit, double delta,
-                       double* xout) {
+                       double* xout, int refine_max = 0) {
   Scalars init;
   memset(&init, 0, sizeof(init));
   init.maxit = maxit;
   init.delta2 = delta * delta;
+  init.refine_max = refine_max;
   init.xsel = 0;
   c->sc_host[0] = init;
   CK(cudaMemcpyAsync(c->sc, &c->sc_host[0], sizeof(Scalars), cudaMemcpyHostToDevice, c->stream));
@@ -208,7 +209,7 @@ int solve_fp64(pic_ctx* c, const double* rho, double* phi, double tol, int maxit
 // --------------------------------------------------------------------------
 // Mixed precision: FP32 CG with FP64 reductions and reliable updates
 // --------------------------------------------------------------------------
-int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta,
+int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta, int refine_max,
                 pic_solve_info* info) {
   SolverWs& w = c->ws;
   int e;
@@ -235,7 +236,7 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
   if ((e = ensure_partials(c, (size_t)3 * mb + 3 * 4096))) return e;
 
   CK(cudaEventRecord(c->ev0, c->stream));
-  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
+  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0], refine_max))) return e;
   CK(cudaMemsetAsync(w.x32, 0, c->n * sizeof(float), c->stream));
   CK(cudaMemsetAsync(w.p32[0], 0, c->n * sizeof(float), c->stream));
   const int tp = round32(gp.threads), tr = round32(gr.threads);
@@ -305,7 +306,8 @@ int solve_mixed(pic_ctx* c, const double* rho, double* phi, double tol, int maxi
 // reliable update if due, network z = s N(r/s), dots (r,z), (z,q), (r,q) with
 // the descent guard and beta = -(z,q)/(p,q), Jacobi fallback if it fired.
 // --------------------------------------------------------------------------
-int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta, int pc,
+int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit, int m, double delta, int refine_max,
+              int pc,
               pic_solve_info* info) {
   SolverWs& w = c->ws;
   int e;
@@ -338,7 +340,7 @@ int solve_fcg(pic_ctx* c, const double* rho, double* phi, double tol, int maxit,
   if ((e = ensure_partials(c, (size_t)4 * mb + 3 * 4096))) return e;
 
   CK(cudaEventRecord(c->ev0, c->stream));
-  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0]))) return e;
+  if ((e = solve_common_setup(c, rho, phi, tol, maxit, delta, w.xm[0], refine_max))) return e;
   c->sc_host[1] = c->sc_host[0];
   c->sc_host[1].fcg = 1;
   CK(cudaMemcpyAsync(&c->sc->fcg, &c->sc_host[1].fcg, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -687,7 +689,7 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
   if (!c || !dev_ptr_ok(rho) || !dev_ptr_ok(phi)) return PIC_EINVAL;
   if (!c->has_grid) return PIC_ESTATE;
   if (!(tol >= 0.0) || maxit < 0) return PIC_EINVAL;
-  pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
+  pic_solve_opts opts = {PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0, 0};
   if (o) opts = *o;
   if (opts.precond < PIC_PC_JACOBI || opts.precond > PIC_PC_SSOR) return PIC_EINVAL;
   // status-check cadence: the multigrid solve converges in about ten
@@ -709,8 +711,10 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
     const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta
                                                    : (opts.precond == PIC_PC_JACOBI ? 0.1 : (mgpc ? 0.003 : 0.03));
     if (!(delta < 1.0)) return PIC_EINVAL;
-    if (opts.precond != PIC_PC_JACOBI) return solve_fcg(c, rho, phi, tol, maxit, m, delta, opts.precond, info);
-    return solve_mixed(c, rho, phi, tol, maxit, m, delta, info);
+    if (opts.refine_max < 0) return PIC_EINVAL;
+    if (opts.precond != PIC_PC_JACOBI)
+      return solve_fcg(c, rho, phi, tol, maxit, m, delta, opts.refine_max, opts.precond, info);
+    return solve_mixed(c, rho, phi, tol, maxit, m, delta, opts.refine_max, info);
   }
   return PIC_EINVAL;
 }

@@ -47,6 +47,7 @@ struct Scalars {
   int x32_reset;    // MIXED: the FP32 correction was folded; read it as zero
   int fcg;          // flexible CG: alpha = (r, z) / (p, A p)
   int fallback_now; // FCG: this iteration's z is replaced by the Jacobi direction
+  int refine_max;   // MIXED: FP64 residual recomputations allowed (0 = no cap)
   int redo;         // FCG: a reliable update replaced r after the fused update;
                     // z and the direction's dots are recomputed from it
 };

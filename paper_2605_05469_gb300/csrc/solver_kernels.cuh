@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(kStreamSmall) k_reliable(double* __restrict__ 
     if (!isfinite(rr64)) sc->done = 3;
     else if (rr64 <= sc->tol2) sc->done = 1;
     else if (mode == 1 && sc->iter >= sc->maxit) sc->done = 2;
+    else if (mode == 1 && sc->refine_max > 0 && sc->updates >= sc->refine_max) sc->done = 2;
   }
 }
 

@@ -160,7 +160,7 @@ int validate(pic_ctx* v, const double* rho, double* phi, size_t n, const float* 
   int e;
   if ((e = cnn_state_set(v, state, 0))) return e;
   CK(cudaMemsetAsync(phi, 0, n * sizeof(double), v->stream));
-  pic_solve_opts o{PIC_PREC_MIXED, pc, 0.0, 0};
+  pic_solve_opts o{PIC_PREC_MIXED, pc, 0.0, 0, 0};
   pic_solve_info info;
   e = poisson_solve_ex(v, rho, phi, 1e-10, 2000, &o, &info);
   if (e != PIC_OK && e != PIC_ENOCONV) return e;
@@ -231,7 +231,7 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
     if ((e = dfield(pool, n, &rho))) return e;
     if ((e = pic_deposit(dg.c, rho))) return e;
     CK(cudaMemsetAsync(S.a, 0, n * sizeof(double), c->stream));
-    pic_solve_opts fp64{PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0};
+    pic_solve_opts fp64{PIC_PREC_FP64, PIC_PC_JACOBI, 0.0, 0, 0};
     if ((e = poisson_solve_ex(dg.c, rho, S.a, 1e-12, 50 * N + 1000, &fp64, nullptr))) return e;
     for (int k : kSnapIters) {
       double *x, *r;

@@ -329,3 +329,27 @@ def test_landau_damping_rate_on_the_gpu_path(pg, solver):
     assert abs(period - np.pi / g["omega_r"]) < 0.1 * np.pi / g["omega_r"], period
     print(f"\nGPU Landau damping ({solver}): gamma {gamma:.4f} (theory {g['gamma']}), "
           f"period {period:.3f} (theory {np.pi / g['omega_r']:.3f})")
+
+
+def test_refine_max_caps_the_fp64_recomputations(pg):
+    """pic_solve_opts.refine_max: the mixed solve stops with PIC_ENOCONV after
+    that many FP64 residual recomputations (the last iterate returned, its
+    true residual reported); 0 leaves it uncapped; negative is rejected."""
+    N = 64
+    c = solver_ctx(pg, N)
+    b = dev(inputs.landau_noise_rhs(N, 2))
+    phi = torch.zeros_like(b)
+    free = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED)
+    assert free["converged"] and free["reliable_updates"] >= 3, free
+    for cap in (1, 2):
+        phi.zero_()
+        info = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, refine_max=cap,
+                       raise_on_error=False)
+        assert info["code"] == pg.PIC_ENOCONV and not info["converged"], info
+        assert info["reliable_updates"] == cap, info
+        assert 1e-10 < info["rel_res"] < 1.0, info
+        assert torch.isfinite(phi).all()
+    phi.zero_()
+    info = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, refine_max=-1, raise_on_error=False)
+    assert info["code"] == pg.PIC_EINVAL
+    c.close()
