@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kStreamSmall) k_reliable(double* __restrict__ 
       sc->rmax2 = rr;
       sc->iter = 0;
     } else {
-      sc->updates += 1;
+      if (mode == 1) sc->updates += 1;  // the forced final fold (mode 2) is not a reliable update
       // continue the recursion from the recomputed residual
       sc->beta = rr / sc->rr_prev;
       sc->rr = rr;
