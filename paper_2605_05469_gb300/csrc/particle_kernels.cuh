@@ -667,8 +667,11 @@ __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint
   }
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double x = fmod(v[q], g.L);  // exact; |x| < L
-    if (x < 0.0) x += g.L;       // may round to L, which to_cell_offset wraps to 0
+    double x = v[q];
+    if (!(x >= 0.0 && x < g.L)) {  // outside the box (rare): its periodic image
+      x = fmod(x, g.L);            // exact; |x| < L
+      if (x < 0.0) x += g.L;       // may round to L, which to_cell_offset wraps to 0
+    }
     v[q] = x;
   }
   PRec rec;
