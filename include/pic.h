@@ -82,9 +82,11 @@ typedef struct {
   int precision;         /* PIC_PREC_* */
   int precond;           /* PIC_PC_* */
   double reliable_delta; /* MIXED: recompute the FP64 residual when the FP32 residual
-                            norm fell by this factor since the last recomputation;
+                            norm fell by this factor since the last recomputation
+                            (1e-4 <= reliable_delta < 1, else PIC_EINVAL: below
+                            1e-4 the FP32 recursion runs out of precision first);
                             0 selects the default: 0.1 with Jacobi, 0.03 with
-                            the learned preconditioner, 0.003 with the V-cycle */
+                            the learned preconditioner, 0.001 with the V-cycle */
   int check_every;       /* iterations between host reads of the convergence flag;
                             0 = default (1 with the V-cycle, 32 up to 64^3, else 8) */
   int refine_max;        /* MIXED: at most this many FP64 residual recomputations (the

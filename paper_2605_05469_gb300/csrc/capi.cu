@@ -705,12 +705,15 @@ int poisson_solve_ex(pic_ctx* c, const double* rho, double* phi, double tol, int
     // (r, r) falls by delta^2; measured on GB300 (256^3, 512^3 Landau
     // deposits), 0.1 is best for Jacobi-CG (smaller values cost iterations),
     // 0.03 for flexible CG with the learned preconditioner (fewer FP64
-    // recomputations at the same iteration count) and 0.003 with the V-cycle
-    // (its residual falls ~10x an iteration; each FP64 recomputation costs
-    // about half a V-cycle)
+    // recomputations at the same iteration count) and 0.001 with the V-cycle
+    // (its residual falls ~10x an iteration; at 512^3 0.001 kept 11
+    // iterations with 3 recomputations instead of 4 at 0.003). Below 1e-4 the
+    // FP32 recursion runs out of precision before its first recomputation
+    // (measured: p.Ap <= 0 after ~20 V-cycle iterations at 1e-6), so smaller
+    // values are rejected.
     const double delta = opts.reliable_delta > 0.0 ? opts.reliable_delta
-                                                   : (opts.precond == PIC_PC_JACOBI ? 0.1 : (mgpc ? 0.003 : 0.03));
-    if (!(delta < 1.0)) return PIC_EINVAL;
+                                                   : (opts.precond == PIC_PC_JACOBI ? 0.1 : (mgpc ? 0.001 : 0.03));
+    if (!(delta < 1.0) || delta < 1e-4) return PIC_EINVAL;
     if (opts.refine_max < 0) return PIC_EINVAL;
     if (opts.precond != PIC_PC_JACOBI)
       return solve_fcg(c, rho, phi, tol, maxit, m, delta, opts.refine_max, opts.precond, info);

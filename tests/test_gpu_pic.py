@@ -353,3 +353,21 @@ def test_refine_max_caps_the_fp64_recomputations(pg):
     info = c.solve(b, phi, tol=1e-10, maxit=5000, precision=pg.PREC_MIXED, refine_max=-1, raise_on_error=False)
     assert info["code"] == pg.PIC_EINVAL
     c.close()
+
+
+def test_reliable_delta_range(pg):
+    """reliable_delta below 1e-4 (where the FP32 recursion runs out of
+    precision before its first FP64 recomputation) and at or above 1 is
+    rejected; 1e-4 converges."""
+    N = 32
+    c = solver_ctx(pg, N)
+    b = dev(inputs.landau_noise_rhs(N, 4))
+    phi = torch.zeros_like(b)
+    for bad in (1e-5, 1.0, 2.0):
+        info = c.solve(b, phi, tol=1e-10, maxit=2000, precision=pg.PREC_MIXED, reliable_delta=bad,
+                       raise_on_error=False)
+        assert info["code"] == pg.PIC_EINVAL, bad
+    info = c.solve(b, phi.zero_(), tol=1e-10, maxit=2000, precision=pg.PREC_MIXED, precond=pg.PC_MG,
+                   reliable_delta=1e-4)
+    assert info["converged"] and info["rel_res"] <= 1e-10, info
+    c.close()
