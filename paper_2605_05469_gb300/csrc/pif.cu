@@ -14,7 +14,12 @@
 //           q_j = -L^3 / Np (the electrons; the background is the k = 0 mode).
 // The modes of the three field components are formed directly on the
 // half spectrum of the real oversampled grid (Hermitian by construction), so
-// the inverse transforms are complex-to-real. FP64 throughout.
+// the inverse transforms are complex-to-real. FP64 arithmetic for tolerances
+// below 1e-5; at 1e-5 and above (the paper's runs use 1e-4) the window sums,
+// the spread grid and the transforms are FP32, whose rounding (about 1e-6 of
+// the field's maximum, measured against the direct sums) stays well inside
+// the tolerance, with the particle positions taken to FP32 as an integer grid
+// index plus an exact fraction so the window arguments keep full precision.
 #include <cufft.h>
 #include <math.h>
 
@@ -36,6 +41,14 @@ struct PifState {
   cufftDoubleComplex* Gh = nullptr;    // M x M x (M/2 + 1)
   cufftDoubleComplex* F = nullptr;     // M x M x (M/2 + 1)
   double* phihat = nullptr;            // window transform at the signed modes -N/2 .. N/2 - 1
+  // FP32 form (tolerances >= 1e-5)
+  bool f32 = false;
+  cufftHandle fwd32 = 0, inv32 = 0;
+  bool have_fwd32 = false, have_inv32 = false;
+  float* G32 = nullptr;                 // M^3: spread charge, then E_x
+  float* Gyz32[2] = {nullptr, nullptr}; // M^3 each: E_y, E_z
+  cufftComplex* Gh32 = nullptr;         // M x M x (M/2 + 1)
+  cufftComplex* F32 = nullptr;
 };
 
 void pif_state_free(PifState* s) {
@@ -48,6 +61,13 @@ void pif_state_free(PifState* s) {
   cudaFree(s->Gh);
   cudaFree(s->F);
   cudaFree(s->phihat);
+  if (s->have_fwd32) cufftDestroy(s->fwd32);
+  if (s->have_inv32) cufftDestroy(s->inv32);
+  cudaFree(s->G32);
+  cudaFree(s->Gyz32[0]);
+  cudaFree(s->Gyz32[1]);
+  cudaFree(s->Gh32);
+  cudaFree(s->F32);
   delete s;
 }
 
@@ -230,6 +250,129 @@ __global__ void __launch_bounds__(128) k_pif_gather3(const PRec* __restrict__ P,
   Ep[2 * np + p] = acc2;
 }
 
+// ---- FP32 form --------------------------------------------------------------
+// Position of particle p in oversampled grid units as an integer plus an exact
+// fraction: u_d = 2 (i_d + f_d 2^-64) = s_d + t_d, t_d in [0, 1) (24 bits).
+__device__ __forceinline__ void grid_units32(const PRec* P, uint64_t p, int s[3], float t[3]) {
+  const uint4* rec = reinterpret_cast<const uint4*>(P + p);
+  const uint4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r3 = __ldg(rec + 3);
+  const uint64_t f[3] = {((uint64_t)r0.y << 32) | r0.x, ((uint64_t)r0.w << 32) | r0.z, ((uint64_t)r1.y << 32) | r1.x};
+  const int c[3] = {(int)(r3.z & 0xFFFFu), (int)(r3.z >> 16), (int)(r3.w & 0xFFFFu)};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    s[d] = 2 * c[d] + (int)(f[d] >> 63);
+    t[d] = __uint2float_rn((uint32_t)((f[d] << 1) >> 40)) * 0x1p-24f;
+  }
+}
+
+__device__ __forceinline__ float es_window32(float z, float beta) {
+  return fabsf(z) <= 1.0f ? expf(beta * (sqrtf(1.0f - z * z) - 1.0f)) : 0.0f;
+}
+
+// First window index (unwrapped) and the W weights along one axis; the
+// distances (s - g0 - a) + t are exact small integers plus the fraction.
+template <int W>
+__device__ __forceinline__ int axis_weights32(int s, float t, float beta, float* wt) {
+  const int g0 = s + (int)ceilf(t - 0.5f * (float)W);
+#pragma unroll
+  for (int a = 0; a < W; ++a) wt[a] = es_window32(2.0f * ((float)(s - g0 - a) + t) / (float)W, beta);
+  return g0;
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) k_pif_spread32(const PRec* __restrict__ P, uint64_t np, int M, float beta,
+                                                      float q, float* G) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  int s[3];
+  float t[3];
+  grid_units32(P, p, s, t);
+  float wx[W], wy[W], wz[W];
+  const int gx = axis_weights32<W>(s[0], t[0], beta, wx), gy = axis_weights32<W>(s[1], t[1], beta, wy);
+  const int gz = axis_weights32<W>(s[2], t[2], beta, wz);
+  const size_t Ms = M;
+  int xs[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) xs[a] = wrap_m(gx + a, M);
+  for (int c = 0; c < W; ++c) {
+    const int z = wrap_m(gz + c, M);
+    const float qz = q * wz[c];
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      const float qzy = qz * wy[b];
+      float* row = G + ((size_t)z * Ms + wrap_m(gy + b, M)) * Ms;
+#pragma unroll
+      for (int a = 0; a < W; ++a) atomicAdd(row + xs[a], qzy * wx[a]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pif_modes32(const cufftComplex* __restrict__ Gh, cufftComplex* __restrict__ F,
+                                                     int N, int M, const double* __restrict__ phihat,
+                                                     double two_pi_over_L, double inv_L3, int d) {
+  const int Mh = M / 2 + 1;
+  const size_t total = (size_t)M * M * Mh;
+  const int lim = N / 2 - 1;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(t % Mh), iy = (int)((t / Mh) % M), iz = (int)(t / ((size_t)Mh * M));
+    const int sx = ix, sy = iy <= M / 2 ? iy : iy - M, sz = iz <= M / 2 ? iz : iz - M;
+    cufftComplex out = make_cuComplex(0.f, 0.f);
+    if (sx <= lim && sy >= -lim && sy <= lim && sz >= -lim && sz <= lim && (sx | sy | sz) != 0) {
+      const double kx = two_pi_over_L * sx, ky = two_pi_over_L * sy, kz = two_pi_over_L * sz;
+      const double k2 = kx * kx + ky * ky + kz * kz;
+      const double ph = phihat[sx + N / 2] * phihat[sy + N / 2] * phihat[sz + N / 2];
+      const double kd = d == 0 ? kx : (d == 1 ? ky : kz);
+      const float f = (float)(kd * inv_L3 / (k2 * ph * ph));
+      const cufftComplex g = Gh[t];
+      out = make_cuComplex(f * g.y, -f * g.x);  // -i f (a + i b) = f b - i f a
+    }
+    F[t] = out;
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128) k_pif_gather3_32(const PRec* __restrict__ P, uint64_t np, int M, float beta,
+                                                        const float* __restrict__ f0, const float* __restrict__ f1,
+                                                        const float* __restrict__ f2, double* __restrict__ Ep) {
+  const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  int s[3];
+  float t[3];
+  grid_units32(P, p, s, t);
+  float wx[W], wy[W], wz[W];
+  const int gx = axis_weights32<W>(s[0], t[0], beta, wx), gy = axis_weights32<W>(s[1], t[1], beta, wy);
+  const int gz = axis_weights32<W>(s[2], t[2], beta, wz);
+  const size_t Ms = M;
+  int xs[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) xs[a] = wrap_m(gx + a, M);
+  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  for (int c = 0; c < W; ++c) {
+    const int z = wrap_m(gz + c, M);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      const size_t row = ((size_t)z * Ms + wrap_m(gy + b, M)) * Ms;
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        t0 = fmaf(__ldg(f0 + row + xs[a]), wx[a], t0);
+        t1 = fmaf(__ldg(f1 + row + xs[a]), wx[a], t1);
+        t2 = fmaf(__ldg(f2 + row + xs[a]), wx[a], t2);
+      }
+      s0 = fmaf(t0, wy[b], s0);
+      s1 = fmaf(t1, wy[b], s1);
+      s2 = fmaf(t2, wy[b], s2);
+    }
+    acc0 = fmaf(s0, wz[c], acc0);
+    acc1 = fmaf(s1, wz[c], acc1);
+    acc2 = fmaf(s2, wz[c], acc2);
+  }
+  Ep[p] = (double)acc0;
+  Ep[np + p] = (double)acc1;
+  Ep[2 * np + p] = (double)acc2;
+}
+
 // Launch kernel template K<W> for the runtime width w (kPifMinW..kPifMaxW).
 #define PIF_DISPATCH_W(w, KER, ...)                              \
   switch (w) {                                                   \
@@ -257,8 +400,11 @@ int width_for(double tol) {
   return w;
 }
 
-int ensure_pif(pic_ctx* c, int w) {
-  if (c->pif && c->pif->N == c->N && c->pif->w == w) return PIC_OK;
+// The FP32 form for tolerances >= 1e-5 (window widths 4 to 6).
+constexpr double kPifF32Tol = 1e-5;
+
+int ensure_pif(pic_ctx* c, int w, bool f32) {
+  if (c->pif && c->pif->N == c->N && c->pif->w == w && c->pif->f32 == f32) return PIC_OK;
   pif_state_free(c->pif);
   c->pif = nullptr;
   PifState* s = new (std::nothrow) PifState();
@@ -267,9 +413,20 @@ int ensure_pif(pic_ctx* c, int w) {
   s->M = 2 * c->N;
   s->w = w;
   s->beta = 2.30 * w;
+  s->f32 = f32;
   const size_t M = s->M, nr = M * M * M, nc = M * M * (M / 2 + 1);
   int e = PIC_OK;
-  if (cudaMalloc(reinterpret_cast<void**>(&s->G), nr * sizeof(double)) != cudaSuccess ||
+  if (f32) {
+    if (cudaMalloc(reinterpret_cast<void**>(&s->G32), nr * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&s->Gyz32[0]), nr * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&s->Gyz32[1]), nr * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&s->Gh32), nc * sizeof(cufftComplex)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&s->F32), nc * sizeof(cufftComplex)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&s->phihat), (size_t)s->N * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      e = PIC_ENOMEM;
+    }
+  } else if (cudaMalloc(reinterpret_cast<void**>(&s->G), nr * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->Gyz[0]), nr * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->Gyz[1]), nr * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&s->Gh), nc * sizeof(cufftDoubleComplex)) != cudaSuccess ||
@@ -286,10 +443,17 @@ int ensure_pif(pic_ctx* c, int w) {
     if (cudaMemcpy(s->phihat, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       e = PIC_ECUDA;
   }
-  if (!e && cufftPlan3d(&s->fwd, s->M, s->M, s->M, CUFFT_D2Z) == CUFFT_SUCCESS) s->have_fwd = true;
-  else if (!e) e = PIC_ECUDA;
-  if (!e && cufftPlan3d(&s->inv, s->M, s->M, s->M, CUFFT_Z2D) == CUFFT_SUCCESS) s->have_inv = true;
-  else if (!e) e = PIC_ECUDA;
+  if (f32) {
+    if (!e && cufftPlan3d(&s->fwd32, s->M, s->M, s->M, CUFFT_R2C) == CUFFT_SUCCESS) s->have_fwd32 = true;
+    else if (!e) e = PIC_ECUDA;
+    if (!e && cufftPlan3d(&s->inv32, s->M, s->M, s->M, CUFFT_C2R) == CUFFT_SUCCESS) s->have_inv32 = true;
+    else if (!e) e = PIC_ECUDA;
+  } else {
+    if (!e && cufftPlan3d(&s->fwd, s->M, s->M, s->M, CUFFT_D2Z) == CUFFT_SUCCESS) s->have_fwd = true;
+    else if (!e) e = PIC_ECUDA;
+    if (!e && cufftPlan3d(&s->inv, s->M, s->M, s->M, CUFFT_Z2D) == CUFFT_SUCCESS) s->have_inv = true;
+    else if (!e) e = PIC_ECUDA;
+  }
   if (e) {
     pif_state_free(s);
     return e;
@@ -307,14 +471,41 @@ int pif_field(pic_ctx* c, double tol, double* Ep) {
   // which also keeps every window index within [-M, 2M) for wrap_m
   if (w > 2 * c->N) return PIC_EINVAL;
   int e;
-  if ((e = ensure_pif(c, w))) return e;
+  const bool f32 = tol >= kPifF32Tol;
+  if ((e = ensure_pif(c, w, f32))) return e;
   PifState* s = c->pif;
-  if (cufftSetStream(s->fwd, c->stream) != CUFFT_SUCCESS || cufftSetStream(s->inv, c->stream) != CUFFT_SUCCESS)
-    return PIC_ECUDA;
   const size_t M = s->M, nr = M * M * M, nc = M * M * (M / 2 + 1);
   const double L = c->grid.L;
   const PRec* P = c->prec[c->cur];
   const unsigned pb = (unsigned)((c->np + 127) / 128);
+  const double pi = 3.14159265358979323846;
+  if (f32) {
+    if (cufftSetStream(s->fwd32, c->stream) != CUFFT_SUCCESS || cufftSetStream(s->inv32, c->stream) != CUFFT_SUCCESS)
+      return PIC_ECUDA;
+    CK(cudaMemsetAsync(s->G32, 0, nr * sizeof(float), c->stream));
+    int slot32 = c->prof_on ? c->ker[PIC_KER_PIF_SPREAD].begin(c->stream) : -1;
+    PIF_DISPATCH_W(s->w, k_pif_spread32, pb, 128, 0, P, c->np, s->M, (float)s->beta,
+                   (float)(-L * L * L / (double)c->np), s->G32);
+    if (c->prof_on) c->ker[PIC_KER_PIF_SPREAD].end(slot32, c->stream);
+    if (cufftExecR2C(s->fwd32, s->G32, s->Gh32) != CUFFT_SUCCESS) return PIC_ECUDA;
+    size_t b32 = (nc + 255) / 256;
+    const size_t cap32 = (size_t)c->sms * 16;
+    const unsigned grid32 = (unsigned)(b32 < cap32 ? b32 : cap32);
+    float* comp32[3] = {s->G32, s->Gyz32[0], s->Gyz32[1]};
+    for (int d = 0; d < 3; ++d) {
+      launch(c, k_pif_modes32, grid32, 256, 0, (const cufftComplex*)s->Gh32, s->F32, s->N, s->M,
+             (const double*)s->phihat, 2.0 * pi / L, 1.0 / (L * L * L), d);
+      if (cufftExecC2R(s->inv32, s->F32, comp32[d]) != CUFFT_SUCCESS) return PIC_ECUDA;
+    }
+    slot32 = c->prof_on ? c->ker[PIC_KER_PIF_GATHER].begin(c->stream) : -1;
+    PIF_DISPATCH_W(s->w, k_pif_gather3_32, pb, 128, 0, P, c->np, s->M, (float)s->beta, (const float*)comp32[0],
+                   (const float*)comp32[1], (const float*)comp32[2], Ep);
+    if (c->prof_on) c->ker[PIC_KER_PIF_GATHER].end(slot32, c->stream);
+    CK(cudaGetLastError());
+    return PIC_OK;
+  }
+  if (cufftSetStream(s->fwd, c->stream) != CUFFT_SUCCESS || cufftSetStream(s->inv, c->stream) != CUFFT_SUCCESS)
+    return PIC_ECUDA;
   CK(cudaMemsetAsync(s->G, 0, nr * sizeof(double), c->stream));
   int slot = c->prof_on ? c->ker[PIC_KER_PIF_SPREAD].begin(c->stream) : -1;
   PIF_DISPATCH_W(s->w, k_pif_spread, pb, 128, 0, P, c->np, s->M, s->beta, -L * L * L / (double)c->np, s->G);
@@ -323,7 +514,6 @@ int pif_field(pic_ctx* c, double tol, double* Ep) {
   size_t b = (nc + 255) / 256;
   const size_t cap = (size_t)c->sms * 16;
   const unsigned grid = (unsigned)(b < cap ? b : cap);
-  const double pi = 3.14159265358979323846;
   // G is free again after the forward transform: it takes the x component
   double* comp[3] = {s->G, s->Gyz[0], s->Gyz[1]};
   for (int d = 0; d < 3; ++d) {

@@ -116,15 +116,18 @@ def test_first_steps_at_bench_size(pg, N):
     torch.cuda.empty_cache()  # give the cached blocks back before the next full-size test
 
 
-def test_particle_in_fourier_field_conserves_momentum_at_bench_size(pg):
+@pytest.mark.parametrize("tol,bound", [(1e-4, 1e-6), (1e-6, 1e-10)])
+def test_particle_in_fourier_field_conserves_momentum_at_bench_size(pg, tol, bound):
+    """The bench's tolerance 1e-4 runs the FP32 NUFFTs, whose rounding bounds
+    the conservation at ~1e-7 relative; 1e-6 runs them in FP64."""
     N, ppc = 128, 8
     npart = ppc * N ** 3
     c = pg.Context().init(N, ppc, 0x5EED)
     E = torch.empty(3 * npart, dtype=torch.float64, device="cuda")
-    c.pif_field(E, tol=1e-4)
+    c.pif_field(E, tol=tol)
     E3 = E.view(3, npart)
     assert bool(torch.isfinite(E3).all())
     net = E3.sum(dim=1).abs()
     scale = E3.abs().sum(dim=1)
     assert bool(torch.all(scale > 0))
-    assert bool(torch.all(net <= 1e-10 * scale)), (net.tolist(), scale.tolist())
+    assert bool(torch.all(net <= bound * scale)), (net.tolist(), scale.tolist())

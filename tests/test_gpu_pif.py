@@ -2,10 +2,11 @@
 against the CPU oracle's direct non-uniform DFT sums (oracle/pif.py): the
 field at the particles, and a few leapfrog steps with it.
 
-The GPU evaluates the sums by NUFFTs (window width w = ceil(-log10 tol) + 1,
-FP64 cuFFT); their error follows the tolerance: about 1.0-1.3 tol of the
+The GPU evaluates the sums by NUFFTs (window width w = ceil(-log10 tol) + 1;
+FP32 window sums and cuFFT at tol >= 1e-5, FP64 below); their error follows
+the tolerance: about 1.0-1.3 tol of the
 field's maximum for tol = 1e-4 (the tolerance of the paper's runs, w = 5),
-1e-6 and 1e-12, so the bounds below are 5 tol, and 1e-9 where FP64 rounding
+1e-5, 1e-6 and 1e-12, so the bounds below are 5 tol, and 1e-9 where FP64 rounding
 of the sums dominates (tol <= 1e-12; tol = 1e-15 takes the widest window,
 w = 16, which spans the whole oversampled grid at N = 8)."""
 import numpy as np
@@ -29,7 +30,7 @@ def pg():
 
 
 @pytest.mark.parametrize("N,ppc,tol,bound", [(8, 1, 1e-12, 1e-9), (16, 1, 1e-12, 1e-9), (8, 1, 1e-15, 1e-9),
-                                             (16, 2, 1e-4, 5e-4), (16, 1, 1e-6, 5e-6)])
+                                             (16, 2, 1e-4, 5e-4), (16, 2, 1e-5, 5e-5), (16, 1, 1e-6, 5e-6)])
 def test_pif_field_matches_direct_sums(pg, N, ppc, tol, bound):
     c = pg.Context().init(N, ppc, 21)
     npart = ppc * N ** 3
