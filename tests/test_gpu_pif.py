@@ -41,10 +41,12 @@ def test_pif_field_matches_direct_sums(pg, N, ppc, tol, bound):
     got = E.cpu().numpy().reshape(3, -1)
     assert np.max(np.abs(got - ref)) <= bound * np.max(np.abs(ref))
     assert np.max(np.abs(imag)) <= 1e-12 * np.max(np.abs(ref))
-    # a second evaluation finds the particles already in cell order
+    # a second evaluation finds the particles already in cell order (the
+    # spreading's atomics add in another order: FP32 rounding at tol >= 1e-5)
     E2 = torch.full_like(E, float("nan"))
     c.pif_field(E2, tol=tol)
-    assert torch.allclose(E2, E, rtol=0.0, atol=1e-12 * float(np.max(np.abs(ref))))
+    rep = 1e-6 if tol >= 1e-5 else 1e-12
+    assert torch.allclose(E2, E, rtol=0.0, atol=rep * float(np.max(np.abs(ref))))
 
 
 def test_pif_field_at_sampled_particles_with_32cubed_modes(pg):
