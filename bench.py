@@ -317,7 +317,8 @@ def end_to_end(c, step, np_, n, rho, phi, steps, solve_only, world, dist, barrie
         return {"value": whole_job_rate(world, steps, s), "unit": unit, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "note": "rho from pinned host memory, phi back to it, every solve"}
     state_bytes = 48 * np_
-    avail = mem_available_bytes()
+    # every rank on this host takes its own copy of the state
+    avail = mem_available_bytes() // max(1, int(os.environ.get("LOCAL_WORLD_SIZE", "1")))
     if avail < 2 * state_bytes + (48 << 30):
         # not enough host memory for the state: the device-resident loop, the
         # field energy read back every step

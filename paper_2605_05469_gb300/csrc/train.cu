@@ -284,40 +284,40 @@ extern "C" int pic_cnn_train(pic_ctx* c, const pic_train_opts* o, pic_train_info
     return PIC_OK;
   };
   for (restart = 0; restart < O.restarts; ++restart) {
-  // each restart: its own initial weights and crop stream (restart 0 is the plain training)
-  const uint64_t key = (O.seed + 0x9E3779B97F4A7C15ull * (uint64_t)restart) ^ 0xC7A1B5EEDull;
-  if (O.resume) {
-    if ((e = cnn_state_set(t, start.get<float>(), adam_t0))) return e;
-  } else {
-    std::vector<float> w0(kWeightsN);
-    initial_weights(O.seed + 7919ull * (uint64_t)restart, w0.data());
-    if ((e = pic_cnn_set_weights(t, w0.data()))) return e;
-  }
-  const int adam_t = adam_t0;
-  losses.clear();
-  for (int step = 0; step < O.steps; ++step) {
-    const uint32_t ctr = (uint32_t)(adam_t + step);
-    const U4 pick = philox({ctr, 0u, 0u, 0u}, key);
-    const Set& S = sets[pick.x % (uint32_t)O.sets];
-    const size_t sn = pick.y % (uint32_t)S.r.size();
-    for (int b = 0; b < B; ++b) {
-      const U4 r = philox({ctr, 1u + (uint32_t)b, 0u, 0u}, key);
-      origins[3 * b] = (int)(r.x % (uint32_t)N);
-      origins[3 * b + 1] = (int)(r.y % (uint32_t)N);
-      origins[3 * b + 2] = (int)(r.z % (uint32_t)N);
+    // each restart: its own initial weights and crop stream (restart 0 is the plain training)
+    const uint64_t key = (O.seed + 0x9E3779B97F4A7C15ull * (uint64_t)restart) ^ 0xC7A1B5EEDull;
+    if (O.resume) {
+      if ((e = cnn_state_set(t, start.get<float>(), adam_t0))) return e;
+    } else {
+      std::vector<float> w0(kWeightsN);
+      initial_weights(O.seed + 7919ull * (uint64_t)restart, w0.data());
+      if ((e = pic_cnn_set_weights(t, w0.data()))) return e;
     }
-    double loss = 0.0;
-    if ((e = pic_cnn_make_batch(t, S.r[sn], S.a, S.b[sn], origins.data(), B, D, xb.get<float>(), tb.get<float>(),
-                                h * h)) ||
-        (e = pic_cnn_forward(t, xb.get<float>(), yb.get<float>(), B, D)) ||
-        (e = pic_cnn_loss(t, yb.get<float>(), tb.get<float>(), B, D, gb.get<float>(), &loss)) ||
-        (e = pic_cnn_backward(t, gb.get<float>(), B, D)) || (e = pic_cnn_adam(t, O.lr)))
-      return e;
-    losses.push_back(loss);
-    if (O.validate_every > 0 && (step + 1) % O.validate_every == 0 && step + 1 < O.steps && (e = score(step + 1)))
-      return e;
-  }
-  if (O.validate_every > 0 && (e = score(O.steps))) return e;
+    const int adam_t = adam_t0;
+    losses.clear();
+    for (int step = 0; step < O.steps; ++step) {
+      const uint32_t ctr = (uint32_t)(adam_t + step);
+      const U4 pick = philox({ctr, 0u, 0u, 0u}, key);
+      const Set& S = sets[pick.x % (uint32_t)O.sets];
+      const size_t sn = pick.y % (uint32_t)S.r.size();
+      for (int b = 0; b < B; ++b) {
+        const U4 r = philox({ctr, 1u + (uint32_t)b, 0u, 0u}, key);
+        origins[3 * b] = (int)(r.x % (uint32_t)N);
+        origins[3 * b + 1] = (int)(r.y % (uint32_t)N);
+        origins[3 * b + 2] = (int)(r.z % (uint32_t)N);
+      }
+      double loss = 0.0;
+      if ((e = pic_cnn_make_batch(t, S.r[sn], S.a, S.b[sn], origins.data(), B, D, xb.get<float>(), tb.get<float>(),
+                                  h * h)) ||
+          (e = pic_cnn_forward(t, xb.get<float>(), yb.get<float>(), B, D)) ||
+          (e = pic_cnn_loss(t, yb.get<float>(), tb.get<float>(), B, D, gb.get<float>(), &loss)) ||
+          (e = pic_cnn_backward(t, gb.get<float>(), B, D)) || (e = pic_cnn_adam(t, O.lr)))
+        return e;
+      losses.push_back(loss);
+      if (O.validate_every > 0 && (step + 1) % O.validate_every == 0 && step + 1 < O.steps && (e = score(step + 1)))
+        return e;
+    }
+    if (O.validate_every > 0 && (e = score(O.steps))) return e;
   }  // restarts
   int final_t = 0;
   if (O.validate_every > 0) {
