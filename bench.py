@@ -73,9 +73,15 @@ KER_BYTES = {
 KER_FP64_OPS = {(0, "pap"): 8, (0, "update"): 3}
 # learned preconditioner applied as its composed 9^3 kernel: 729 FMA per cell
 PRECOND_FLOP_PER_CELL = 2 * 729
-# ... which the tensor-core form executes as 81 Toeplitz products of K = 32
-# x-inputs per output (9 of the 32 weights in each product are nonzero)
-PRECOND_MMA_FLOP_PER_CELL = 2 * 81 * 32
+# ... which the tensor-core forms execute as 81 Toeplitz products per output:
+# the 16-wide form (default) takes K = 32 x-inputs per output (9 of the 32
+# weights in each product nonzero); the 8-wide form takes K = 16, its N = 80
+# stack carrying 9 groups of 8 outputs and one zero group (2 * 81 * 16 * 80 / 72)
+PRECOND_MMA_FLOP_PER_CELL = {"tc": 2 * 81 * 32, "tc8": 2 * 81 * 16 * 80 // 72, "tc_fused": 2 * 81 * 32}
+PRECOND_TC_KERNEL = {"tc": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16, 16-wide Toeplitz)",
+                     "tc8": "k_apply_k_tc8 (composed 9^3 learned preconditioner, tcgen05 BF16, 8-wide Toeplitz)",
+                     "tc_fused": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16, 16-wide "
+                                 "Toeplitz, fused FCG update)"}
 # algorithmic bytes per fine cell of the V-cycle's finest-level kernels (FP32)
 MG_BYTES = {
     "mg_pre": 8,               # read r; write x (both damped sweeps from x = 0)
@@ -176,9 +182,10 @@ def parse(argv=None):
                          "well")
     ap.add_argument("--pif-tol", type=float, default=1e-4,
                     help="relative tolerance of the particle-in-Fourier NUFFTs (sets the window width; 1e-4 as in the paper's runs)")
-    ap.add_argument("--cnn-apply", choices=["tc", "tc_fused", "fp32", "layers"], default="tc",
+    ap.add_argument("--cnn-apply", choices=["tc", "tc8", "tc_fused", "fp32", "layers"], default="tc",
                     help="evaluation of the learned preconditioner: composed 9^3 kernel on the tensor cores "
-                         "(BF16), on the CUDA cores (FP32), or the four BF16 convs")
+                         "(BF16; 16-wide Toeplitz form, or the slower 8-wide form), on the CUDA cores (FP32), or the "
+                         "four BF16 convs")
     ap.add_argument("--workload", choices=["pic", "solve"], default="pic",
                     help="pic: full PIC step; solve: one cold-start Poisson solve of a Landau density + noise rhs")
     ap.add_argument("--N", type=int, default=DEFAULT_N)
@@ -414,7 +421,8 @@ def dtype_label(pg, solver, cnn_apply="tc", pif_tol=1e-4, solve_only=False):
         return "; ".join(parts + ["solve FP64 throughout"])
     parts.append("solve FP32 vectors + FP64 reductions and residual recomputation")
     if solver == "cnn":
-        parts.append({"tc": "BF16 tensor-core", "tc_fused": "BF16 tensor-core (fused)", "fp32": "FP32",
+        parts.append({"tc": "BF16 tensor-core", "tc8": "BF16 tensor-core (8-wide)",
+                      "tc_fused": "BF16 tensor-core (fused)", "fp32": "FP32",
                       "layers": "BF16 four-conv"}[cnn_apply] + " learned preconditioner (composed 9^3 kernel)")
     elif solver == "mg":
         parts.append("FP32 multigrid V-cycle")
@@ -463,8 +471,8 @@ def run_ours(args):
     if any(s_ in ("cnn", "mg_cnn") for s_ in [args.solver] + alt_solvers) or not args.no_compare:
         weights, train_info = train_networks(pg, torch, args.weights_dir)
     c = pg.Context(stream).init(N, 0 if solve_only else ppc, SEED + rank)
-    apply_mode = {"tc": pg.CNN_APPLY_TC, "tc_fused": pg.CNN_APPLY_TC_FUSED, "fp32": pg.CNN_APPLY_FP32,
-                  "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
+    apply_mode = {"tc": pg.CNN_APPLY_TC, "tc8": pg.CNN_APPLY_TC8, "tc_fused": pg.CNN_APPLY_TC_FUSED,
+                  "fp32": pg.CNN_APPLY_FP32, "layers": pg.CNN_APPLY_LAYERS}[args.cnn_apply]
     nets = Networks(c, weights)
     if weights is not None:
         nets.use(pc if pc in weights else pg.PC_CNN)
@@ -704,16 +712,17 @@ def run_ours(args):
                 "note": f"window sums: 2 {prec_} flops per window point, component and particle (window "
                         "evaluation not counted); the spreading's atomics into the oversampled grid in L2 "
                         "bound it more than its arithmetic"}
-    elif dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC_FUSED):
+    elif dom == "precond" and apply_mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC8, pg.CNN_APPLY_TC_FUSED):
         r = rows[dom]
         _, _, pk = peaks()
         peak = pk.get("bf16_tflops_sustained", 1700.0)
-        roof = {"kernel": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16)", "bound": "tensor",
+        roof = {"kernel": PRECOND_TC_KERNEL[args.cnn_apply], "bound": "tensor",
                 "achieved": round(r["tflops"], 2), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(r["tflops"] / peak, 4),
                 "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long solve)",
                 "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n,
-                "executed_mma_tflops": round(r["tflops"] * PRECOND_MMA_FLOP_PER_CELL / PRECOND_FLOP_PER_CELL, 2),
+                "executed_mma_tflops": round(r["tflops"] * PRECOND_MMA_FLOP_PER_CELL[args.cnn_apply]
+                                             / PRECOND_FLOP_PER_CELL, 2),
                 "avg_launch_us": round(r["avg_us"], 2)}
     elif dom == "precond":
         r = rows[dom]
@@ -915,7 +924,7 @@ def compare_solvers(c, rho, n, pg, torch, nets=None, reps=2, maxit=MAXIT, rhs=""
         if sample:
             prof = c.profile_read(reset=True)
             c.profile(False)
-            learned_roof = tc_roofline(prof, n)
+            learned_roof = tc_roofline(prof, n, "tc")
         res[name] = {"s": best["t_ms"] / 1e3, "iters": best["iters"], "rel_res": best["rel_res"],
                      "converged": bool(best["converged"])}
         if name != "fp64_jacobi_pcg" and "fp64_jacobi_pcg" in res and "s" in res["fp64_jacobi_pcg"]:
@@ -947,11 +956,13 @@ def compare_solvers(c, rho, n, pg, torch, nets=None, reps=2, maxit=MAXIT, rhs=""
     return res, learned_roof
 
 
-def tc_roofline(prof, n):
-    """Roofline of the tensor-core learned preconditioner (k_apply_k_tc) from
-    its sampled launches: algorithmic FLOP of the composed 9^3 kernel per
-    launch over the average CUDA-event duration, against the measured
-    sustained BF16 peak."""
+def tc_roofline(prof, n, form="tc"):
+    """Roofline of the tensor-core learned preconditioner (k_apply_k_tc, or
+    k_apply_k_tc8 for the 8-wide form) from its sampled launches:
+    algorithmic FLOP of the composed 9^3 kernel per launch over the average
+    CUDA-event duration, against the measured sustained BF16 peak."""
+    if form not in PRECOND_MMA_FLOP_PER_CELL:
+        form = "tc"
     k = prof["ker_samples"]["precond"]
     if not k:
         return None
@@ -959,11 +970,11 @@ def tc_roofline(prof, n):
     tf = PRECOND_FLOP_PER_CELL * n / (avg_ms * 1e-3) / 1e12
     _, _, pk = peaks()
     peak = pk.get("bf16_tflops_sustained", 1700.0)
-    return {"kernel": "k_apply_k_tc (composed 9^3 learned preconditioner, tcgen05 BF16)", "bound": "tensor",
+    return {"kernel": PRECOND_TC_KERNEL[form], "bound": "tensor",
             "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tf / peak, 4),
             "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long solve)",
             "traffic": None, "algorithmic_flop": PRECOND_FLOP_PER_CELL * n,
-            "executed_mma_tflops": round(tf * PRECOND_MMA_FLOP_PER_CELL / PRECOND_FLOP_PER_CELL, 2),
+            "executed_mma_tflops": round(tf * PRECOND_MMA_FLOP_PER_CELL[form] / PRECOND_FLOP_PER_CELL, 2),
             "avg_launch_us": round(avg_ms * 1e3, 2), "samples": k}
 
 

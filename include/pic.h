@@ -308,17 +308,32 @@ int pic_mg_apply(pic_ctx *c, const float *r, float *z, int learned);
 /* Evaluation of the preconditioner (pic_cnn_apply and the solver's
  * preconditioner step) on grids with N % 32 == 0:
  *   PIC_CNN_APPLY_TC     composed kernel on the tensor cores (N % 128 == 0):
- *                        x-direction Toeplitz products, r and K rounded to
- *                        BF16, FP32 accumulation (default); on grids that are
- *                        not a multiple of 128 this mode runs PIC_CNN_APPLY_FP32;
+ *                        x-direction Toeplitz products over 16 outputs and
+ *                        32 inputs (two K = 16 MMA steps per (plane, dy)), r
+ *                        and K rounded to BF16, FP32 accumulation (default);
+ *                        on grids that are not a multiple of 128 this mode
+ *                        runs PIC_CNN_APPLY_FP32;
  *   PIC_CNN_APPLY_FP32   composed kernel on the CUDA cores, FP32 throughout;
  *   PIC_CNN_APPLY_LAYERS the four BF16 tensor-core convs of the network;
  *   PIC_CNN_APPLY_TC_FUSED as PIC_CNN_APPLY_TC, and flexible CG runs its
  *                        residual/solution update and the direction's dot
  *                        products inside the preconditioner kernel (one pass
- *                        instead of three; N % 128 == 0, else as TC).
+ *                        instead of three; N % 128 == 0, else as TC);
+ *   PIC_CNN_APPLY_TC8    the same products over 8 outputs and 16 inputs (one
+ *                        K = 16 step, 9 of 16 weights nonzero against 9 of
+ *                        32), kept for comparison: it issues twice the MMAs
+ *                        per output and runs slower on GB300 (one thread's
+ *                        MMA issue, not the tensor work, bounds both forms);
+ *                        the same sums in another order, so its result
+ *                        differs from TC by FP32 rounding only.
  * Returns PIC_EINVAL for another mode. */
-enum { PIC_CNN_APPLY_TC = 0, PIC_CNN_APPLY_FP32 = 1, PIC_CNN_APPLY_LAYERS = 2, PIC_CNN_APPLY_TC_FUSED = 3 };
+enum {
+  PIC_CNN_APPLY_TC = 0,
+  PIC_CNN_APPLY_FP32 = 1,
+  PIC_CNN_APPLY_LAYERS = 2,
+  PIC_CNN_APPLY_TC_FUSED = 3,
+  PIC_CNN_APPLY_TC8 = 4
+};
 int pic_cnn_set_apply(pic_ctx *c, int mode);
 
 /* Forward pass over B crops: y = N(x) (device FP32 [B][D^3] each); keeps the

@@ -43,6 +43,7 @@ CNN_APPLY_TC = 0
 CNN_APPLY_FP32 = 1
 CNN_APPLY_LAYERS = 2
 CNN_APPLY_TC_FUSED = 3
+CNN_APPLY_TC8 = 4
 CNN_WEIGHTS = 14688
 CNN_TRAIN_BF16 = 0
 CNN_TRAIN_FP32 = 1

@@ -10,6 +10,7 @@
 
 #include "cnn.h"
 #include "cnn_kernels.cuh"
+#include "cnn_tc8.cuh"
 #include "ctx.h"
 
 namespace pic {
@@ -39,7 +40,8 @@ struct CnnState {
   float* q = nullptr;      // loss: A_I (y - t)
   size_t q_cells = 0;
   float* K = nullptr;      // composed 9^3 kernel of N = G^T G (FP32)
-  unsigned char* Bt = nullptr;  // its 81 Toeplitz matrices, packed BF16 B operand
+  unsigned char* Bt = nullptr;  // its 81 Toeplitz matrices, packed BF16 B operand (16-wide form)
+  unsigned char* Bt8 = nullptr; // the 8-wide form's zero-led B stacks
   cnn::K729 K_host;        // its host copy (launch parameter)
   bool K_stale = true;     // the device kernel changed since the host copy
 };
@@ -59,7 +61,7 @@ int ensure_state(pic_ctx* c) {
   int e;
   if ((e = dalloc(&s->w, kWeights)) || (e = dalloc(&s->g, kWeights)) || (e = dalloc(&s->m, kWeights)) ||
       (e = dalloc(&s->v, kWeights)) || (e = dalloc(&s->packed, (size_t)kPackBytes)) || (e = dalloc(&s->K, 729)) ||
-      (e = dalloc(&s->Bt, (size_t)tck::B_BYTES))) {
+      (e = dalloc(&s->Bt, (size_t)tck::B_BYTES)) || (e = dalloc(&s->Bt8, (size_t)tc8::B_BYTES))) {
     cnn_state_free(s);
     return e;
   }
@@ -160,6 +162,7 @@ int repack(pic_ctx* c) {
   launch(c, k_pack_weights, 32, 256, 0, (const float*)c->cnn->w, c->cnn->packed);
   launch(c, k_compose, 1, 256, 0, (const float*)c->cnn->w, c->cnn->K);
   launch(c, k_pack_toeplitz, 41, 256, 0, (const float*)c->cnn->K, c->cnn->Bt);
+  launch(c, k_pack_toeplitz8, 117, 256, 0, (const float*)c->cnn->K, c->cnn->Bt8);
   c->cnn->K_stale = true;
   CK(cudaGetLastError());
   return PIC_OK;
@@ -171,7 +174,7 @@ namespace pic {
 
 void cnn_state_free(CnnState* s) {
   if (!s) return;
-  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K); dfree(s->Bt);
+  dfree(s->w); dfree(s->g); dfree(s->m); dfree(s->v); dfree(s->packed); dfree(s->K); dfree(s->Bt); dfree(s->Bt8);
   dfree(s->a1); dfree(s->a2); dfree(s->a3); dfree(s->ga); dfree(s->gb);
   dfree(s->f1); dfree(s->f2); dfree(s->f3); dfree(s->fa); dfree(s->fb);
   dfree(s->i1); dfree(s->i2);
@@ -183,7 +186,8 @@ void cnn_state_free(CnnState* s) {
 bool cnn_ready(const pic_ctx* c) { return c->cnn && c->cnn->has_weights; }
 
 bool cnn_tc_ok(const pic_ctx* c) {
-  return c->N % tck::BY == 0 && (c->cnn_apply_mode == PIC_CNN_APPLY_TC || c->cnn_apply_mode == PIC_CNN_APPLY_TC_FUSED);
+  return c->N % tck::BY == 0 && (c->cnn_apply_mode == PIC_CNN_APPLY_TC || c->cnn_apply_mode == PIC_CNN_APPLY_TC_FUSED ||
+                                 c->cnn_apply_mode == PIC_CNN_APPLY_TC8);
 }
 
 bool cnn_fused_ok(const pic_ctx* c) { return c->N % tck::BY == 0 && c->cnn_apply_mode == PIC_CNN_APPLY_TC_FUSED; }
@@ -207,6 +211,24 @@ int launch_tc(pic_ctx* c, const float* r, float* z, const TcFcg& F) {
   return PIC_OK;
 }
 
+// The 8-wide composed kernel (opt-in, PIC_CNN_APPLY_TC8), persistent like the
+// 16-wide one. With `stop` (the solver's scalars) it returns at once once the
+// solve has finished, like the solver's other kernels.
+int launch_tc8(pic_ctx* c, const float* r, float* z, const Scalars* stop) {
+  static bool configured = false;
+  if (!configured) {
+    CK(cudaFuncSetAttribute((const void*)k_apply_k_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)tc8::SMEM));
+    configured = true;
+  }
+  const int N = c->N;
+  const long units = (long)(N / tc8::BX) * (N / tc8::BY) * N;
+  const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
+  launch(c, k_apply_k_tc8, grid, tc8::THREADS, tc8::SMEM, r, z, N, (const unsigned char*)c->cnn->Bt8, c->err, stop, 0);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
 int cnn_apply_fused(pic_ctx* c, const float* r, float* r_new, float* z, const float* q, const float* p, float* x) {
   if (!cnn_fused_ok(c)) return PIC_EINVAL;
   TcFcg F{q, p, x, r_new, c->sc, c->partials, c->counter, 0};
@@ -226,7 +248,11 @@ int cnn_apply(pic_ctx* c, const float* r, float* z, const double* rr, size_t n) 
   const int N = c->N;
   // linear network: z = s N(r / s) = N r, one composed 9^3 convolution
   if (cnn_tc_ok(c)) {
+    // inside a solve (rr given) the kernel skips its work once the solve is done
+    const Scalars* stop = rr ? c->sc : nullptr;
+    if (c->cnn_apply_mode == PIC_CNN_APPLY_TC8) return launch_tc8(c, r, z, stop);
     TcFcg F{};
+    F.sc = const_cast<Scalars*>(stop);
     return launch_tc<false>(c, r, z, F);
   }
   // grids that are not a multiple of 128 run the FP32 composed kernel in TC mode
@@ -373,7 +399,7 @@ int pic_cnn_apply(pic_ctx* c, const float* r, float* z) {
 }
 
 int pic_cnn_set_apply(pic_ctx* c, int mode) {
-  if (!c || mode < PIC_CNN_APPLY_TC || mode > PIC_CNN_APPLY_TC_FUSED) return PIC_EINVAL;
+  if (!c || mode < PIC_CNN_APPLY_TC || mode > PIC_CNN_APPLY_TC8) return PIC_EINVAL;
   c->cnn_apply_mode = mode;
   return PIC_OK;
 }

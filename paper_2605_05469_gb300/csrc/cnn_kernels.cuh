@@ -553,8 +553,10 @@ __device__ __forceinline__ void tc_issue_plane(uint64_t ad0, uint64_t b0, uint32
   }
 }
 
-// Ring slot of output index v (v >= 0 counts the CTA's output planes).
-__device__ __forceinline__ int tc_ring_slot(long v) { return (int)((tck::TSLOTS - v % tck::TSLOTS) % tck::TSLOTS); }
+// Ring slot of output number v (v >= 0 counts the CTA's output planes;
+// 32-bit: a CTA holds a few thousand, and a 64-bit modulo on the issue path
+// costs more than the MMAs it feeds).
+__device__ __forceinline__ int tc_ring_slot(int v) { return (tck::TSLOTS - v % tck::TSLOTS) % tck::TSLOTS; }
 
 // One input plane of the CTA's stream: column `col`, run of output planes
 // [pa, pb), input plane z (unwrapped, pa-4 <= z <= pb+3).
@@ -562,21 +564,77 @@ struct TcPlane {
   int col, pa, pb, z;
 };
 
-__device__ __forceinline__ bool tc_run_at(long u, long uend, int N, TcPlane& P) {
-  if (u >= uend) return false;
-  P.col = (int)(u / N);
-  P.pa = (int)(u % N);
-  P.pb = (int)min((long)N, (long)P.pa + (uend - u));
-  P.z = P.pa - 4;
+// Work order of the persistent tensor-core kernels. The C columns (output
+// blocks of one x-range and 128 rows, numbered x-block fastest) are dealt out
+// whole and round-robin: CTA b takes columns b, b + G, ... for R = C / G
+// rounds, so the G CTAs resident at a time walk G neighbouring columns
+// through z together and share in L2 the rows of r that their windows
+// overlap (a contiguous split of the (column, plane) units puts neighbouring
+// columns at unrelated depths, and r is read from DRAM again for each; the
+// change measured 980 -> 820 us for the 8-wide form at 512^3). The C - R G
+// leftover columns' units are split contiguously. Output planes are numbered
+// by a CTA-local counter that runs on across the CTA's runs.
+struct TcWork {
+  int N, R, G, b;
+  int tcol0;    // first leftover column
+  long tb, te;  // this CTA's share of the leftover units
+};
+
+__device__ __forceinline__ TcWork tc_work(int N, int C) {
+  TcWork W;
+  W.N = N;
+  W.G = gridDim.x;
+  W.b = blockIdx.x;
+  W.R = C / W.G;
+  W.tcol0 = W.R * W.G;
+  const long TU = (long)(C - W.tcol0) * N;
+  W.tb = TU * W.b / W.G;
+  W.te = TU * (W.b + 1) / W.G;
+  return W;
+}
+
+__device__ __forceinline__ bool tc_has_work(const TcWork& W) { return W.R > 0 || W.tb < W.te; }
+
+struct TcCur {
+  TcPlane P;  // column, run [pa, pb), input plane z
+  int k;      // run index: k < R whole columns, then leftover runs
+  long u;     // next leftover unit
+  int vbase;  // output planes of the earlier runs
+};
+
+__device__ __forceinline__ bool tc_run(const TcWork& W, TcCur& c) {
+  if (c.k < W.R) {
+    c.P.col = W.b + c.k * W.G;
+    c.P.pa = 0;
+    c.P.pb = W.N;
+  } else {
+    if (c.u >= W.te) return false;
+    c.P.col = W.tcol0 + (int)(c.u / W.N);
+    c.P.pa = (int)(c.u % W.N);
+    c.P.pb = (int)min((long)W.N, (long)c.P.pa + (W.te - c.u));
+  }
+  c.P.z = c.P.pa - 4;
   return true;
 }
 
-__device__ __forceinline__ bool tc_next(long uend, int N, TcPlane& P) {
-  if (P.z + 1 < P.pb + 4) {
-    ++P.z;
+__device__ __forceinline__ bool tc_start(const TcWork& W, TcCur& c) {
+  c.k = 0;
+  c.u = W.tb;
+  c.vbase = 0;
+  return tc_has_work(W) && tc_run(W, c);
+}
+
+// Next input plane: z + 1 within the run (pa - 4 .. pb + 3), else the next run.
+__device__ __forceinline__ bool tc_next(const TcWork& W, TcCur& c) {
+  if (c.P.z + 1 < c.P.pb + 4) {
+    ++c.P.z;
     return true;
   }
-  return tc_run_at((long)P.col * N + P.pb, uend, N, P);
+  const int len = c.P.pb - c.P.pa;
+  c.vbase += len;
+  if (c.k >= W.R) c.u += len;
+  ++c.k;
+  return tc_run(W, c);
 }
 
 __device__ __forceinline__ void tc_origin(const TcPlane& P, int N, int& x0, int& y0) {
@@ -745,12 +803,12 @@ __device__ __forceinline__ void tc_epi_barrier() { asm volatile("bar.sync 1, 128
 // memory four threads per 64-byte row segment (coalesced).
 template <bool FUSED>
 __device__ __forceinline__ void tc_epilogue(const TcPlane& P, float* __restrict__ z, int N, uint32_t tmem,
-                                            long ubegin, const TcFcg& F, float alpha, bool x_zero, TcDots& D,
+                                            int vbase, const TcFcg& F, float alpha, bool x_zero, TcDots& D,
                                             float4* tile, const float4* ops) {
   using namespace tck;
   const int p = P.z - 4;
   if (p < P.pa) return;  // an input plane of the lower halo: no output completes (uniform)
-  const int s = tc_ring_slot((long)P.col * N + p - ubegin);
+  const int s = tc_ring_slot(vbase + p - P.pa);
   const int et = threadIdx.x - EPI_WARP0 * 32;  // 0..127
   const int quarter = (threadIdx.x >> 5) & 3, lane = threadIdx.x & 31;
   const int row = quarter * 32 + lane;          // TMEM lane = y row of the block
@@ -847,9 +905,8 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
   float4* tile = reinterpret_cast<float4*>(slots + ASLOTS * SLOT_B);  // TILE_OUT_B (epilogue transpose)
   float4* ebuf = tile + TILE_OUT_B / 16;                            // fused: 2 x EPI_PLANE_B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long U = (long)(N / BX) * (N / BY) * N;
-  const long ubegin = U * blockIdx.x / gridDim.x, uend = U * (blockIdx.x + 1) / gridDim.x;
-  const bool has_work = ubegin < uend;
+  const TcWork W = tc_work(N, (N / BX) * (N / BY));
+  const bool has_work = tc_has_work(W);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -858,13 +915,15 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
   }
   if (tid == 0) {
     abort_flag = 0;
+    // one arrival per producer / epilogue warp (per-thread arrivals on one
+    // barrier word serialise)
     for (int i = 0; i < ASLOTS; ++i) {
-      mbar_init(&a_full[i], PTHREADS);
+      mbar_init(&a_full[i], PTHREADS / 32);
       mbar_init(&a_empty[i], 1);
     }
     for (int i = 0; i < ERING; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 128);
+      mbar_init(&acc_empty[i], 4);
     }
     mbar_init(&b_bar, 1);
     fence_mbar_init();
@@ -889,8 +948,9 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
   if (warp == 0) {
     // ---- MMA issuer: one thread ----
     if (lane == 0 && has_work) {
-      TcPlane P;
-      bool have = tc_run_at(ubegin, uend, N, P);
+      TcCur c;
+      bool have = tc_start(W, c);
+      const TcPlane& P = c.P;
       const bool b_ok = tc_wait(&b_bar, 0, err, &abort_flag);
       const uint64_t bd0 = smem_desc(smem_u32(Bs), BCHUNK_B, 128);
       for (uint32_t j = 0; have && b_ok; ++j) {
@@ -903,8 +963,7 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // groups dz_lo..dz_hi feed output planes z + 4 - dz inside [pa, pb)
         const int dz_lo = max(0, P.z + 4 - (P.pb - 1)), dz_hi = min(8, P.z + 4 - P.pa);
-        const long v_lo = (long)P.col * N + (P.z - dz_lo + 4) - ubegin;
-        const int s_lo = tc_ring_slot(v_lo);
+        const int s_lo = tc_ring_slot(c.vbase + (P.z + 4 - dz_lo - P.pa));
         const int ng = dz_hi - dz_lo + 1;
         const uint64_t ad0 = smem_desc(smem_u32(slots + sa * SLOT_B), CHUNK_B, 128);
         const uint64_t b0 = bd0 + (uint64_t)(dz_lo * 16);  // 16 B-rows per group = 256 B
@@ -916,24 +975,24 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&acc_full[j % ERING]))
                      : "memory");
-        have = tc_next(uend, N, P);
+        have = tc_next(W, c);
       }
       if (!b_ok) abort_flag = 1;
     }
     __syncwarp();
   } else if (warp < PROD_WARP0) {
     // ---- epilogue: 128 threads ----
-    TcPlane P;
-    bool have = tc_run_at(ubegin, uend, N, P);
+    TcCur c;
+    bool have = tc_start(W, c);
     constexpr int EB = EPI_PLANE_B / 16;  // float4 per operand buffer
-    TcPlane ahead = P;
+    TcCur ahead = c;
     bool have_a = have;
     if (FUSED) {
       // operands of planes 0 and 1 in flight
       for (int b = 0; b < 2; ++b) {
         if (have_a) {
-          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + b * EB);
-          have_a = tc_next(uend, N, ahead);
+          tc_epi_fetch(ahead.P, r, N, F, x_zero, ebuf + b * EB);
+          have_a = tc_next(W, ahead);
         } else {
           cp_async_commit();
         }
@@ -941,21 +1000,23 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
     }
     for (uint32_t j = 0; have; ++j) {
       if (FUSED) cp_async_wait<1>();  // plane j's operands (own pieces)
-      if (!tc_wait(&acc_full[j % ERING], (j / ERING) & 1u, err, &abort_flag)) break;
+      // warp-uniform: a lane that gave up takes its whole warp out
+      if (!__all_sync(0xffffffffu, tc_wait(&acc_full[j % ERING], (j / ERING) & 1u, err, &abort_flag))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tc_epilogue<FUSED>(P, z, N, tmem, ubegin, F, alpha, x_zero, dots, tile, ebuf + (j & 1u) * EB);
+      tc_epilogue<FUSED>(c.P, z, N, tmem, c.vbase, F, alpha, x_zero, dots, tile, ebuf + (j & 1u) * EB);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&acc_empty[j % ERING]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[j % ERING]);
       if (FUSED) {
         // refill the buffer plane j used with plane j + 2
         if (have_a) {
-          tc_epi_fetch(ahead, r, N, F, x_zero, ebuf + (j & 1u) * EB);
-          have_a = tc_next(uend, N, ahead);
+          tc_epi_fetch(ahead.P, r, N, F, x_zero, ebuf + (j & 1u) * EB);
+          have_a = tc_next(W, ahead);
         } else {
           cp_async_commit();
         }
       }
-      have = tc_next(uend, N, P);
+      have = tc_next(W, c);
     }
     if (FUSED) cp_async_wait<0>();
   } else {
@@ -964,42 +1025,45 @@ __global__ void __launch_bounds__(tck::THREADS, 1) k_apply_k_tc(const float* __r
     TcRows rows;
     rows.col = -1;
     TcIn<FUSED> in0, in1;
-    TcPlane cur, ahead;
-    bool have = tc_run_at(ubegin, uend, N, cur);
+    TcCur cur, ahead;
+    bool have = tc_start(W, cur);
     ahead = cur;
     bool have_a = have;
     if (have_a) {
-      tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in0);
-      have_a = tc_next(uend, N, ahead);
+      tc_load<FUSED>(ahead.P, r, F.q, N, ptid, rows, in0);
+      have_a = tc_next(W, ahead);
     }
     if (have_a) {
-      tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in1);
-      have_a = tc_next(uend, N, ahead);
+      tc_load<FUSED>(ahead.P, r, F.q, N, ptid, rows, in1);
+      have_a = tc_next(W, ahead);
     }
     uint32_t j = 0;
     // plane j from buffer `in`, which is then refilled with plane j + 2
     auto step = [&](TcIn<FUSED>& in) -> bool {
       const uint32_t sa = j % ASLOTS;
+      bool ok = true;
       if (j >= (uint32_t)ASLOTS) {
         // the MMAs of plane j - ASLOTS, which read this A slot, are done
         const uint32_t k = j - ASLOTS;
-        if (!tc_wait(&a_empty[sa], (k / ASLOTS) & 1u, err, &abort_flag)) return false;
+        ok = tc_wait(&a_empty[sa], (k / ASLOTS) & 1u, err, &abort_flag);
       }
+      if (!__all_sync(0xffffffffu, ok)) return false;  // warp-uniform
       tc_store<FUSED>(in, slots + sa * SLOT_B, ptid, alpha);
       fence_proxy_async_smem();  // the BF16 writes, visible to the tensor cores
-      mbar_arrive(&a_full[sa]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&a_full[sa]);
       if (have_a) {
-        tc_load<FUSED>(ahead, r, F.q, N, ptid, rows, in);
-        have_a = tc_next(uend, N, ahead);
+        tc_load<FUSED>(ahead.P, r, F.q, N, ptid, rows, in);
+        have_a = tc_next(W, ahead);
       }
       ++j;
       return true;
     };
     while (have) {
       if (!step(in0)) break;
-      if (!(have = tc_next(uend, N, cur))) break;
+      if (!(have = tc_next(W, cur))) break;
       if (!step(in1)) break;
-      have = tc_next(uend, N, cur);
+      have = tc_next(W, cur);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

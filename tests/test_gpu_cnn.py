@@ -123,13 +123,14 @@ def oracle_sampled_apply(r, N, ws, points):
 
 
 @pytest.mark.parametrize("N", [128, 256, 384])
-def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N):
+@pytest.mark.parametrize("mode", ["tc", "tc8"])
+def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N, mode):
     """The composed 9^3 kernel on the tensor cores (BF16 r and K, FP32
-    accumulation in TMEM) against the oracle's FP64 network at 200 sampled
-    cells (BF16 tolerance), and against the FP32 CUDA-core evaluation of the
-    same composed kernel at every cell. The sample includes the grid's corners
-    and faces, where the periodic wrap and the edges of the 16 x 128 column
-    blocks are exercised."""
+    accumulation in TMEM; the 16-wide default and the 8-wide form) against the
+    oracle's FP64 network at 200 sampled cells (BF16 tolerance), and against
+    the FP32 CUDA-core evaluation of the same composed kernel at every cell.
+    The sample includes the grid's corners and faces, where the periodic wrap
+    and the edges of the 8 x 128 and 16 x 128 column blocks are exercised."""
     ws = ocnn.init_weights(9)
     flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
     ws32 = [w.astype(np.float32).astype(np.float64) for w in ws]
@@ -139,7 +140,7 @@ def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N):
     rt = torch.from_numpy(r.astype(np.float32)).cuda()
     z_tc = torch.full_like(rt, float("nan"))
     z_32 = torch.full_like(rt, float("nan"))
-    c.cnn_set_apply(pg.CNN_APPLY_TC)
+    c.cnn_set_apply(pg.CNN_APPLY_TC if mode == "tc" else pg.CNN_APPLY_TC8)
     c.cnn_apply(rt, z_tc)
     c.cnn_set_apply(pg.CNN_APPLY_FP32)
     c.cnn_apply(rt, z_32)
@@ -156,6 +157,62 @@ def test_tensor_core_preconditioner_matches_oracle_sampled(pg, N):
     ref = oracle_sampled_apply(r.astype(np.float32).astype(np.float64), N, ws32, pts)
     got = np.array([zt.reshape(N, N, N)[p] for p in pts])
     assert rel(got, ref) <= 1e-2
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("N", [128, 256, 384])
+def test_tensor_core_preconditioner_exact_in_bf16(pg, N):
+    """Both tensor-core forms compute z = K * r exactly for the BF16-rounded
+    r and K, up to FP32 accumulation: the composed kernel K is read back as
+    the FP32 CUDA-core path's response to a unit impulse, both operands are
+    rounded to BF16 on the host, and z at 300 sampled cells is the FP64 sum
+    over the 729 taps. The bound is 1e-5 of the sum of |products| at each cell
+    (a wrong, missing or shifted tap moves z by a whole product). 8-wide and
+    16-wide forms agree to FP32 rounding at every cell. At 128^3 the CTAs' unit
+    ranges end inside columns every ~13 planes, so every truncated group list
+    at the ends of a run (and the split zero-led pairs) is exercised."""
+    ws = ocnn.init_weights(9)
+    flat = np.concatenate([w.reshape(-1) for w in ws]).astype(np.float32)
+    c = pg.Context().init(N, 0, 0)
+    c.cnn_set_weights(flat)
+    ctr = N // 2
+    delta = torch.zeros(N ** 3, dtype=torch.float32, device="cuda")
+    delta[(ctr * N + ctr) * N + ctr] = 1.0
+    resp = torch.empty_like(delta)
+    c.cnn_set_apply(pg.CNN_APPLY_FP32)
+    c.cnn_apply(delta, resp)
+    Kr = resp.cpu().numpy().reshape(N, N, N)[ctr - 4:ctr + 5, ctr - 4:ctr + 5, ctr - 4:ctr + 5]
+    Kb = bf16_round(Kr)  # Kb[e + 4] = response at offset e; z = Kb (convolution) r
+    r = inputs.noise_field(N, 6).astype(np.float32)
+    rb = bf16_round(r).reshape(N, N, N)
+    rt = torch.from_numpy(r).cuda()
+    out = {}
+    for mode in (pg.CNN_APPLY_TC, pg.CNN_APPLY_TC8):
+        z = torch.full_like(rt, float("nan"))
+        c.cnn_set_apply(mode)
+        c.cnn_apply(rt, z)
+        out[mode] = z.cpu().numpy().astype(np.float64).reshape(N, N, N)
+        assert np.all(np.isfinite(out[mode])), mode
+    rng = np.random.default_rng(N + 1)
+    pts = [tuple(p) for p in rng.integers(0, N, size=(260, 3))]
+    for x in (0, 7, 8, 15, 16, N - 9, N - 8, N - 1):  # column edges in x, both widths
+        for y in (0, 127, 128 % N, N - 1):
+            pts.append((int(rng.integers(0, N)), y, x))
+    e = np.arange(-4, 5)
+    for p in pts:
+        idx = [(p[a] - e) % N for a in range(3)]
+        win = rb[np.ix_(*idx)]
+        prod = Kb * win
+        ref, bound = prod.sum(), np.abs(prod).sum()
+        for mode, z in out.items():
+            assert abs(z[p] - ref) <= 1e-5 * bound + 1e-30, (mode, p, z[p], ref, bound)
+    assert rel(out[pg.CNN_APPLY_TC].reshape(-1), out[pg.CNN_APPLY_TC8].reshape(-1)) <= 1e-6
 
 
 def test_network_forward_loss_and_gradients_match_oracle(pg):
