@@ -78,3 +78,14 @@ def test_dtype_label_names_the_arithmetic():
     assert "64-bit fixed-point positions + double-float velocities" in d
     assert "rho, phi FP64" in d and "FP32 vectors + FP64 reductions" in d and "BF16 tensor-core" in d
     assert "particles" not in bench.dtype_label(pg, "mg", solve_only=True)
+
+
+def test_host_state_buffer_is_zeroed_and_sized():
+    """The end-to-end particle state buffer (huge-page backed where the
+    kernel allows): zeroed, FP64, the requested length, writable."""
+    import torch
+    t, _ = bench.host_state_buffer(3 * 1000003, torch)
+    assert t.dtype == torch.float64 and t.numel() == 3 * 1000003
+    assert float(t.abs().max()) == 0.0
+    t[-1] = 2.5
+    assert float(t.sum()) == 2.5
