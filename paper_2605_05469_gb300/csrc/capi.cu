@@ -35,15 +35,21 @@ void free_particles(pic_ctx* c) {
   c->np = 0;
 }
 
-// Particles per chunk of a host transfer (6 FP64 blocks: 805 MB of staging).
+// Particles per chunk of a host transfer (6 FP64 blocks: 805 MB per staging
+// buffer, two buffers).
 constexpr uint64_t kStageParticles = 1ull << 24;
 
 int ensure_stage(pic_ctx* c) {
   int e;
-  if (!c->stage && (e = dalloc(&c->stage, 6 * kStageParticles))) return e;
+  if (!c->stage && (e = dalloc(&c->stage, 2 * 6 * kStageParticles))) return e;
   if (!c->io_flag && (e = dalloc(&c->io_flag, 1))) return e;
+  if (!c->io_stream) CK(cudaStreamCreateWithFlags(&c->io_stream, cudaStreamNonBlocking));
+  for (int i = 0; i < 5; ++i)
+    if (!c->io_ev[i]) CK(cudaEventCreateWithFlags(&c->io_ev[i], cudaEventDisableTiming));
   return PIC_OK;
 }
+
+double* stage_buf(pic_ctx* c, int b) { return c->stage + (size_t)b * 6 * kStageParticles; }
 
 void free_solver(pic_ctx* c) {
   SolverWs& w = c->ws;
@@ -569,6 +575,10 @@ void pic_destroy(pic_ctx* c) {
   if (c->sc_host) cudaFreeHost(c->sc_host);
   if (c->err_host) cudaFreeHost(c->err_host);
   if (c->out3_host) cudaFreeHost(c->out3_host);
+  if (c->io_stream) cudaStreamSynchronize(c->io_stream);
+  for (int i = 0; i < 5; ++i)
+    if (c->io_ev[i]) cudaEventDestroy(c->io_ev[i]);
+  if (c->io_stream) cudaStreamDestroy(c->io_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   for (int i = 0; i < 2; ++i)
@@ -857,15 +867,25 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   if ((e = ensure_stage(c))) return e;
   PRec* orig = pptrs(c, c->cur ^ 1);
   launch(c, k_unsort_records, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), orig, c->np);
-  for (uint64_t base = 0; base < c->np; base += kStageParticles) {
+  // chunk i: converted into buffer i % 2 on the context stream, copied out on
+  // the copy stream while chunk i + 1 is converted into the other buffer
+  int i = 0;
+  for (uint64_t base = 0; base < c->np; base += kStageParticles, ++i) {
     const uint64_t cnt = c->np - base < kStageParticles ? c->np - base : kStageParticles;
-    launch(c, k_records_to_soa, (unsigned)((cnt + 255) / 256), 256, 0, (const PRec*)orig, base, cnt, c->grid,
-           c->stage, cnt);
+    const int b = i & 1;
+    double* st = stage_buf(c, b);
+    if (i >= 2) CK(cudaStreamWaitEvent(c->stream, c->io_ev[b], 0));  // chunk i - 2 has left this buffer
+    launch(c, k_records_to_soa, (unsigned)((cnt + 255) / 256), 256, 0, (const PRec*)orig, base, cnt, c->grid, st,
+           cnt);
+    CK(cudaEventRecord(c->io_ev[2 + b], c->stream));
+    CK(cudaStreamWaitEvent(c->io_stream, c->io_ev[2 + b], 0));
     for (int q = 0; q < 6; ++q)
-      CK(cudaMemcpyAsync(out + q * c->np + base, c->stage + q * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost,
-                         c->stream));
+      CK(cudaMemcpyAsync(out + q * c->np + base, st + q * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->io_stream));
+    CK(cudaEventRecord(c->io_ev[b], c->io_stream));
   }
   CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->io_stream));
   CK(cudaStreamSynchronize(c->stream));
   return PIC_OK;
 }
@@ -889,13 +909,24 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
     launch(c, k_set_particles, (unsigned)((c->np + 255) / 256), 256, 0, in, c->np, c->np, (uint64_t)0, P, c->grid,
            c->io_flag);
   } else {
-    for (uint64_t base = 0; base < c->np; base += kStageParticles) {
+    // chunk i: copied into buffer i % 2 on the copy stream while chunk i - 1
+    // is converted from the other buffer on the context stream
+    CK(cudaEventRecord(c->io_ev[4], c->stream));
+    CK(cudaStreamWaitEvent(c->io_stream, c->io_ev[4], 0));
+    int i = 0;
+    for (uint64_t base = 0; base < c->np; base += kStageParticles, ++i) {
       const uint64_t cnt = c->np - base < kStageParticles ? c->np - base : kStageParticles;
+      const int b = i & 1;
+      double* st = stage_buf(c, b);
+      if (i >= 2) CK(cudaStreamWaitEvent(c->io_stream, c->io_ev[2 + b], 0));  // chunk i - 2 converted
       for (int q = 0; q < 6; ++q)
-        CK(cudaMemcpyAsync(c->stage + q * cnt, in + q * c->np + base, cnt * sizeof(double), cudaMemcpyHostToDevice,
-                           c->stream));
-      launch(c, k_set_particles, (unsigned)((cnt + 255) / 256), 256, 0, (const double*)c->stage, cnt, cnt, base, P,
+        CK(cudaMemcpyAsync(st + q * cnt, in + q * c->np + base, cnt * sizeof(double), cudaMemcpyHostToDevice,
+                           c->io_stream));
+      CK(cudaEventRecord(c->io_ev[b], c->io_stream));
+      CK(cudaStreamWaitEvent(c->stream, c->io_ev[b], 0));
+      launch(c, k_set_particles, (unsigned)((cnt + 255) / 256), 256, 0, (const double*)st, cnt, cnt, base, P,
              c->grid, c->io_flag);
+      CK(cudaEventRecord(c->io_ev[2 + b], c->stream));
     }
   }
   CK(cudaGetLastError());

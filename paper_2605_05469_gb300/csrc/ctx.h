@@ -115,9 +115,15 @@ struct pic_ctx {
   pic::FftState* fft = nullptr;
   pic::PifState* pif = nullptr;
   double* pif_E = nullptr;  // 3 np: the particle-in-Fourier field, current particle order
-  // host <-> device particle transfers: FP64 staging of up to kStageParticles
-  // particles (6 blocks) and a device flag for rejected input
+  // host <-> device particle transfers: two FP64 staging buffers of up to
+  // kStageParticles particles each (6 blocks), the copies on their own stream
+  // so that one chunk's copy overlaps the neighbouring chunk's conversion
+  // kernel (io_ev: [b] copy through buffer b done, [2 + b] kernel on buffer b
+  // done, [4] the context stream's work before the transfer), and a device
+  // flag for rejected input
   double* stage = nullptr;
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int* io_flag = nullptr;
 };
 
