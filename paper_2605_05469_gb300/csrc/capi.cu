@@ -865,8 +865,11 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
   // (free between calls), then converted and copied in chunks
   int e;
   if ((e = ensure_stage(c))) return e;
-  PRec* orig = pptrs(c, c->cur ^ 1);
-  launch(c, k_unsort_records, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), orig, c->np);
+  // the inverse permutation of the sort (4 B a particle, in the sort's
+  // scratch buffer, free between calls); each chunk then gathers its
+  // particles from the sorted records (no pass that moves every record)
+  uint32_t* inv = reinterpret_cast<uint32_t*>(pptrs(c, c->cur ^ 1));
+  launch(c, k_inverse_ids, blocks, 256, 0, (const PRec*)pptrs(c, c->cur), c->np, inv);
   // chunk i: converted into buffer i % 2 on the context stream, copied out on
   // the copy stream while chunk i + 1 is converted into the other buffer
   int i = 0;
@@ -875,8 +878,8 @@ int pic_get_particles(pic_ctx* c, double* out, int on_device, int* half_step) {
     const int b = i & 1;
     double* st = stage_buf(c, b);
     if (i >= 2) CK(cudaStreamWaitEvent(c->stream, c->io_ev[b], 0));  // chunk i - 2 has left this buffer
-    launch(c, k_records_to_soa, (unsigned)((cnt + 255) / 256), 256, 0, (const PRec*)orig, base, cnt, c->grid, st,
-           cnt);
+    launch(c, k_records_to_soa, (unsigned)((cnt + 255) / 256), 256, 0, (const PRec*)pptrs(c, c->cur), base, cnt,
+           c->grid, st, cnt, (const uint32_t*)inv);
     CK(cudaEventRecord(c->io_ev[2 + b], c->stream));
     CK(cudaStreamWaitEvent(c->io_stream, c->io_ev[2 + b], 0));
     for (int q = 0; q < 6; ++q)

@@ -691,22 +691,25 @@ __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint
   P[base + i] = rec;
 }
 
-// The records back in the original order: dst[id] = src[p] (a permutation).
-__global__ void __launch_bounds__(256) k_unsort_records(const PRec* __restrict__ src, PRec* __restrict__ dst,
-                                                        uint64_t np) {
+
+// inv[id] = p: the current (cell-sorted) position of every particle, by the
+// index it was sampled with (reads only the records' id words).
+__global__ void __launch_bounds__(256) k_inverse_ids(const PRec* __restrict__ P, uint64_t np,
+                                                     uint32_t* __restrict__ inv) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const PRec r = src[p];
-  dst[r.id] = r;
+  inv[P[p].id] = (uint32_t)p;
 }
 
-// Records base .. base + count - 1 of an array in the original order to FP64
-// structure of arrays (blocks of `ld` values: x, y, z, vx, vy, vz).
+// Particles base .. base + count - 1 of the original order to FP64 structure
+// of arrays (blocks of `ld` values: x, y, z, vx, vy, vz): from an array in the
+// original order, or (inv given) gathered from the sorted records through
+// the inverse permutation.
 __global__ void k_records_to_soa(const PRec* __restrict__ P, uint64_t base, uint64_t count, Grid g, double* out,
-                                 uint64_t ld) {
+                                 uint64_t ld, const uint32_t* __restrict__ inv) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
-  const PRec r = P[base + i];
+  const PRec r = P[inv ? (uint64_t)inv[base + i] : base + i];
   out[i] = from_cell_offset(r.ix, r.fx, g);
   out[ld + i] = from_cell_offset(r.iy, r.fy, g);
   out[2 * ld + i] = from_cell_offset(r.iz, r.fz, g);
