@@ -907,10 +907,12 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
   int e;
   if ((e = ensure_stage(c))) return e;
   CK(cudaMemsetAsync(c->io_flag, 0, sizeof(int), c->stream));
+  // the conversion also counts the cells for the next sort
+  CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
   PRec* P = pptrs(c, c->cur);
   if (on_device) {
     launch(c, k_set_particles, (unsigned)((c->np + 255) / 256), 256, 0, in, c->np, c->np, (uint64_t)0, P, c->grid,
-           c->io_flag);
+           c->io_flag, c->keys, c->ranks, c->counts);
   } else {
     // chunk i: copied into buffer i % 2 on the copy stream while chunk i - 1
     // is converted from the other buffer on the context stream
@@ -928,7 +930,7 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
       CK(cudaEventRecord(c->io_ev[b], c->io_stream));
       CK(cudaStreamWaitEvent(c->stream, c->io_ev[b], 0));
       launch(c, k_set_particles, (unsigned)((cnt + 255) / 256), 256, 0, (const double*)st, cnt, cnt, base, P,
-             c->grid, c->io_flag);
+             c->grid, c->io_flag, c->keys, c->ranks, c->counts);
       CK(cudaEventRecord(c->io_ev[2 + b], c->stream));
     }
   }
@@ -937,9 +939,9 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
   CK(cudaMemcpyAsync(c->err_host, c->io_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   flag = *c->err_host;
-  // the records are in the caller's order: keys and ranks are recounted by
-  // the next sort
-  c->keys_valid = false;
+  // the records are in the caller's order, their keys and ranks counted:
+  // the next deposit sorts them
+  c->keys_valid = true;
   c->sorted = false;
   c->half_step = half_step != 0;
   return (flag & DEV_ERR_NONFINITE) ? PIC_EINVAL : PIC_OK;

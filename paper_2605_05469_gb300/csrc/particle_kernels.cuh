@@ -651,7 +651,7 @@ __global__ void k_unsort(const PRec* P, uint64_t np, Grid g, double* out) {
 // sets DEV_ERR_NONFINITE in *flag and the particle is stored at the origin at
 // rest.
 __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint64_t count, uint64_t base, PRec* P,
-                                Grid g, int* flag) {
+                                Grid g, int* flag, uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   double v[6];
@@ -689,6 +689,9 @@ __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint
   rec.iz = (uint16_t)iz;
   rec.pad = 0;
   P[base + i] = rec;
+  // the next sort's cell key and in-cell rank (counts zeroed by the caller)
+  keys[base + i] = rec.key;
+  ranks[base + i] = atomicAdd(&counts[rec.key], 1u);
 }
 
 
