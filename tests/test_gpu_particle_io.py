@@ -111,11 +111,14 @@ def test_non_finite_state_is_rejected(pg):
 
 def test_host_round_trip_spans_several_chunks(pg):
     """128^3 x 20 ppc = 41.9 M particles: three 2^24-particle chunks, the last
-    one ragged, in both directions."""
+    one ragged, in both directions, and the deposit of the state set from
+    the host."""
     N, ppc = 128, 20
     c = pg.Context().init(N, ppc, 11)
     np_ = c.num_particles
     assert np_ > 2 * (1 << 24)
+    rho0 = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    c.deposit(rho0)
     dev = torch.empty(6 * np_, dtype=torch.float64, device="cuda")
     c.particles_into(dev)
     host = torch.empty(6 * np_, dtype=torch.float64).pin_memory()
@@ -131,4 +134,9 @@ def test_host_round_trip_spans_several_chunks(pg):
     back = dev.cpu().view(6, np_)
     assert torch.equal(back[3:], hs.view(6, np_)[3:])
     assert (back[:3] - hs.view(6, np_)[:3]).abs().max().item() <= 1e-15 * L
+    # the cells counted while the chunks were converted sort the permuted
+    # state: its deposit is the original state's (summation order aside)
+    rho1 = torch.empty_like(rho0)
+    c.deposit(rho1)
+    assert (rho1 - rho0).abs().max().item() <= 1e-12
     c.close()
