@@ -107,10 +107,10 @@ PARTICLE_BYTES = {
     "push": (96, 24),
 }
 # bytes per particle the library's kernels move by design: the 64-byte record
-# (cell index and 64-bit fixed-point offsets, double-float velocities, id and
-# key) read and written, plus the 4-byte key and rank arrays (the deposit
-# reads the record's first 32-byte sector)
-PARTICLE_IMPL_BYTES = {"scatter": 136, "deposit": 32, "push": 136}
+# (64-bit fixed-point offsets, double-float velocities, id, cell key, packed
+# cell index and in-cell rank) read and written (the deposit reads the
+# record's first 32-byte sector)
+PARTICLE_IMPL_BYTES = {"scatter": 128, "deposit": 32, "push": 128}
 # particle-in-Fourier window sums: a multiply and an atomic add (spreading)
 # or one FMA (interpolation) per window point and particle
 PIF_FLOP_PER_POINT = 2
@@ -128,7 +128,7 @@ def pif_width(tol):
 # dram__bytes_write.sum over the particle count) measured by ncu on the
 # 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
 # count): it stands for the same kernels at other sizes
-MEASURED_TRAFFIC_PER_PARTICLE = {"push": 136.59, "scatter": 133.72}
+MEASURED_TRAFFIC_PER_PARTICLE = {"push": 128.56, "scatter": 125.43}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
 

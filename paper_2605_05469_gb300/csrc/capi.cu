@@ -23,8 +23,6 @@ void free_particles(pic_ctx* c) {
   for (int b = 0; b < 2; ++b) {
     dfree(c->prec[b]);
   }
-  dfree(c->keys);
-  dfree(c->ranks);
   dfree(c->counts);
   dfree(c->offsets);
   dfree(c->chunks);
@@ -498,7 +496,7 @@ int launch_push(pic_ctx* c, const double* phi, const double* Efield, double kick
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push<false>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float4*)c->E,
          (const float2*)(c->E + 2 * c->n), c->grid, df_const(-kick),
-         df_const(dt * c->grid.inv_h), drift, c->keys, c->ranks, c->counts, (const double*)nullptr, c->err);
+         df_const(dt * c->grid.inv_h), drift, c->counts, (const double*)nullptr, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -632,14 +630,14 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
   for (int b = 0; b < 2; ++b)
     if ((e = dalloc(&c->prec[b], np))) return e;
   const size_t nchunks = (n + kScanChunk - 1) / kScanChunk;
-  if ((e = dalloc(&c->keys, np)) || (e = dalloc(&c->ranks, np)) || (e = dalloc(&c->counts, n)) ||
+  if ((e = dalloc(&c->counts, n)) ||
       (e = dalloc(&c->offsets, n + 1)) || (e = dalloc(&c->chunks, nchunks)))
     return e;
   c->np = np;
   CK(cudaMemsetAsync(c->counts, 0, n * sizeof(uint32_t), c->stream));
   const unsigned blocks = (unsigned)((np + 255) / 256);
   launch(c, k_init_particles, blocks, 256, 0, pptrs(c, 0), np, seed, p->alpha, p->k, vth, p->init_mode, c->grid,
-         c->keys, c->ranks, c->counts);
+         c->counts);
   CK(cudaGetLastError());
   c->keys_valid = true;
   return PIC_OK;
@@ -648,15 +646,15 @@ int pic_init(pic_ctx* c, const pic_params* p, uint64_t seed) {
 int64_t pic_num_particles(const pic_ctx* c) { return c ? (int64_t)c->np : 0; }
 
 // Counting sort of the particle records by cell key (a no-op when they are
-// sorted): keys and in-cell ranks (from the last push, else counted here), an
-// exclusive scan of the per-cell counts, and the scatter of the records into
-// the other buffer.
+// sorted): the keys and in-cell ranks in the records (written by the last
+// push or state load, else counted here), an exclusive scan of the per-cell
+// counts, and the scatter of the records into the other buffer.
 static int sort_particles(pic_ctx* c) {
   if (c->sorted) return PIC_OK;
   const unsigned pblocks = (unsigned)((c->np + 255) / 256);
   if (!c->keys_valid) {
     CK(cudaMemsetAsync(c->counts, 0, c->n * sizeof(uint32_t), c->stream));
-    launch(c, k_count_keys, pblocks, 256, 0, pptrs(c, c->cur), c->np, c->grid, c->keys, c->ranks, c->counts);
+    launch(c, k_count_keys, pblocks, 256, 0, pptrs(c, c->cur), c->np, c->grid, c->counts);
   }
   const int nchunks = (int)((c->n + kScanChunk - 1) / kScanChunk);
   launch(c, k_scan_chunks, nchunks, 256, 0, c->counts, c->n, c->chunks);
@@ -664,8 +662,8 @@ static int sort_particles(pic_ctx* c) {
   launch(c, k_scan_apply, nchunks, 256, 0, c->counts, c->n, c->chunks, c->offsets);
   const unsigned sblocks = (unsigned)(((c->np + 31) / 32 * 32 + 255) / 256);
   const int slot = c->prof_on ? c->ker[PIC_KER_SCATTER].begin(c->stream) : -1;
-  launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np, (const uint32_t*)c->keys,
-         (const uint32_t*)c->ranks, (const uint32_t*)c->offsets);
+  launch(c, k_scatter, sblocks, 256, 0, pptrs(c, c->cur), pptrs(c, c->cur ^ 1), c->np,
+         (const uint32_t*)c->offsets);
   if (c->prof_on) c->ker[PIC_KER_SCATTER].end(slot, c->stream);
   CK(cudaGetLastError());
   c->cur ^= 1;
@@ -842,7 +840,7 @@ int pic_pif_push(pic_ctx* c, double tol, double dt) {
   const int slot = c->prof_on ? c->ker[PIC_KER_PUSH].begin(c->stream) : -1;
   launch(c, k_gather_push<true>, blocks, 256, 0, pptrs(c, c->cur), c->np, (const float4*)nullptr,
          (const float2*)nullptr, c->grid, df_const(-kick), df_const(dt * c->grid.inv_h), 1,
-         c->keys, c->ranks, c->counts, (const double*)c->pif_E, c->err);
+         c->counts, (const double*)c->pif_E, c->err);
   if (c->prof_on) c->ker[PIC_KER_PUSH].end(slot, c->stream);
   CK(cudaGetLastError());
   c->half_step = true;
@@ -912,7 +910,7 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
   PRec* P = pptrs(c, c->cur);
   if (on_device) {
     launch(c, k_set_particles, (unsigned)((c->np + 255) / 256), 256, 0, in, c->np, c->np, (uint64_t)0, P, c->grid,
-           c->io_flag, c->keys, c->ranks, c->counts);
+           c->io_flag, c->counts);
   } else {
     // chunk i: copied into buffer i % 2 on the copy stream while chunk i - 1
     // is converted from the other buffer on the context stream
@@ -930,7 +928,7 @@ int pic_set_particles(pic_ctx* c, const double* in, int on_device, int half_step
       CK(cudaEventRecord(c->io_ev[b], c->io_stream));
       CK(cudaStreamWaitEvent(c->stream, c->io_ev[b], 0));
       launch(c, k_set_particles, (unsigned)((cnt + 255) / 256), 256, 0, (const double*)st, cnt, cnt, base, P,
-             c->grid, c->io_flag, c->keys, c->ranks, c->counts);
+             c->grid, c->io_flag, c->counts);
       CK(cudaEventRecord(c->io_ev[2 + b], c->stream));
     }
   }

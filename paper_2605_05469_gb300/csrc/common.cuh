@@ -59,14 +59,25 @@ struct Scalars {
 //   vx, vy, vz  velocity as double-float pairs (hi + lo, ~48-bit significand;
 //               the push runs on the FP32 pipes);
 //   id          the index the particle was sampled with;
-//   key         its cell ix + N (iy + N iz), and ix, iy, iz themselves.
+//   key         its cell ix + N (iy + N iz);
+//   cell        ix | iy << 10 | iz << 20 (N <= 1024);
+//   rank        its rank among the particles of its cell, for the next sort
+//               (key and rank are written together by whoever moves the
+//               particle to a new cell: the initial sampling, the push, the
+//               state loaded from the caller).
 struct __align__(64) PRec {
   uint64_t fx, fy, fz;
   float2 vx, vy, vz;
-  uint32_t id, key;
-  uint16_t ix, iy, iz, pad;
+  uint32_t id, key, cell, rank;
 };
 static_assert(sizeof(PRec) == 64, "particle record");
+
+__host__ __device__ __forceinline__ uint32_t pack_cell(int ix, int iy, int iz) {
+  return (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+}
+__host__ __device__ __forceinline__ int cell_x(uint32_t c) { return (int)(c & 1023u); }
+__host__ __device__ __forceinline__ int cell_y(uint32_t c) { return (int)((c >> 10) & 1023u); }
+__host__ __device__ __forceinline__ int cell_z(uint32_t c) { return (int)(c >> 20); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -85,7 +85,7 @@ struct pic_ctx {
   // particles
   pic::PRec* prec[2] = {nullptr, nullptr};  // particle records, current sort order and scratch
   int cur = 0;
-  uint32_t *keys = nullptr, *ranks = nullptr, *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
+  uint32_t *counts = nullptr, *offsets = nullptr, *chunks = nullptr;
   bool keys_valid = false, sorted = false, half_step = false;
   float2* E = nullptr;    // 4 n: E_x, E_y, E_z at the nodes and phi, double-float
   float2* dep = nullptr;  // 8 n: per cell, the CIC charge of its particles at each of its 8 corners

@@ -156,7 +156,7 @@ constexpr int kSumFormTrials = 32;
 // (3 alpha / (1 + 3 alpha))^32). Velocities: vth times Box-Muller normals
 // (calls 2 and 3).
 __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alpha, double k, double vth, int mode,
-                                 Grid g, uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
+                                 Grid g, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -200,24 +200,19 @@ __global__ void k_init_particles(PRec* P, uint64_t np, uint64_t seed, double alp
   rec.vz = df_pack(df_of_double(r2 * c2));
   rec.id = (uint32_t)p;
   rec.key = cell_key(ix, iy, iz, g.N);
-  rec.ix = (uint16_t)ix;
-  rec.iy = (uint16_t)iy;
-  rec.iz = (uint16_t)iz;
-  rec.pad = 0;
+  rec.cell = pack_cell(ix, iy, iz);
+  rec.rank = atomicAdd(&counts[rec.key], 1u);
   P[p] = rec;
-  keys[p] = rec.key;
-  ranks[p] = atomicAdd(&counts[rec.key], 1u);
 }
 
 // Cell keys and in-cell ranks of the current particles.
-__global__ void k_count_keys(PRec* P, uint64_t np, Grid g, uint32_t* keys, uint32_t* ranks,
-                             uint32_t* counts) {
+__global__ void k_count_keys(PRec* P, uint64_t np, Grid g, uint32_t* counts) {
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
-  const uint32_t kk = cell_key(P[p].ix, P[p].iy, P[p].iz, g.N);
+  const uint32_t c = P[p].cell;
+  const uint32_t kk = cell_key(cell_x(c), cell_y(c), cell_z(c), g.N);
   P[p].key = kk;
-  keys[p] = kk;
-  ranks[p] = atomicAdd(&counts[kk], 1u);
+  P[p].rank = atomicAdd(&counts[kk], 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,22 +306,26 @@ __global__ void __launch_bounds__(256) k_scan_apply(const uint32_t* __restrict__
   if (base + 16 >= n && base < n) offsets[n] = run;  // the thread holding the last count
 }
 
-// Move particle p to offsets[key] + rank (the other buffer). Each warp moves
-// 32 consecutive particles; lane l holds 16-byte word (l & 3) of particles
+// Move particle p to offsets[key] + rank (the other buffer), key and rank
+// read from the record itself. Each warp moves 32 consecutive particles; lane
+// l first reads the last 16-byte word (id, key, cell, rank) of particle l and
+// starts its destination lookup, then holds 16-byte word (l & 3) of particles
 // 8k + (l >> 2), k = 0..3, so every load and every store instruction of the
-// warp covers 8 whole 64-byte records (whole sectors at both ends).
+// warp covers 8 whole 64-byte records (whole sectors at both ends; the early
+// word read touches sectors the record loads read again from L1).
 __global__ void __launch_bounds__(256) k_scatter(const PRec* __restrict__ src, PRec* __restrict__ dst, uint64_t np,
-                                                 const uint32_t* __restrict__ keys,
-                                                 const uint32_t* __restrict__ ranks,
                                                  const uint32_t* __restrict__ offsets) {
   const uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
   if (base >= np) return;  // uniform over the warp
   const int lane = threadIdx.x & 31;
-  const uint64_t p = base + lane;
-  uint64_t d = 0;
-  if (p < np) d = (uint64_t)__ldg(offsets + __ldg(keys + p)) + __ldg(ranks + p);
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   uint4* d4 = reinterpret_cast<uint4*>(dst);
+  const uint64_t p = base + lane;
+  uint64_t d = 0;
+  if (p < np) {
+    const uint4 w3 = __ldg(s4 + p * 4 + 3);
+    d = (uint64_t)__ldg(offsets + w3.y) + w3.w;
+  }
   const int word = lane & 3;
   uint4 v[4];
 #pragma unroll
@@ -508,8 +507,9 @@ __global__ void __launch_bounds__(256) k_field_energy(const double* __restrict__
 
 // ---------------------------------------------------------------------------
 // S6: CIC gather of E and leapfrog push (Eqs. 3-4), in double-float; then the
-// new cell key and in-cell rank (counts must be zero on entry) for the next
-// sort. drift == 0 gives the closing half-kick only (no key update).
+// new cell key and in-cell rank for the next sort, written into the record's
+// last word (counts must be zero on entry). drift == 0 gives the closing
+// half-kick only (no key update).
 //   kick_qm = -kick (q/m = -1), dth = dt / h, both double-float (hi, lo).
 // The node field is E_x and E_y interleaved as one float4 a node
 // {x.hi, y.hi, x.lo, y.lo} and E_z as a float2: the x and y components run
@@ -527,13 +527,14 @@ constexpr int kPushThreads = 256;
 template <bool GIVEN>
 __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64_t np, const float4* __restrict__ Exy,
                                                               const float2* __restrict__ Ez, Grid g, float2 kick_qm,
-                                                              float2 dth, int drift, uint32_t* keys, uint32_t* ranks,
+                                                              float2 dth, int drift,
                                                               uint32_t* counts, const double* __restrict__ Ep,
                                                               int* err) {
   const uint64_t base = (uint64_t)blockIdx.x * kPushThreads;
   const uint64_t p = base + threadIdx.x;
   const bool valid = p < np;
   uint32_t kk = 0xFFFFFFFFu;
+  uint32_t rid = 0, rcell = 0;  // the record's id and (new) packed cell
   if (valid) {
     uint4* rec = reinterpret_cast<uint4*>(P + p);
     const uint4 r0 = rec[0], r1 = rec[1], r3 = rec[3];
@@ -542,7 +543,8 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
     uint64_t fz = ((uint64_t)r1.y << 32) | r1.x;
     df2 vxy = {make_float2(__uint_as_float(r1.z), r2.x), make_float2(__uint_as_float(r1.w), r2.y)};
     df vz = {r2.z, r2.w};
-    int ix = (int)(r3.z & 0xFFFFu), iy = (int)(r3.z >> 16), iz = (int)(r3.w & 0xFFFFu);
+    int ix = cell_x(r3.z), iy = cell_y(r3.z), iz = cell_z(r3.z);
+    rid = r3.x;
     const int N = g.N;
     df2 exy;
     df ez;
@@ -595,10 +597,10 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
       move_coord(fy, iy, df2_y(dxy), N);
       move_coord(fz, iz, df_mul(vz, s), N);
       rec[0] = make_uint4((uint32_t)fx, (uint32_t)(fx >> 32), (uint32_t)fy, (uint32_t)(fy >> 32));
+    }
+    if (drift) {
       kk = cell_key(ix, iy, iz, N);
-      rec[3] = make_uint4(r3.x, kk, (uint32_t)ix | ((uint32_t)iy << 16), (uint32_t)iz | (r3.w & 0xFFFF0000u));
-    } else if (drift) {
-      kk = cell_key(ix, iy, iz, N);
+      rcell = pack_cell(ix, iy, iz);
     }
     rec[1] = make_uint4((uint32_t)fz, (uint32_t)(fz >> 32), __float_as_uint(vxy.hi.x), __float_as_uint(vxy.lo.x));
   }
@@ -615,10 +617,8 @@ __global__ void __launch_bounds__(kPushThreads, 4) k_gather_push(PRec* P, uint64
   uint32_t b = 0;
   if (start && valid) b = atomicAdd(&counts[kk], (uint32_t)(run1 - run0));
   b = __shfl_sync(0xffffffffu, b, run0);
-  if (valid) {
-    keys[p] = kk;
-    ranks[p] = b + (uint32_t)(lane - run0);
-  }
+  // the record's last word: id, the new key and cell, and the rank
+  if (valid) reinterpret_cast<uint4*>(P + p)[3] = make_uint4(rid, kk, rcell, b + (uint32_t)(lane - run0));
 }
 
 // A per-particle field (3 np, current order) back to the original order.
@@ -637,9 +637,9 @@ __global__ void k_unsort(const PRec* P, uint64_t np, Grid g, double* out) {
   if (p >= np) return;
   const PRec r = P[p];
   const uint64_t d = r.id;
-  out[d] = from_cell_offset(r.ix, r.fx, g);
-  out[np + d] = from_cell_offset(r.iy, r.fy, g);
-  out[2 * np + d] = from_cell_offset(r.iz, r.fz, g);
+  out[d] = from_cell_offset(cell_x(r.cell), r.fx, g);
+  out[np + d] = from_cell_offset(cell_y(r.cell), r.fy, g);
+  out[2 * np + d] = from_cell_offset(cell_z(r.cell), r.fz, g);
   out[3 * np + d] = double_of_df(df_from(r.vx));
   out[4 * np + d] = double_of_df(df_from(r.vy));
   out[5 * np + d] = double_of_df(df_from(r.vz));
@@ -651,7 +651,7 @@ __global__ void k_unsort(const PRec* P, uint64_t np, Grid g, double* out) {
 // sets DEV_ERR_NONFINITE in *flag and the particle is stored at the origin at
 // rest.
 __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint64_t count, uint64_t base, PRec* P,
-                                Grid g, int* flag, uint32_t* keys, uint32_t* ranks, uint32_t* counts) {
+                                Grid g, int* flag, uint32_t* counts) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   double v[6];
@@ -684,14 +684,10 @@ __global__ void k_set_particles(const double* __restrict__ in, uint64_t ld, uint
   rec.vz = df_pack(df_of_double(v[5]));
   rec.id = (uint32_t)(base + i);
   rec.key = cell_key(ix, iy, iz, g.N);
-  rec.ix = (uint16_t)ix;
-  rec.iy = (uint16_t)iy;
-  rec.iz = (uint16_t)iz;
-  rec.pad = 0;
+  rec.cell = pack_cell(ix, iy, iz);
+  // the next sort's in-cell rank (counts zeroed by the caller)
+  rec.rank = atomicAdd(&counts[rec.key], 1u);
   P[base + i] = rec;
-  // the next sort's cell key and in-cell rank (counts zeroed by the caller)
-  keys[base + i] = rec.key;
-  ranks[base + i] = atomicAdd(&counts[rec.key], 1u);
 }
 
 
@@ -713,9 +709,9 @@ __global__ void k_records_to_soa(const PRec* __restrict__ P, uint64_t base, uint
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const PRec r = P[inv ? (uint64_t)inv[base + i] : base + i];
-  out[i] = from_cell_offset(r.ix, r.fx, g);
-  out[ld + i] = from_cell_offset(r.iy, r.fy, g);
-  out[2 * ld + i] = from_cell_offset(r.iz, r.fz, g);
+  out[i] = from_cell_offset(cell_x(r.cell), r.fx, g);
+  out[ld + i] = from_cell_offset(cell_y(r.cell), r.fy, g);
+  out[2 * ld + i] = from_cell_offset(cell_z(r.cell), r.fz, g);
   out[3 * ld + i] = double_of_df(df_from(r.vx));
   out[4 * ld + i] = double_of_df(df_from(r.vy));
   out[5 * ld + i] = double_of_df(df_from(r.vz));

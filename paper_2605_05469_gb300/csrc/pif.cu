@@ -129,7 +129,7 @@ __device__ __forceinline__ void grid_units(const PRec* P, uint64_t p, double u[3
   const uint4* rec = reinterpret_cast<const uint4*>(P + p);
   const uint4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r3 = __ldg(rec + 3);
   const uint64_t f[3] = {((uint64_t)r0.y << 32) | r0.x, ((uint64_t)r0.w << 32) | r0.z, ((uint64_t)r1.y << 32) | r1.x};
-  const int c[3] = {(int)(r3.z & 0xFFFFu), (int)(r3.z >> 16), (int)(r3.w & 0xFFFFu)};
+  const int c[3] = {cell_x(r3.z), cell_y(r3.z), cell_z(r3.z)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) u[d] = 2.0 * ((double)c[d] + (double)(f[d] >> 11) * (1.0 / 9007199254740992.0));
 }
@@ -257,7 +257,7 @@ __device__ __forceinline__ void grid_units32(const PRec* P, uint64_t p, int s[3]
   const uint4* rec = reinterpret_cast<const uint4*>(P + p);
   const uint4 r0 = __ldg(rec), r1 = __ldg(rec + 1), r3 = __ldg(rec + 3);
   const uint64_t f[3] = {((uint64_t)r0.y << 32) | r0.x, ((uint64_t)r0.w << 32) | r0.z, ((uint64_t)r1.y << 32) | r1.x};
-  const int c[3] = {(int)(r3.z & 0xFFFFu), (int)(r3.z >> 16), (int)(r3.w & 0xFFFFu)};
+  const int c[3] = {cell_x(r3.z), cell_y(r3.z), cell_z(r3.z)};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     s[d] = 2 * c[d] + (int)(f[d] >> 63);

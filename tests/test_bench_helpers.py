@@ -21,11 +21,12 @@ def test_particle_kernel_bytes():
     # by the push, positions read by the deposit, E read once per node
     assert bench.PARTICLE_BYTES["push"] == (96, 24)
     assert bench.PARTICLE_BYTES["deposit"] == (24, 8)
-    # the library's record layout: 64-byte record read and written, key and rank
-    assert bench.PARTICLE_IMPL_BYTES["push"] == 136
-    assert bench.PARTICLE_IMPL_BYTES["scatter"] == 136
+    # the library's record layout: 64-byte record (with its cell key and
+    # in-cell rank) read and written
+    assert bench.PARTICLE_IMPL_BYTES["push"] == 128
+    assert bench.PARTICLE_IMPL_BYTES["scatter"] == 128
     for k in ("push", "scatter"):
-        assert abs(bench.MEASURED_TRAFFIC_PER_PARTICLE[k] - 136) < 5
+        assert abs(bench.MEASURED_TRAFFIC_PER_PARTICLE[k] - 128) < 5
 
 
 def test_particle_roofline_counts_algorithmic_bytes():
@@ -33,12 +34,12 @@ def test_particle_roofline_counts_algorithmic_bytes():
     n, np_ = 256 ** 3, 8 * 256 ** 3
     b = 96 * np_ + 24 * n
     rows = {"push": {"avg_us": 4991.4, "bytes_per_particle": 96, "bytes_per_node": 24,
-                     "gbs": b / 4991.4e-6 / 1e9, "impl_bytes_per_particle": 136}}
+                     "gbs": b / 4991.4e-6 / 1e9, "impl_bytes_per_particle": 128}}
     r = bench.particle_roofline(rows, "push", np_, n, 6787.2, "measured")
     assert r["algorithmic_bytes"] == b
     assert abs(r["frac"] - b / 4991.4e-6 / 1e9 / 6787.2) < 1e-4
     assert abs(r["frac"] - 0.392) < 0.002
-    assert abs(r["traffic_over_algorithmic"] - 136.70 * np_ / b) < 1e-3
+    assert abs(r["traffic_over_algorithmic"] - bench.MEASURED_TRAFFIC_PER_PARTICLE["push"] * np_ / b) < 1e-3
 
 
 def test_whole_job_rate_and_ranks():
