@@ -128,7 +128,7 @@ def pif_width(tol):
 # dram__bytes_write.sum over the particle count) measured by ncu on the
 # 128^3 x 8 ppc step (16.8 M particles; the traffic scales with the particle
 # count): it stands for the same kernels at other sizes
-MEASURED_TRAFFIC_PER_PARTICLE = {"push": 128.56, "scatter": 125.43}
+MEASURED_TRAFFIC_PER_PARTICLE = {"push": 128.56, "scatter": 125.76}
 # coarse-grid levels streamed like the finest (sizes above 16, halving while even)
 MG_SMALL_N = 16
 
