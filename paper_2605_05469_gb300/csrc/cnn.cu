@@ -224,7 +224,7 @@ int launch_tc8(pic_ctx* c, const float* r, float* z, const Scalars* stop) {
   const int N = c->N;
   const long units = (long)(N / tc8::BX) * (N / tc8::BY) * N;
   const unsigned grid = (unsigned)(units < c->sms ? units : c->sms);
-  launch(c, k_apply_k_tc8, grid, tc8::THREADS, tc8::SMEM, r, z, N, (const unsigned char*)c->cnn->Bt8, c->err, stop, 0);
+  launch(c, k_apply_k_tc8, grid, tc8::THREADS, tc8::SMEM, r, z, N, (const unsigned char*)c->cnn->Bt8, c->err, stop);
   CK(cudaGetLastError());
   return PIC_OK;
 }

@@ -248,12 +248,9 @@ __device__ __forceinline__ void tc8_epilogue(const TcCur& c, float* __restrict__
 // every role leaves its loop, and the TMEM is freed.
 __global__ void __launch_bounds__(tc8::THREADS, 1) k_apply_k_tc8(const float* __restrict__ r, float* __restrict__ z,
                                                                  int N, const unsigned char* __restrict__ Bg,
-                                                                 int* err, const Scalars* sc, int only_redo) {
+                                                                 int* err, const Scalars* sc) {
   using namespace tc8;
-  if (sc) {
-    if (sc->done) return;
-    if (only_redo && !sc->redo) return;
-  }
+  if (sc && sc->done) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
