@@ -279,30 +279,88 @@ __device__ __forceinline__ int axis_weights32(int s, float t, float beta, float*
   return g0;
 }
 
+// Type-1 spreading of 128 particles a block. The particles are in cell order,
+// so a block's windows usually cover a small box of the oversampled grid: the
+// block finds that box, accumulates its windows there in shared memory and
+// adds the box to the grid with one global atomic per point (far fewer than
+// one per particle and window point, which the L2 atomics bound). A box
+// larger than the tile (a block that spans the end of a row of cells) takes
+// the direct path.
+constexpr int kSpreadTile = 4096;  // floats of shared memory per block (16 KB)
+
 template <int W>
 __global__ void __launch_bounds__(128) k_pif_spread32(const PRec* __restrict__ P, uint64_t np, int M, float beta,
                                                       float q, float* G) {
+  __shared__ float tile[kSpreadTile];
+  __shared__ int lo[3], hi[3];
   const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  int s[3];
-  float t[3];
-  grid_units32(P, p, s, t);
+  const bool valid = p < np;
+  if (threadIdx.x < 3) {
+    lo[threadIdx.x] = 0x7fffffff;
+    hi[threadIdx.x] = -0x7fffffff;
+  }
   float wx[W], wy[W], wz[W];
-  const int gx = axis_weights32<W>(s[0], t[0], beta, wx), gy = axis_weights32<W>(s[1], t[1], beta, wy);
-  const int gz = axis_weights32<W>(s[2], t[2], beta, wz);
+  int g[3] = {0, 0, 0};
+  if (valid) {
+    int s[3];
+    float t[3];
+    grid_units32(P, p, s, t);
+    g[0] = axis_weights32<W>(s[0], t[0], beta, wx);
+    g[1] = axis_weights32<W>(s[1], t[1], beta, wy);
+    g[2] = axis_weights32<W>(s[2], t[2], beta, wz);
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      atomicMin(&lo[d], g[d]);
+      atomicMax(&hi[d], g[d]);
+    }
+  }
+  __syncthreads();
+  const int bx = hi[0] - lo[0] + W, by = hi[1] - lo[1] + W, bz = hi[2] - lo[2] + W;
+  const bool tiled = lo[0] <= hi[0] && (long)bx * by * bz <= kSpreadTile;  // uniform over the block
   const size_t Ms = M;
-  int xs[W];
+  if (!tiled) {
+    if (!valid) return;
+    int xs[W];
 #pragma unroll
-  for (int a = 0; a < W; ++a) xs[a] = wrap_m(gx + a, M);
-  for (int c = 0; c < W; ++c) {
-    const int z = wrap_m(gz + c, M);
-    const float qz = q * wz[c];
+    for (int a = 0; a < W; ++a) xs[a] = wrap_m(g[0] + a, M);
+    for (int c = 0; c < W; ++c) {
+      const int z = wrap_m(g[2] + c, M);
+      const float qz = q * wz[c];
 #pragma unroll
-    for (int b = 0; b < W; ++b) {
-      const float qzy = qz * wy[b];
-      float* row = G + ((size_t)z * Ms + wrap_m(gy + b, M)) * Ms;
+      for (int b = 0; b < W; ++b) {
+        const float qzy = qz * wy[b];
+        float* row = G + ((size_t)z * Ms + wrap_m(g[1] + b, M)) * Ms;
 #pragma unroll
-      for (int a = 0; a < W; ++a) atomicAdd(row + xs[a], qzy * wx[a]);
+        for (int a = 0; a < W; ++a) atomicAdd(row + xs[a], qzy * wx[a]);
+      }
+    }
+    return;
+  }
+  const int vol = bx * by * bz;
+  for (int i = threadIdx.x; i < vol; i += blockDim.x) tile[i] = 0.f;
+  __syncthreads();
+  if (valid) {
+    const int ox = g[0] - lo[0], oy = g[1] - lo[1], oz = g[2] - lo[2];
+    for (int c = 0; c < W; ++c) {
+      const float qz = q * wz[c];
+#pragma unroll
+      for (int b = 0; b < W; ++b) {
+        const float qzy = qz * wy[b];
+        float* row = tile + ((oz + c) * by + (oy + b)) * bx + ox;
+#pragma unroll
+        for (int a = 0; a < W; ++a) atomicAdd(row + a, qzy * wx[a]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < vol; i += blockDim.x) {
+    const float v = tile[i];
+    if (v != 0.f) {
+      const int x = i % bx, y = (i / bx) % by, z = i / (bx * by);
+      atomicAdd(G + ((size_t)wrap_m(lo[2] + z, M) * Ms + wrap_m(lo[1] + y, M)) * Ms + wrap_m(lo[0] + x, M), v);
     }
   }
 }
